@@ -1,0 +1,306 @@
+"""Benchmark: exact model counting at n = 36 on one B300 (and N replicas).
+
+Workload (count mode, 2^36 assignments each, nothing stored): transitive
+relations on 6 points (36 letters r(i,j), transitivity only), triangle-free
+labelled graphs on 9 vertices (36 edge letters), automorphisms of the seeded
+random graph G(6, 1/2) (seed 3) as 6 x 6 permutation matrices.  One step
+counts all three.  Metric: assignments per second (Gassign/s) over the whole
+job; the roofline is the integer-logic (lop3) pipe.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs the same workload on its own GPU (replicas:
+the formulas are independent problems, no data-path collective); value =
+all ranks' assignments / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SM_COUNT = 148
+LOP3_LANES_PER_CLK_SM = 64      # measured issue rate of lop3.b32 per SM per clock (sm_103a)
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        mhz.sort()
+        return {"sm_mhz": mhz[len(mhz) // 2] if mhz else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def workloads():
+    from paper_1310_6978_b300 import workloads as W
+    return [W.TRANSITIVE6, W.TRIFREE9, W.AUT6]
+
+
+# ----------------------------------------------------------------- oracle --
+
+def cpu_oracle_rate(wls, seconds_budget: float, seed: int = 7):
+    """The oracle as it stands, all host cores, on random subcubes of each
+    formula (2^22 assignments each) until the budget is used."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(seed)
+    cores = oracle.max_threads()
+    done = 0
+    t0 = time.perf_counter()
+    chunks = 0
+    while time.perf_counter() - t0 < seconds_budget or chunks < len(wls):
+        wl = wls[chunks % len(wls)]
+        th = oracle.Theory(wl.text, wl.k)
+        fixed = [int(v) for v in rng.choice(wl.n, wl.n - 22, replace=False)]
+        mask = sum(1 << v for v in fixed)
+        vals = int(rng.integers(0, 1 << 62)) & mask
+        th.count_cube_par(mask, vals)
+        done += 1 << 22
+        chunks += 1
+    dt = time.perf_counter() - t0
+    return done / dt, cores, f"{chunks} random subcubes of 2^22 assignments (22 free letters) over the three n=36 formulas, {dt:.1f} s"
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    wls = workloads()
+    steps = []
+    for _ in range(args.warmup):
+        cpu_oracle_rate(wls, 0.5)
+    for _ in range(args.steps):
+        rate, cores, sample = cpu_oracle_rate(wls, args.ref_seconds)
+        steps.append(rate)
+    rate = sorted(steps)[len(steps) // 2]
+    line = {"metric": "model-count throughput at n=36 (Gassign/s)", "value": rate / 1e9, "unit": "Gassign/s",
+            "impl": "reference", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 3 * (1 << 22) / rate * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "count n=36: transitive k=6, triangle-free k=9, Aut(G(6,1/2)) seed 3",
+                       "engine": "CPU oracle (model checking per assignment)", "flush_l2": False},
+            "cpu_baseline": {"value": rate / 1e9, "unit": "Gassign/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": rate / 1e9, "unit": "Gassign/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------------- ours --
+
+def run_ours(args, rank, world):
+    import torch
+    import paper_1310_6978_b300 as F
+    from paper_1310_6978_b300 import _lib as L
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    wls = workloads()
+    progs = [F.compile(w.text, w.k) for w in wls]
+    stream = torch.cuda.Stream()
+    out = torch.zeros(len(progs), dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > L2 (126 MB)
+
+    def step(record=None):
+        with torch.cuda.stream(stream):
+            for i, p in enumerate(progs):
+                if record is not None:
+                    record[i][0].record(stream)
+                p.count_async(out[i:i + 1], stream=stream)
+                if record is not None:
+                    record[i][1].record(stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    stream.synchronize()
+    expected = out.cpu().tolist()
+
+    evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in progs]
+           for _ in range(args.steps)]
+    kernel_ms = [0.0] * len(progs)
+    step_ms = []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        for s in range(args.steps):
+            flush.zero_()                                  # L2 flushed between timed steps
+            torch.cuda.synchronize()
+            step(evs[s])
+            stream.synchronize()
+            got = out.cpu().tolist()
+            assert got == expected, (got, expected)
+            for i in range(len(progs)):
+                kernel_ms[i] += evs[s][i][0].elapsed_time(evs[s][i][1])
+            step_ms.append(evs[s][0][0].elapsed_time(evs[s][-1][1]))
+    torch.cuda.synchronize()
+    t_local = sum(step_ms) / 1e3
+    t = torch.tensor([t_local], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    t_max = float(t.item())
+    assign_per_step = sum(1 << w.n for w in wls)
+    value = world * assign_per_step * args.steps / t_max / 1e9
+
+    # executed work of the same kernels (level iteration counters), untimed
+    executed = 0.0
+    nominal = 0.0
+    for p in progs:
+        p.set_option(L.OPT_STATS, 1)
+        p.count()
+        es = p.exec_stats()
+        executed += es.lop3_executed
+        nominal += es.lop3_nominal
+        p.set_option(L.OPT_STATS, 0)
+    kern_s = sum(kernel_ms) / args.steps / 1e3
+    clocks = clk.summary()
+    peak_lop3 = SM_COUNT * LOP3_LANES_PER_CLK_SM * 2032e6
+
+    # the paper's brute-force evaluation (every word), same kernels without pruning
+    brute = {}
+    if not args.quick:
+        bp = [F.compile(w.text, w.k).set_option(L.OPT_PRUNE, 0).set_option(L.OPT_STATS, 1) for w in wls]
+        for p in bp:
+            p.count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        bo = torch.zeros(len(bp), dtype=torch.int64, device="cuda")
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for i, p in enumerate(bp):
+                p.count_async(bo[i:i + 1], stream=stream)
+            e1.record(stream)
+        stream.synchronize()
+        assert bo.cpu().tolist() == expected
+        bt = e0.elapsed_time(e1) / 1e3
+        bex = 0.0
+        for p in bp:
+            p.count()
+            bex += p.exec_stats().lop3_executed
+        brute = {"value": assign_per_step / bt / 1e9, "unit": "Gassign/s", "ms": bt * 1e3,
+                 "lop3_tops": bex / bt / 1e12, "frac": bex / bt / peak_lop3}
+
+    # end to end through the public API: text -> compile -> count -> host
+    e2e_steps = 2 if args.quick else max(2, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        res = [F.compile(w.text, w.k).count(stream=stream) for w in wls]
+        assert res == expected
+    e2e_t = (time.perf_counter() - t0) / e2e_steps
+
+    if rank != 0:
+        return
+    cpu = {}
+    if world == 1 and not args.no_cpu:
+        rate, cores, sample = cpu_oracle_rate(wls, args.cpu_seconds)
+        cpu = {"value": rate / 1e9, "unit": "Gassign/s", "cores": cores, "kind": "oracle", "sample": sample}
+    peaks = load_peaks()
+    line = {
+        "metric": "model-count throughput at n=36 (Gassign/s)",
+        "value": value, "unit": "Gassign/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": {"workload": "count n=36: transitive k=6, triangle-free k=9, Aut(G(6,1/2)) seed 3",
+                   "formulas": 3, "assignments_per_step": assign_per_step, "engine": "nvrtc straight-line, pruned",
+                   "flush_l2": True, "parallelism": f"replicas x{world}", "counts": expected},
+        "roofline": {"bound": "alu", "achieved": executed / kern_s / 1e12, "peak": peak_lop3 / 1e12,
+                     "unit": "Tlop3/s", "frac": executed / kern_s / peak_lop3, "traffic": None,
+                     "basis": "executed lop3.b32 lane-ops (in-kernel level counters) / CUDA-event kernel time; "
+                              "peak = 148 SM x 64 lanes/clk x 2032 MHz"},
+        "nominal_lop3_ratio": executed / nominal if nominal else None,
+        "brute_force": brute,
+        "clocks": clocks,
+        "e2e": {"value": assign_per_step / e2e_t / 1e9, "unit": "Gassign/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 8 * len(wls)},
+        "gpu_launches": 3 * len(wls) * args.steps,
+        "cpu_baseline": cpu,
+        "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops")},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=4.0)
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch
+        torch.distributed.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+    if world > 1 and args.impl == "ours":
+        import torch
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,251 @@
+/*
+ * fbg.h -- C ABI of the free-Boolean-generator evaluator (libfbg.so).
+ *
+ * Method (Mijajlovic & Pejovic, "Computing finite models using free Boolean
+ * generators"): a first-order theory T over a k-element domain is translated
+ * into a propositional formula t(x_0..x_{n-1}) (the map * of Sec. 3.1); t is
+ * evaluated bitwise over the free generators b_i of the free Boolean algebra
+ * with n generators (Sec. 2.2), which gives the vector d whose position j is
+ * t(mu_j) -- the full DNF of t (Prop. 2.2, Sec. 2.3).  Its number of ones is
+ * the number l_{T,n} of labelled models (Sec. 3.2).
+ *
+ * Conventions fixed by this library:
+ *   - assignment integer j in [0, 2^n): variable x_i takes bit i of j (the
+ *     generator matrix of Sec. 2.2 with the index order flipped: x_i is the
+ *     paper's b_{n-i});
+ *   - truth table bit j lives in 64-bit word j>>6, bit j&63; for n < 6 the
+ *     single word's bits >= 2^n are 0;
+ *   - variables are numbered in declaration order, each declared family in
+ *     lexicographic tuple order (r(i,j) of a k x k relation is i*k+j);
+ *   - model lists are ascending in j.
+ *
+ * Formula text (the script language of Sec. 4.2, subset plus declarations):
+ *   var x, y, r(S,S), e(S<S)      declarations ('<' = strictly increasing)
+ *   const E(S,S) = 0110...        constant relation, k^arity bits
+ *   [label =] formula             one axiom per line; the theory is their
+ *                                 conjunction.  Operators ~ & ^ | with Python
+ *                                 precedence, then -> (right assoc) and <->;
+ *                                 constants 0 1; bounded quantifiers
+ *                                 A[i,j:S | i<j] and E[i:S2] (S = range(k),
+ *                                 S2/S3 = ordered tuples of distinct
+ *                                 elements) scoping over the next unary term,
+ *                                 optionally followed by '.'; '#' comments.
+ *
+ * Ownership and threads: the caller owns every device buffer and every CUDA
+ * stream passed in (streams as cudaStream_t cast to void*, NULL = the legacy
+ * default stream).  A program owns its compiled kernels' scratch (a few
+ * counters and per-unit partial counts, allocated on first use, freed by
+ * fbg_program_free).  Calls on one program must not overlap; distinct
+ * programs may be used from different threads.  No call falls back to the
+ * CPU: without a CUDA device every evaluation returns FBG_ECUDA.
+ * Errors: every call returns an fbg_status; fbg_last_error() gives the
+ * calling thread's last message.
+ */
+#ifndef FBG_H
+#define FBG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fbg_program fbg_program;
+typedef struct fbg_batch fbg_batch;
+typedef struct fbg_server fbg_server;
+
+typedef enum {
+  FBG_OK = 0,
+  FBG_EINVAL = 1,      /* bad argument (null pointer, wrong buffer size, bad option) */
+  FBG_EPARSE = 2,      /* formula text does not parse or names an undeclared tuple */
+  FBG_ETOOBIG = 3,     /* n > 63 for counts, n > 40 for tables / model lists,
+                          or a program too large for the interpreter */
+  FBG_ENOMEM = 4,      /* device allocation failed */
+  FBG_ECUDA = 5,       /* CUDA runtime error (including: no device) */
+  FBG_EJIT = 6,        /* NVRTC compilation of the specialised kernel failed */
+  FBG_ETIMEOUT = 7,    /* a wait exceeded its limit */
+  FBG_ECANCELLED = 8,  /* request cancelled */
+  FBG_EBUSY = 9        /* server: result not ready yet */
+} fbg_status;
+
+/* evaluation engines */
+enum {
+  FBG_ENGINE_AUTO = 0,   /* specialised kernel for single programs, else interpreter */
+  FBG_ENGINE_JIT = 1,    /* NVRTC straight-line kernel (count and table) */
+  FBG_ENGINE_INTERP = 2  /* generic bytecode interpreter kernel */
+};
+
+/* program options (fbg_set_option) */
+enum {
+  FBG_OPT_ENGINE = 1,          /* FBG_ENGINE_* */
+  FBG_OPT_PRUNE = 2,           /* 1 (default): levels whose partial conjunction is
+                                  zero skip their inner levels; 0: evaluate every word */
+  FBG_OPT_REGS_LOG2 = 3,       /* JIT: 32-bit registers per thread tile, log2 (1..3, default 2) */
+  FBG_OPT_WARPS_LOG2 = 4,      /* JIT: warps per block, log2 (0..5, default 3) */
+  FBG_OPT_UNIT_BITS = 5,       /* max block-uniform unit bits (default 13) */
+  FBG_OPT_LOOP_LEVEL_BITS = 6, /* bits per loop level (default 4) */
+  FBG_OPT_SEARCH_ORDER = 7,    /* counts: 1 (default) heuristic variable order, 0 identity */
+  FBG_OPT_MIN_BLOCKS = 8,      /* JIT: __launch_bounds__ min blocks per SM (default 2) */
+  FBG_OPT_STATS = 9            /* 1: record executed level iterations (fbg_exec_stats) */
+};
+
+typedef struct {
+  int n;                    /* number of propositional letters */
+  int domain_k;
+  int64_t dag_nodes;        /* hash-consed DAG after grounding */
+  int64_t gates;            /* 2-input gates after level-aware lowering (count layout) */
+  int64_t luts;             /* 3-input LUTs after mapping (count layout) */
+  int nlevels;              /* 2 + loop levels */
+  int64_t lop3_per_level[16];  /* lop3.b32 per thread per execution of each level */
+  int regs_log2, lane_bits, warp_bits, unit_bits;
+  int loop_bits[8];
+  int interp_slots;         /* shared-memory slots of the interpreter program */
+} fbg_stats;
+
+typedef struct {
+  uint64_t level_iters[16]; /* warp-level executions of each level in the last count */
+  double lop3_executed;     /* lop3.b32 lane operations those executions issued */
+  double lop3_nominal;      /* lane operations without pruning: every word evaluated */
+  int engine;               /* engine that ran */
+} fbg_exec_stats;
+
+/*
+ * Compile formula text over the domain range(domain_k) (Sec. 3.1 map *, then
+ * the hash-consed DAG with constants removed: the Reduction of Sec. 4.1).
+ * Host only, no GPU work.  *out is owned by the caller (fbg_program_free).
+ * Returns FBG_EPARSE with a message for bad text, FBG_ETOOBIG above 64 letters.
+ */
+fbg_status fbg_compile(const char *formula, int domain_k, fbg_program **out);
+
+/* number n of propositional letters (the set P of Sec. 3.1), -1 on null */
+int fbg_num_vars(const fbg_program *prog);
+
+/* name of letter i, e.g. "r(2,0)"; FBG_EINVAL if i is out of range or len too small */
+fbg_status fbg_var_name(const fbg_program *prog, int i, char *buf, size_t len);
+
+fbg_status fbg_set_option(fbg_program *prog, int option, int64_t value);
+
+fbg_status fbg_program_stats(fbg_program *prog, fbg_stats *out);
+
+/*
+ * Exact number of models l_{T,n} = popcount of d (Sec. 3.2): evaluates every
+ * assignment, never stores d.  Synchronises `stream`; *out_count is host
+ * memory.  n <= 63.
+ */
+fbg_status fbg_count(fbg_program *prog, void *stream, uint64_t *out_count);
+
+/* as fbg_count, but writes the count to device memory dev_out (8 bytes,
+   caller-owned, overwritten) and returns without synchronising */
+fbg_status fbg_count_async(fbg_program *prog, void *stream, uint64_t *dev_out);
+
+/*
+ * Per-unit partial counts of the count layout: unit u fixes the letters
+ * returned by fbg_unit_vars to the bits of u (bit b of u = value of letter
+ * vars[b]); the counts sum to fbg_count.  dev_counts: nunits device u64s.
+ * Synchronises `stream`.
+ */
+fbg_status fbg_count_units(fbg_program *prog, void *stream, uint64_t *dev_counts, uint64_t nunits);
+fbg_status fbg_unit_vars(fbg_program *prog, int *vars, int max_vars, int *nvars, uint64_t *nunits);
+
+/*
+ * Full truth table d = t(b_1..b_n) (Prop. 2.2, Sec. 2.3) into caller-owned
+ * device memory dev_words of exactly nwords = max(1, 2^(n-6)) 64-bit words
+ * (bit j at word j>>6, bit j&63).  Asynchronous on `stream`.  n <= 40.
+ */
+fbg_status fbg_truth_table(fbg_program *prog, void *stream, uint64_t *dev_words, size_t nwords);
+
+/*
+ * Models of T* in ascending j (the valuations of out.txt, Sec. 4.2; each
+ * decodes to a labelled model by the map h of Sec. 3.2): the first
+ * min(cap, total) are written to caller-owned device memory dev_models;
+ * *total (host) receives the exact number of models, *written the number
+ * stored.  Synchronises `stream`.  n <= 40.
+ */
+fbg_status fbg_enumerate_models(fbg_program *prog, void *stream, uint64_t *dev_models, size_t cap,
+                                uint64_t *total, uint64_t *written);
+
+/* executed work of the last fbg_count with FBG_OPT_STATS = 1 */
+fbg_status fbg_last_exec_stats(fbg_program *prog, fbg_exec_stats *out);
+
+/* CUDA source of the specialised kernel (mode 0 count, 1 table); *len
+   receives the size; buf may be NULL to query it */
+fbg_status fbg_program_source(fbg_program *prog, int mode, char *buf, size_t *len);
+
+/*
+ * Diagnostic: the compiled program as JSON text -- which = 0 / 1: LUT program
+ * of the specialised count / table kernel (layout, constants per register,
+ * LUTs with levels); 2 / 3: interpreter bytecode of the count / identity
+ * layout.  Used to check the compiler on a machine without a GPU; it does
+ * not evaluate anything.  *len receives the size; buf may be NULL.
+ */
+fbg_status fbg_debug_dump(fbg_program *prog, int which, char *buf, size_t *len);
+
+/* NVRTC/ptxas log of the last specialised-kernel build (registers, spills) */
+const char *fbg_program_jit_log(fbg_program *prog);
+
+void fbg_program_free(fbg_program *prog);
+
+/* calling thread's last error message ("" if none) */
+const char *fbg_last_error(void);
+
+/*
+ * Batch (the inner loop of the counting procedure of Sec. 3.4 runs over many
+ * reduced formulas): count many programs in one persistent interpreter launch
+ * fed by a device work queue of (program, unit range) items, largest first.
+ * fbg_batch_create compiles nothing new; programs must outlive the batch.
+ * max_item_units bounds the units per queue item (0 = automatic).
+ * use_graph = 1 captures memset + launch + result copy in a CUDA graph on the
+ * first run and replays it afterwards.
+ */
+fbg_status fbg_batch_create(fbg_program *const *progs, int nprogs, uint64_t max_item_units, int use_graph,
+                            fbg_batch **out);
+/* enqueue one evaluation of every program on `stream` (asynchronous) */
+fbg_status fbg_batch_run(fbg_batch *batch, void *stream);
+/* wait for the last run and copy the exact counts into host memory (nprogs u64) */
+fbg_status fbg_batch_results(fbg_batch *batch, void *stream, uint64_t *host_counts);
+/* queue geometry: items, total units, blocks launched */
+fbg_status fbg_batch_info(fbg_batch *batch, uint64_t *items, uint64_t *units, int *grid);
+void fbg_batch_free(fbg_batch *batch);
+
+/*
+ * Serving loop: requests (formula text, domain, count or enumerate) are
+ * compiled on submission, admitted while their device memory fits the budget,
+ * and evaluated in ticks; each tick runs one persistent launch over the work
+ * of every admitted request (chunks of units), so requests that arrive while
+ * others run join the next tick.  Partial counts stay on the device across
+ * ticks.  A host thread drives the ticks on its own stream.
+ */
+typedef struct {
+  uint64_t mem_budget_bytes;   /* device memory for admitted requests (0 = 1 GiB) */
+  uint64_t tick_units;         /* max units evaluated per tick (0 = automatic) */
+  int max_inflight;            /* max admitted requests (0 = 4096) */
+} fbg_server_options;
+
+enum { FBG_MODE_COUNT = 0, FBG_MODE_ENUMERATE = 1 };
+
+typedef struct {
+  fbg_status status;
+  uint64_t count;              /* exact number of models */
+  uint64_t written;            /* enumerate: models stored */
+  const uint64_t *models;      /* enumerate: host array of `written` models, owned by the server */
+  double submit_s, admit_s, done_s;   /* server clock (seconds) */
+} fbg_result;
+
+fbg_status fbg_server_create(const fbg_server_options *opt, fbg_server **out);
+fbg_status fbg_server_submit(fbg_server *srv, const char *formula, int domain_k, int mode, uint64_t cap,
+                             uint64_t *request_id);
+/* FBG_OK with *out filled when done, FBG_EBUSY while pending */
+fbg_status fbg_server_poll(fbg_server *srv, uint64_t request_id, fbg_result *out);
+/* block until every submitted request is done (timeout_s <= 0: no limit) */
+fbg_status fbg_server_drain(fbg_server *srv, double timeout_s);
+/* release a finished request's result memory */
+fbg_status fbg_server_release(fbg_server *srv, uint64_t request_id);
+fbg_status fbg_server_stats(fbg_server *srv, uint64_t *ticks, uint64_t *launches, double *busy_s);
+void fbg_server_free(fbg_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FBG_H */

@@ -53,6 +53,8 @@ def _load():
             lib.oracle_range.argtypes = [vp, u64, u64, ctypes.POINTER(u64), vp, vp, u64, ctypes.POINTER(u64)]
             lib.oracle_count_cube.argtypes = [vp, u64, u64]
             lib.oracle_count_cube.restype = u64
+            lib.oracle_count_cube_par.argtypes = [vp, u64, u64, ctypes.c_int]
+            lib.oracle_count_cube_par.restype = u64
             lib.oracle_count_par.argtypes = [vp, u64, u64, ctypes.c_int]
             lib.oracle_count_par.restype = u64
             lib.oracle_max_threads.restype = ctypes.c_int
@@ -118,6 +120,9 @@ class Theory:
     def count_cube(self, mask: int, vals: int) -> int:
         """Models with the variables of ``mask`` fixed to the bits of ``vals``."""
         return self._lib.oracle_count_cube(self._h, mask, vals)
+
+    def count_cube_par(self, mask: int, vals: int, threads: int = 0) -> int:
+        return self._lib.oracle_count_cube_par(self._h, mask, vals, threads)
 
     def count_par(self, lo: int, hi: int, threads: int = 0) -> int:
         return self._lib.oracle_count_par(self._h, lo, hi, threads)

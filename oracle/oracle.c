@@ -657,6 +657,26 @@ uint64_t oracle_count_cube(const oracle_prog *p, uint64_t mask, uint64_t vals) {
   return cnt;
 }
 
+/* count_cube with the free assignments split across threads (same arithmetic) */
+uint64_t oracle_count_cube_par(const oracle_prog *p, uint64_t mask, uint64_t vals, int nthreads) {
+  int freev[64], nf = 0;
+  for (int i = 0; i < p->nvars; i++)
+    if (!((mask >> i) & 1)) freev[nf++] = i;
+  uint64_t cnt = 0;
+  long long total = nf >= 63 ? 0 : (1ll << nf);
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for reduction(+ : cnt) schedule(static)
+#endif
+  for (long long t = 0; t < total; t++) {
+    uint64_t j = vals & mask;
+    for (int b = 0; b < nf; b++) j |= (((uint64_t)t >> b) & 1ull) << freev[b];
+    cnt += (uint64_t)oracle_eval(p, j);
+  }
+  (void)nthreads;
+  return cnt;
+}
+
 /* the same count over [lo, hi) with the range split statically across
    threads (timing of the CPU baseline only; identical arithmetic) */
 uint64_t oracle_count_par(const oracle_prog *p, uint64_t lo, uint64_t hi, int nthreads) {

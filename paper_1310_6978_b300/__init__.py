@@ -1,0 +1,214 @@
+"""Free-Boolean-generator model counting on B300 (sm_103a).
+
+Python binding of libfbg.so (include/fbg.h).  A theory is compiled on the host
+(``compile``); counts, truth tables and model lists are computed by the
+library's CUDA kernels.  PyTorch is used only to hold device buffers and
+streams: pass ``torch.cuda.Stream`` objects (or None for the current stream)
+and CUDA tensors (their ``data_ptr()`` is handed to the library).
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+
+__all__ = ["compile", "Program", "Batch", "Server", "FbgError"]
+
+
+def _L():
+    from . import _lib
+    return _lib
+
+
+def __getattr__(name):
+    if name == "FbgError":
+        return _L().FbgError
+    raise AttributeError(name)
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _ptr(t) -> int:
+    return t if isinstance(t, int) else int(t.data_ptr())
+
+
+class Program:
+    """A compiled theory (fbg_compile).  n = number of propositional letters."""
+
+    def __init__(self, text: str, domain_k: int = 1):
+        L = _L()
+        h = ctypes.c_void_p()
+        L.check(L.lib.fbg_compile(text.encode(), int(domain_k), ctypes.byref(h)))
+        self._h = h
+        self._L = L
+        self.text = text
+        self.k = domain_k
+        self.n = L.lib.fbg_num_vars(h)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._L.lib.fbg_program_free(h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_option(self, option: int, value: int) -> "Program":
+        self._L.check(self._L.lib.fbg_set_option(self._h, option, int(value)))
+        return self
+
+    def var_name(self, i: int) -> str:
+        buf = ctypes.create_string_buffer(128)
+        self._L.check(self._L.lib.fbg_var_name(self._h, i, buf, 128))
+        return buf.value.decode()
+
+    def stats(self):
+        s = self._L.FbgStats()
+        self._L.check(self._L.lib.fbg_program_stats(self._h, ctypes.byref(s)))
+        return s
+
+    def count(self, stream=None) -> int:
+        out = ctypes.c_uint64()
+        self._L.check(self._L.lib.fbg_count(self._h, _stream_ptr(stream), ctypes.byref(out)))
+        return out.value
+
+    def count_async(self, dev_out, stream=None) -> None:
+        self._L.check(self._L.lib.fbg_count_async(self._h, _stream_ptr(stream), _ptr(dev_out)))
+
+    def unit_vars(self):
+        vars_ = (ctypes.c_int * 64)()
+        nv = ctypes.c_int()
+        nu = ctypes.c_uint64()
+        self._L.check(self._L.lib.fbg_unit_vars(self._h, vars_, 64, ctypes.byref(nv), ctypes.byref(nu)))
+        return [vars_[i] for i in range(nv.value)], nu.value
+
+    def count_units(self, dev_counts, stream=None) -> None:
+        self._L.check(self._L.lib.fbg_count_units(self._h, _stream_ptr(stream), _ptr(dev_counts), dev_counts.numel()))
+
+    def table_words(self) -> int:
+        return 1 if self.n <= 6 else 1 << (self.n - 6)
+
+    def truth_table(self, dev_words, stream=None) -> None:
+        self._L.check(self._L.lib.fbg_truth_table(self._h, _stream_ptr(stream), _ptr(dev_words), dev_words.numel()))
+
+    def enumerate_models(self, dev_models, cap: int | None = None, stream=None):
+        cap = dev_models.numel() if cap is None else cap
+        total = ctypes.c_uint64()
+        written = ctypes.c_uint64()
+        self._L.check(self._L.lib.fbg_enumerate_models(self._h, _stream_ptr(stream), _ptr(dev_models), cap,
+                                                       ctypes.byref(total), ctypes.byref(written)))
+        return total.value, written.value
+
+    def exec_stats(self):
+        s = self._L.FbgExecStats()
+        self._L.check(self._L.lib.fbg_last_exec_stats(self._h, ctypes.byref(s)))
+        return s
+
+    def source(self, mode: int = 0) -> str:
+        n = ctypes.c_size_t()
+        self._L.check(self._L.lib.fbg_program_source(self._h, mode, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        self._L.check(self._L.lib.fbg_program_source(self._h, mode, buf, ctypes.byref(n)))
+        return buf.value.decode()
+
+    def debug_dump(self, which: int) -> dict:
+        n = ctypes.c_size_t()
+        self._L.check(self._L.lib.fbg_debug_dump(self._h, which, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        self._L.check(self._L.lib.fbg_debug_dump(self._h, which, buf, ctypes.byref(n)))
+        return json.loads(buf.value.decode())
+
+    def jit_log(self) -> str:
+        return self._L.lib.fbg_program_jit_log(self._h).decode(errors="replace")
+
+
+def compile(text: str, domain_k: int = 1) -> Program:   # noqa: A001 - mirrors fbg_compile
+    return Program(text, domain_k)
+
+
+class Batch:
+    """Many programs counted in one persistent launch (fbg_batch_*)."""
+
+    def __init__(self, programs, max_item_units: int = 0, use_graph: bool = True):
+        L = _L()
+        self._L = L
+        self.programs = list(programs)
+        arr = (ctypes.c_void_p * len(self.programs))(*[p.handle.value for p in self.programs])
+        h = ctypes.c_void_p()
+        L.check(L.lib.fbg_batch_create(arr, len(self.programs), max_item_units, 1 if use_graph else 0, ctypes.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._L.lib.fbg_batch_free(h)
+            self._h = None
+
+    def run(self, stream=None) -> None:
+        self._L.check(self._L.lib.fbg_batch_run(self._h, _stream_ptr(stream)))
+
+    def results(self, stream=None):
+        import numpy as np
+        out = np.zeros(len(self.programs), dtype=np.uint64)
+        self._L.check(self._L.lib.fbg_batch_results(self._h, _stream_ptr(stream), out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def info(self):
+        items, units, grid = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int()
+        self._L.check(self._L.lib.fbg_batch_info(self._h, ctypes.byref(items), ctypes.byref(units), ctypes.byref(grid)))
+        return items.value, units.value, grid.value
+
+
+class Server:
+    """Continuous-batching request loop (fbg_server_*)."""
+
+    def __init__(self, mem_budget_bytes: int = 0, tick_units: int = 0, max_inflight: int = 0):
+        L = _L()
+        self._L = L
+        o = L.FbgServerOptions(mem_budget_bytes, tick_units, max_inflight)
+        h = ctypes.c_void_p()
+        L.check(L.lib.fbg_server_create(ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._L.lib.fbg_server_free(h)
+            self._h = None
+
+    def submit(self, text: str, domain_k: int, mode: int = 0, cap: int = 0) -> int:
+        rid = ctypes.c_uint64()
+        self._L.check(self._L.lib.fbg_server_submit(self._h, text.encode(), int(domain_k), mode, cap, ctypes.byref(rid)))
+        return rid.value
+
+    def poll(self, rid: int):
+        r = self._L.FbgResult()
+        st = self._L.lib.fbg_server_poll(self._h, rid, ctypes.byref(r))
+        if st == self._L.FBG_EBUSY:
+            return None
+        self._L.check(st)
+        models = [r.models[i] for i in range(r.written)] if r.written else []
+        return {"status": r.status, "count": r.count, "written": r.written, "models": models,
+                "submit_s": r.submit_s, "admit_s": r.admit_s, "done_s": r.done_s}
+
+    def drain(self, timeout_s: float = 0.0) -> None:
+        self._L.check(self._L.lib.fbg_server_drain(self._h, timeout_s))
+
+    def release(self, rid: int) -> None:
+        self._L.check(self._L.lib.fbg_server_release(self._h, rid))
+
+    def stats(self):
+        t, l, b = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_double()
+        self._L.check(self._L.lib.fbg_server_stats(self._h, ctypes.byref(t), ctypes.byref(l), ctypes.byref(b)))
+        return {"ticks": t.value, "launches": l.value, "busy_s": b.value}

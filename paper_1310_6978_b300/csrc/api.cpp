@@ -1,0 +1,573 @@
+// api.cpp -- the C ABI of include/fbg.h for single programs.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <sstream>
+
+#include "emit.hpp"
+#include "fbg.h"
+#include "fbg_internal.hpp"
+#include "jit.hpp"
+#include "kernels.hpp"
+#include "program.hpp"
+
+using namespace fbg;
+
+namespace fbg {
+
+thread_local std::string g_last_error;
+
+fbg_status set_error(fbg_status s, const std::string& m) {
+  g_last_error = m;
+  return s;
+}
+
+fbg_status cuda_error(cudaError_t e, const char* where) {
+  return set_error(e == cudaErrorMemoryAllocation ? FBG_ENOMEM : FBG_ECUDA,
+                   std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+int device_sms() {
+  static int sms = 0;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  });
+  return sms;
+}
+
+}  // namespace fbg
+
+#define CK(call)                                          \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_error(e_, #call);  \
+  } while (0)
+
+namespace {
+
+LayoutParams interp_params(const fbg_program* p) {
+  LayoutParams lp;
+  lp.r_max = 1;
+  lp.warps_log2 = FBG_INTERP_WARPS_LOG2;
+  lp.unit_bits_max = (int)p->opt_unit_bits;
+  lp.loop_level_bits = (int)p->opt_loop_level_bits;
+  return lp;
+}
+
+LayoutParams jit_params(const fbg_program* p) {
+  LayoutParams lp;
+  lp.r_max = (int)p->opt_regs_log2;
+  lp.warps_log2 = (int)p->opt_warps_log2;
+  lp.unit_bits_max = (int)p->opt_unit_bits;
+  lp.loop_level_bits = (int)p->opt_loop_level_bits;
+  return lp;
+}
+
+void strip_prune(LutProgram& lp) {
+  for (auto& li : lp.levels) li.has_acc = false;
+}
+
+std::vector<int> order_for(const fbg_program* p, bool count_layout) {
+  if (count_layout && p->opt_search) return search_order(p->g);
+  return identity_order(p->n);
+}
+
+fbg_status ensure_scratch(fbg_program* p, size_t words) {
+  if (p->d_scratch && p->scratch_words >= words) return FBG_OK;
+  if (p->d_scratch) cudaFree(p->d_scratch);
+  p->d_scratch = nullptr;
+  p->scratch_words = 0;
+  CK(cudaMalloc(&p->d_scratch, words * sizeof(unsigned long long)));
+  p->scratch_words = words;
+  return FBG_OK;
+}
+
+}  // namespace
+
+namespace fbg {
+
+fbg_status build_interp(fbg_program* p, int which) {
+  InterpBuild& b = p->ib[which];
+  if (b.valid) return FBG_OK;
+  try {
+    Layout L = make_layout(p->n, interp_params(p), order_for(p, which == 0));
+    b.lp = lower_and_map(p->g, L);
+    if (!p->opt_prune) strip_prune(b.lp);
+    b.code = emit_bytecode(b.lp);
+  } catch (CompileError& e) {
+    return set_error(FBG_ETOOBIG, e.msg);
+  }
+  b.nunits = b.code.prog.nunits;
+  // work items: single units while that keeps the queue short, else ranges
+  uint64_t per = 1;
+  while (b.nunits / per > 65536) per <<= 1;
+  std::vector<FbgWorkItem> items;
+  for (uint64_t u = 0; u < b.nunits; u += per) items.push_back(FbgWorkItem{0u, 0u, u, std::min(b.nunits, u + per)});
+  b.units_per_item = per;
+  b.nitems = items.size();
+  b.free_device();
+  CK(cudaMalloc(&b.d_ins, std::max<size_t>(1, b.code.ins.size()) * 8));
+  CK(cudaMalloc(&b.d_consts, std::max<size_t>(1, b.code.consts.size()) * 8));
+  CK(cudaMalloc(&b.d_prog, sizeof(FbgInterpProg)));
+  CK(cudaMalloc(&b.d_items, items.size() * sizeof(FbgWorkItem)));
+  if (!b.code.ins.empty()) CK(cudaMemcpy(b.d_ins, b.code.ins.data(), b.code.ins.size() * 8, cudaMemcpyHostToDevice));
+  if (!b.code.consts.empty())
+    CK(cudaMemcpy(b.d_consts, b.code.consts.data(), b.code.consts.size() * 8, cudaMemcpyHostToDevice));
+  FbgInterpProg G = b.code.prog;
+  G.ins = b.d_ins;
+  G.consts = b.d_consts;
+  CK(cudaMemcpy(b.d_prog, &G, sizeof G, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(b.d_items, items.data(), items.size() * sizeof(FbgWorkItem), cudaMemcpyHostToDevice));
+  int per_sm = interp_blocks_per_sm(which == 0 ? 0 : 2, b.code.nslots);
+  if (per_sm <= 0) return set_error(FBG_ETOOBIG, "interpreter program does not fit in shared memory");
+  b.grid = (int)std::min<uint64_t>(b.nitems, (uint64_t)device_sms() * (uint64_t)per_sm);
+  b.valid = true;
+  return FBG_OK;
+}
+
+fbg_status build_jit(fbg_program* p, int mode) {
+  JitBuild& b = p->jb[mode];
+  if (b.valid) return FBG_OK;
+  try {
+    Layout L = make_layout(p->n, jit_params(p), order_for(p, mode == 0));
+    b.lp = lower_and_map(p->g, L);
+    if (!p->opt_prune) strip_prune(b.lp);
+    b.block = b.lp.layout.lane_bits < 5 ? 32 : 32 << b.lp.layout.warp_bits;
+    b.src = emit_cuda_source(b.lp, mode, b.block, (int)p->opt_min_blocks);
+  } catch (CompileError& e) {
+    return set_error(FBG_ETOOBIG, e.msg);
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  JitResult r = jit_compile(b.src, mode == 0 ? "fbg_jit_count" : "fbg_jit_table", dev);
+  b.log = r.log;
+  p->jit_log = r.log;
+  if (!r.ok) return set_error(FBG_EJIT, r.log);
+  b.kern = r.kernel;
+  int per_sm = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)b.kern, b.block, 0));
+  if (per_sm <= 0) per_sm = 1;
+  b.nunits = 1ull << b.lp.layout.unit_bits;
+  b.grid = (int)std::min<uint64_t>(b.nunits, (uint64_t)device_sms() * (uint64_t)per_sm);
+  b.valid = true;
+  return FBG_OK;
+}
+
+// which engine runs counts/tables: JIT unless the interpreter is requested
+// (or, with the automatic choice, the JIT build failed)
+fbg_status pick_engine(fbg_program* p, int mode, bool* use_jit) {
+  if (p->opt_engine == FBG_ENGINE_INTERP) {
+    *use_jit = false;
+    return build_interp(p, mode == 0 ? 0 : 1);
+  }
+  fbg_status s = build_jit(p, mode);
+  if (s == FBG_OK) {
+    *use_jit = true;
+    return FBG_OK;
+  }
+  if (p->opt_engine == FBG_ENGINE_JIT) return s;
+  *use_jit = false;
+  return build_interp(p, mode == 0 ? 0 : 1);
+}
+
+// scratch words: [0] unit counter [1] count [2] item counter [3] total
+// [4,20) level iterations, then two arrays of `units` words
+constexpr size_t kScratchHead = 32;
+
+fbg_status launch_count(fbg_program* p, cudaStream_t st, unsigned long long* dev_count, unsigned long long* unit_counts,
+                        bool* used_jit) {
+  bool jit = false;
+  fbg_status s = pick_engine(p, 0, &jit);
+  if (s != FBG_OK) return s;
+  if (p->n > 63) return set_error(FBG_ETOOBIG, "counts need n <= 63");
+  s = ensure_scratch(p, kScratchHead);
+  if (s != FBG_OK) return s;
+  if (!dev_count) dev_count = p->d_scratch + 1;
+  CK(cudaMemsetAsync(p->d_scratch, 0, kScratchHead * 8, st));
+  if (dev_count != p->d_scratch + 1) CK(cudaMemsetAsync(dev_count, 0, 8, st));
+  FbgLaunch P{};
+  P.count = dev_count;
+  P.unit_counts = unit_counts;
+  P.unit_ctr = p->d_scratch + 0;
+  P.iters = p->opt_stats ? p->d_scratch + 4 : nullptr;
+  P.unit_begin = 0;
+  if (jit) {
+    JitBuild& b = p->jb[0];
+    P.unit_end = b.nunits;
+    void* args[] = {&P};
+    CK(cudaLaunchKernel((const void*)b.kern, dim3((unsigned)b.grid), dim3((unsigned)b.block), args, 0, st));
+  } else {
+    InterpBuild& b = p->ib[0];
+    P.unit_end = b.nunits;
+    if (unit_counts && b.units_per_item != 1) return set_error(FBG_ETOOBIG, "too many units for per-unit counts");
+    CK(launch_interp(0, b.d_prog, b.d_items, b.nitems, p->d_scratch + 2, dev_count, unit_counts, P, b.code.nslots,
+                     b.grid, st));
+  }
+  *used_jit = jit;
+  return FBG_OK;
+}
+
+}  // namespace fbg
+
+// ------------------------------------------------------------------ ABI --
+
+extern "C" {
+
+fbg_status fbg_compile(const char* formula, int domain_k, fbg_program** out) {
+  if (!formula || !out) return set_error(FBG_EINVAL, "null argument");
+  *out = nullptr;
+  auto* p = new fbg_program();
+  try {
+    p->th = parse_theory(formula, domain_k);
+    p->g = ground(p->th);
+  } catch (CompileError& e) {
+    delete p;
+    bool big = e.msg.find("more than 64") != std::string::npos;
+    return set_error(big ? FBG_ETOOBIG : FBG_EPARSE, e.msg);
+  }
+  p->text = formula;
+  p->k = domain_k;
+  p->n = p->g.nvars;
+  *out = p;
+  return FBG_OK;
+}
+
+int fbg_num_vars(const fbg_program* p) { return p ? p->n : -1; }
+
+fbg_status fbg_var_name(const fbg_program* p, int i, char* buf, size_t len) {
+  if (!p || !buf || i < 0 || i >= p->n) return set_error(FBG_EINVAL, "bad variable index");
+  const std::string& s = p->th.var_names[(size_t)i];
+  if (len < s.size() + 1) return set_error(FBG_EINVAL, "buffer too small");
+  std::memcpy(buf, s.c_str(), s.size() + 1);
+  return FBG_OK;
+}
+
+fbg_status fbg_set_option(fbg_program* p, int option, int64_t v) {
+  if (!p) return set_error(FBG_EINVAL, "null program");
+  auto bad = [] { return set_error(FBG_EINVAL, "option value out of range"); };
+  switch (option) {
+    case FBG_OPT_ENGINE:
+      if (v < 0 || v > 2) return bad();
+      p->opt_engine = v;
+      break;
+    case FBG_OPT_PRUNE: p->opt_prune = v ? 1 : 0; break;
+    case FBG_OPT_REGS_LOG2:
+      if (v < 1 || v > 3) return bad();
+      p->opt_regs_log2 = v;
+      break;
+    case FBG_OPT_WARPS_LOG2:
+      if (v < 0 || v > 5) return bad();
+      p->opt_warps_log2 = v;
+      break;
+    case FBG_OPT_UNIT_BITS:
+      if (v < 0 || v > 24) return bad();
+      p->opt_unit_bits = v;
+      break;
+    case FBG_OPT_LOOP_LEVEL_BITS:
+      if (v < 1 || v > 16) return bad();
+      p->opt_loop_level_bits = v;
+      break;
+    case FBG_OPT_SEARCH_ORDER: p->opt_search = v ? 1 : 0; break;
+    case FBG_OPT_MIN_BLOCKS:
+      if (v < 1 || v > 32) return bad();
+      p->opt_min_blocks = v;
+      break;
+    case FBG_OPT_STATS: p->opt_stats = v ? 1 : 0; return FBG_OK;
+    default: return set_error(FBG_EINVAL, "unknown option");
+  }
+  p->invalidate();
+  return FBG_OK;
+}
+
+fbg_status fbg_program_stats(fbg_program* p, fbg_stats* out) {
+  if (!p || !out) return set_error(FBG_EINVAL, "null argument");
+  std::memset(out, 0, sizeof *out);
+  out->n = p->n;
+  out->domain_k = p->k;
+  out->dag_nodes = p->g.dag.size();
+  LutProgram lp;
+  try {
+    Layout L = make_layout(p->n, jit_params(p), order_for(p, true));
+    lp = lower_and_map(p->g, L);
+  } catch (CompileError& e) {
+    return set_error(FBG_ETOOBIG, e.msg);
+  }
+  out->gates = lp.gates;
+  out->luts = (int64_t)lp.luts.size();
+  out->nlevels = lp.layout.nlevels();
+  for (int i = 0; i < 16 && i < out->nlevels; i++) out->lop3_per_level[i] = lp.lop3_per_level[i];
+  out->regs_log2 = lp.layout.r;
+  out->lane_bits = lp.layout.lane_bits;
+  out->warp_bits = lp.layout.warp_bits;
+  out->unit_bits = lp.layout.unit_bits;
+  for (size_t i = 0; i < lp.layout.loop_bits.size() && i < 8; i++) out->loop_bits[i] = lp.layout.loop_bits[i];
+  if (build_interp(p, 0) == FBG_OK) out->interp_slots = (int)p->ib[0].code.nslots;
+  return FBG_OK;
+}
+
+fbg_status fbg_count(fbg_program* p, void* stream, uint64_t* out_count) {
+  if (!p || !out_count) return set_error(FBG_EINVAL, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  bool jit = false;
+  fbg_status s = launch_count(p, st, nullptr, nullptr, &jit);
+  if (s != FBG_OK) return s;
+  unsigned long long host[kScratchHead];
+  CK(cudaMemcpyAsync(host, p->d_scratch, sizeof host, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  *out_count = host[1];
+  // executed work
+  fbg_exec_stats& es = p->last;
+  std::memset(&es, 0, sizeof es);
+  es.engine = jit ? FBG_ENGINE_JIT : FBG_ENGINE_INTERP;
+  if (p->opt_stats) {
+    const LutProgram& lp = jit ? p->jb[0].lp : p->ib[0].lp;
+    (void)lp;
+    const Layout& L = lp.layout;
+    double warps_per_block = (double)(1 << L.warp_bits);
+    double execs = (double)(1ull << L.unit_bits) * warps_per_block;
+    for (int lv = 0; lv < L.nlevels() && lv < 16; lv++) {
+      es.level_iters[lv] = host[4 + lv];
+      double per = (double)lp.lop3_per_level[lv] * (jit ? 1.0 : 2.0) * 32.0;
+      if (!jit && L.r == 0) per = (double)(lp.levels[lv].lut_end - lp.levels[lv].lut_begin) * 64.0;
+      es.lop3_executed += (double)host[4 + lv] * per;
+      if (lv >= 2) execs *= (double)(1u << L.loop_bits[(size_t)(lv - 2)]);
+      double nominal_execs = lv == 0 ? 0.0 : execs;
+      es.lop3_nominal += nominal_execs * per;
+    }
+  }
+  return FBG_OK;
+}
+
+fbg_status fbg_count_async(fbg_program* p, void* stream, uint64_t* dev_out) {
+  if (!p || !dev_out) return set_error(FBG_EINVAL, "null argument");
+  bool jit = false;
+  return launch_count(p, (cudaStream_t)stream, (unsigned long long*)dev_out, nullptr, &jit);
+}
+
+fbg_status fbg_unit_vars(fbg_program* p, int* vars, int max_vars, int* nvars, uint64_t* nunits) {
+  if (!p || !nvars || !nunits) return set_error(FBG_EINVAL, "null argument");
+  bool jit = false;
+  fbg_status s = pick_engine(p, 0, &jit);
+  if (s != FBG_OK) return s;
+  const Layout& L = jit ? p->jb[0].lp.layout : p->ib[0].lp.layout;
+  *nvars = L.unit_bits;
+  *nunits = 1ull << L.unit_bits;
+  for (int b = 0; b < L.unit_bits && b < max_vars; b++) vars[b] = L.var_of_pos[(size_t)(L.first_unit_pos() + b)];
+  return FBG_OK;
+}
+
+fbg_status fbg_count_units(fbg_program* p, void* stream, uint64_t* dev_counts, uint64_t nunits) {
+  if (!p || !dev_counts) return set_error(FBG_EINVAL, "null argument");
+  int vars[64], nv = 0;
+  uint64_t nu = 0;
+  fbg_status s = fbg_unit_vars(p, vars, 64, &nv, &nu);
+  if (s != FBG_OK) return s;
+  if (nunits != nu) return set_error(FBG_EINVAL, "nunits must be " + std::to_string(nu));
+  cudaStream_t st = (cudaStream_t)stream;
+  s = ensure_scratch(p, kScratchHead);
+  if (s != FBG_OK) return s;
+  CK(cudaMemsetAsync(dev_counts, 0, nunits * 8, st));
+  bool jit = false;
+  s = launch_count(p, st, nullptr, (unsigned long long*)dev_counts, &jit);
+  if (s != FBG_OK) return s;
+  CK(cudaStreamSynchronize(st));
+  return FBG_OK;
+}
+
+fbg_status fbg_truth_table(fbg_program* p, void* stream, uint64_t* dev_words, size_t nwords) {
+  if (!p || !dev_words) return set_error(FBG_EINVAL, "null argument");
+  if (p->n > 40) return set_error(FBG_ETOOBIG, "truth tables need n <= 40");
+  size_t need = p->n <= 6 ? 1 : (size_t)1 << (p->n - 6);
+  if (nwords != need) return set_error(FBG_EINVAL, "nwords must be " + std::to_string(need));
+  cudaStream_t st = (cudaStream_t)stream;
+  bool jit = false;
+  fbg_status s = pick_engine(p, 1, &jit);
+  if (s != FBG_OK) return s;
+  s = ensure_scratch(p, kScratchHead);
+  if (s != FBG_OK) return s;
+  CK(cudaMemsetAsync(p->d_scratch, 0, kScratchHead * 8, st));
+  FbgLaunch P{};
+  P.table = (fbg_u32*)dev_words;
+  P.unit_ctr = p->d_scratch + 0;
+  P.unit_begin = 0;
+  if (jit) {
+    JitBuild& b = p->jb[1];
+    if (p->n < 6) CK(cudaMemsetAsync(dev_words, 0, 8, st));
+    P.unit_end = b.nunits;
+    void* args[] = {&P};
+    CK(cudaLaunchKernel((const void*)b.kern, dim3((unsigned)b.grid), dim3((unsigned)b.block), args, 0, st));
+  } else {
+    InterpBuild& b = p->ib[1];
+    CK(cudaMemsetAsync(dev_words, 0, nwords * 8, st));
+    P.unit_end = b.nunits;
+    CK(launch_interp(1, b.d_prog, b.d_items, b.nitems, p->d_scratch + 2, nullptr, nullptr, P, b.code.nslots, b.grid,
+                     st));
+  }
+  return FBG_OK;
+}
+
+fbg_status fbg_enumerate_models(fbg_program* p, void* stream, uint64_t* dev_models, size_t cap, uint64_t* total,
+                                uint64_t* written) {
+  if (!p || !total || !written || (cap && !dev_models)) return set_error(FBG_EINVAL, "null argument");
+  if (p->n > 40) return set_error(FBG_ETOOBIG, "model lists need n <= 40");
+  cudaStream_t st = (cudaStream_t)stream;
+  fbg_status s = build_interp(p, 1);
+  if (s != FBG_OK) return s;
+  InterpBuild& b = p->ib[1];
+  if (b.units_per_item != 1) return set_error(FBG_ETOOBIG, "too many units");
+  s = ensure_scratch(p, kScratchHead + 2 * b.nunits);
+  if (s != FBG_OK) return s;
+  unsigned long long* unit_counts = p->d_scratch + kScratchHead;
+  unsigned long long* offsets = unit_counts + b.nunits;
+  CK(cudaMemsetAsync(p->d_scratch, 0, (kScratchHead + b.nunits) * 8, st));
+  FbgLaunch P{};
+  P.unit_ctr = p->d_scratch + 0;
+  P.unit_begin = 0;
+  P.unit_end = b.nunits;
+  // pass 1: models per unit
+  CK(launch_interp(0, b.d_prog, b.d_items, b.nitems, p->d_scratch + 2, nullptr, unit_counts, P, b.code.nslots, b.grid,
+                   st));
+  // exclusive scan -> offsets, total
+  CK(launch_scan(unit_counts, offsets, b.nunits, p->d_scratch + 3, st));
+  // pass 2: ordered write
+  CK(cudaMemsetAsync(p->d_scratch + 2, 0, 8, st));
+  P.models = (unsigned long long*)dev_models;
+  P.cap = cap;
+  P.unit_offsets = offsets;
+  CK(launch_interp(2, b.d_prog, b.d_items, b.nitems, p->d_scratch + 2, nullptr, nullptr, P, b.code.nslots, b.grid, st));
+  unsigned long long tot = 0;
+  CK(cudaMemcpyAsync(&tot, p->d_scratch + 3, 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  *total = tot;
+  *written = std::min<uint64_t>(tot, cap);
+  return FBG_OK;
+}
+
+fbg_status fbg_last_exec_stats(fbg_program* p, fbg_exec_stats* out) {
+  if (!p || !out) return set_error(FBG_EINVAL, "null argument");
+  *out = p->last;
+  return FBG_OK;
+}
+
+fbg_status fbg_program_source(fbg_program* p, int mode, char* buf, size_t* len) {
+  if (!p || !len || mode < 0 || mode > 1) return set_error(FBG_EINVAL, "bad argument");
+  std::string src;
+  try {
+    Layout L = make_layout(p->n, jit_params(p), order_for(p, mode == 0));
+    LutProgram lp = lower_and_map(p->g, L);
+    if (!p->opt_prune) strip_prune(lp);
+    src = emit_cuda_source(lp, mode, 32 << (int)p->opt_warps_log2, (int)p->opt_min_blocks);
+  } catch (CompileError& e) {
+    return set_error(FBG_ETOOBIG, e.msg);
+  }
+  if (buf) {
+    if (*len < src.size() + 1) return set_error(FBG_EINVAL, "buffer too small");
+    std::memcpy(buf, src.c_str(), src.size() + 1);
+  }
+  *len = src.size() + 1;
+  return FBG_OK;
+}
+
+fbg_status fbg_debug_dump(fbg_program* p, int which, char* buf, size_t* len) {
+  if (!p || !len || which < 0 || which > 3) return set_error(FBG_EINVAL, "bad argument");
+  std::ostringstream o;
+  auto layout_json = [&](const Layout& L) {
+    o << "\"layout\": {\"n\": " << L.n << ", \"r\": " << L.r << ", \"lane_bits\": " << L.lane_bits
+      << ", \"warp_bits\": " << L.warp_bits << ", \"unit_bits\": " << L.unit_bits << ", \"loop_bits\": [";
+    for (size_t i = 0; i < L.loop_bits.size(); i++) o << (i ? ", " : "") << L.loop_bits[i];
+    o << "], \"loop_pos\": [";
+    for (size_t i = 0; i < L.loop_bits.size(); i++) o << (i ? ", " : "") << L.loop_pos((int)i);
+    o << "], \"first_unit_pos\": " << L.first_unit_pos() << ", \"pos_of_var\": [";
+    for (int i = 0; i < L.n; i++) o << (i ? ", " : "") << L.pos_of_var[(size_t)i];
+    o << "]}";
+  };
+  auto val_json = [&](const Val& v) { o << "[" << (int)v.kind << ", " << v.id << "]"; };
+  if (which < 2) {
+    LutProgram lp;
+    try {
+      Layout L = make_layout(p->n, jit_params(p), order_for(p, which == 0));
+      lp = lower_and_map(p->g, L);
+      if (!p->opt_prune) strip_prune(lp);
+    } catch (CompileError& e) {
+      return set_error(FBG_ETOOBIG, e.msg);
+    }
+    o << "{";
+    layout_json(lp.layout);
+    o << ", \"consts\": [";
+    for (size_t i = 0; i < lp.consts.size(); i++) {
+      o << (i ? ", " : "") << "[";
+      for (size_t j = 0; j < lp.consts[i].w.size(); j++) o << (j ? ", " : "") << lp.consts[i].w[j];
+      o << "]";
+    }
+    o << "], \"luts\": [";
+    for (size_t i = 0; i < lp.luts.size(); i++) {
+      const Lut& lu = lp.luts[i];
+      o << (i ? ", " : "") << "[" << (int)lu.tt << ", ";
+      val_json(lu.in[0]);
+      o << ", ";
+      val_json(lu.in[1]);
+      o << ", ";
+      val_json(lu.in[2]);
+      o << ", " << lu.level << ", " << lu.rmask << "]";
+    }
+    o << "], \"levels\": [";
+    for (size_t i = 0; i < lp.levels.size(); i++) {
+      const LevelInfo& li = lp.levels[i];
+      o << (i ? ", " : "") << "[" << li.lut_begin << ", " << li.lut_end << ", " << (li.has_acc ? 1 : 0) << ", ";
+      val_json(li.acc);
+      o << "]";
+    }
+    o << "], \"out\": ";
+    val_json(lp.out);
+    o << ", \"const_acc\": [";
+    for (size_t j = 0; j < lp.const_acc.w.size(); j++) o << (j ? ", " : "") << lp.const_acc.w[j];
+    o << "]}";
+  } else {
+    InterpCode code;
+    LutProgram lp;
+    try {
+      Layout L = make_layout(p->n, interp_params(p), order_for(p, which == 2));
+      lp = lower_and_map(p->g, L);
+      if (!p->opt_prune) strip_prune(lp);
+      code = emit_bytecode(lp);
+    } catch (CompileError& e) {
+      return set_error(FBG_ETOOBIG, e.msg);
+    }
+    const FbgInterpProg& G = code.prog;
+    o << "{";
+    layout_json(lp.layout);
+    o << ", \"ins\": [";
+    for (size_t i = 0; i < code.ins.size(); i++) o << (i ? ", " : "") << code.ins[i];
+    o << "], \"consts\": [";
+    for (size_t i = 0; i < code.consts.size(); i++) o << (i ? ", " : "") << code.consts[i];
+    o << "], \"levels\": [";
+    for (unsigned i = 0; i < G.nlevels; i++)
+      o << (i ? ", " : "") << "[" << G.lev[i].ins_begin << ", " << G.lev[i].ins_end << ", " << G.lev[i].bits << ", "
+        << G.lev[i].pos << ", " << G.lev[i].has_acc << ", " << G.lev[i].acc_op << "]";
+    o << "], \"out_op\": " << G.out_op << ", \"nslots\": " << G.nslots << ", \"tvalid\": " << G.tvalid
+      << ", \"vmask\": " << G.vmask << ", \"first_unit_pos\": " << G.first_unit_pos << ", \"unit_bits\": "
+      << G.unit_bits << ", \"nunits\": " << G.nunits << "}";
+  }
+  std::string s = o.str();
+  if (buf) {
+    if (*len < s.size() + 1) return set_error(FBG_EINVAL, "buffer too small");
+    std::memcpy(buf, s.c_str(), s.size() + 1);
+  }
+  *len = s.size() + 1;
+  return FBG_OK;
+}
+
+const char* fbg_program_jit_log(fbg_program* p) { return p ? p->jit_log.c_str() : ""; }
+
+void fbg_program_free(fbg_program* p) { delete p; }
+
+const char* fbg_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,355 @@
+// emit.cpp -- code generation from a LUT program:
+//   * CUDA source of a straight-line kernel specialised to one formula
+//     (compiled by NVRTC for sm_103a), count or truth-table mode;
+//   * bytecode, constant table and slot allocation for the interpreter.
+#include <algorithm>
+#include <cstdio>
+#include <sstream>
+
+#include "emit.hpp"
+
+namespace fbg {
+
+// ---------------------------------------------------------------- NVRTC --
+
+namespace {
+
+std::string hex32(uint32_t v) {
+  char b[16];
+  std::snprintf(b, sizeof b, "0x%08xu", v);
+  return b;
+}
+
+struct SrcGen {
+  const LutProgram& p;
+  const Layout& L;
+  int nreg;
+  std::ostringstream o;
+
+  explicit SrcGen(const LutProgram& prog) : p(prog), L(prog.layout), nreg(1 << prog.layout.r) {}
+
+  std::string operand(const Val& v, int s) const {
+    switch (v.kind) {
+      case V_CONST: return hex32(p.consts[(size_t)v.id].w[(size_t)s]);
+      case V_VAR: return "V" + std::to_string(v.id);
+      default: {
+        uint32_t m = p.luts[(size_t)v.id].rmask;
+        return "L" + std::to_string(v.id) + "_" + std::to_string((uint32_t)s & m);
+      }
+    }
+  }
+
+  // positions of non-constant variables used by the program, by level
+  std::vector<std::vector<int>> used_vars() const {
+    std::vector<bool> used((size_t)L.n, false);
+    for (const Lut& lu : p.luts)
+      for (const Val& v : lu.in)
+        if (v.kind == V_VAR) used[(size_t)v.id] = true;
+    if (p.out.kind == V_VAR) used[(size_t)p.out.id] = true;
+    for (const auto& li : p.levels)
+      if (li.has_acc && li.acc.kind == V_VAR) used[(size_t)li.acc.id] = true;
+    std::vector<std::vector<int>> byl((size_t)L.nlevels());
+    for (int pos = 0; pos < L.n; pos++)
+      if (used[(size_t)pos]) {
+        int lv = L.level_of_pos(pos);
+        if (lv >= 0) byl[(size_t)lv].push_back(pos);
+      }
+    return byl;
+  }
+
+  void declare_level(int lv, const std::string& ind) {
+    const LevelInfo& li = p.levels[(size_t)lv];
+    for (int i = li.lut_begin; i < li.lut_end; i++) {
+      uint32_t m = p.luts[(size_t)i].rmask;
+      for (int s = 0; s < nreg; s++)
+        if (((uint32_t)s & m) == (uint32_t)s) o << ind << "fbg_u32 L" << i << "_" << s << ";\n";
+    }
+  }
+
+  void luts(int lv, const std::string& ind) {
+    const LevelInfo& li = p.levels[(size_t)lv];
+    for (int i = li.lut_begin; i < li.lut_end; i++) {
+      const Lut& lu = p.luts[(size_t)i];
+      for (int s = 0; s < nreg; s++) {
+        if (((uint32_t)s & lu.rmask) != (uint32_t)s) continue;
+        o << ind << "L" << i << "_" << s << " = fbg_lop3<" << (int)lu.tt << ">(" << operand(lu.in[0], s) << ", "
+          << operand(lu.in[1], s) << ", " << operand(lu.in[2], s) << ");\n";
+      }
+    }
+  }
+
+  std::string any_nonzero(const Val& v) const {
+    std::string e;
+    uint32_t m = v.kind == V_LUT ? p.luts[(size_t)v.id].rmask : rmask_of(p, v);
+    for (int s = 0; s < nreg; s++) {
+      if (((uint32_t)s & m) != (uint32_t)s) continue;
+      if (!e.empty()) e += " | ";
+      e += operand(v, s);
+    }
+    return "((" + e + ") != 0u)";
+  }
+
+  void var_words(int lv, const std::vector<int>& vars, const std::string& src, int base, const std::string& ind,
+                 bool wide) {
+    (void)lv;
+    for (int pos : vars) {
+      int b = pos - base;
+      if (wide)
+        o << ind << "const fbg_u32 V" << pos << " = 0u - (fbg_u32)((" << src << " >> " << b << ") & 1ull);\n";
+      else
+        o << ind << "const fbg_u32 V" << pos << " = 0u - ((" << src << " >> " << b << ") & 1u);\n";
+    }
+  }
+
+  uint32_t valid_mask() const {
+    if (L.n >= 5) return 0xFFFFFFFFu;
+    return (uint32_t)((1ull << (1u << L.n)) - 1ull);
+  }
+
+  std::string generate(int mode, int block, int minb) {
+    auto vars = used_vars();
+    const int nl = L.nlevels();
+    const int tvalid = 1 << (L.lane_bits + L.warp_bits);
+    const char* kname = mode == 0 ? "fbg_jit_count" : "fbg_jit_table";
+    o << "extern \"C\" __global__ void __launch_bounds__(" << block << ", " << minb << ") " << kname
+      << "(FbgLaunch P) {\n";
+    o << "  const fbg_u32 tb = threadIdx.x;\n";
+    o << "  const fbg_u32 tm = (tb < " << tvalid << "u) ? " << hex32(valid_mask()) << " : 0u;\n";
+    o << "  fbg_u64 lvl_iters[" << nl << "] = {0};\n";
+    var_words(0, vars[0], "tb", L.first_lane_pos(), "  ", false);
+    declare_level(0, "  ");
+    luts(0, "  ");
+    o << "  bool alive0 = true;\n";
+    if (p.levels[0].has_acc) o << "  alive0 = __any_sync(FBG_FULL, " << any_nonzero(p.levels[0].acc) << ");\n";
+    o << "  fbg_u64 total = 0;\n";
+    o << "  __shared__ fbg_u64 s_unit;\n";
+    o << "  for (;;) {\n";
+    o << "    const fbg_u64 u = fbg_next_unit(P, &s_unit);\n";
+    o << "    if (u >= P.unit_end) break;\n";
+    if (mode == 0) {
+      o << "    if (!alive0) continue;\n";
+      o << "    lvl_iters[1]++;\n";
+      var_words(1, vars[1], "u", L.first_unit_pos(), "    ", true);
+      declare_level(1, "    ");
+      luts(1, "    ");
+      if (p.levels[1].has_acc) o << "    if (!__any_sync(FBG_FULL, " << any_nonzero(p.levels[1].acc) << ")) continue;\n";
+      o << "    fbg_u32 ucnt = 0;\n";
+      std::string ind = "    ";
+      for (int lv = 2; lv < nl; lv++) {
+        int li = lv - 2;
+        std::string iv = "i" + std::to_string(lv);
+        o << ind << "for (fbg_u32 " << iv << " = 0; " << iv << " < " << (1u << L.loop_bits[(size_t)li]) << "u; ++" << iv
+          << ") {\n";
+        ind += "  ";
+        o << ind << "lvl_iters[" << lv << "]++;\n";
+        var_words(lv, vars[(size_t)lv], iv, L.loop_pos(li), ind, false);
+        declare_level(lv, ind);
+        luts(lv, ind);
+        if (p.levels[(size_t)lv].has_acc)
+          o << ind << "if (!__any_sync(FBG_FULL, " << any_nonzero(p.levels[(size_t)lv].acc) << ")) continue;\n";
+      }
+      for (int s = 0; s < nreg; s++) o << ind << "ucnt += __popc(" << operand(p.out, s) << " & tm);\n";
+      for (int lv = nl - 1; lv >= 2; lv--) {
+        ind.resize(ind.size() - 2);
+        o << ind << "}\n";
+      }
+      o << "    total += ucnt;\n";
+      o << "    if (P.unit_counts) {\n";
+      o << "      fbg_u64 w = fbg_warp_sum((fbg_u64)ucnt);\n";
+      o << "      if ((tb & 31u) == 0u && w) atomicAdd(P.unit_counts + (u - P.unit_begin), w);\n";
+      o << "    }\n";
+      o << "  }\n";
+      o << "  total = fbg_warp_sum(total);\n";
+      o << "  if ((tb & 31u) == 0u && total) atomicAdd(P.count, total);\n";
+    } else {
+      // truth table: every tile is stored; pruned levels store zeros
+      o << "    bool a1 = alive0;\n";
+      declare_level(1, "    ");
+      var_words(1, vars[1], "u", L.first_unit_pos(), "    ", true);
+      o << "    if (a1) {\n";
+      o << "      lvl_iters[1]++;\n";
+      luts(1, "      ");
+      if (p.levels[1].has_acc) o << "      a1 = __any_sync(FBG_FULL, " << any_nonzero(p.levels[1].acc) << ");\n";
+      o << "    }\n";
+      std::string ind = "    ";
+      for (int lv = 2; lv < nl; lv++) {
+        int li = lv - 2;
+        std::string iv = "i" + std::to_string(lv);
+        o << ind << "for (fbg_u32 " << iv << " = 0; " << iv << " < " << (1u << L.loop_bits[(size_t)li]) << "u; ++" << iv
+          << ") {\n";
+        ind += "  ";
+        o << ind << "bool a" << lv << " = a" << (lv - 1) << ";\n";
+        declare_level(lv, ind);
+        var_words(lv, vars[(size_t)lv], iv, L.loop_pos(li), ind, false);
+        o << ind << "if (a" << lv << ") {\n";
+        o << ind << "  lvl_iters[" << lv << "]++;\n";
+        luts(lv, ind + "  ");
+        if (p.levels[(size_t)lv].has_acc)
+          o << ind << "  a" << lv << " = __any_sync(FBG_FULL, " << any_nonzero(p.levels[(size_t)lv].acc) << ");\n";
+        o << ind << "}\n";
+      }
+      int last = nl - 1;
+      o << ind << "const fbg_u32 keep = a" << last << " ? tm : 0u;\n";
+      // tile index: thread bits, loop levels, unit bits
+      o << ind << "fbg_u64 T = (fbg_u64)tb";
+      for (int lv = 2; lv < nl; lv++)
+        o << " | ((fbg_u64)i" << lv << " << " << (L.loop_pos(lv - 2) - 5 - L.r) << ")";
+      if (L.unit_bits) o << " | (u << " << (L.first_unit_pos() - 5 - L.r) << ")";
+      o << ";\n";
+      std::vector<std::string> w;
+      for (int s = 0; s < nreg; s++) w.push_back("(" + operand(p.out, s) + " & keep)");
+      o << ind << "if (tm) {\n";
+      if (L.r == 0) {
+        o << ind << "  reinterpret_cast<fbg_u64*>(P.table)[0] = (fbg_u64)" << w[0] << ";\n";
+      } else if (L.r == 1) {
+        o << ind << "  reinterpret_cast<uint2*>(P.table)[T] = make_uint2(" << w[0] << ", " << w[1] << ");\n";
+      } else if (L.r == 2) {
+        o << ind << "  reinterpret_cast<uint4*>(P.table)[T] = make_uint4(" << w[0] << ", " << w[1] << ", " << w[2]
+          << ", " << w[3] << ");\n";
+      } else {
+        for (int q = 0; q < nreg / 4; q++)
+          o << ind << "  reinterpret_cast<uint4*>(P.table)[T * " << nreg / 4 << " + " << q << "] = make_uint4(" << w[4 * q]
+            << ", " << w[4 * q + 1] << ", " << w[4 * q + 2] << ", " << w[4 * q + 3] << ");\n";
+      }
+      o << ind << "}\n";
+      for (int lv = nl - 1; lv >= 2; lv--) {
+        ind.resize(ind.size() - 2);
+        o << ind << "}\n";
+      }
+      o << "  }\n";
+    }
+    o << "  if (P.iters && (tb & 31u) == 0u) {\n";
+    o << "    for (int l = 0; l < " << nl << "; l++) if (lvl_iters[l]) atomicAdd(P.iters + l, lvl_iters[l]);\n";
+    o << "  }\n";
+    o << "}\n";
+    return o.str();
+  }
+};
+
+}  // namespace
+
+std::string emit_cuda_source(const LutProgram& p, int mode, int block, int minblocks) {
+  SrcGen g(p);
+  return g.generate(mode, block, minblocks);
+}
+
+// ---------------------------------------------------------- interpreter --
+
+InterpCode emit_bytecode(const LutProgram& p) {
+  const Layout& L = p.layout;
+  if (L.r > 1) throw CompileError{"internal: the interpreter uses 64-bit tiles (r <= 1)"};
+  InterpCode c;
+  c.prog = FbgInterpProg{};
+  const int nluts = (int)p.luts.size();
+  // constants as 64-bit words (register 0 low, register 1 high)
+  for (const ConstVec& cv : p.consts) {
+    uint64_t lo = cv.w[0], hi = cv.w.size() > 1 ? cv.w[1] : cv.w[0];
+    c.consts.push_back(lo | (hi << 32));
+  }
+  if (c.consts.size() > FBG_INTERP_MAX_CONSTS) throw CompileError{"too many distinct constants for the interpreter"};
+  // last use of every LUT value; values used by a deeper level, by a prune
+  // check of a deeper level or by the epilogue stay live to the end
+  std::vector<int> last_use((size_t)nluts, -1);
+  std::vector<int> users((size_t)nluts, 0);
+  std::vector<int> only_user((size_t)nluts, -1);
+  std::vector<bool> to_end((size_t)nluts, false), pinned((size_t)nluts, false);
+  for (int i = 0; i < nluts; i++) {
+    const Lut& lu = p.luts[(size_t)i];
+    int prev = -1;
+    for (const Val& v : lu.in) {
+      if (v.kind != V_LUT || v.id == prev) continue;
+      bool dup = false;
+      for (const Val& w : lu.in)
+        if (&w < &v && w.kind == V_LUT && w.id == v.id) dup = true;
+      if (dup) continue;
+      int j = v.id;
+      last_use[(size_t)j] = std::max(last_use[(size_t)j], i);
+      users[(size_t)j]++;
+      only_user[(size_t)j] = i;
+      if (p.luts[(size_t)j].level < lu.level) to_end[(size_t)j] = true;
+    }
+  }
+  for (int lv = 0; lv < (int)p.levels.size(); lv++) {
+    const LevelInfo& li = p.levels[(size_t)lv];
+    if (!li.has_acc || li.acc.kind != V_LUT) continue;
+    int j = li.acc.id;
+    pinned[(size_t)j] = true;
+    if (p.luts[(size_t)j].level < lv) to_end[(size_t)j] = true;
+    else last_use[(size_t)j] = std::max(last_use[(size_t)j], std::max(li.lut_end - 1, j));
+  }
+  if (p.out.kind == V_LUT) {
+    to_end[(size_t)p.out.id] = true;
+    pinned[(size_t)p.out.id] = true;
+  }
+  // slots: accumulator for a value read only by the next instruction of its level
+  std::vector<int> slot((size_t)nluts, -1);
+  std::vector<int> free_slots;
+  std::vector<std::pair<int, int>> busy;   // (last use, slot)
+  int nslots = 0;
+  for (int i = 0; i < nluts; i++) {
+    // release values whose last use is this instruction or earlier
+    for (size_t q = 0; q < busy.size();) {
+      if (busy[q].first <= i) {
+        free_slots.push_back(busy[q].second);
+        busy[q] = busy.back();
+        busy.pop_back();
+      } else {
+        q++;
+      }
+    }
+    bool acc = !to_end[(size_t)i] && !pinned[(size_t)i] && users[(size_t)i] == 1 && only_user[(size_t)i] == i + 1 &&
+               p.luts[(size_t)(i + 1)].level == p.luts[(size_t)i].level;
+    if (acc) continue;
+    int s;
+    if (!free_slots.empty()) {
+      auto it = std::min_element(free_slots.begin(), free_slots.end());
+      s = *it;
+      free_slots.erase(it);
+    } else {
+      s = nslots++;
+    }
+    slot[(size_t)i] = s;
+    if (!to_end[(size_t)i]) busy.push_back({std::max(last_use[(size_t)i], i), s});
+  }
+  if (nslots > FBG_INTERP_MAX_SLOTS) throw CompileError{"program needs " + std::to_string(nslots) + " live values (max " + std::to_string(FBG_INTERP_MAX_SLOTS) + ")"};
+  auto code = [&](const Val& v) -> uint32_t {
+    if (v.kind == V_CONST) return FBG_OP_CONST | (uint32_t)v.id;
+    if (v.kind == V_VAR) return FBG_OP_VAR | (uint32_t)v.id;
+    return slot[(size_t)v.id] < 0 ? FBG_OP_ACC : (uint32_t)slot[(size_t)v.id];
+  };
+  for (int i = 0; i < nluts; i++) {
+    const Lut& lu = p.luts[(size_t)i];
+    uint64_t dst = slot[(size_t)i] < 0 ? FBG_DST_ACC : (uint64_t)slot[(size_t)i];
+    uint64_t w = (uint64_t)lu.tt | (dst << 8) | ((uint64_t)code(lu.in[0]) << 16) | ((uint64_t)code(lu.in[1]) << 32) |
+                 ((uint64_t)code(lu.in[2]) << 48);
+    c.ins.push_back(w);
+  }
+  FbgInterpProg& G = c.prog;
+  G.n = (unsigned)L.n;
+  G.nlevels = (unsigned)L.nlevels();
+  if (G.nlevels > FBG_INTERP_MAX_LEVELS) throw CompileError{"too many loop levels"};
+  G.nslots = (unsigned)std::max(1, nslots);
+  G.nconst = (unsigned)c.consts.size();
+  G.tvalid = 1u << (L.lane_bits + L.warp_bits);
+  G.first_unit_pos = (unsigned)L.first_unit_pos();
+  G.unit_bits = (unsigned)L.unit_bits;
+  G.out_op = code(p.out);
+  G.vmask = L.n >= 6 ? ~0ull : ((1ull << (1u << L.n)) - 1ull);
+  G.nunits = 1ull << L.unit_bits;
+  for (int lv = 0; lv < (int)G.nlevels; lv++) {
+    const LevelInfo& li = p.levels[(size_t)lv];
+    FbgInterpLevel& X = G.lev[lv];
+    X.ins_begin = (unsigned)li.lut_begin;
+    X.ins_end = (unsigned)li.lut_end;
+    X.has_acc = li.has_acc ? 1u : 0u;
+    X.acc_op = li.has_acc ? code(li.acc) : 0u;
+    if (lv >= 2) {
+      X.bits = (unsigned)L.loop_bits[(size_t)(lv - 2)];
+      X.pos = (unsigned)L.loop_pos(lv - 2);
+    }
+  }
+  c.nslots = G.nslots;
+  return c;
+}
+
+}  // namespace fbg

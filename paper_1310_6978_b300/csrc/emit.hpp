@@ -1,0 +1,25 @@
+// emit.hpp -- code generators for the two evaluation kernels.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "fbg_internal.hpp"
+#include "interp_format.h"
+
+namespace fbg {
+
+// CUDA source of the specialised kernel (mode 0: count, 1: truth table);
+// the caller prepends fbg_device.cuh.
+std::string emit_cuda_source(const LutProgram& p, int mode, int block, int minblocks);
+
+struct InterpCode {
+  FbgInterpProg prog;                 // device pointers left null
+  std::vector<unsigned long long> ins;
+  std::vector<unsigned long long> consts;
+  unsigned nslots = 1;
+};
+
+InterpCode emit_bytecode(const LutProgram& p);
+
+}  // namespace fbg

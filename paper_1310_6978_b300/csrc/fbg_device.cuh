@@ -1,0 +1,54 @@
+// fbg_device.cuh -- definitions shared by the interpreter kernels (nvcc) and
+// the NVRTC-specialised kernels (this file is embedded as text and prepended
+// to every generated source).  No includes: NVRTC compiles it standalone.
+#pragma once
+
+typedef unsigned int fbg_u32;
+typedef unsigned long long fbg_u64;
+
+// One launch of a count / table / enumerate pass over the units
+// [unit_begin, unit_end) of one program.
+struct FbgLaunch {
+  fbg_u64* count;          // += number of models (device u64), may be null
+  fbg_u64* unit_counts;    // per-unit model counts (index u - unit_begin), may be null
+  fbg_u32* table;          // truth table as 32-bit words (table mode)
+  fbg_u64* models;         // model list (enumerate mode)
+  const fbg_u64* unit_offsets;   // enumerate: exclusive prefix of unit counts
+  fbg_u64* unit_ctr;       // dynamic unit counter, zero before the launch
+  fbg_u64* iters;          // optional: innermost-level iterations executed (+=)
+  fbg_u64 cap;             // enumerate: capacity of `models`
+  fbg_u64 unit_begin, unit_end;
+};
+
+#define FBG_FULL 0xffffffffu
+
+#if defined(__CUDACC__) || defined(__CUDACC_RTC__)
+
+template <int LUT>
+__device__ __forceinline__ fbg_u32 fbg_lop3(fbg_u32 a, fbg_u32 b, fbg_u32 c) {
+  fbg_u32 d;
+  asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(LUT));
+  return d;
+}
+
+__device__ __forceinline__ fbg_u64 fbg_warp_sum(fbg_u64 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FBG_FULL, v, o);
+  return v;
+}
+
+// generator word of a non-constant bit position: all ones where the bit is 1
+__device__ __forceinline__ fbg_u32 fbg_genword(fbg_u64 coord, int bit) {
+  return 0u - (fbg_u32)((coord >> bit) & 1ull);
+}
+
+// fetch the next unit for the whole block (dynamic, atomic counter)
+__device__ __forceinline__ fbg_u64 fbg_next_unit(const FbgLaunch& P, fbg_u64* s_unit) {
+  if (threadIdx.x == 0) *s_unit = P.unit_begin + atomicAdd(P.unit_ctr, 1ull);
+  __syncthreads();
+  fbg_u64 u = *s_unit;
+  __syncthreads();
+  return u;
+}
+
+#endif  // __CUDACC__ || __CUDACC_RTC__

@@ -1,0 +1,47 @@
+// interp_format.h -- bytecode of the generic interpreter kernel.
+//
+// A program is a list of 64-bit instructions, each one 3-input LUT on 64-bit
+// words (two lop3.b32: the thread's tile is 2 registers, r = 1), grouped by
+// loop level.  Instruction word: lut[0:8) dst[8:16) a[16:32) b[32:48) c[48:64).
+// Operand codes (16 bit): a shared-memory slot 0..255, FBG_OP_CONST|i (entry
+// i of the constant table), FBG_OP_VAR|p (generator word of bit position p,
+// p >= 6), FBG_OP_ACC (the accumulator register).  dst: slot or FBG_DST_ACC.
+#pragma once
+
+#define FBG_INTERP_MAX_LEVELS 10
+#define FBG_INTERP_BLOCK 64
+#define FBG_INTERP_WARPS_LOG2 1
+#define FBG_INTERP_MAX_SLOTS 160
+#define FBG_INTERP_MAX_CONSTS 512   // constant table entries staged in shared memory
+
+#define FBG_OP_CONST 0x4000u
+#define FBG_OP_VAR 0x8000u
+#define FBG_OP_ACC 0xFFFFu
+#define FBG_DST_ACC 255u
+
+struct FbgInterpLevel {
+  unsigned int ins_begin, ins_end;   // instructions of this level
+  unsigned int bits, pos;            // loop levels: bit count and first bit position
+  unsigned int has_acc, acc_op;      // prune check on this operand (warp vote)
+};
+
+struct FbgInterpProg {
+  unsigned int n;                    // number of variables
+  unsigned int nlevels;              // 2 + loop levels (level 0 thread, 1 unit)
+  unsigned int nslots, nconst;
+  unsigned int tvalid;               // threads of a block that hold real tiles
+  unsigned int first_unit_pos, unit_bits;
+  unsigned int out_op;               // operand holding the formula value
+  unsigned long long vmask;          // valid bits of a tile word (n < 6)
+  unsigned long long nunits;
+  const unsigned long long* ins;     // device pointer to instructions
+  const unsigned long long* consts;  // device pointer to the constant table
+  FbgInterpLevel lev[FBG_INTERP_MAX_LEVELS];
+};
+
+// one entry of the persistent batch queue: units [unit_begin, unit_end) of a program
+struct FbgWorkItem {
+  unsigned int prog;
+  unsigned int flags;
+  unsigned long long unit_begin, unit_end;
+};

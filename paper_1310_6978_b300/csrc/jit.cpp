@@ -1,0 +1,97 @@
+// jit.cpp -- NVRTC compilation of specialised kernels for sm_103a and a
+// process-wide cache keyed by the generated source, so identical programs
+// (same formula, layout and mode) are compiled once.
+#include <cuda_runtime.h>
+#include <nvrtc.h>
+
+#include <mutex>
+#include <unordered_map>
+
+#include "jit.hpp"
+
+namespace fbg {
+
+extern const char fbg_device_header[];   // fbg_device.cuh as text (generated)
+
+namespace {
+
+struct Entry {
+  cudaLibrary_t lib = nullptr;
+  cudaKernel_t kern = nullptr;
+};
+
+std::mutex g_mu;
+std::unordered_map<std::string, Entry> g_cache;   // key: device + source
+
+}  // namespace
+
+JitResult jit_compile(const std::string& body, const char* kernel_name, int device) {
+  JitResult r;
+  std::string src = std::string(fbg_device_header) + "\n" + body;
+  std::string key = std::to_string(device) + ":" + kernel_name + ":" + src;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) {
+      r.ok = true;
+      r.kernel = it->second.kern;
+      r.cached = true;
+      return r;
+    }
+  }
+  nvrtcProgram prog;
+  nvrtcResult e = nvrtcCreateProgram(&prog, src.c_str(), "fbg_jit.cu", 0, nullptr, nullptr);
+  if (e != NVRTC_SUCCESS) {
+    r.log = std::string("nvrtcCreateProgram: ") + nvrtcGetErrorString(e);
+    return r;
+  }
+  const char* opts[] = {"-arch=sm_103a", "-std=c++17", "-lineinfo", "--ptxas-options=-v"};
+  e = nvrtcCompileProgram(prog, 4, opts);
+  size_t logn = 0;
+  nvrtcGetProgramLogSize(prog, &logn);
+  if (logn > 1) {
+    r.log.resize(logn);
+    nvrtcGetProgramLog(prog, &r.log[0]);
+    while (!r.log.empty() && (r.log.back() == 0 || r.log.back() == '\n')) r.log.pop_back();
+  }
+  if (e != NVRTC_SUCCESS) {
+    r.log = std::string("nvrtcCompileProgram: ") + nvrtcGetErrorString(e) + "\n" + r.log;
+    nvrtcDestroyProgram(&prog);
+    return r;
+  }
+  size_t n = 0;
+  nvrtcGetCUBINSize(prog, &n);
+  std::string cubin(n, '\0');
+  nvrtcGetCUBIN(prog, &cubin[0]);
+  nvrtcDestroyProgram(&prog);
+  Entry ent;
+  cudaError_t ce = cudaLibraryLoadData(&ent.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+  if (ce != cudaSuccess) {
+    r.log = std::string("cudaLibraryLoadData: ") + cudaGetErrorString(ce);
+    return r;
+  }
+  ce = cudaLibraryGetKernel(&ent.kern, ent.lib, kernel_name);
+  if (ce != cudaSuccess) {
+    r.log = std::string("cudaLibraryGetKernel: ") + cudaGetErrorString(ce);
+    cudaLibraryUnload(ent.lib);
+    return r;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto ins = g_cache.emplace(key, ent);
+    if (!ins.second) {
+      cudaLibraryUnload(ent.lib);
+      ent = ins.first->second;
+    }
+  }
+  r.ok = true;
+  r.kernel = ent.kern;
+  return r;
+}
+
+size_t jit_cache_size() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_cache.size();
+}
+
+}  // namespace fbg

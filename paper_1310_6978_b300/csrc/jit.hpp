@@ -1,0 +1,21 @@
+// jit.hpp -- NVRTC front end for the specialised kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+namespace fbg {
+
+struct JitResult {
+  bool ok = false;
+  bool cached = false;
+  cudaKernel_t kernel = nullptr;
+  std::string log;     // NVRTC / ptxas messages (registers, spills) or the error
+};
+
+// Compile fbg_device.cuh + body for sm_103a and load it on the current device.
+JitResult jit_compile(const std::string& body, const char* kernel_name, int device);
+size_t jit_cache_size();
+
+}  // namespace fbg

@@ -1,0 +1,20 @@
+// kernels.hpp -- host-side launchers of the device kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fbg_device.cuh"
+#include "interp_format.h"
+
+namespace fbg {
+
+size_t interp_smem_bytes(unsigned nslots);
+cudaError_t launch_interp(int mode, const FbgInterpProg* progs, const FbgWorkItem* items, unsigned long long nitems,
+                          unsigned long long* item_ctr, unsigned long long* prog_counts,
+                          unsigned long long* item_counts, const FbgLaunch& P, unsigned nslots, int grid,
+                          cudaStream_t stream);
+cudaError_t launch_scan(const unsigned long long* in, unsigned long long* out, unsigned long long n,
+                        unsigned long long* total, cudaStream_t stream);
+int interp_blocks_per_sm(int mode, unsigned nslots);
+
+}  // namespace fbg

@@ -1,0 +1,83 @@
+// program.hpp -- the compiled program behind the opaque fbg_program handle.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "emit.hpp"
+#include "fbg.h"
+#include "fbg_internal.hpp"
+
+namespace fbg {
+
+struct InterpBuild {
+  bool valid = false;
+  LutProgram lp;
+  InterpCode code;
+  FbgInterpProg* d_prog = nullptr;
+  unsigned long long* d_ins = nullptr;
+  unsigned long long* d_consts = nullptr;
+  FbgWorkItem* d_items = nullptr;
+  uint64_t nitems = 0, nunits = 0, units_per_item = 1;
+  int grid = 1;
+  void free_device() {
+    if (d_prog) cudaFree(d_prog);
+    if (d_ins) cudaFree(d_ins);
+    if (d_consts) cudaFree(d_consts);
+    if (d_items) cudaFree(d_items);
+    d_prog = nullptr;
+    d_ins = d_consts = nullptr;
+    d_items = nullptr;
+  }
+};
+
+struct JitBuild {
+  bool valid = false;
+  LutProgram lp;
+  std::string src, log;
+  cudaKernel_t kern = nullptr;   // owned by the process-wide JIT cache
+  int block = 256, grid = 1;
+  uint64_t nunits = 1;
+};
+
+fbg_status set_error(fbg_status s, const std::string& m);
+fbg_status cuda_error(cudaError_t e, const char* where);
+int device_sms();
+
+}  // namespace fbg
+
+struct fbg_program {
+  std::string text;
+  int k = 1;
+  int n = 0;
+  fbg::Theory th;
+  fbg::Grounded g;
+  // options (fbg_set_option)
+  int64_t opt_engine = FBG_ENGINE_AUTO, opt_prune = 1, opt_regs_log2 = 2, opt_warps_log2 = 3, opt_unit_bits = 13,
+          opt_loop_level_bits = 4, opt_search = 1, opt_min_blocks = 2, opt_stats = 0;
+  fbg::InterpBuild ib[2];   // [0] count layout, [1] identity layout (tables, model lists)
+  fbg::JitBuild jb[2];      // [0] count kernel, [1] truth-table kernel
+  unsigned long long* d_scratch = nullptr;
+  size_t scratch_words = 0;
+  fbg_exec_stats last{};
+  std::string jit_log;
+
+  void invalidate() {
+    for (auto& b : ib) {
+      b.free_device();
+      b = fbg::InterpBuild{};
+    }
+    for (auto& b : jb) b = fbg::JitBuild{};
+  }
+  ~fbg_program() {
+    for (auto& b : ib) b.free_device();
+    if (d_scratch) cudaFree(d_scratch);
+  }
+};
+
+namespace fbg {
+fbg_status build_interp(fbg_program* p, int which);
+fbg_status build_jit(fbg_program* p, int mode);
+fbg_status pick_engine(fbg_program* p, int mode, bool* use_jit);
+}  // namespace fbg

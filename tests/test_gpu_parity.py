@@ -1,0 +1,214 @@
+"""GPU parity: the CUDA kernels (through the C ABI) against the CPU oracle.
+
+Counts, truth tables and model lists are integer results and must be
+bit-exact.  Small theories are compared in full on both engines (the NVRTC
+straight-line kernel and the bytecode interpreter) under several layouts;
+the full-size workloads are compared on sampled outputs the oracle computes
+one by one (truth-table words, per-unit partial counts) and on identities
+that hold at any size.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import counters as C
+import paper_1310_6978_b300 as F
+from paper_1310_6978_b300 import _lib as L
+from paper_1310_6978_b300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SMALL = [
+    W.BAEQU4, W.posets(2), W.POSET3, W.posets(4), W.equivalences(3), W.equivalences(4), W.transitive(4),
+    W.graphs(3), W.triangle_free(5), W.triangle_free(6), W.automorphisms(4, 3), W.cnf3(7, 5), W.cnf3(12, 1),
+    W.cnf3(16, 3), W.cnf3(20, 4), W.minterm(3, 5), W.single_var(7, 6),
+    W.Workload("xor", 0, "var a, b, c, d, e, f, g, h\n(a ^ b ^ c) | (d & ~e) <-> (f -> g ^ h)\n", 1, 8),
+    W.Workload("taut", 0, "var a, b, c\na | ~a\n", 1, 3),
+    W.Workload("unsat", 0, "var a, b, c, d, e, f, g\n(a & ~a) | (b & 0)\n", 1, 7),
+    W.Workload("one", 0, "var a\na\n", 1, 1),
+]
+
+LAYOUTS = [
+    {},
+    {L.OPT_REGS_LOG2: 1, L.OPT_WARPS_LOG2: 0, L.OPT_UNIT_BITS: 1, L.OPT_LOOP_LEVEL_BITS: 1},
+    {L.OPT_REGS_LOG2: 3, L.OPT_WARPS_LOG2: 2, L.OPT_UNIT_BITS: 2, L.OPT_LOOP_LEVEL_BITS: 2},
+    {L.OPT_PRUNE: 0},
+]
+
+ENGINES = {"jit": L.ENGINE_JIT, "interp": L.ENGINE_INTERP}
+
+
+def program(wl, engine, opts=None):
+    p = F.compile(wl.text, wl.k)
+    p.set_option(L.OPT_ENGINE, ENGINES[engine])
+    for k, v in (opts or {}).items():
+        p.set_option(k, v)
+    return p
+
+
+def gpu_table(p):
+    t = torch.zeros(p.table_words(), dtype=torch.int64, device="cuda")
+    p.truth_table(t)
+    torch.cuda.synchronize()
+    return t.cpu().numpy().view(np.uint64)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+
+
+@pytest.mark.parametrize("wl", SMALL, ids=lambda w: f"{w.family}{w.param}n{w.n}")
+@pytest.mark.parametrize("engine", ["jit", "interp"])
+@pytest.mark.parametrize("li", range(len(LAYOUTS)))
+def test_count_and_table_small(wl, engine, li):
+    th = oracle.Theory(wl.text, wl.k)
+    p = program(wl, engine, LAYOUTS[li])
+    assert p.count() == th.count()
+    assert np.array_equal(gpu_table(p), th.table())
+
+
+@pytest.mark.parametrize("wl", SMALL, ids=lambda w: f"{w.family}{w.param}n{w.n}")
+@pytest.mark.parametrize("cap", [0, 5, 1 << 20])
+def test_enumerate_small(wl, cap):
+    th = oracle.Theory(wl.text, wl.k)
+    p = F.compile(wl.text, wl.k)
+    buf = torch.full((max(1, cap),), -1, dtype=torch.int64, device="cuda")
+    total, written = p.enumerate_models(buf, cap)
+    om, ot = th.models(cap)
+    assert total == ot and written == len(om)
+    got = buf[:written].cpu().numpy().view(np.uint64)
+    assert np.array_equal(got, om)
+    if cap > written:   # nothing written past the models
+        assert bool((buf[written:] == -1).all())
+
+
+def test_poset3_config():
+    # partial orders on 3 points: 512-bit table (8 words) and 19 models
+    wl = W.POSET3
+    th = oracle.Theory(wl.text, wl.k)
+    for engine in ENGINES:
+        p = program(wl, engine)
+        assert p.count() == 19
+        t = gpu_table(p)
+        assert t.shape == (8,) and np.array_equal(t, th.table())
+
+
+@pytest.mark.parametrize("engine", ["jit", "interp"])
+def test_counts_match_closed_forms(engine):
+    for k, want in [(3, 19), (4, 219), (5, 4231)]:
+        assert program(W.posets(k), engine).count() == want
+    for k in range(1, 7):
+        assert program(W.equivalences(k), engine).count() == C.bell(k)
+    for k in range(2, 6):
+        assert program(W.graphs(k), engine).count() == C.labelled_graphs(k)
+
+
+def test_tail_and_degenerate():
+    for n in range(1, 7):
+        names = ", ".join(f"v{i}" for i in range(n))
+        for body, f in [("v0 | ~v0", lambda j: 1), ("v0 & ~v0", lambda j: 0), (f"v{n - 1}", lambda j: (j >> (n - 1)) & 1)]:
+            p = F.compile(f"var {names}\n{body}\n")
+            for engine in ENGINES.values():
+                p.set_option(L.OPT_ENGINE, engine)
+                t = gpu_table(p)
+                want = sum(f(j) << j for j in range(1 << n))
+                assert t.shape == (1,) and int(t[0]) == want
+                assert p.count() == bin(want).count("1")
+
+
+def test_tautology_counts_every_assignment():
+    names = ", ".join(f"v{i}" for i in range(40))
+    p = F.compile(f"var {names}\nv3 | ~v3 | v17\n")
+    assert p.count() == 1 << 40
+
+
+def test_shannon_split_on_gpu():
+    wl = W.cnf3(30, 7)
+    base = wl.text.rstrip("\n")
+    c = F.compile(wl.text, wl.k).count()
+    c0 = F.compile(base + "\n~x(11)\n", wl.k).count()
+    c1 = F.compile(base + "\nx(11)\n", wl.k).count()
+    assert c0 + c1 == c
+    neg = F.compile("var x(S)\n~(" + " & ".join(f"({ln})" for ln in wl.text.splitlines()[1:] if ln.strip()) + ")\n", wl.k)
+    assert neg.count() + c == 1 << 30
+
+
+def test_errors_are_reported():
+    p = F.compile(W.POSET3.text, 3)
+    t = torch.zeros(4, dtype=torch.int64, device="cuda")
+    with pytest.raises(L.FbgError) as ei:
+        p.truth_table(t)
+    assert ei.value.status == L.FBG_EINVAL
+    big = F.compile("var " + ", ".join(f"v{i}" for i in range(41)) + "\nv0\n")
+    with pytest.raises(L.FbgError) as ei:
+        big.truth_table(t)
+    assert ei.value.status == L.FBG_ETOOBIG
+
+
+def test_count_async_on_caller_stream():
+    s = torch.cuda.Stream()
+    out = torch.full((1,), 7, dtype=torch.int64, device="cuda")
+    p = F.compile(W.posets(4).text, 4)
+    with torch.cuda.stream(s):
+        p.count_async(out, stream=s)
+    s.synchronize()
+    assert int(out.item()) == 219
+
+
+# ---------------------------------------------------------------- full size --
+
+def test_cnf32_table_sampled_and_count():
+    """3-CNF, n = 32, m = 136, seed 1: the 512 MiB table in the launch the
+    benchmark times; sampled words against the oracle, popcount = count, and
+    per-unit counts against the oracle on sampled subcubes."""
+    wl = W.CNF32
+    th = oracle.Theory(wl.text, wl.k)
+    p = F.compile(wl.text, wl.k)
+    table = torch.empty(p.table_words(), dtype=torch.int64, device="cuda")
+    p.truth_table(table)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(11)
+    idx = np.unique(np.concatenate([rng.integers(0, table.numel(), 1500), [0, table.numel() - 1]]))
+    words = table[torch.from_numpy(idx).cuda()].cpu().numpy().view(np.uint64)
+    for w, word in zip(idx, words):
+        want = 0
+        for b in range(64):
+            want |= th.eval((int(w) << 6) | b) << b
+        assert int(word) == want, f"word {w}"
+    pop = int(np.bitwise_count(table.cpu().numpy().view(np.uint64)).sum())
+    assert pop == p.count()
+    _check_units(p, th, rng, samples=3)
+
+
+def _check_units(p, th, rng, samples):
+    vars_, nunits = p.unit_vars()
+    counts = torch.zeros(nunits, dtype=torch.int64, device="cuda")
+    p.count_units(counts)
+    uc = counts.cpu().numpy().view(np.uint64)
+    assert int(uc.sum()) == p.count()
+    mask = sum(1 << v for v in vars_)
+    for u in list(rng.integers(0, nunits, samples)) + [0, nunits - 1]:
+        vals = sum(((int(u) >> b) & 1) << v for b, v in enumerate(vars_))
+        assert int(uc[int(u)]) == th.count_cube_par(mask, vals), f"unit {u}"
+
+
+@pytest.mark.parametrize("name", ["transitive6", "trifree9", "aut6"])
+def test_n36_counts(name):
+    wl = {"transitive6": W.TRANSITIVE6, "trifree9": W.TRIFREE9, "aut6": W.AUT6}[name]
+    th = oracle.Theory(wl.text, wl.k)
+    p = F.compile(wl.text, wl.k)
+    cnt = p.count()
+    if name == "aut6":
+        assert cnt == C.count_automorphisms(W.random_graph_bits(6, 3), 6)
+    # the interpreter and the unpruned JIT kernel agree with it
+    q = F.compile(wl.text, wl.k).set_option(L.OPT_ENGINE, L.ENGINE_INTERP)
+    assert q.count() == cnt
+    r = F.compile(wl.text, wl.k).set_option(L.OPT_PRUNE, 0)
+    assert r.count() == cnt
+    _check_units(p, th, np.random.default_rng(5), samples=2)
