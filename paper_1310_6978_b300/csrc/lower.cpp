@@ -344,11 +344,26 @@ class Lowerer {
   // level's group is recorded there.
   int nary(GOp op, const std::vector<int>& kids, std::vector<int>* accs) {
     std::vector<std::pair<int, int>> items;   // (level, literal)
+    std::vector<std::vector<int>> keys;
     for (size_t i = 0; i < kids.size(); i++) {
       int l = lower(kids[i]);
       items.push_back({level_of_lit(l), l});
+      // operands that share sub-operands (clauses with common literals) are
+      // placed next to each other, which keeps shared partial values short-lived
+      const FNode& f = g_.dag.node(kids[i]);
+      keys.push_back(f.op == FAND || f.op == FOR ? f.kids : std::vector<int>{kids[i]});
     }
-    std::stable_sort(items.begin(), items.end(), [](auto& x, auto& y) { return x.first < y.first; });
+    std::vector<size_t> ord(items.size());
+    for (size_t i = 0; i < ord.size(); i++) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) {
+      if (items[a].first != items[b].first) return items[a].first < items[b].first;
+      return keys[a] < keys[b];
+    });
+    {
+      std::vector<std::pair<int, int>> sorted;
+      for (size_t i : ord) sorted.push_back(items[i]);
+      items.swap(sorted);
+    }
     int x = -1;
     size_t i = 0;
     while (i < items.size()) {
@@ -424,14 +439,25 @@ class Lowerer {
   void enumerate_cuts(int g) {
     const GNode& gn = nodes_[(size_t)g];
     struct Opt { int leaf[3]; int n; long long extra; };
+    // a child is either a leaf of the cut, or its own cut is absorbed: always
+    // for a child used only here; for a shared child (same level) when its
+    // cut's leaves are already computed values -- the shared logic is then
+    // duplicated inside this LUT for free instead of kept live in a register
     auto options = [&](int x, std::vector<Opt>& o) {
-      Opt leaf{{x, 0, 0}, 1, exclusive(x) ? best_[(size_t)x] : 0};
+      const bool ex = exclusive(x);
+      Opt leaf{{x, 0, 0}, 1, ex ? best_[(size_t)x] : 0};
       o.push_back(leaf);
-      if (exclusive(x))
-        for (const Cut& c : cuts_[(size_t)x]) {
-          Opt t{{c.leaf[0], c.leaf[1], c.leaf[2]}, c.nleaf, c.cost - weight(x)};
-          o.push_back(t);
+      const GNode& gx = nodes_[(size_t)x];
+      if (gx.kind != K_GATE || gx.level != gn.level) return;
+      for (const Cut& c : cuts_[(size_t)x]) {
+        if (ex) {
+          o.push_back(Opt{{c.leaf[0], c.leaf[1], c.leaf[2]}, c.nleaf, c.cost - weight(x)});
+        } else {
+          bool free_leaves = true;
+          for (int i = 0; i < c.nleaf; i++) free_leaves &= !exclusive(c.leaf[i]);
+          if (free_leaves) o.push_back(Opt{{c.leaf[0], c.leaf[1], c.leaf[2]}, c.nleaf, 0});
         }
+      }
     };
     std::vector<Opt> oa, ob;
     options(lnode(gn.in[0]), oa);
@@ -483,14 +509,23 @@ class Lowerer {
     return Val{V_LUT, emit(x)};
   }
 
+  // the operands of a LUT: the most recently built (deepest, e.g. a running
+  // conjunction) first, so that short side values are computed right before
+  // their use and do not stay live across a long chain
+  void emit_leaves(const Cut& c, Lut& lu) {
+    int order[3] = {0, 1, 2};
+    std::sort(order, order + c.nleaf, [&](int a, int b) { return c.leaf[a] > c.leaf[b]; });
+    for (int q = 0; q < c.nleaf; q++) lu.in[order[q]] = leaf_val(c.leaf[order[q]]);
+    for (int i = c.nleaf; i < 3; i++) lu.in[i] = lu.in[0];
+  }
+
   // emit node x (a gate) as a LUT with its best cut; returns the LUT index
   int emit(int x) {
     auto it = emitted_.find(x);
     if (it != emitted_.end()) return it->second;
     const Cut& c = cuts_[(size_t)x][0];
     Lut lu;
-    for (int i = 0; i < c.nleaf; i++) lu.in[i] = leaf_val(c.leaf[i]);
-    for (int i = c.nleaf; i < 3; i++) lu.in[i] = lu.in[0];
+    emit_leaves(c, lu);
     std::unordered_map<int, uint8_t> memo;
     lu.tt = cone_tt(x, c.leaf, c.nleaf, memo);
     lu.level = nodes_[(size_t)x].level;
@@ -518,8 +553,7 @@ class Lowerer {
       lu.tt = (uint8_t)~0xF0;
     } else {
       const Cut& c = cuts_[(size_t)x][0];
-      for (int i = 0; i < c.nleaf; i++) lu.in[i] = leaf_val(c.leaf[i]);
-      for (int i = c.nleaf; i < 3; i++) lu.in[i] = lu.in[0];
+      emit_leaves(c, lu);
       std::unordered_map<int, uint8_t> memo;
       lu.tt = (uint8_t)~cone_tt(x, c.leaf, c.nleaf, memo);
     }
