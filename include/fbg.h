@@ -165,6 +165,30 @@ fbg_status fbg_truth_table(fbg_program *prog, void *stream, uint64_t *dev_words,
 fbg_status fbg_enumerate_models(fbg_program *prog, void *stream, uint64_t *dev_models, size_t cap,
                                 uint64_t *total, uint64_t *written);
 
+/*
+ * Count without any device allocation by the library.  The paper has no
+ * counterpart of this entry point; it exists for callers that cannot let a
+ * library call cudaMalloc -- a process whose caching allocator already owns
+ * the free device memory, or code that must keep to a fixed, pre-reserved
+ * budget -- while fbg_count allocates the program's device buffers and
+ * scratch on first use.  Here the work counters, program descriptor,
+ * bytecode, constants and work queue of the interpreter count kernel live in
+ * one file-scope device array of FBG_NOALLOC_SCRATCH_BYTES, held by every GPU
+ * that loads the library until the process exits; no cudaMalloc, cudaFree or
+ * other allocating routine is called.  Programs whose bytecode and queue do
+ * not fit return FBG_ETOOBIG with the size they need.
+ * The caller passes the compiled program and dev_out, one caller-owned device
+ * u64 that receives the count (overwritten).  The call synchronises `stream`.
+ * The first call on a device looks up the array's device address for that
+ * device (cudaGetSymbolAddress, with the device current); make that first
+ * call before any stream capture.  All calls share the one array, which
+ * keeps the last call's contents (counters are cleared by each call): calls
+ * that overlap on the GPU -- from several host threads or streams -- race and
+ * must be serialised by the caller.
+ */
+#define FBG_NOALLOC_SCRATCH_BYTES (128u * 1024u)
+fbg_status fbg_count_noalloc(fbg_program *prog, void *stream, uint64_t *dev_out);
+
 /* executed work of the last fbg_count with FBG_OPT_STATS = 1 */
 fbg_status fbg_last_exec_stats(fbg_program *prog, fbg_exec_stats *out);
 

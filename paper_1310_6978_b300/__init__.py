@@ -83,6 +83,11 @@ class Program:
     def count_async(self, dev_out, stream=None) -> None:
         self._L.check(self._L.lib.fbg_count_async(self._h, _stream_ptr(stream), _ptr(dev_out)))
 
+    def count_noalloc(self, dev_out, stream=None) -> None:
+        """fbg_count_noalloc: the count into device memory ``dev_out`` (one
+        64-bit element) with no device allocation by the library."""
+        self._L.check(self._L.lib.fbg_count_noalloc(self._h, _stream_ptr(stream), _ptr(dev_out)))
+
     def unit_vars(self):
         vars_ = (ctypes.c_int * 64)()
         nv = ctypes.c_int()
