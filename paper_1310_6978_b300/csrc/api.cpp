@@ -140,7 +140,7 @@ fbg_status build_jit(fbg_program* p, int mode) {
     b.lp = lower_and_map(p->g, L);
     if (!p->opt_prune) strip_prune(b.lp);
     b.block = b.lp.layout.lane_bits < 5 ? 32 : 32 << b.lp.layout.warp_bits;
-    b.src = emit_cuda_source(b.lp, mode, b.block, (int)p->opt_min_blocks);
+    b.src = emit_cuda_source(b.lp, mode, b.block, (int)p->opt_min_blocks, &b.ops);
   } catch (CompileError& e) {
     return set_error(FBG_ETOOBIG, e.msg);
   }
@@ -302,7 +302,9 @@ fbg_status fbg_program_stats(fbg_program* p, fbg_stats* out) {
   out->gates = lp.gates;
   out->luts = (int64_t)lp.luts.size();
   out->nlevels = lp.layout.nlevels();
-  for (int i = 0; i < 16 && i < out->nlevels; i++) out->lop3_per_level[i] = lp.lop3_per_level[i];
+  std::vector<long long> ops;
+  emit_cuda_source(lp, 0, 32 << lp.layout.warp_bits, (int)p->opt_min_blocks, &ops);
+  for (int i = 0; i < 16 && i < out->nlevels; i++) out->lop3_per_level[i] = ops[(size_t)i];
   out->regs_log2 = lp.layout.r;
   out->lane_bits = lp.layout.lane_bits;
   out->warp_bits = lp.layout.warp_bits;
@@ -334,8 +336,10 @@ fbg_status fbg_count(fbg_program* p, void* stream, uint64_t* out_count) {
     double execs = (double)(1ull << L.unit_bits) * warps_per_block;
     for (int lv = 0; lv < L.nlevels() && lv < 16; lv++) {
       es.level_iters[lv] = host[4 + lv];
-      double per = (double)lp.lop3_per_level[lv] * (jit ? 1.0 : 2.0) * 32.0;
-      if (!jit && L.r == 0) per = (double)(lp.levels[lv].lut_end - lp.levels[lv].lut_begin) * 64.0;
+      // JIT: lop3.b32 each thread issues per level execution (folded source);
+      // interpreter: two lop3.b32 per instruction (64-bit tiles)
+      double per = jit ? (double)p->jb[0].ops[(size_t)lv] * 32.0
+                       : (double)(lp.levels[(size_t)lv].lut_end - lp.levels[(size_t)lv].lut_begin) * 64.0;
       es.lop3_executed += (double)host[4 + lv] * per;
       if (lv >= 2) execs *= (double)(1u << L.loop_bits[(size_t)(lv - 2)]);
       double nominal_execs = lv == 0 ? 0.0 : execs;

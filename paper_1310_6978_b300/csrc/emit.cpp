@@ -4,6 +4,8 @@
 //   * bytecode, constant table and slot allocation for the interpreter.
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
+#include <map>
 #include <sstream>
 
 #include "emit.hpp"
@@ -20,24 +22,179 @@ std::string hex32(uint32_t v) {
   return b;
 }
 
+// One 32-bit register of a LUT value after per-register folding: a constant,
+// or a reference to an emitted register / generator word, possibly negated
+// (negations are absorbed into the consumers' truth tables).
+struct Sym {
+  bool is_const = true;
+  uint32_t c = 0;
+  std::string name;
+  bool neg = false;
+  bool operator==(const Sym& o) const {
+    return is_const == o.is_const && (is_const ? c == o.c : (name == o.name && neg == o.neg));
+  }
+};
+
 struct SrcGen {
   const LutProgram& p;
   const Layout& L;
   int nreg;
   std::ostringstream o;
+  // per LUT and register index (s & rmask): folded value, emitted or not
+  std::vector<std::vector<Sym>> sym;
+  std::vector<std::vector<char>> real;
+  std::vector<std::vector<std::string>> code;   // the lop3 call of real registers
+  std::vector<long long> ops;                   // lop3.b32 per thread per level execution
 
-  explicit SrcGen(const LutProgram& prog) : p(prog), L(prog.layout), nreg(1 << prog.layout.r) {}
+  explicit SrcGen(const LutProgram& prog) : p(prog), L(prog.layout), nreg(1 << prog.layout.r) { fold(); }
 
-  std::string operand(const Val& v, int s) const {
-    switch (v.kind) {
-      case V_CONST: return hex32(p.consts[(size_t)v.id].w[(size_t)s]);
-      case V_VAR: return "V" + std::to_string(v.id);
-      default: {
-        uint32_t m = p.luts[(size_t)v.id].rmask;
-        return "L" + std::to_string(v.id) + "_" + std::to_string((uint32_t)s & m);
+  Sym operand_sym(const Val& v, int s) const {
+    Sym x;
+    if (v.kind == V_CONST) {
+      x.is_const = true;
+      x.c = p.consts[(size_t)v.id].w[(size_t)s];
+    } else if (v.kind == V_VAR) {
+      x.is_const = false;
+      x.name = "V" + std::to_string(v.id);
+    } else {
+      x = sym[(size_t)v.id][(size_t)((uint32_t)s & p.luts[(size_t)v.id].rmask)];
+    }
+    return x;
+  }
+
+  static std::string expr(const Sym& x) {
+    if (x.is_const) return hex32(x.c);
+    return x.neg ? "(~" + x.name + ")" : x.name;
+  }
+
+  // Fold every LUT register: constant all-zero/all-one inputs fix their bit,
+  // negated inputs flip, repeated inputs merge; a function of no or one input
+  // becomes a constant or an alias, identical operations inside one level
+  // share one register.  What remains is one lop3.b32.
+  void fold() {
+    const size_t nl = p.luts.size();
+    sym.assign(nl, {});
+    real.assign(nl, {});
+    code.assign(nl, {});
+    ops.assign((size_t)L.nlevels(), 0);
+    std::map<std::string, std::string> cse;
+    int cur_level = -100;
+    for (size_t i = 0; i < nl; i++) {
+      const Lut& lu = p.luts[i];
+      if (lu.level != cur_level) {
+        cse.clear();
+        cur_level = lu.level;
+      }
+      sym[i].assign((size_t)nreg, Sym{});
+      real[i].assign((size_t)nreg, 0);
+      code[i].assign((size_t)nreg, "");
+      for (int s = 0; s < nreg; s++) {
+        if (((uint32_t)s & lu.rmask) != (uint32_t)s) continue;
+        Sym in[3];
+        for (int k = 0; k < 3; k++) in[k] = operand_sym(lu.in[k], s);
+        uint8_t f[8];
+        for (int m = 0; m < 8; m++) f[m] = (uint8_t)((lu.tt >> m) & 1);
+        int fixed[3] = {-1, -1, -1};
+        for (int k = 0; k < 3; k++) {
+          if (in[k].is_const && (in[k].c == 0u || in[k].c == 0xFFFFFFFFu)) fixed[k] = in[k].c ? 1 : 0;
+          if (!in[k].is_const && in[k].neg) {   // absorb the negation
+            uint8_t g[8];
+            for (int m = 0; m < 8; m++) g[m] = f[m ^ (4 >> k)];
+            std::memcpy(f, g, 8);
+            in[k].neg = false;
+          }
+        }
+        // distinct free symbols
+        std::vector<Sym> fs;
+        int map[3] = {-1, -1, -1};
+        for (int k = 0; k < 3; k++) {
+          if (fixed[k] >= 0) continue;
+          for (size_t t = 0; t < fs.size(); t++)
+            if (fs[t] == in[k]) map[k] = (int)t;
+          if (map[k] < 0) {
+            map[k] = (int)fs.size();
+            fs.push_back(in[k]);
+          }
+        }
+        auto g_of = [&](unsigned alpha) {
+          int bit[3];
+          for (int k = 0; k < 3; k++) bit[k] = fixed[k] >= 0 ? fixed[k] : (int)((alpha >> map[k]) & 1u);
+          return f[(bit[0] << 2) | (bit[1] << 1) | bit[2]];
+        };
+        unsigned kf = (unsigned)fs.size();
+        std::vector<uint8_t> g(1u << kf);
+        for (unsigned a = 0; a < (1u << kf); a++) g[a] = g_of(a);
+        // drop symbols the function does not depend on
+        for (int t = (int)kf - 1; t >= 0; t--) {
+          bool dep = false;
+          for (unsigned a = 0; a < (1u << kf); a++)
+            if (g[a] != g[a ^ (1u << t)]) dep = true;
+          if (dep) continue;
+          std::vector<uint8_t> h;
+          std::vector<Sym> fs2;
+          // rebuild g over the remaining symbols
+          unsigned k2 = kf - 1;
+          h.assign(1u << k2, 0);
+          for (unsigned a = 0; a < (1u << k2); a++) {
+            unsigned lo = a & ((1u << t) - 1u), hi = a >> t;
+            h[a] = g[lo | (hi << (t + 1))];
+          }
+          for (unsigned q = 0; q < kf; q++)
+            if ((int)q != t) fs2.push_back(fs[q]);
+          g.swap(h);
+          fs.swap(fs2);
+          kf = k2;
+        }
+        Sym out;
+        bool all_imm = true;
+        for (auto& x : fs) all_imm &= x.is_const;
+        if (kf == 0) {
+          out.is_const = true;
+          out.c = g[0] ? 0xFFFFFFFFu : 0u;
+        } else if (all_imm) {
+          uint32_t v = 0;
+          for (int bitpos = 0; bitpos < 32; bitpos++) {
+            unsigned a = 0;
+            for (unsigned q = 0; q < kf; q++) a |= ((fs[q].c >> bitpos) & 1u) << q;
+            v |= (uint32_t)g[a] << bitpos;
+          }
+          out.is_const = true;
+          out.c = v;
+        } else if (kf == 1 && !fs[0].is_const) {
+          out = fs[0];
+          out.neg = g[0] == 1;   // g = (0,1): identity; (1,0): complement
+        } else {
+          // one lop3: free symbols become inputs 0..kf-1 (unused inputs repeat input 0)
+          int tt = 0;
+          for (int m = 0; m < 8; m++) {
+            unsigned ab[3] = {(unsigned)(m >> 2) & 1u, (unsigned)(m >> 1) & 1u, (unsigned)m & 1u};
+            unsigned a = 0;
+            for (unsigned q = 0; q < kf; q++) a |= ab[q] << q;
+            tt |= g[a] << m;
+          }
+          std::string ops3[3];
+          for (unsigned q = 0; q < 3; q++) ops3[q] = expr(fs[q < kf ? q : 0]);
+          std::string call = "fbg_lop3<" + std::to_string(tt) + ">(" + ops3[0] + ", " + ops3[1] + ", " + ops3[2] + ")";
+          auto it = cse.find(call);
+          if (it != cse.end()) {
+            out.is_const = false;
+            out.name = it->second;
+          } else {
+            std::string nm = "L" + std::to_string(i) + "_" + std::to_string(s);
+            cse.emplace(call, nm);
+            out.is_const = false;
+            out.name = nm;
+            real[i][(size_t)s] = 1;
+            code[i][(size_t)s] = call;
+            if (lu.level >= 0 && lu.level < (int)ops.size()) ops[(size_t)lu.level]++;
+          }
+        }
+        sym[i][(size_t)s] = out;
       }
     }
   }
+
+  std::string operand(const Val& v, int s) const { return expr(operand_sym(v, s)); }
 
   // positions of non-constant variables used by the program, by level
   std::vector<std::vector<int>> used_vars() const {
@@ -59,30 +216,21 @@ struct SrcGen {
 
   void declare_level(int lv, const std::string& ind) {
     const LevelInfo& li = p.levels[(size_t)lv];
-    for (int i = li.lut_begin; i < li.lut_end; i++) {
-      uint32_t m = p.luts[(size_t)i].rmask;
+    for (int i = li.lut_begin; i < li.lut_end; i++)
       for (int s = 0; s < nreg; s++)
-        if (((uint32_t)s & m) == (uint32_t)s) o << ind << "fbg_u32 L" << i << "_" << s << ";\n";
-    }
+        if (real[(size_t)i][(size_t)s]) o << ind << "fbg_u32 L" << i << "_" << s << ";\n";
   }
 
   void luts(int lv, const std::string& ind) {
     const LevelInfo& li = p.levels[(size_t)lv];
-    for (int i = li.lut_begin; i < li.lut_end; i++) {
-      const Lut& lu = p.luts[(size_t)i];
-      for (int s = 0; s < nreg; s++) {
-        if (((uint32_t)s & lu.rmask) != (uint32_t)s) continue;
-        o << ind << "L" << i << "_" << s << " = fbg_lop3<" << (int)lu.tt << ">(" << operand(lu.in[0], s) << ", "
-          << operand(lu.in[1], s) << ", " << operand(lu.in[2], s) << ");\n";
-      }
-    }
+    for (int i = li.lut_begin; i < li.lut_end; i++)
+      for (int s = 0; s < nreg; s++)
+        if (real[(size_t)i][(size_t)s]) o << ind << "L" << i << "_" << s << " = " << code[(size_t)i][(size_t)s] << ";\n";
   }
 
   std::string any_nonzero(const Val& v) const {
     std::string e;
-    uint32_t m = v.kind == V_LUT ? p.luts[(size_t)v.id].rmask : rmask_of(p, v);
     for (int s = 0; s < nreg; s++) {
-      if (((uint32_t)s & m) != (uint32_t)s) continue;
       if (!e.empty()) e += " | ";
       e += operand(v, s);
     }
@@ -228,9 +376,12 @@ struct SrcGen {
 
 }  // namespace
 
-std::string emit_cuda_source(const LutProgram& p, int mode, int block, int minblocks) {
+std::string emit_cuda_source(const LutProgram& p, int mode, int block, int minblocks,
+                             std::vector<long long>* ops_per_level) {
   SrcGen g(p);
-  return g.generate(mode, block, minblocks);
+  std::string src = g.generate(mode, block, minblocks);
+  if (ops_per_level) *ops_per_level = g.ops;
+  return src;
 }
 
 // ---------------------------------------------------------- interpreter --

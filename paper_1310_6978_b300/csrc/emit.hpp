@@ -11,7 +11,10 @@ namespace fbg {
 
 // CUDA source of the specialised kernel (mode 0: count, 1: truth table);
 // the caller prepends fbg_device.cuh.
-std::string emit_cuda_source(const LutProgram& p, int mode, int block, int minblocks);
+// ops_per_level (optional) receives the lop3.b32 each thread issues per
+// execution of each level after per-register folding.
+std::string emit_cuda_source(const LutProgram& p, int mode, int block, int minblocks,
+                             std::vector<long long>* ops_per_level = nullptr);
 
 struct InterpCode {
   FbgInterpProg prog;                 // device pointers left null

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <vector>
 
 #include "emit.hpp"
 #include "fbg.h"
@@ -36,6 +37,7 @@ struct JitBuild {
   bool valid = false;
   LutProgram lp;
   std::string src, log;
+  std::vector<long long> ops;    // lop3.b32 per thread per level execution (after folding)
   cudaKernel_t kern = nullptr;   // owned by the process-wide JIT cache
   int block = 256, grid = 1;
   uint64_t nunits = 1;

@@ -1,0 +1,106 @@
+"""Compile the generated CUDA source of the specialised kernels as host C++
+(test infrastructure).  The kernel body is straight-line integer code; the
+few device builtins it uses get host stand-ins here, and one "thread" runs at
+a time over all units.  Warp votes become per-thread votes (a thread skips
+only levels whose partial conjunction is zero for itself, so counts and
+tables are unchanged) and warp sums add over the lanes of a warp, run from
+lane 31 down to lane 0.  This checks the emitter (folding, loops, stores) on
+a machine without a GPU; it is not an evaluation path of the library.
+"""
+from __future__ import annotations
+
+import ctypes
+import hashlib
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HDR = os.path.join(ROOT, "paper_1310_6978_b300", "csrc", "fbg_device.cuh")
+
+PRELUDE = r'''
+#include <cstdint>
+#include <cstring>
+#include "%s"
+struct dim3_ { unsigned x, y, z; };
+static dim3_ threadIdx;
+#define __global__
+#define __launch_bounds__(a, b)
+#define __shared__ static
+template <int LUT> static inline fbg_u32 fbg_lop3(fbg_u32 a, fbg_u32 b, fbg_u32 c) {
+  fbg_u32 r = 0;
+  for (int m = 0; m < 8; m++)
+    if ((LUT >> m) & 1) r |= ((m & 4) ? a : ~a) & ((m & 2) ? b : ~b) & ((m & 1) ? c : ~c);
+  return r;
+}
+static inline int __popc(fbg_u32 x) { return __builtin_popcount(x); }
+static inline bool __any_sync(unsigned, bool p) { return p; }
+static fbg_u64 g_warp_acc = 0;
+static inline fbg_u64 fbg_warp_sum(fbg_u64 v) {
+  g_warp_acc += v;
+  if ((threadIdx.x & 31u) == 0u) { fbg_u64 r = g_warp_acc; g_warp_acc = 0; return r; }
+  return v;
+}
+static inline unsigned long long atomicAdd(unsigned long long* p, unsigned long long v) { auto o = *p; *p += v; return o; }
+struct uint2 { fbg_u32 x, y; };
+struct uint4 { fbg_u32 x, y, z, w; };
+static inline uint2 make_uint2(fbg_u32 a, fbg_u32 b) { return uint2{a, b}; }
+static inline uint4 make_uint4(fbg_u32 a, fbg_u32 b, fbg_u32 c, fbg_u32 d) { return uint4{a, b, c, d}; }
+static fbg_u64 g_next = 0;
+static inline fbg_u64 fbg_next_unit(const FbgLaunch& P, fbg_u64*) { return P.unit_begin + g_next++; }
+'''
+
+DRIVER = r'''
+extern "C" int run(int mode, int block, unsigned long long nunits, unsigned long long* count, unsigned* table) {
+  FbgLaunch P;
+  std::memset(&P, 0, sizeof P);
+  unsigned long long cnt = 0, ctr = 0;
+  P.count = &cnt; P.unit_ctr = &ctr; P.table = table; P.unit_begin = 0; P.unit_end = nunits;
+  for (int w = 0; w < block / 32 || w == 0; w++) {
+    for (int lane = 31; lane >= 0; lane--) {
+      threadIdx.x = (unsigned)(w * 32 + lane);
+      if ((int)threadIdx.x >= block) continue;
+      g_next = 0;
+      if (mode == 0) fbg_jit_count(P); else fbg_jit_table(P);
+    }
+  }
+  *count = cnt;
+  return 0;
+}
+'''
+
+
+def build_kernel(src: str, mode: int) -> ctypes.CDLL:
+    kname = "fbg_jit_count" if mode == 0 else "fbg_jit_table"
+    body = (PRELUDE % HDR) + src + DRIVER.replace("fbg_jit_count(P); else fbg_jit_table(P);",
+                                                   f"{kname}(P); else {kname}(P);")
+    h = hashlib.sha1(body.encode()).hexdigest()[:16]
+    d = os.path.join(tempfile.gettempdir(), "fbg_jit_host")
+    os.makedirs(d, exist_ok=True)
+    so = os.path.join(d, f"k{h}.so")
+    if not os.path.exists(so):
+        cpp = os.path.join(d, f"k{h}.cpp")
+        with open(cpp, "w") as f:
+            f.write(body)
+        subprocess.check_call(["g++", "-O1", "-std=c++17", "-shared", "-fPIC", "-w", "-o", so + ".tmp", cpp])
+        os.replace(so + ".tmp", so)
+    lib = ctypes.CDLL(so)
+    lib.run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_void_p]
+    return lib
+
+
+def run_count(src: str, block: int, nunits: int) -> int:
+    lib = build_kernel(src, 0)
+    c = ctypes.c_ulonglong()
+    lib.run(0, block, nunits, ctypes.byref(c), None)
+    return c.value
+
+
+def run_table(src: str, block: int, nunits: int, nwords: int) -> np.ndarray:
+    lib = build_kernel(src, 1)
+    t = np.zeros(nwords, dtype=np.uint64)
+    c = ctypes.c_ulonglong()
+    lib.run(1, block, nunits, ctypes.byref(c), t.ctypes.data_as(ctypes.c_void_p))
+    return t
