@@ -164,6 +164,121 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args, torch, F, L):
+    """4096 mixed formulas (seed 2) in one persistent launch replayed from a
+    CUDA graph, against one interpreter launch per formula (same kernel,
+    per-formula synchronisation)."""
+    from paper_1310_6978_b300 import workloads as W
+    mix = W.batch_mix(4096, 2)
+    progs = [F.compile(w.text, w.k) for w in mix]
+    stream = torch.cuda.Stream()
+    b = F.Batch(progs, use_graph=True)
+    for _ in range(3):
+        b.run(stream)
+    counts = b.results(stream)
+    reps = max(3, min(args.steps, 20))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(reps):
+            b.run(stream)
+        e1.record(stream)
+    stream.synchronize()
+    assert [int(x) for x in b.results(stream)] == [int(x) for x in counts]
+    t_batch = e0.elapsed_time(e1) / 1e3 / reps
+    # one launch per formula, interpreter, synchronised each time
+    singles = [F.compile(w.text, w.k).set_option(L.OPT_ENGINE, L.ENGINE_INTERP) for w in mix]
+    for p in singles[:64]:
+        p.count(stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    single_counts = [p.count(stream) for p in singles]
+    t_single = time.perf_counter() - t0
+    assert single_counts == [int(x) for x in counts]
+    small = [i for i, w in enumerate(mix) if w.n <= 20]
+    sb = F.Batch([progs[i] for i in small], use_graph=True)
+    for _ in range(3):
+        sb.run(stream)
+    sb.results(stream)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(reps):
+            sb.run(stream)
+        e1.record(stream)
+    stream.synchronize()
+    t_small_b = e0.elapsed_time(e1) / 1e3 / reps
+    t0 = time.perf_counter()
+    for i in small:
+        singles[i].count(stream)
+    t_small_s = time.perf_counter() - t0
+    assign = sum(1 << w.n for w in mix)
+    assign_small = sum(1 << mix[i].n for i in small)
+    items, units, grid = b.info()
+    return {"formulas": len(mix), "assignments": assign, "value": assign / t_batch / 1e9, "unit": "Gassign/s",
+            "ms": t_batch * 1e3, "per_formula_ms": t_single * 1e3, "speedup_vs_per_formula": t_single / t_batch,
+            "small_n_le_20": {"formulas": len(small), "batched_ms": t_small_b * 1e3, "per_formula_ms": t_small_s * 1e3,
+                              "speedup": t_small_s / t_small_b,
+                              "batched_gassign_s": assign_small / t_small_b / 1e9},
+            "queue": {"items": items, "units": units, "grid": grid}, "graph": True,
+            "counts_match_per_formula": True}
+
+
+def run_serving(args, torch, F, L):
+    """Poisson stream of requests (seed 5): n uniform in 16..38, a family with
+    exactly n letters else 3-CNF; 90% count, 10% enumerate (cap 1e6).  The
+    rate is 0.7x the throughput of a calibration burst."""
+    import threading
+    from paper_1310_6978_b300 import workloads as W
+    nreq = args.serve_requests
+    calib = W.request_stream(min(400, nreq), rate_per_s=1.0, seed=55)
+    srv = F.Server()
+    t0 = time.perf_counter()
+    ids = [srv.submit(r.workload.text, r.workload.k,
+                      L.MODE_ENUMERATE if r.mode == "enumerate" else L.MODE_COUNT, r.cap) for r in calib]
+    srv.drain(600)
+    t_cal = time.perf_counter() - t0
+    srv.close()
+    rate = 0.7 * len(calib) / t_cal
+    reqs = W.request_stream(nreq, rate_per_s=rate, seed=5)
+    srv = F.Server()
+    ids = [None] * len(reqs)
+    start = time.perf_counter()
+
+    def producer():
+        for i, r in enumerate(reqs):
+            delay = start + r.arrival_s - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            ids[i] = srv.submit(r.workload.text, r.workload.k,
+                                L.MODE_ENUMERATE if r.mode == "enumerate" else L.MODE_COUNT, r.cap)
+
+    th = threading.Thread(target=producer)
+    th.start()
+    th.join()
+    srv.drain(1800)
+    wall = time.perf_counter() - start
+    lat, assign, counts = [], 0, []
+    for i, r in zip(ids, reqs):
+        res = srv.poll(i)
+        assert res["status"] == 0
+        lat.append(res["done_s"] - res["submit_s"])
+        assign += 1 << r.workload.n
+        counts.append(res["count"])
+    st = srv.stats()
+    srv.close()
+    # exactness on a sample: the server's counts equal standalone counts
+    rng = __import__("random").Random(5)
+    sample = rng.sample(range(len(reqs)), min(60, len(reqs)))
+    for i in sample:
+        r = reqs[i]
+        assert F.compile(r.workload.text, r.workload.k).count() == counts[i]
+    lat.sort()
+    return {"requests": len(reqs), "rate_per_s": rate, "wall_s": wall, "p50_ms": lat[len(lat) // 2] * 1e3,
+            "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))] * 1e3, "value": assign / wall / 1e9,
+            "unit": "Gassign/s", "ticks": st["ticks"], "launches": st["launches"],
+            "checked_against_single_counts": len(sample), "calibration": {"requests": len(calib), "s": t_cal}}
+
+
 # -------------------------------------------------------------------- ours --
 
 def run_ours(args, rank, world):
@@ -259,6 +374,9 @@ def run_ours(args, rank, world):
         brute = {"value": assign_per_step / bt / 1e9, "unit": "Gassign/s", "ms": bt * 1e3,
                  "lop3_tops": bex / bt / 1e12, "frac": bex / bt / peak_lop3}
 
+    batched = {} if args.quick or args.no_batch else run_batched(args, torch, F, L)
+    serving = {} if args.quick or args.no_serve else run_serving(args, torch, F, L)
+
     # end to end through the public API: text -> compile -> count -> host
     e2e_steps = 2 if args.quick else max(2, min(args.steps, 5))
     t0 = time.perf_counter()
@@ -288,6 +406,8 @@ def run_ours(args, rank, world):
                               "peak = 148 SM x 64 lanes/clk x 2032 MHz"},
         "nominal_lop3_ratio": executed / nominal if nominal else None,
         "brute_force": brute,
+        "batched": batched,
+        "serving": serving,
         "clocks": clocks,
         "e2e": {"value": assign_per_step / e2e_t / 1e9, "unit": "Gassign/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 8 * len(wls)},
@@ -306,6 +426,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=3000)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=4.0)
     args = ap.parse_args()

@@ -247,25 +247,32 @@ __global__ void scan_kernel(const fbg_u64* in, fbg_u64* out, fbg_u64 n, fbg_u64*
 
 size_t interp_smem_bytes(unsigned nslots) { return (size_t)nslots * B * sizeof(fbg_u64); }
 
+// the dynamic shared memory limit is raised only when a larger size is needed,
+// so launches (also inside stream capture) do not call cudaFuncSetAttribute
+static cudaError_t ensure_smem(int mode, size_t smem) {
+  static size_t set_to[3] = {0, 0, 0};
+  if (smem <= set_to[mode]) return cudaSuccess;
+  cudaError_t e;
+  if (mode == 0) e = cudaFuncSetAttribute(interp_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  else if (mode == 1) e = cudaFuncSetAttribute(interp_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  else e = cudaFuncSetAttribute(interp_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) set_to[mode] = smem;
+  return e;
+}
+
 cudaError_t launch_interp(int mode, const FbgInterpProg* progs, const FbgWorkItem* items, unsigned long long nitems,
                           unsigned long long* item_ctr, unsigned long long* prog_counts,
                           unsigned long long* item_counts, const FbgLaunch& P, unsigned nslots, int grid,
                           cudaStream_t stream) {
   size_t smem = interp_smem_bytes(nslots);
-  cudaError_t e;
-  if (mode == 0) {
-    e = cudaFuncSetAttribute(interp_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+  cudaError_t e = ensure_smem(mode, smem);
+  if (e != cudaSuccess) return e;
+  if (mode == 0)
     interp_kernel<0><<<grid, B, smem, stream>>>(progs, items, nitems, item_ctr, prog_counts, item_counts, P);
-  } else if (mode == 1) {
-    e = cudaFuncSetAttribute(interp_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+  else if (mode == 1)
     interp_kernel<1><<<grid, B, smem, stream>>>(progs, items, nitems, item_ctr, prog_counts, item_counts, P);
-  } else {
-    e = cudaFuncSetAttribute(interp_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+  else
     interp_kernel<2><<<grid, B, smem, stream>>>(progs, items, nitems, item_ctr, prog_counts, item_counts, P);
-  }
   return cudaGetLastError();
 }
 
@@ -278,16 +285,10 @@ cudaError_t launch_scan(const unsigned long long* in, unsigned long long* out, u
 int interp_blocks_per_sm(int mode, unsigned nslots) {
   int nb = 0;
   size_t smem = interp_smem_bytes(nslots);
-  if (mode == 0) {
-    cudaFuncSetAttribute(interp_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, interp_kernel<0>, B, smem);
-  } else if (mode == 1) {
-    cudaFuncSetAttribute(interp_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, interp_kernel<1>, B, smem);
-  } else {
-    cudaFuncSetAttribute(interp_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, interp_kernel<2>, B, smem);
-  }
+  if (ensure_smem(mode, smem) != cudaSuccess) return 0;
+  if (mode == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, interp_kernel<0>, B, smem);
+  else if (mode == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, interp_kernel<1>, B, smem);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, interp_kernel<2>, B, smem);
   return nb;
 }
 

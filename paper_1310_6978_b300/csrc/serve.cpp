@@ -1,0 +1,374 @@
+// serve.cpp -- continuous-batching request loop.
+//
+// Requests (formula text, domain, count or enumerate) are compiled on the
+// submitting thread and queued.  A server thread runs ticks on its own
+// stream: it admits queued requests while their device memory fits the
+// budget and a slot is free, gives every admitted count request a share of
+// the tick's units, and evaluates all of them in ONE interpreter launch over
+// a work queue of (slot, unit range) items.  Partial counts stay in device
+// memory across ticks (one u64 per slot); a request finishes when its last
+// unit has run.  Requests arriving while a tick runs join the next tick.
+// Model lists (enumerate) run as ordered two-pass evaluations between ticks.
+// Every tick is a bounded launch: nothing runs forever on the GPU.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "fbg.h"
+#include "kernels.hpp"
+#include "program.hpp"
+
+using namespace fbg;
+
+namespace {
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct Request {
+  uint64_t id = 0;
+  int mode = FBG_MODE_COUNT;
+  uint64_t cap = 0;
+  fbg_program* prog = nullptr;
+  int slot = -1;
+  uint64_t next_unit = 0, nunits = 0;
+  uint64_t mem = 0;
+  fbg_status status = FBG_EBUSY;
+  uint64_t count = 0;
+  std::vector<uint64_t> models;
+  double submit_s = 0, admit_s = 0, done_s = 0;
+  bool done = false;
+  ~Request() { fbg_program_free(prog); }
+};
+
+}  // namespace
+
+struct fbg_server {
+  fbg_server_options opt{};
+  int device = 0;
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv, done_cv;
+  bool stop = false;
+  uint64_t next_id = 1;
+  std::deque<Request*> pending;
+  std::vector<Request*> active;                   // admitted, not finished
+  std::unordered_map<uint64_t, std::unique_ptr<Request>> all;
+  uint64_t outstanding = 0;
+  uint64_t mem_used = 0;
+  // device state
+  cudaStream_t stream = nullptr;
+  FbgInterpProg* d_progs = nullptr;               // one descriptor per slot
+  FbgInterpProg* h_progs = nullptr;               // pinned staging
+  unsigned long long* d_counts = nullptr;         // per-slot partial counts, then the item counter
+  unsigned long long* h_counts = nullptr;         // pinned
+  FbgWorkItem* d_items = nullptr;
+  FbgWorkItem* h_items = nullptr;                 // pinned
+  uint64_t item_cap = 0;
+  std::vector<int> free_slots;
+  unsigned long long* d_models = nullptr;         // enumerate output buffer
+  size_t models_cap = 0;
+  // statistics
+  std::atomic<uint64_t> ticks{0}, launches{0};
+  double busy_s = 0;
+  fbg_status fatal = FBG_OK;
+
+  void run();
+  void tick();
+  fbg_status admit_locked(Request* r);
+  void finish(Request* r, fbg_status s);
+};
+
+namespace {
+
+constexpr uint64_t kDefaultBudget = 1ull << 30;
+
+uint64_t request_mem(const fbg_program* p, int mode, uint64_t cap) {
+  const InterpBuild& b = p->ib[mode == FBG_MODE_COUNT ? 0 : 1];
+  uint64_t m = b.code.ins.size() * 8 + b.code.consts.size() * 8 + sizeof(FbgInterpProg) + b.nitems * sizeof(FbgWorkItem);
+  if (mode == FBG_MODE_ENUMERATE) m += cap * 8 + b.nunits * 16;
+  return m;
+}
+
+}  // namespace
+
+void fbg_server::finish(Request* r, fbg_status s) {
+  r->status = s;
+  r->done_s = now_s();
+  r->done = true;
+  if (r->slot >= 0) {
+    free_slots.push_back(r->slot);
+    r->slot = -1;
+  }
+  mem_used -= std::min(mem_used, r->mem);
+  outstanding--;
+  done_cv.notify_all();
+}
+
+fbg_status fbg_server::admit_locked(Request* r) {
+  // build the interpreter program on this (server) thread
+  fbg_status s = build_interp(r->prog, r->mode == FBG_MODE_COUNT ? 0 : 1);
+  if (s != FBG_OK) return s;
+  r->mem = request_mem(r->prog, r->mode, r->cap);
+  r->admit_s = now_s();
+  if (r->mode == FBG_MODE_COUNT) {
+    const InterpBuild& b = r->prog->ib[0];
+    r->slot = free_slots.back();
+    free_slots.pop_back();
+    r->nunits = b.nunits;
+    r->next_unit = 0;
+    FbgInterpProg G = b.code.prog;
+    G.ins = b.d_ins;
+    G.consts = b.d_consts;
+    h_progs[r->slot] = G;
+    cudaError_t e = cudaMemcpyAsync(d_progs + r->slot, h_progs + r->slot, sizeof G, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_counts + r->slot, 0, 8, stream);
+    if (e != cudaSuccess) return cuda_error(e, "server admit");
+  }
+  mem_used += r->mem;
+  active.push_back(r);
+  return FBG_OK;
+}
+
+void fbg_server::tick() {
+  double t0 = now_s();
+  std::vector<Request*> count_reqs, enum_reqs;
+  {
+    std::unique_lock<std::mutex> lk(mu);
+    // admission by device memory and free slots, in arrival order
+    while (!pending.empty()) {
+      Request* r = pending.front();
+      bool needs_slot = r->mode == FBG_MODE_COUNT;
+      if (needs_slot && free_slots.empty()) break;
+      // estimate before building; a request larger than the whole budget still runs alone
+      uint64_t est = (uint64_t)r->prog->g.dag.size() * 64 + (r->mode == FBG_MODE_ENUMERATE ? r->cap * 8 : 0);
+      if (mem_used && mem_used + est > opt.mem_budget_bytes) break;
+      pending.pop_front();
+      fbg_status s = admit_locked(r);
+      if (s != FBG_OK) finish(r, s);
+    }
+    for (Request* r : active) (r->mode == FBG_MODE_COUNT ? count_reqs : enum_reqs).push_back(r);
+  }
+  // one launch over a share of every admitted count request
+  if (!count_reqs.empty()) {
+    uint64_t budget = opt.tick_units;
+    uint64_t share = std::max<uint64_t>(1, budget / count_reqs.size());
+    uint64_t n = 0, units = 0;
+    unsigned nslots = 1;
+    for (Request* r : count_reqs) {
+      uint64_t take = std::min<uint64_t>(r->nunits - r->next_unit, share);
+      // at most 8 units per item so that blocks share large requests
+      uint64_t need = (take + 7) / 8;
+      if (n + need > item_cap) break;   // the rest waits for the next tick
+      for (uint64_t u = r->next_unit; u < r->next_unit + take; u += 8)
+        h_items[n++] = FbgWorkItem{(unsigned)r->slot, 0u, u, std::min(r->next_unit + take, u + 8)};
+      r->next_unit += take;
+      units += take;
+      nslots = std::max(nslots, r->prog->ib[0].code.nslots);
+    }
+    (void)units;
+    cudaError_t e = cudaMemcpyAsync(d_items, h_items, n * sizeof(FbgWorkItem), cudaMemcpyHostToDevice, stream);
+    uint64_t slots = (uint64_t)opt.max_inflight;
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_counts + slots, 0, 8, stream);
+    int per_sm = interp_blocks_per_sm(0, nslots);
+    int grid = (int)std::min<uint64_t>(n, (uint64_t)device_sms() * (uint64_t)std::max(1, per_sm));
+    FbgLaunch P{};
+    P.unit_begin = 0;
+    P.unit_end = ~0ull;
+    if (e == cudaSuccess)
+      e = launch_interp(0, d_progs, d_items, n, d_counts + slots, d_counts, nullptr, P, nslots, std::max(1, grid), stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_counts, d_counts, slots * 8, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    launches++;
+    std::unique_lock<std::mutex> lk(mu);
+    if (e != cudaSuccess) {
+      cuda_error(e, "server tick");
+      fatal = FBG_ECUDA;
+      for (Request* r : count_reqs) finish(r, FBG_ECUDA);
+    } else {
+      for (Request* r : count_reqs)
+        if (r->next_unit >= r->nunits) {
+          r->count = h_counts[r->slot];
+          finish(r, FBG_OK);
+        }
+    }
+    active.erase(std::remove_if(active.begin(), active.end(), [](Request* r) { return r->done; }), active.end());
+  }
+  // model lists: ordered two-pass evaluation, one request after another
+  for (Request* r : enum_reqs) {
+    size_t cap = (size_t)r->cap;
+    if (cap > models_cap) {
+      if (d_models) cudaFree(d_models);
+      d_models = nullptr;
+      models_cap = 0;
+      if (cudaMalloc(&d_models, std::max<size_t>(cap, 1) * 8) == cudaSuccess) models_cap = std::max<size_t>(cap, 1);
+    }
+    uint64_t total = 0, written = 0;
+    fbg_status s = models_cap >= cap ? fbg_enumerate_models(r->prog, stream, (uint64_t*)d_models, cap, &total, &written)
+                                     : FBG_ENOMEM;
+    if (s == FBG_OK) {
+      r->models.resize(written);
+      if (written && cudaMemcpy(r->models.data(), d_models, written * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+        s = FBG_ECUDA;
+      r->count = total;
+    }
+    launches += 3;
+    std::unique_lock<std::mutex> lk(mu);
+    finish(r, s);
+    active.erase(std::remove(active.begin(), active.end(), r), active.end());
+  }
+  ticks++;
+  busy_s += now_s() - t0;
+}
+
+void fbg_server::run() {
+  cudaSetDevice(device);
+  for (;;) {
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      cv.wait(lk, [&] { return stop || !pending.empty() || !active.empty(); });
+      if (stop) return;
+    }
+    tick();
+  }
+}
+
+extern "C" {
+
+fbg_status fbg_server_create(const fbg_server_options* opt, fbg_server** out) {
+  if (!out) return set_error(FBG_EINVAL, "null argument");
+  *out = nullptr;
+  auto* s = new fbg_server();
+  if (opt) s->opt = *opt;
+  if (!s->opt.mem_budget_bytes) s->opt.mem_budget_bytes = kDefaultBudget;
+  if (s->opt.max_inflight <= 0) s->opt.max_inflight = 4096;
+  if (!s->opt.tick_units) s->opt.tick_units = 65536;
+  s->item_cap = s->opt.tick_units / 8 + 2 * (uint64_t)s->opt.max_inflight + 16;
+  cudaGetDevice(&s->device);
+  const size_t slots = (size_t)s->opt.max_inflight;
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaMalloc(&s->d_progs, slots * sizeof(FbgInterpProg))) != cudaSuccess ||
+      (e = cudaMallocHost(&s->h_progs, slots * sizeof(FbgInterpProg))) != cudaSuccess ||
+      (e = cudaMalloc(&s->d_counts, (slots + 1) * 8)) != cudaSuccess ||
+      (e = cudaMallocHost(&s->h_counts, slots * 8)) != cudaSuccess ||
+      (e = cudaMalloc(&s->d_items, s->item_cap * sizeof(FbgWorkItem))) != cudaSuccess ||
+      (e = cudaMallocHost(&s->h_items, s->item_cap * sizeof(FbgWorkItem))) != cudaSuccess) {
+    fbg_server_free(s);
+    return cuda_error(e, "server setup");
+  }
+  for (int i = (int)slots - 1; i >= 0; i--) s->free_slots.push_back(i);
+  s->worker = std::thread([s] { s->run(); });
+  *out = s;
+  return FBG_OK;
+}
+
+fbg_status fbg_server_submit(fbg_server* s, const char* formula, int domain_k, int mode, uint64_t cap,
+                             uint64_t* request_id) {
+  if (!s || !formula || !request_id || (mode != FBG_MODE_COUNT && mode != FBG_MODE_ENUMERATE))
+    return set_error(FBG_EINVAL, "bad argument");
+  fbg_program* p = nullptr;
+  fbg_status st = fbg_compile(formula, domain_k, &p);
+  if (st != FBG_OK) return st;
+  if (p->n > (mode == FBG_MODE_COUNT ? 63 : 40)) {
+    fbg_program_free(p);
+    return set_error(FBG_ETOOBIG, "request too large");
+  }
+  auto r = std::make_unique<Request>();
+  r->prog = p;
+  r->mode = mode;
+  r->cap = cap;
+  r->submit_s = now_s();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    r->id = s->next_id++;
+    *request_id = r->id;
+    s->pending.push_back(r.get());
+    s->outstanding++;
+    s->all.emplace(r->id, std::move(r));
+  }
+  s->cv.notify_one();
+  return FBG_OK;
+}
+
+fbg_status fbg_server_poll(fbg_server* s, uint64_t id, fbg_result* out) {
+  if (!s || !out) return set_error(FBG_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->all.find(id);
+  if (it == s->all.end()) return set_error(FBG_EINVAL, "unknown request");
+  Request* r = it->second.get();
+  if (!r->done) return FBG_EBUSY;
+  out->status = r->status;
+  out->count = r->count;
+  out->written = r->models.size();
+  out->models = r->models.empty() ? nullptr : r->models.data();
+  out->submit_s = r->submit_s;
+  out->admit_s = r->admit_s;
+  out->done_s = r->done_s;
+  return FBG_OK;
+}
+
+fbg_status fbg_server_drain(fbg_server* s, double timeout_s) {
+  if (!s) return set_error(FBG_EINVAL, "null server");
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto ready = [&] { return s->outstanding == 0; };
+  if (timeout_s > 0) {
+    if (!s->done_cv.wait_for(lk, std::chrono::duration<double>(timeout_s), ready))
+      return set_error(FBG_ETIMEOUT, "requests still running");
+  } else {
+    s->done_cv.wait(lk, ready);
+  }
+  return s->fatal;
+}
+
+fbg_status fbg_server_release(fbg_server* s, uint64_t id) {
+  if (!s) return set_error(FBG_EINVAL, "null server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->all.find(id);
+  if (it == s->all.end() || !it->second->done) return set_error(FBG_EINVAL, "unknown or unfinished request");
+  s->all.erase(it);
+  return FBG_OK;
+}
+
+fbg_status fbg_server_stats(fbg_server* s, uint64_t* ticks, uint64_t* launches, double* busy_s) {
+  if (!s) return set_error(FBG_EINVAL, "null server");
+  if (ticks) *ticks = s->ticks.load();
+  if (launches) *launches = s->launches.load();
+  if (busy_s) *busy_s = s->busy_s;
+  return FBG_OK;
+}
+
+void fbg_server_free(fbg_server* s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+  }
+  s->cv.notify_all();
+  if (s->worker.joinable()) s->worker.join();
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  s->all.clear();
+  if (s->d_progs) cudaFree(s->d_progs);
+  if (s->h_progs) cudaFreeHost(s->h_progs);
+  if (s->d_counts) cudaFree(s->d_counts);
+  if (s->h_counts) cudaFreeHost(s->h_counts);
+  if (s->d_items) cudaFree(s->d_items);
+  if (s->h_items) cudaFreeHost(s->h_items);
+  if (s->d_models) cudaFree(s->d_models);
+  if (s->stream) cudaStreamDestroy(s->stream);
+  delete s;
+}
+
+}  // extern "C"
