@@ -22,8 +22,8 @@ std::string hex32(uint32_t v) {
   return b;
 }
 
-// One 32-bit register of a LUT value after per-register folding: a constant,
-// or a reference to an emitted register / generator word, possibly negated
+// One 32-bit register of a LUT value after folding: a constant, or a
+// reference to an emitted register / generator word, possibly negated
 // (negations are absorbed into the consumers' truth tables).
 struct Sym {
   bool is_const = true;
@@ -35,29 +35,61 @@ struct Sym {
   }
 };
 
-struct SrcGen {
+// Source generator.  Every LUT register is folded: all-zero/all-one inputs
+// fix their bit, negated inputs flip, repeated inputs merge; a function of at
+// most one input becomes a constant or an alias, identical operations inside
+// one scope share a register, and what remains is one lop3.b32.  The
+// innermost loop level is unrolled: in each of its 2^b copies the level's
+// generator words are constants, so the copy is folded further.
+class SrcGen {
+ public:
+  explicit SrcGen(const LutProgram& prog)
+      : p(prog), L(prog.layout), nreg(1 << prog.layout.r), nl(prog.layout.nlevels()) {
+    if (nl > 2 && L.loop_bits.back() <= 5) {
+      unroll_lv = nl - 1;
+      unroll_bits = L.loop_bits.back();
+      unroll_base = L.loop_pos(nl - 3);
+    }
+    ops.assign((size_t)nl, 0);
+    fold_base();
+    if (unroll_lv >= 0) fold_unrolled();
+  }
+
+  std::vector<long long> ops;   // lop3.b32 per thread per execution of each level
+  int unroll_lv = -1;
+
+  std::string generate(int mode, int block, int minb);
+
+ private:
   const LutProgram& p;
   const Layout& L;
-  int nreg;
+  int nreg, nl;
+  int unroll_bits = 0, unroll_base = 0;
+  std::vector<std::vector<Sym>> sym;                  // [lut][s], levels other than unroll_lv
+  std::vector<std::vector<std::string>> code;         // real lop3 calls of those
+  std::vector<std::vector<std::vector<Sym>>> usym;    // [copy][lut - first][s]
+  std::vector<std::vector<std::string>> ustmt;        // [copy] statements
   std::ostringstream o;
-  // per LUT and register index (s & rmask): folded value, emitted or not
-  std::vector<std::vector<Sym>> sym;
-  std::vector<std::vector<char>> real;
-  std::vector<std::vector<std::string>> code;   // the lop3 call of real registers
-  std::vector<long long> ops;                   // lop3.b32 per thread per level execution
 
-  explicit SrcGen(const LutProgram& prog) : p(prog), L(prog.layout), nreg(1 << prog.layout.r) { fold(); }
+  bool in_unrolled(int lut) const { return unroll_lv >= 0 && p.luts[(size_t)lut].level == unroll_lv; }
 
-  Sym operand_sym(const Val& v, int s) const {
+  Sym operand_sym(const Val& v, int s, int copy) const {
     Sym x;
     if (v.kind == V_CONST) {
-      x.is_const = true;
       x.c = p.consts[(size_t)v.id].w[(size_t)s];
     } else if (v.kind == V_VAR) {
-      x.is_const = false;
-      x.name = "V" + std::to_string(v.id);
+      if (copy >= 0 && L.level_of_pos(v.id) == unroll_lv) {
+        x.c = ((copy >> (v.id - unroll_base)) & 1) ? 0xFFFFFFFFu : 0u;
+      } else {
+        x.is_const = false;
+        x.name = "V" + std::to_string(v.id);
+      }
     } else {
-      x = sym[(size_t)v.id][(size_t)((uint32_t)s & p.luts[(size_t)v.id].rmask)];
+      size_t r = (size_t)((uint32_t)s & p.luts[(size_t)v.id].rmask);
+      if (copy >= 0 && in_unrolled(v.id))
+        x = usym[(size_t)copy][(size_t)(v.id - p.levels[(size_t)unroll_lv].lut_begin)][r];
+      else
+        x = sym[(size_t)v.id][r];
     }
     return x;
   }
@@ -67,134 +99,147 @@ struct SrcGen {
     return x.neg ? "(~" + x.name + ")" : x.name;
   }
 
-  // Fold every LUT register: constant all-zero/all-one inputs fix their bit,
-  // negated inputs flip, repeated inputs merge; a function of no or one input
-  // becomes a constant or an alias, identical operations inside one level
-  // share one register.  What remains is one lop3.b32.
-  void fold() {
-    const size_t nl = p.luts.size();
-    sym.assign(nl, {});
-    real.assign(nl, {});
-    code.assign(nl, {});
-    ops.assign((size_t)L.nlevels(), 0);
-    std::map<std::string, std::string> cse;
-    int cur_level = -100;
-    for (size_t i = 0; i < nl; i++) {
-      const Lut& lu = p.luts[i];
-      if (lu.level != cur_level) {
-        cse.clear();
-        cur_level = lu.level;
+  std::string operand(const Val& v, int s, int copy = -1) const { return expr(operand_sym(v, s, copy)); }
+
+  // fold one LUT register; *call receives the lop3 call when one is needed
+  Sym fold_one(const Lut& lu, int s, int copy, const std::string& name, std::map<std::string, std::string>& cse,
+               std::string* call) {
+    call->clear();
+    Sym in[3];
+    for (int k = 0; k < 3; k++) in[k] = operand_sym(lu.in[k], s, copy);
+    uint8_t f[8];
+    for (int m = 0; m < 8; m++) f[m] = (uint8_t)((lu.tt >> m) & 1);
+    int fixed[3] = {-1, -1, -1};
+    for (int k = 0; k < 3; k++) {
+      if (in[k].is_const && (in[k].c == 0u || in[k].c == 0xFFFFFFFFu)) fixed[k] = in[k].c ? 1 : 0;
+      if (!in[k].is_const && in[k].neg) {
+        uint8_t g[8];
+        for (int m = 0; m < 8; m++) g[m] = f[m ^ (4 >> k)];
+        std::memcpy(f, g, 8);
+        in[k].neg = false;
       }
+    }
+    std::vector<Sym> fs;
+    int map[3] = {-1, -1, -1};
+    for (int k = 0; k < 3; k++) {
+      if (fixed[k] >= 0) continue;
+      for (size_t t = 0; t < fs.size(); t++)
+        if (fs[t] == in[k]) map[k] = (int)t;
+      if (map[k] < 0) {
+        map[k] = (int)fs.size();
+        fs.push_back(in[k]);
+      }
+    }
+    unsigned kf = (unsigned)fs.size();
+    std::vector<uint8_t> g(1u << kf);
+    for (unsigned a = 0; a < (1u << kf); a++) {
+      int bit[3];
+      for (int k = 0; k < 3; k++) bit[k] = fixed[k] >= 0 ? fixed[k] : (int)((a >> map[k]) & 1u);
+      g[a] = f[(bit[0] << 2) | (bit[1] << 1) | bit[2]];
+    }
+    for (int t = (int)kf - 1; t >= 0; t--) {   // drop inputs the function ignores
+      bool dep = false;
+      for (unsigned a = 0; a < (1u << kf); a++)
+        if (g[a] != g[a ^ (1u << t)]) dep = true;
+      if (dep) continue;
+      std::vector<uint8_t> h(1u << (kf - 1));
+      for (unsigned a = 0; a < h.size(); a++) {
+        unsigned lo = a & ((1u << t) - 1u), hi = a >> t;
+        h[a] = g[lo | (hi << (t + 1))];
+      }
+      fs.erase(fs.begin() + t);
+      g.swap(h);
+      kf--;
+    }
+    Sym out;
+    bool all_imm = true;
+    for (auto& x : fs) all_imm &= x.is_const;
+    if (kf == 0) {
+      out.c = g[0] ? 0xFFFFFFFFu : 0u;
+    } else if (all_imm) {
+      uint32_t v = 0;
+      for (int b = 0; b < 32; b++) {
+        unsigned a = 0;
+        for (unsigned q = 0; q < kf; q++) a |= ((fs[q].c >> b) & 1u) << q;
+        v |= (uint32_t)g[a] << b;
+      }
+      out.c = v;
+    } else if (kf == 1 && !fs[0].is_const) {
+      out = fs[0];
+      out.neg = g[0] == 1;
+    } else {
+      int tt = 0;
+      for (int m = 0; m < 8; m++) {
+        unsigned ab[3] = {(unsigned)(m >> 2) & 1u, (unsigned)(m >> 1) & 1u, (unsigned)m & 1u};
+        unsigned a = 0;
+        for (unsigned q = 0; q < kf; q++) a |= ab[q] << q;
+        tt |= g[a] << m;
+      }
+      std::string c3 = "fbg_lop3<" + std::to_string(tt) + ">(" + expr(fs[0]) + ", " + expr(fs[kf > 1 ? 1 : 0]) + ", " +
+                       expr(fs[kf > 2 ? 2 : 0]) + ")";
+      out.is_const = false;
+      auto it = cse.find(c3);
+      if (it != cse.end()) {
+        out.name = it->second;
+      } else {
+        cse.emplace(c3, name);
+        out.name = name;
+        *call = c3;
+      }
+    }
+    return out;
+  }
+
+  void fold_base() {
+    const size_t n = p.luts.size();
+    sym.assign(n, {});
+    code.assign(n, {});
+    std::map<std::string, std::string> cse;
+    int cur = -100;
+    for (size_t i = 0; i < n; i++) {
+      const Lut& lu = p.luts[i];
       sym[i].assign((size_t)nreg, Sym{});
-      real[i].assign((size_t)nreg, 0);
       code[i].assign((size_t)nreg, "");
+      if (lu.level == unroll_lv) continue;
+      if (lu.level != cur) {
+        cse.clear();
+        cur = lu.level;
+      }
       for (int s = 0; s < nreg; s++) {
         if (((uint32_t)s & lu.rmask) != (uint32_t)s) continue;
-        Sym in[3];
-        for (int k = 0; k < 3; k++) in[k] = operand_sym(lu.in[k], s);
-        uint8_t f[8];
-        for (int m = 0; m < 8; m++) f[m] = (uint8_t)((lu.tt >> m) & 1);
-        int fixed[3] = {-1, -1, -1};
-        for (int k = 0; k < 3; k++) {
-          if (in[k].is_const && (in[k].c == 0u || in[k].c == 0xFFFFFFFFu)) fixed[k] = in[k].c ? 1 : 0;
-          if (!in[k].is_const && in[k].neg) {   // absorb the negation
-            uint8_t g[8];
-            for (int m = 0; m < 8; m++) g[m] = f[m ^ (4 >> k)];
-            std::memcpy(f, g, 8);
-            in[k].neg = false;
-          }
+        std::string call;
+        sym[i][(size_t)s] = fold_one(lu, s, -1, "L" + std::to_string(i) + "_" + std::to_string(s), cse, &call);
+        if (!call.empty()) {
+          code[i][(size_t)s] = call;
+          ops[(size_t)lu.level]++;
         }
-        // distinct free symbols
-        std::vector<Sym> fs;
-        int map[3] = {-1, -1, -1};
-        for (int k = 0; k < 3; k++) {
-          if (fixed[k] >= 0) continue;
-          for (size_t t = 0; t < fs.size(); t++)
-            if (fs[t] == in[k]) map[k] = (int)t;
-          if (map[k] < 0) {
-            map[k] = (int)fs.size();
-            fs.push_back(in[k]);
-          }
-        }
-        auto g_of = [&](unsigned alpha) {
-          int bit[3];
-          for (int k = 0; k < 3; k++) bit[k] = fixed[k] >= 0 ? fixed[k] : (int)((alpha >> map[k]) & 1u);
-          return f[(bit[0] << 2) | (bit[1] << 1) | bit[2]];
-        };
-        unsigned kf = (unsigned)fs.size();
-        std::vector<uint8_t> g(1u << kf);
-        for (unsigned a = 0; a < (1u << kf); a++) g[a] = g_of(a);
-        // drop symbols the function does not depend on
-        for (int t = (int)kf - 1; t >= 0; t--) {
-          bool dep = false;
-          for (unsigned a = 0; a < (1u << kf); a++)
-            if (g[a] != g[a ^ (1u << t)]) dep = true;
-          if (dep) continue;
-          std::vector<uint8_t> h;
-          std::vector<Sym> fs2;
-          // rebuild g over the remaining symbols
-          unsigned k2 = kf - 1;
-          h.assign(1u << k2, 0);
-          for (unsigned a = 0; a < (1u << k2); a++) {
-            unsigned lo = a & ((1u << t) - 1u), hi = a >> t;
-            h[a] = g[lo | (hi << (t + 1))];
-          }
-          for (unsigned q = 0; q < kf; q++)
-            if ((int)q != t) fs2.push_back(fs[q]);
-          g.swap(h);
-          fs.swap(fs2);
-          kf = k2;
-        }
-        Sym out;
-        bool all_imm = true;
-        for (auto& x : fs) all_imm &= x.is_const;
-        if (kf == 0) {
-          out.is_const = true;
-          out.c = g[0] ? 0xFFFFFFFFu : 0u;
-        } else if (all_imm) {
-          uint32_t v = 0;
-          for (int bitpos = 0; bitpos < 32; bitpos++) {
-            unsigned a = 0;
-            for (unsigned q = 0; q < kf; q++) a |= ((fs[q].c >> bitpos) & 1u) << q;
-            v |= (uint32_t)g[a] << bitpos;
-          }
-          out.is_const = true;
-          out.c = v;
-        } else if (kf == 1 && !fs[0].is_const) {
-          out = fs[0];
-          out.neg = g[0] == 1;   // g = (0,1): identity; (1,0): complement
-        } else {
-          // one lop3: free symbols become inputs 0..kf-1 (unused inputs repeat input 0)
-          int tt = 0;
-          for (int m = 0; m < 8; m++) {
-            unsigned ab[3] = {(unsigned)(m >> 2) & 1u, (unsigned)(m >> 1) & 1u, (unsigned)m & 1u};
-            unsigned a = 0;
-            for (unsigned q = 0; q < kf; q++) a |= ab[q] << q;
-            tt |= g[a] << m;
-          }
-          std::string ops3[3];
-          for (unsigned q = 0; q < 3; q++) ops3[q] = expr(fs[q < kf ? q : 0]);
-          std::string call = "fbg_lop3<" + std::to_string(tt) + ">(" + ops3[0] + ", " + ops3[1] + ", " + ops3[2] + ")";
-          auto it = cse.find(call);
-          if (it != cse.end()) {
-            out.is_const = false;
-            out.name = it->second;
-          } else {
-            std::string nm = "L" + std::to_string(i) + "_" + std::to_string(s);
-            cse.emplace(call, nm);
-            out.is_const = false;
-            out.name = nm;
-            real[i][(size_t)s] = 1;
-            code[i][(size_t)s] = call;
-            if (lu.level >= 0 && lu.level < (int)ops.size()) ops[(size_t)lu.level]++;
-          }
-        }
-        sym[i][(size_t)s] = out;
       }
     }
   }
 
-  std::string operand(const Val& v, int s) const { return expr(operand_sym(v, s)); }
+  void fold_unrolled() {
+    const LevelInfo& li = p.levels[(size_t)unroll_lv];
+    const int copies = 1 << unroll_bits;
+    usym.assign((size_t)copies, {});
+    ustmt.assign((size_t)copies, {});
+    std::map<std::string, std::string> cse;   // shared: the copies are one straight-line block
+    for (int c = 0; c < copies; c++) {
+      usym[(size_t)c].assign((size_t)(li.lut_end - li.lut_begin), std::vector<Sym>((size_t)nreg));
+      for (int i = li.lut_begin; i < li.lut_end; i++) {
+        const Lut& lu = p.luts[(size_t)i];
+        for (int s = 0; s < nreg; s++) {
+          if (((uint32_t)s & lu.rmask) != (uint32_t)s) continue;
+          std::string call, nm = "L" + std::to_string(i) + "_" + std::to_string(s) + "_u" + std::to_string(c);
+          Sym v = fold_one(lu, s, c, nm, cse, &call);
+          usym[(size_t)c][(size_t)(i - li.lut_begin)][(size_t)s] = v;
+          if (!call.empty()) {
+            ustmt[(size_t)c].push_back("const fbg_u32 " + nm + " = " + call + ";");
+            ops[(size_t)unroll_lv]++;
+          }
+        }
+      }
+    }
+  }
 
   // positions of non-constant variables used by the program, by level
   std::vector<std::vector<int>> used_vars() const {
@@ -205,11 +250,11 @@ struct SrcGen {
     if (p.out.kind == V_VAR) used[(size_t)p.out.id] = true;
     for (const auto& li : p.levels)
       if (li.has_acc && li.acc.kind == V_VAR) used[(size_t)li.acc.id] = true;
-    std::vector<std::vector<int>> byl((size_t)L.nlevels());
+    std::vector<std::vector<int>> byl((size_t)nl);
     for (int pos = 0; pos < L.n; pos++)
       if (used[(size_t)pos]) {
         int lv = L.level_of_pos(pos);
-        if (lv >= 0) byl[(size_t)lv].push_back(pos);
+        if (lv >= 0 && lv != unroll_lv) byl[(size_t)lv].push_back(pos);
       }
     return byl;
   }
@@ -218,14 +263,14 @@ struct SrcGen {
     const LevelInfo& li = p.levels[(size_t)lv];
     for (int i = li.lut_begin; i < li.lut_end; i++)
       for (int s = 0; s < nreg; s++)
-        if (real[(size_t)i][(size_t)s]) o << ind << "fbg_u32 L" << i << "_" << s << ";\n";
+        if (!code[(size_t)i][(size_t)s].empty()) o << ind << "fbg_u32 L" << i << "_" << s << ";\n";
   }
 
   void luts(int lv, const std::string& ind) {
     const LevelInfo& li = p.levels[(size_t)lv];
     for (int i = li.lut_begin; i < li.lut_end; i++)
       for (int s = 0; s < nreg; s++)
-        if (real[(size_t)i][(size_t)s]) o << ind << "L" << i << "_" << s << " = " << code[(size_t)i][(size_t)s] << ";\n";
+        if (!code[(size_t)i][(size_t)s].empty()) o << ind << "L" << i << "_" << s << " = " << code[(size_t)i][(size_t)s] << ";\n";
   }
 
   std::string any_nonzero(const Val& v) const {
@@ -237,9 +282,7 @@ struct SrcGen {
     return "((" + e + ") != 0u)";
   }
 
-  void var_words(int lv, const std::vector<int>& vars, const std::string& src, int base, const std::string& ind,
-                 bool wide) {
-    (void)lv;
+  void var_words(const std::vector<int>& vars, const std::string& src, int base, const std::string& ind, bool wide) {
     for (int pos : vars) {
       int b = pos - base;
       if (wide)
@@ -254,133 +297,168 @@ struct SrcGen {
     return (uint32_t)((1ull << (1u << L.n)) - 1ull);
   }
 
-  std::string generate(int mode, int block, int minb) {
-    auto vars = used_vars();
-    const int nl = L.nlevels();
-    const int tvalid = 1 << (L.lane_bits + L.warp_bits);
-    const char* kname = mode == 0 ? "fbg_jit_count" : "fbg_jit_table";
-    o << "extern \"C\" __global__ void __launch_bounds__(" << block << ", " << minb << ") " << kname
-      << "(FbgLaunch P) {\n";
-    o << "  const fbg_u32 tb = threadIdx.x;\n";
-    o << "  const fbg_u32 tm = (tb < " << tvalid << "u) ? " << hex32(valid_mask()) << " : 0u;\n";
-    o << "  fbg_u64 lvl_iters[" << nl << "] = {0};\n";
-    var_words(0, vars[0], "tb", L.first_lane_pos(), "  ", false);
-    declare_level(0, "  ");
-    luts(0, "  ");
-    o << "  bool alive0 = true;\n";
-    if (p.levels[0].has_acc) o << "  alive0 = __any_sync(FBG_FULL, " << any_nonzero(p.levels[0].acc) << ");\n";
-    o << "  fbg_u64 total = 0;\n";
-    o << "  __shared__ fbg_u64 s_unit;\n";
-    o << "  for (;;) {\n";
-    o << "    const fbg_u64 u = fbg_next_unit(P, &s_unit);\n";
-    o << "    if (u >= P.unit_end) break;\n";
-    if (mode == 0) {
-      o << "    if (!alive0) continue;\n";
-      o << "    lvl_iters[1]++;\n";
-      var_words(1, vars[1], "u", L.first_unit_pos(), "    ", true);
-      declare_level(1, "    ");
-      luts(1, "    ");
-      if (p.levels[1].has_acc) o << "    if (!__any_sync(FBG_FULL, " << any_nonzero(p.levels[1].acc) << ")) continue;\n";
-      o << "    fbg_u32 ucnt = 0;\n";
-      std::string ind = "    ";
-      for (int lv = 2; lv < nl; lv++) {
-        int li = lv - 2;
-        std::string iv = "i" + std::to_string(lv);
-        o << ind << "for (fbg_u32 " << iv << " = 0; " << iv << " < " << (1u << L.loop_bits[(size_t)li]) << "u; ++" << iv
-          << ") {\n";
-        ind += "  ";
-        o << ind << "lvl_iters[" << lv << "]++;\n";
-        var_words(lv, vars[(size_t)lv], iv, L.loop_pos(li), ind, false);
-        declare_level(lv, ind);
-        luts(lv, ind);
-        if (p.levels[(size_t)lv].has_acc)
-          o << ind << "if (!__any_sync(FBG_FULL, " << any_nonzero(p.levels[(size_t)lv].acc) << ")) continue;\n";
-      }
-      for (int s = 0; s < nreg; s++) o << ind << "ucnt += __popc(" << operand(p.out, s) << " & tm);\n";
-      for (int lv = nl - 1; lv >= 2; lv--) {
-        ind.resize(ind.size() - 2);
-        o << ind << "}\n";
-      }
-      o << "    total += ucnt;\n";
-      o << "    if (P.unit_counts) {\n";
-      o << "      fbg_u64 w = fbg_warp_sum((fbg_u64)ucnt);\n";
-      o << "      if ((tb & 31u) == 0u && w) atomicAdd(P.unit_counts + (u - P.unit_begin), w);\n";
-      o << "    }\n";
-      o << "  }\n";
-      o << "  total = fbg_warp_sum(total);\n";
-      o << "  if ((tb & 31u) == 0u && total) atomicAdd(P.count, total);\n";
+  void store(const std::string& ind, const std::string& T, const std::vector<std::string>& w) {
+    if (L.r == 0) {
+      o << ind << "reinterpret_cast<fbg_u64*>(P.table)[0] = (fbg_u64)" << w[0] << ";\n";
+    } else if (L.r == 1) {
+      o << ind << "reinterpret_cast<uint2*>(P.table)[" << T << "] = make_uint2(" << w[0] << ", " << w[1] << ");\n";
+    } else if (L.r == 2) {
+      o << ind << "reinterpret_cast<uint4*>(P.table)[" << T << "] = make_uint4(" << w[0] << ", " << w[1] << ", " << w[2]
+        << ", " << w[3] << ");\n";
     } else {
-      // truth table: every tile is stored; pruned levels store zeros
-      o << "    bool a1 = alive0;\n";
-      declare_level(1, "    ");
-      var_words(1, vars[1], "u", L.first_unit_pos(), "    ", true);
-      o << "    if (a1) {\n";
-      o << "      lvl_iters[1]++;\n";
-      luts(1, "      ");
-      if (p.levels[1].has_acc) o << "      a1 = __any_sync(FBG_FULL, " << any_nonzero(p.levels[1].acc) << ");\n";
-      o << "    }\n";
-      std::string ind = "    ";
-      for (int lv = 2; lv < nl; lv++) {
-        int li = lv - 2;
-        std::string iv = "i" + std::to_string(lv);
-        o << ind << "for (fbg_u32 " << iv << " = 0; " << iv << " < " << (1u << L.loop_bits[(size_t)li]) << "u; ++" << iv
-          << ") {\n";
-        ind += "  ";
-        o << ind << "bool a" << lv << " = a" << (lv - 1) << ";\n";
-        declare_level(lv, ind);
-        var_words(lv, vars[(size_t)lv], iv, L.loop_pos(li), ind, false);
-        o << ind << "if (a" << lv << ") {\n";
-        o << ind << "  lvl_iters[" << lv << "]++;\n";
-        luts(lv, ind + "  ");
-        if (p.levels[(size_t)lv].has_acc)
-          o << ind << "  a" << lv << " = __any_sync(FBG_FULL, " << any_nonzero(p.levels[(size_t)lv].acc) << ");\n";
-        o << ind << "}\n";
+      for (int q = 0; q < nreg / 4; q++)
+        o << ind << "reinterpret_cast<uint4*>(P.table)[(" << T << ") * " << nreg / 4 << " + " << q << "] = make_uint4("
+          << w[4 * q] << ", " << w[4 * q + 1] << ", " << w[4 * q + 2] << ", " << w[4 * q + 3] << ");\n";
+    }
+  }
+};
+
+std::string SrcGen::generate(int mode, int block, int minb) {
+  auto vars = used_vars();
+  const int tvalid = 1 << (L.lane_bits + L.warp_bits);
+  const int last = nl - 1;
+  const char* kname = mode == 0 ? "fbg_jit_count" : "fbg_jit_table";
+  o << "extern \"C\" __global__ void __launch_bounds__(" << block << ", " << minb << ") " << kname << "(FbgLaunch P) {\n";
+  o << "  const fbg_u32 tb = threadIdx.x;\n";
+  o << "  const fbg_u32 tm = (tb < " << tvalid << "u) ? " << hex32(valid_mask()) << " : 0u;\n";
+  o << "  fbg_u64 lvl_iters[" << nl << "] = {0};\n";
+  var_words(vars[0], "tb", L.first_lane_pos(), "  ", false);
+  declare_level(0, "  ");
+  luts(0, "  ");
+  o << "  bool alive0 = true;\n";
+  if (p.levels[0].has_acc) o << "  alive0 = __any_sync(FBG_FULL, " << any_nonzero(p.levels[0].acc) << ");\n";
+  o << "  fbg_u64 total = 0;\n";
+  o << "  __shared__ fbg_u64 s_unit;\n";
+  o << "  for (;;) {\n";
+  o << "    const fbg_u64 u = fbg_next_unit(P, &s_unit);\n";
+  o << "    if (u >= P.unit_end) break;\n";
+  // tile index of this thread with every loop counter at zero (table mode)
+  auto tile_base = [&](int upto) {
+    std::string t = "(fbg_u64)tb";
+    for (int lv = 2; lv < upto; lv++) t += " | ((fbg_u64)i" + std::to_string(lv) + " << " + std::to_string(L.loop_pos(lv - 2) - 5 - L.r) + ")";
+    if (L.unit_bits) t += " | (u << " + std::to_string(L.first_unit_pos() - 5 - L.r) + ")";
+    return t;
+  };
+  if (mode == 0) {
+    o << "    if (!alive0) continue;\n";
+    o << "    lvl_iters[1]++;\n";
+    var_words(vars[1], "u", L.first_unit_pos(), "    ", true);
+    declare_level(1, "    ");
+    luts(1, "    ");
+    if (p.levels[1].has_acc && last > 1)
+      o << "    if (!__any_sync(FBG_FULL, " << any_nonzero(p.levels[1].acc) << ")) continue;\n";
+    o << "    fbg_u32 ucnt = 0;\n";
+    std::string ind = "    ";
+    for (int lv = 2; lv < nl; lv++) {
+      if (lv == unroll_lv) break;
+      std::string iv = "i" + std::to_string(lv);
+      o << ind << "for (fbg_u32 " << iv << " = 0; " << iv << " < " << (1u << L.loop_bits[(size_t)(lv - 2)]) << "u; ++" << iv << ") {\n";
+      ind += "  ";
+      o << ind << "lvl_iters[" << lv << "]++;\n";
+      var_words(vars[(size_t)lv], iv, L.loop_pos(lv - 2), ind, false);
+      declare_level(lv, ind);
+      luts(lv, ind);
+      if (p.levels[(size_t)lv].has_acc && lv < last)
+        o << ind << "if (!__any_sync(FBG_FULL, " << any_nonzero(p.levels[(size_t)lv].acc) << ")) continue;\n";
+    }
+    if (unroll_lv >= 0) {
+      o << ind << "lvl_iters[" << unroll_lv << "]++;\n";
+      for (int c = 0; c < (1 << unroll_bits); c++) {
+        for (auto& st : ustmt[(size_t)c]) o << ind << st << "\n";
+        for (int s = 0; s < nreg; s++) o << ind << "ucnt += __popc(" << operand(p.out, s, c) << " & tm);\n";
       }
-      int last = nl - 1;
-      o << ind << "const fbg_u32 keep = a" << last << " ? tm : 0u;\n";
-      // tile index: thread bits, loop levels, unit bits
-      o << ind << "fbg_u64 T = (fbg_u64)tb";
-      for (int lv = 2; lv < nl; lv++)
-        o << " | ((fbg_u64)i" << lv << " << " << (L.loop_pos(lv - 2) - 5 - L.r) << ")";
-      if (L.unit_bits) o << " | (u << " << (L.first_unit_pos() - 5 - L.r) << ")";
-      o << ";\n";
+    } else {
+      for (int s = 0; s < nreg; s++) o << ind << "ucnt += __popc(" << operand(p.out, s) << " & tm);\n";
+    }
+    for (int lv = (unroll_lv >= 0 ? unroll_lv - 1 : last); lv >= 2; lv--) {
+      ind.resize(ind.size() - 2);
+      o << ind << "}\n";
+    }
+    o << "    total += ucnt;\n";
+    o << "    if (P.unit_counts) {\n";
+    o << "      fbg_u64 w = fbg_warp_sum((fbg_u64)ucnt);\n";
+    o << "      if ((tb & 31u) == 0u && w) atomicAdd(P.unit_counts + (u - P.unit_begin), w);\n";
+    o << "    }\n";
+    o << "  }\n";
+    o << "  total = fbg_warp_sum(total);\n";
+    o << "  if ((tb & 31u) == 0u && total) atomicAdd(P.count, total);\n";
+  } else {
+    // truth table: every tile is stored; pruned levels store zeros
+    o << "    bool a1 = alive0;\n";
+    declare_level(1, "    ");
+    var_words(vars[1], "u", L.first_unit_pos(), "    ", true);
+    o << "    if (a1) {\n";
+    o << "      lvl_iters[1]++;\n";
+    luts(1, "      ");
+    if (p.levels[1].has_acc && last > 1) o << "      a1 = __any_sync(FBG_FULL, " << any_nonzero(p.levels[1].acc) << ");\n";
+    o << "    }\n";
+    std::string ind = "    ";
+    int prev = 1;
+    for (int lv = 2; lv < nl; lv++) {
+      if (lv == unroll_lv) break;
+      std::string iv = "i" + std::to_string(lv);
+      o << ind << "for (fbg_u32 " << iv << " = 0; " << iv << " < " << (1u << L.loop_bits[(size_t)(lv - 2)]) << "u; ++" << iv << ") {\n";
+      ind += "  ";
+      o << ind << "bool a" << lv << " = a" << (lv - 1) << ";\n";
+      declare_level(lv, ind);
+      var_words(vars[(size_t)lv], iv, L.loop_pos(lv - 2), ind, false);
+      o << ind << "if (a" << lv << ") {\n";
+      o << ind << "  lvl_iters[" << lv << "]++;\n";
+      luts(lv, ind + "  ");
+      if (p.levels[(size_t)lv].has_acc && lv < last)
+        o << ind << "  a" << lv << " = __any_sync(FBG_FULL, " << any_nonzero(p.levels[(size_t)lv].acc) << ");\n";
+      o << ind << "}\n";
+      prev = lv;
+    }
+    if (unroll_lv >= 0) {
+      const int sh = L.loop_pos(unroll_lv - 2) - 5 - L.r;
+      o << ind << "{\n";
+      o << ind << "  const fbg_u64 T = " << tile_base(unroll_lv) << ";\n";
+      o << ind << "  if (a" << prev << " && tm) {\n";
+      o << ind << "    lvl_iters[" << unroll_lv << "]++;\n";
+      for (int c = 0; c < (1 << unroll_bits); c++) {
+        for (auto& st : ustmt[(size_t)c]) o << ind << "    " << st << "\n";
+        std::vector<std::string> w;
+        for (int s = 0; s < nreg; s++) w.push_back("(" + operand(p.out, s, c) + " & tm)");
+        store(ind + "    ", "T | ((fbg_u64)" + std::to_string(c) + "u << " + std::to_string(sh) + ")", w);
+      }
+      o << ind << "  } else if (tm) {\n";
+      o << ind << "    for (fbg_u32 z = 0; z < " << (1u << unroll_bits) << "u; ++z) {\n";
+      std::vector<std::string> zw((size_t)nreg, "0u");
+      store(ind + "      ", "T | ((fbg_u64)z << " + std::to_string(sh) + ")", zw);
+      o << ind << "    }\n";
+      o << ind << "  }\n";
+      o << ind << "}\n";
+    } else {
+      o << ind << "const fbg_u32 keep = a" << prev << " ? tm : 0u;\n";
+      o << ind << "const fbg_u64 T = " << tile_base(nl) << ";\n";
       std::vector<std::string> w;
       for (int s = 0; s < nreg; s++) w.push_back("(" + operand(p.out, s) + " & keep)");
       o << ind << "if (tm) {\n";
-      if (L.r == 0) {
-        o << ind << "  reinterpret_cast<fbg_u64*>(P.table)[0] = (fbg_u64)" << w[0] << ";\n";
-      } else if (L.r == 1) {
-        o << ind << "  reinterpret_cast<uint2*>(P.table)[T] = make_uint2(" << w[0] << ", " << w[1] << ");\n";
-      } else if (L.r == 2) {
-        o << ind << "  reinterpret_cast<uint4*>(P.table)[T] = make_uint4(" << w[0] << ", " << w[1] << ", " << w[2]
-          << ", " << w[3] << ");\n";
-      } else {
-        for (int q = 0; q < nreg / 4; q++)
-          o << ind << "  reinterpret_cast<uint4*>(P.table)[T * " << nreg / 4 << " + " << q << "] = make_uint4(" << w[4 * q]
-            << ", " << w[4 * q + 1] << ", " << w[4 * q + 2] << ", " << w[4 * q + 3] << ");\n";
-      }
+      store(ind + "  ", "T", w);
       o << ind << "}\n";
-      for (int lv = nl - 1; lv >= 2; lv--) {
-        ind.resize(ind.size() - 2);
-        o << ind << "}\n";
-      }
-      o << "  }\n";
     }
-    o << "  if (P.iters && (tb & 31u) == 0u) {\n";
-    o << "    for (int l = 0; l < " << nl << "; l++) if (lvl_iters[l]) atomicAdd(P.iters + l, lvl_iters[l]);\n";
+    for (int lv = (unroll_lv >= 0 ? unroll_lv - 1 : last); lv >= 2; lv--) {
+      ind.resize(ind.size() - 2);
+      o << ind << "}\n";
+    }
     o << "  }\n";
-    o << "}\n";
-    return o.str();
   }
-};
+  o << "  if (P.iters && (tb & 31u) == 0u) {\n";
+  o << "    for (int l = 0; l < " << nl << "; l++) if (lvl_iters[l]) atomicAdd(P.iters + l, lvl_iters[l]);\n";
+  o << "  }\n";
+  o << "}\n";
+  return o.str();
+}
 
 }  // namespace
 
 std::string emit_cuda_source(const LutProgram& p, int mode, int block, int minblocks,
-                             std::vector<long long>* ops_per_level) {
+                             std::vector<long long>* ops_per_level, int* unrolled_level) {
   SrcGen g(p);
   std::string src = g.generate(mode, block, minblocks);
   if (ops_per_level) *ops_per_level = g.ops;
+  if (unrolled_level) *unrolled_level = g.unroll_lv;
   return src;
 }
 

@@ -12,9 +12,11 @@ namespace fbg {
 // CUDA source of the specialised kernel (mode 0: count, 1: truth table);
 // the caller prepends fbg_device.cuh.
 // ops_per_level (optional) receives the lop3.b32 each thread issues per
-// execution of each level after per-register folding.
+// execution of each level after folding; unrolled_level (optional) the loop
+// level whose 2^b iterations are emitted as one folded straight-line block
+// (one "execution" of that level covers all its iterations), or -1.
 std::string emit_cuda_source(const LutProgram& p, int mode, int block, int minblocks,
-                             std::vector<long long>* ops_per_level = nullptr);
+                             std::vector<long long>* ops_per_level = nullptr, int* unrolled_level = nullptr);
 
 struct InterpCode {
   FbgInterpProg prog;                 // device pointers left null

@@ -38,6 +38,7 @@ struct JitBuild {
   LutProgram lp;
   std::string src, log;
   std::vector<long long> ops;    // lop3.b32 per thread per level execution (after folding)
+  int unrolled_level = -1;       // loop level emitted unrolled (one execution = all iterations)
   cudaKernel_t kern = nullptr;   // owned by the process-wide JIT cache
   int block = 256, grid = 1;
   uint64_t nunits = 1;
