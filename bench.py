@@ -169,9 +169,16 @@ def run_table(args, torch, F, L, peaks):
     64-bit words = 512 MiB written per launch into a caller-owned tensor
     (larger than L2, so no flush is needed between launches)."""
     from paper_1310_6978_b300 import workloads as W
+    from paper_1310_6978_b300 import tuning
     wl = W.CNF32
     p = F.compile(wl.text, wl.k)
     stream = torch.cuda.Stream()
+    cache = tuning.load()
+    shape = tuning.ensure(p, 1, cache, tune=args.autotune, stream=stream)
+    if args.autotune and args.tune_out:
+        merged = tuning.load(args.tune_out)
+        merged.update(cache)
+        tuning.save(merged, args.tune_out)
     table = torch.empty(p.table_words(), dtype=torch.int64, device="cuda")
     for _ in range(3):
         p.truth_table(table, stream)
@@ -192,7 +199,7 @@ def run_table(args, torch, F, L, peaks):
     assert pop == cnt
     nbytes = table.numel() * 8
     peak = peaks.get("hbm_gbs")
-    return {"workload": "3-CNF n=32 m=136 seed 1, full truth table", "value": (1 << 32) / t / 1e9, "unit": "Gassign/s",
+    return {"workload": "3-CNF n=32 m=136 seed 1, full truth table", "shape": shape, "value": (1 << 32) / t / 1e9, "unit": "Gassign/s",
             "ms": t * 1e3, "bytes_written": nbytes, "count": cnt, "popcount_equals_count": True,
             "roofline": {"bound": "hbm", "achieved": nbytes / t / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": (nbytes / t / 1e9) / peak if peak else None, "traffic": None,
@@ -323,9 +330,14 @@ def run_ours(args, rank, world):
 
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
+    from paper_1310_6978_b300 import tuning
     wls = workloads()
     progs = [F.compile(w.text, w.k) for w in wls]
     stream = torch.cuda.Stream()
+    cache = tuning.load()
+    shapes = [tuning.ensure(p, 0, cache, tune=args.autotune, stream=stream) for p in progs]
+    if args.autotune and args.tune_out:
+        tuning.save(cache, args.tune_out)
     out = torch.zeros(len(progs), dtype=torch.int64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > L2 (126 MB)
 
@@ -435,7 +447,8 @@ def run_ours(args, rank, world):
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": {"workload": "count n=36: transitive k=6, triangle-free k=9, Aut(G(6,1/2)) seed 3",
                    "formulas": 3, "assignments_per_step": assign_per_step, "engine": "nvrtc straight-line, pruned",
-                   "flush_l2": True, "parallelism": f"replicas x{world}", "counts": expected},
+                   "flush_l2": True, "parallelism": f"replicas x{world}", "counts": expected,
+                   "shapes": shapes},
         "roofline": {"bound": "alu", "achieved": executed / kern_s / 1e12, "peak": peak_lop3 / 1e12,
                      "unit": "Tlop3/s", "frac": executed / kern_s / peak_lop3, "traffic": None,
                      "basis": "executed lop3.b32 lane-ops (in-kernel level counters) / CUDA-event kernel time; "
@@ -464,6 +477,9 @@ def main():
     ap.add_argument("--quick", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--only", default="", choices=["", "table"], help="run one leg alone (profiling)")
+    ap.add_argument("--autotune", action="store_true", help="tune kernel shapes missing from the cache")
+    ap.add_argument("--tune-out", default="", help="write the updated shape cache here")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=3000)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -474,6 +490,12 @@ def main():
     if world > 1 and args.impl == "ours":
         import torch
         torch.distributed.init_process_group("nccl")
+    if args.only == "table":
+        import torch
+        import paper_1310_6978_b300 as F
+        from paper_1310_6978_b300 import _lib as L
+        print(json.dumps(run_table(args, torch, F, L, load_peaks())), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:

@@ -189,6 +189,22 @@ fbg_status fbg_enumerate_models(fbg_program *prog, void *stream, uint64_t *dev_m
 #define FBG_NOALLOC_SCRATCH_BYTES (128u * 1024u)
 fbg_status fbg_count_noalloc(fbg_program *prog, void *stream, uint64_t *dev_out);
 
+/*
+ * Autotuner of the specialised kernel (mode 0 count, 1 truth table, n <= 34):
+ * searches the layout knobs -- FBG_OPT_LOOP_LEVEL_BITS (also the depth of
+ * the unrolled innermost level), FBG_OPT_REGS_LOG2 (words per thread),
+ * FBG_OPT_MIN_BLOCKS, FBG_OPT_WARPS_LOG2 (block shape), FBG_OPT_UNIT_BITS --
+ * one at a time from the current setting, compiling each candidate with
+ * NVRTC and timing `reps` launches with CUDA events on `stream`; the program
+ * keeps the fastest shape.  Table tuning allocates one table temporarily.
+ */
+typedef struct {
+  double best_ms;
+  int trials;
+  int regs_log2, warps_log2, min_blocks, loop_level_bits, unit_bits;
+} fbg_tune_result;
+fbg_status fbg_autotune(fbg_program *prog, void *stream, int mode, int reps, fbg_tune_result *out);
+
 /* executed work of the last fbg_count with FBG_OPT_STATS = 1 */
 fbg_status fbg_last_exec_stats(fbg_program *prog, fbg_exec_stats *out);
 

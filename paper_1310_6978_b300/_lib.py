@@ -44,6 +44,11 @@ class FbgExecStats(ctypes.Structure):
                 ("lop3_nominal", ctypes.c_double), ("engine", c_int)]
 
 
+class FbgTuneResult(ctypes.Structure):
+    _fields_ = [("best_ms", ctypes.c_double), ("trials", c_int), ("regs_log2", c_int), ("warps_log2", c_int),
+                ("min_blocks", c_int), ("loop_level_bits", c_int), ("unit_bits", c_int)]
+
+
 class FbgServerOptions(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", c_u64), ("tick_units", c_u64), ("max_inflight", c_int)]
 
@@ -74,6 +79,7 @@ _sig("fbg_count_units", c_int, c_vp, c_vp, c_vp, c_u64)
 _sig("fbg_unit_vars", c_int, c_vp, ctypes.POINTER(c_int), c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_u64))
 _sig("fbg_truth_table", c_int, c_vp, c_vp, c_vp, c_sz)
 _sig("fbg_enumerate_models", c_int, c_vp, c_vp, c_vp, c_sz, ctypes.POINTER(c_u64), ctypes.POINTER(c_u64))
+_sig("fbg_autotune", c_int, c_vp, c_vp, c_int, c_int, ctypes.POINTER(FbgTuneResult))
 _sig("fbg_last_exec_stats", c_int, c_vp, ctypes.POINTER(FbgExecStats))
 _sig("fbg_program_source", c_int, c_vp, c_int, c_char_p, ctypes.POINTER(c_sz))
 _sig("fbg_debug_dump", c_int, c_vp, c_int, c_char_p, ctypes.POINTER(c_sz))

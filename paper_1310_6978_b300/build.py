@@ -19,7 +19,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-Wall", f"-I{os.path.join(ROOT, 'include')}", f"-I{CSRC}"]
 
-SOURCES = ["parse.cpp", "ground.cpp", "lower.cpp", "emit.cpp", "jit.cpp", "api.cpp", "batch.cpp", "serve.cpp",
+SOURCES = ["parse.cpp", "ground.cpp", "lower.cpp", "emit.cpp", "jit.cpp", "api.cpp", "batch.cpp", "serve.cpp", "autotune.cpp",
            "interp.cu", "noalloc.cu"]
 
 
