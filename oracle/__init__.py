@@ -30,10 +30,11 @@ _lib = None
 def build(force: bool = False) -> str:
     """Compile oracle.c into liboracle.so (plain gcc, OpenMP for the timed
     multi-core count only)."""
-    src = os.path.join(_HERE, "oracle.c")
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+    srcs = [os.path.join(_HERE, "oracle.c"), os.path.join(_HERE, "counters.c")]
+    newest = max(os.path.getmtime(s) for s in srcs)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < newest:
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, src])
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, *srcs])
         os.replace(tmp, _SO)
     return _SO
 
@@ -58,6 +59,10 @@ def _load():
             lib.oracle_count_par.argtypes = [vp, u64, u64, ctypes.c_int]
             lib.oracle_count_par.restype = u64
             lib.oracle_max_threads.restype = ctypes.c_int
+            lib.counter_transitive.argtypes = [ctypes.c_int]
+            lib.counter_transitive.restype = u64
+            lib.counter_triangle_free.argtypes = [ctypes.c_int]
+            lib.counter_triangle_free.restype = u64
             _lib = lib
     return _lib
 

@@ -1,0 +1,82 @@
+/*
+ * counters.c -- TEST INFRASTRUCTURE ONLY.  Independent backtracking counters
+ * of labelled structures, written without any formula: they pin the oracle
+ * and give exact values at sizes the oracle cannot finish (n = 36).
+ */
+#include <stdint.h>
+#include <string.h>
+
+/* transitive relations on k points: decide the pairs (i,j) in row-major order;
+   after each decision check every transitivity instance a->b, b->c => a->c
+   whose three pairs are decided and that involves the new pair */
+static int TK;
+static unsigned char R[8][8], D[8][8];
+
+static int trans_ok(int i, int j) {
+  for (int x = 0; x < TK; x++) {
+    /* (i,j) as the first pair: i->j, j->x => i->x */
+    if (D[j][x] && D[i][x] && R[i][j] && R[j][x] && !R[i][x]) return 0;
+    /* (i,j) as the second pair: x->i, i->j => x->j */
+    if (D[x][i] && D[x][j] && R[x][i] && R[i][j] && !R[x][j]) return 0;
+    /* (i,j) as the implied pair: i->x, x->j => i->j */
+    if (D[i][x] && D[x][j] && R[i][x] && R[x][j] && !R[i][j]) return 0;
+  }
+  return 1;
+}
+
+static uint64_t trans_rec(int p) {
+  if (p == TK * TK) return 1;
+  int i = p / TK, j = p % TK;
+  uint64_t total = 0;
+  D[i][j] = 1;
+  for (int v = 0; v < 2; v++) {
+    R[i][j] = (unsigned char)v;
+    if (trans_ok(i, j)) total += trans_rec(p + 1);
+  }
+  D[i][j] = 0;
+  R[i][j] = 0;
+  return total;
+}
+
+uint64_t counter_transitive(int k) {
+  if (k < 0 || k > 8) return 0;
+  TK = k;
+  memset(R, 0, sizeof R);
+  memset(D, 0, sizeof D);
+  return trans_rec(0);
+}
+
+/* triangle-free graphs on k vertices: decide the edges (a,b), a<b, in
+   lexicographic order; an edge may be present only if no decided vertex c
+   is adjacent to both ends */
+static int GK, NE, EA[64], EB[64];
+static unsigned char ADJ[16][16];
+
+static uint64_t tri_rec(int e) {
+  if (e == NE) return 1;
+  int a = EA[e], b = EB[e];
+  uint64_t total = tri_rec(e + 1);   /* edge absent */
+  int ok = 1;
+  for (int c = 0; c < GK && ok; c++)
+    if (ADJ[a][c] && ADJ[b][c]) ok = 0;
+  if (ok) {
+    ADJ[a][b] = ADJ[b][a] = 1;
+    total += tri_rec(e + 1);
+    ADJ[a][b] = ADJ[b][a] = 0;
+  }
+  return total;
+}
+
+uint64_t counter_triangle_free(int k) {
+  if (k < 0 || k > 11) return 0;
+  GK = k;
+  NE = 0;
+  memset(ADJ, 0, sizeof ADJ);
+  for (int a = 0; a < k; a++)
+    for (int b = a + 1; b < k; b++) {
+      EA[NE] = a;
+      EB[NE] = b;
+      NE++;
+    }
+  return tri_rec(0);
+}

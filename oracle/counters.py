@@ -136,3 +136,16 @@ def count_automorphisms(adj_bits: str, k: int) -> int:
         if all(adj[i][j] == adj[perm[i]][perm[j]] for i in range(k) for j in range(k)):
             total += 1
     return total
+
+
+def count_transitive_backtrack(k: int) -> int:
+    """Transitive relations on k labelled points (k <= 8), backtracking in C
+    (oracle/counters.c) -- independent of the oracle's evaluator."""
+    from . import _load
+    return int(_load().counter_transitive(k))
+
+
+def count_triangle_free_backtrack(k: int) -> int:
+    """Triangle-free labelled graphs on k vertices (k <= 11), backtracking in C."""
+    from . import _load
+    return int(_load().counter_triangle_free(k))

@@ -204,8 +204,14 @@ def test_n36_counts(name):
     th = oracle.Theory(wl.text, wl.k)
     p = F.compile(wl.text, wl.k)
     cnt = p.count()
+    # independent full-size pins: brute force over the 720 permutations, and
+    # backtracking counters over relations / graphs (no formula involved)
     if name == "aut6":
         assert cnt == C.count_automorphisms(W.random_graph_bits(6, 3), 6)
+    elif name == "transitive6":
+        assert cnt == C.count_transitive_backtrack(6)
+    else:
+        assert cnt == C.count_triangle_free_backtrack(9)
     # the interpreter and the unpruned JIT kernel agree with it
     q = F.compile(wl.text, wl.k).set_option(L.OPT_ENGINE, L.ENGINE_INTERP)
     assert q.count() == cnt

@@ -209,3 +209,14 @@ def test_known_small_counts():
     # 3..5 vertices (both also fixed by the brute-force tests above)
     assert [oracle.Theory(W.transitive(k).text, k).count() for k in (2, 3, 4)] == [13, 171, 3994]
     assert [oracle.Theory(W.triangle_free(k).text, k).count() for k in (3, 4, 5)] == [7, 41, 388]
+
+
+def test_backtracking_counters_match_brute_force_and_oracle():
+    # the C backtracking counters used as full-size pins (n = 36) agree with
+    # brute force and with the oracle wherever those finish
+    for k in range(1, 5):
+        assert C.count_transitive_backtrack(k) == C.count_relations(k, "transitive")
+    for k in range(3, 8):
+        assert C.count_triangle_free_backtrack(k) == C.count_triangle_free(k)
+    assert C.count_transitive_backtrack(5) == oracle.Theory(W.transitive(5).text, 5).count_par(0, 1 << 25)
+    assert C.count_triangle_free_backtrack(7) == oracle.Theory(W.triangle_free(7).text, 7).count()
