@@ -221,6 +221,15 @@ fbg_status fbg_program_source(fbg_program *prog, int mode, char *buf, size_t *le
  */
 fbg_status fbg_debug_dump(fbg_program *prog, int which, char *buf, size_t *len);
 
+/*
+ * Diagnostics without a device: the NVRTC source of the hybrid batch kernel
+ * for these programs ("" when none would be specialised), and an NVRTC
+ * compile of a kernel body (the library's device headers are available to it)
+ * with the library's options; log receives the NVRTC/ptxas messages.
+ */
+fbg_status fbg_debug_batch_source(fbg_program *const *progs, int nprogs, char *buf, size_t *len);
+fbg_status fbg_debug_nvrtc_compile(const char *body, char *log, size_t loglen);
+
 /* NVRTC/ptxas log of the last specialised-kernel build (registers, spills) */
 const char *fbg_program_jit_log(fbg_program *prog);
 
@@ -231,21 +240,26 @@ const char *fbg_last_error(void);
 
 /*
  * Batch (the inner loop of the counting procedure of Sec. 3.4 runs over many
- * reduced formulas): count many programs in one persistent interpreter launch
- * fed by a device work queue of (program, unit range) items, largest first.
- * fbg_batch_create compiles nothing new; programs must outlive the batch.
- * max_item_units bounds the units per queue item (0 = automatic).
- * use_graph = 1 captures memset + launch + result copy in a CUDA graph on the
- * first run and replays it afterwards.
+ * reduced formulas): count many programs in one persistent launch fed by a
+ * device work queue of (program, unit range) items, largest first.  Programs
+ * must outlive the batch.  max_item_units bounds the units per queue item
+ * (0 = automatic).  flags: FBG_BATCH_GRAPH captures memset + launch + result
+ * copy in a CUDA graph on the first run and replays it afterwards;
+ * FBG_BATCH_SPECIALIZE compiles the distinct programs that carry most of the
+ * work (each >= 1% of the nominal work, at most 16) into straight-line device
+ * functions of the one batch kernel, which interprets every other program.
  */
-fbg_status fbg_batch_create(fbg_program *const *progs, int nprogs, uint64_t max_item_units, int use_graph,
+enum { FBG_BATCH_GRAPH = 1, FBG_BATCH_SPECIALIZE = 2 };
+fbg_status fbg_batch_create(fbg_program *const *progs, int nprogs, uint64_t max_item_units, int flags,
                             fbg_batch **out);
 /* enqueue one evaluation of every program on `stream` (asynchronous) */
 fbg_status fbg_batch_run(fbg_batch *batch, void *stream);
 /* wait for the last run and copy the exact counts into host memory (nprogs u64) */
 fbg_status fbg_batch_results(fbg_batch *batch, void *stream, uint64_t *host_counts);
-/* queue geometry: items, total units, blocks launched */
-fbg_status fbg_batch_info(fbg_batch *batch, uint64_t *items, uint64_t *units, int *grid);
+/* queue geometry: items, total units, blocks launched, specialised programs */
+fbg_status fbg_batch_info(fbg_batch *batch, uint64_t *items, uint64_t *units, int *grid, int *specialized);
+/* per program (nprogs ints): 1 if the batch kernel runs it specialised, 0 if interpreted */
+fbg_status fbg_batch_program_kinds(fbg_batch *batch, int *specialized);
 void fbg_batch_free(fbg_batch *batch);
 
 /*

@@ -159,13 +159,14 @@ def compile(text: str, domain_k: int = 1) -> Program:   # noqa: A001 - mirrors f
 class Batch:
     """Many programs counted in one persistent launch (fbg_batch_*)."""
 
-    def __init__(self, programs, max_item_units: int = 0, use_graph: bool = True):
+    def __init__(self, programs, max_item_units: int = 0, use_graph: bool = True, specialize: bool = True):
         L = _L()
         self._L = L
         self.programs = list(programs)
         arr = (ctypes.c_void_p * len(self.programs))(*[p.handle.value for p in self.programs])
         h = ctypes.c_void_p()
-        L.check(L.lib.fbg_batch_create(arr, len(self.programs), max_item_units, 1 if use_graph else 0, ctypes.byref(h)))
+        flags = (L.BATCH_GRAPH if use_graph else 0) | (L.BATCH_SPECIALIZE if specialize else 0)
+        L.check(L.lib.fbg_batch_create(arr, len(self.programs), max_item_units, flags, ctypes.byref(h)))
         self._h = h
 
     def __del__(self):
@@ -183,10 +184,36 @@ class Batch:
         self._L.check(self._L.lib.fbg_batch_results(self._h, _stream_ptr(stream), out.ctypes.data_as(ctypes.c_void_p)))
         return out
 
+    def program_kinds(self):
+        out = (ctypes.c_int * len(self.programs))()
+        self._L.check(self._L.lib.fbg_batch_program_kinds(self._h, out))
+        return [out[i] for i in range(len(self.programs))]
+
     def info(self):
-        items, units, grid = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int()
-        self._L.check(self._L.lib.fbg_batch_info(self._h, ctypes.byref(items), ctypes.byref(units), ctypes.byref(grid)))
-        return items.value, units.value, grid.value
+        items, units, grid, spec = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int(), ctypes.c_int()
+        self._L.check(self._L.lib.fbg_batch_info(self._h, ctypes.byref(items), ctypes.byref(units), ctypes.byref(grid),
+                                                 ctypes.byref(spec)))
+        return {"items": items.value, "units": units.value, "grid": grid.value, "specialized": spec.value}
+
+
+def batch_source(programs) -> str:
+    """fbg_debug_batch_source: NVRTC source of the hybrid batch kernel."""
+    L = _L()
+    arr = (ctypes.c_void_p * len(programs))(*[p.handle.value for p in programs])
+    n = ctypes.c_size_t()
+    L.check(L.lib.fbg_debug_batch_source(arr, len(programs), None, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    L.check(L.lib.fbg_debug_batch_source(arr, len(programs), buf, ctypes.byref(n)))
+    return buf.value.decode()
+
+
+def nvrtc_check(body: str):
+    """fbg_debug_nvrtc_compile: compile a kernel body with NVRTC (no device);
+    returns (ok, log)."""
+    L = _L()
+    log = ctypes.create_string_buffer(1 << 16)
+    st = L.lib.fbg_debug_nvrtc_compile(body.encode(), log, 1 << 16)
+    return st == L.FBG_OK, log.value.decode(errors="replace")
 
 
 class Server:

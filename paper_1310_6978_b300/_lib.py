@@ -31,6 +31,7 @@ ENGINE_AUTO, ENGINE_JIT, ENGINE_INTERP = 0, 1, 2
 OPT_ENGINE, OPT_PRUNE, OPT_REGS_LOG2, OPT_WARPS_LOG2, OPT_UNIT_BITS, OPT_LOOP_LEVEL_BITS, OPT_SEARCH_ORDER, \
     OPT_MIN_BLOCKS, OPT_STATS = range(1, 10)
 MODE_COUNT, MODE_ENUMERATE = 0, 1
+BATCH_GRAPH, BATCH_SPECIALIZE = 1, 2
 
 
 class FbgStats(ctypes.Structure):
@@ -89,7 +90,11 @@ _sig("fbg_last_error", c_char_p)
 _sig("fbg_batch_create", c_int, ctypes.POINTER(c_vp), c_int, c_u64, c_int, ctypes.POINTER(c_vp))
 _sig("fbg_batch_run", c_int, c_vp, c_vp)
 _sig("fbg_batch_results", c_int, c_vp, c_vp, c_vp)
-_sig("fbg_batch_info", c_int, c_vp, ctypes.POINTER(c_u64), ctypes.POINTER(c_u64), ctypes.POINTER(c_int))
+_sig("fbg_batch_info", c_int, c_vp, ctypes.POINTER(c_u64), ctypes.POINTER(c_u64), ctypes.POINTER(c_int),
+     ctypes.POINTER(c_int))
+_sig("fbg_batch_program_kinds", c_int, c_vp, ctypes.POINTER(c_int))
+_sig("fbg_debug_batch_source", c_int, ctypes.POINTER(c_vp), c_int, c_char_p, ctypes.POINTER(c_sz))
+_sig("fbg_debug_nvrtc_compile", c_int, c_char_p, c_char_p, c_sz)
 _sig("fbg_batch_free", None, c_vp)
 _sig("fbg_server_create", c_int, ctypes.POINTER(FbgServerOptions), ctypes.POINTER(c_vp))
 _sig("fbg_server_submit", c_int, c_vp, c_char_p, c_int, c_int, c_u64, ctypes.POINTER(c_u64))

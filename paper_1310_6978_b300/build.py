@@ -24,10 +24,17 @@ SOURCES = ["parse.cpp", "ground.cpp", "lower.cpp", "emit.cpp", "jit.cpp", "api.c
 
 
 def _embed_header() -> str:
-    src = open(os.path.join(CSRC, "fbg_device.cuh")).read()
+    """Device headers as text, for NVRTC: fbg_device_header (fbg_device.cuh),
+    fbg_interp_format_header (interp_format.h), fbg_interp_device_header
+    (interp_device.cuh)."""
+    parts = [("fbg_device_header", "fbg_device.cuh"), ("fbg_interp_format_header", "interp_format.h"),
+             ("fbg_interp_device_header", "interp_device.cuh")]
+    body = "// generated by build.py from the device headers\nnamespace fbg {\n"
+    for sym, fn in parts:
+        src = open(os.path.join(CSRC, fn)).read()
+        body += f'extern const char {sym}[] = R"FBGSRC({src})FBGSRC";\n'
+    body += "}\n"
     path = os.path.join(OUT, "fbg_device_header.cpp")
-    body = ('// generated by build.py from fbg_device.cuh\n'
-            'namespace fbg {\nextern const char fbg_device_header[] = R"FBGSRC(' + src + ')FBGSRC";\n}\n')
     if not os.path.exists(path) or open(path).read() != body:
         with open(path, "w") as f:
             f.write(body)

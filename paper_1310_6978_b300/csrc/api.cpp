@@ -568,6 +568,18 @@ fbg_status fbg_debug_dump(fbg_program* p, int which, char* buf, size_t* len) {
   return FBG_OK;
 }
 
+fbg_status fbg_debug_nvrtc_compile(const char* body, char* log, size_t loglen) {
+  if (!body) return set_error(FBG_EINVAL, "null argument");
+  std::string lg;
+  bool ok = jit_check(body, &lg);
+  if (log && loglen) {
+    size_t n = std::min(loglen - 1, lg.size());
+    std::memcpy(log, lg.data(), n);
+    log[n] = 0;
+  }
+  return ok ? FBG_OK : set_error(FBG_EJIT, lg);
+}
+
 const char* fbg_program_jit_log(fbg_program* p) { return p ? p->jit_log.c_str() : ""; }
 
 void fbg_program_free(fbg_program* p) { delete p; }

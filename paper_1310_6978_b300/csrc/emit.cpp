@@ -59,6 +59,7 @@ class SrcGen {
   int unroll_lv = -1;
 
   std::string generate(int mode, int block, int minb);
+  std::string generate_batch_fn(const std::string& fname);
 
  private:
   const LutProgram& p;
@@ -451,7 +452,66 @@ std::string SrcGen::generate(int mode, int block, int minb) {
   return o.str();
 }
 
+// Count over the units [u0, u1) for the calling block, returning this
+// thread's number of models: the body of fbg_jit_count as a device function,
+// called by the batch kernel for the work items of one program.
+std::string SrcGen::generate_batch_fn(const std::string& fname) {
+  auto vars = used_vars();
+  const int tvalid = 1 << (L.lane_bits + L.warp_bits);
+  const int last = nl - 1;
+  o << "__device__ __noinline__ fbg_u64 " << fname << "(fbg_u64 u0, fbg_u64 u1) {\n";
+  o << "  const fbg_u32 tb = threadIdx.x;\n";
+  o << "  const fbg_u32 tm = (tb < " << tvalid << "u) ? " << hex32(valid_mask()) << " : 0u;\n";
+  var_words(vars[0], "tb", L.first_lane_pos(), "  ", false);
+  declare_level(0, "  ");
+  luts(0, "  ");
+  if (p.levels[0].has_acc)
+    o << "  if (!__any_sync(FBG_FULL, " << any_nonzero(p.levels[0].acc) << ")) return 0;\n";
+  o << "  fbg_u64 total = 0;\n";
+  o << "  for (fbg_u64 u = u0; u < u1; ++u) {\n";
+  var_words(vars[1], "u", L.first_unit_pos(), "    ", true);
+  declare_level(1, "    ");
+  luts(1, "    ");
+  if (p.levels[1].has_acc && last > 1)
+    o << "    if (!__any_sync(FBG_FULL, " << any_nonzero(p.levels[1].acc) << ")) continue;\n";
+  o << "    fbg_u32 ucnt = 0;\n";
+  std::string ind = "    ";
+  for (int lv = 2; lv < nl; lv++) {
+    if (lv == unroll_lv) break;
+    std::string iv = "i" + std::to_string(lv);
+    o << ind << "for (fbg_u32 " << iv << " = 0; " << iv << " < " << (1u << L.loop_bits[(size_t)(lv - 2)]) << "u; ++" << iv << ") {\n";
+    ind += "  ";
+    var_words(vars[(size_t)lv], iv, L.loop_pos(lv - 2), ind, false);
+    declare_level(lv, ind);
+    luts(lv, ind);
+    if (p.levels[(size_t)lv].has_acc && lv < last)
+      o << ind << "if (!__any_sync(FBG_FULL, " << any_nonzero(p.levels[(size_t)lv].acc) << ")) continue;\n";
+  }
+  if (unroll_lv >= 0) {
+    for (int c = 0; c < (1 << unroll_bits); c++) {
+      for (auto& st : ustmt[(size_t)c]) o << ind << st << "\n";
+      for (int s = 0; s < nreg; s++) o << ind << "ucnt += __popc(" << operand(p.out, s, c) << " & tm);\n";
+    }
+  } else {
+    for (int s = 0; s < nreg; s++) o << ind << "ucnt += __popc(" << operand(p.out, s) << " & tm);\n";
+  }
+  for (int lv = (unroll_lv >= 0 ? unroll_lv - 1 : last); lv >= 2; lv--) {
+    ind.resize(ind.size() - 2);
+    o << ind << "}\n";
+  }
+  o << "    total += ucnt;\n";
+  o << "  }\n";
+  o << "  return total;\n";
+  o << "}\n";
+  return o.str();
+}
+
 }  // namespace
+
+std::string emit_batch_function(const LutProgram& p, const std::string& fname) {
+  SrcGen g(p);
+  return g.generate_batch_fn(fname);
+}
 
 std::string emit_cuda_source(const LutProgram& p, int mode, int block, int minblocks,
                              std::vector<long long>* ops_per_level, int* unrolled_level) {

@@ -18,6 +18,10 @@ namespace fbg {
 std::string emit_cuda_source(const LutProgram& p, int mode, int block, int minblocks,
                              std::vector<long long>* ops_per_level = nullptr, int* unrolled_level = nullptr);
 
+// device function `fname(u0, u1)`: this thread's model count over the units
+// [u0, u1) of p's layout (the count body, for the batch kernel)
+std::string emit_batch_function(const LutProgram& p, const std::string& fname);
+
 struct InterpCode {
   FbgInterpProg prog;                 // device pointers left null
   std::vector<unsigned long long> ins;

@@ -11,7 +11,10 @@
 
 namespace fbg {
 
-extern const char fbg_device_header[];   // fbg_device.cuh as text (generated)
+// device headers as text (generated by the build from the .cuh / .h files)
+extern const char fbg_device_header[];
+extern const char fbg_interp_format_header[];
+extern const char fbg_interp_device_header[];
 
 namespace {
 
@@ -27,7 +30,7 @@ std::unordered_map<std::string, Entry> g_cache;   // key: device + source
 
 JitResult jit_compile(const std::string& body, const char* kernel_name, int device) {
   JitResult r;
-  std::string src = std::string(fbg_device_header) + "\n" + body;
+  std::string src = "#include \"fbg_device.cuh\"\n" + body;
   std::string key = std::to_string(device) + ":" + kernel_name + ":" + src;
   {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -40,7 +43,9 @@ JitResult jit_compile(const std::string& body, const char* kernel_name, int devi
     }
   }
   nvrtcProgram prog;
-  nvrtcResult e = nvrtcCreateProgram(&prog, src.c_str(), "fbg_jit.cu", 0, nullptr, nullptr);
+  const char* hdrs[3] = {fbg_device_header, fbg_interp_format_header, fbg_interp_device_header};
+  const char* names[3] = {"fbg_device.cuh", "interp_format.h", "interp_device.cuh"};
+  nvrtcResult e = nvrtcCreateProgram(&prog, src.c_str(), "fbg_jit.cu", 3, hdrs, names);
   if (e != NVRTC_SUCCESS) {
     r.log = std::string("nvrtcCreateProgram: ") + nvrtcGetErrorString(e);
     return r;
@@ -87,6 +92,24 @@ JitResult jit_compile(const std::string& body, const char* kernel_name, int devi
   r.ok = true;
   r.kernel = ent.kern;
   return r;
+}
+
+bool jit_check(const std::string& body, std::string* log) {
+  std::string src = "#include \"fbg_device.cuh\"\n" + body;
+  const char* hdrs[3] = {fbg_device_header, fbg_interp_format_header, fbg_interp_device_header};
+  const char* names[3] = {"fbg_device.cuh", "interp_format.h", "interp_device.cuh"};
+  nvrtcProgram prog;
+  if (nvrtcCreateProgram(&prog, src.c_str(), "fbg_jit.cu", 3, hdrs, names) != NVRTC_SUCCESS) return false;
+  const char* opts[] = {"-arch=sm_103a", "-std=c++17", "-lineinfo", "--ptxas-options=-v"};
+  nvrtcResult e = nvrtcCompileProgram(prog, 4, opts);
+  size_t logn = 0;
+  nvrtcGetProgramLogSize(prog, &logn);
+  if (log && logn > 1) {
+    log->resize(logn);
+    nvrtcGetProgramLog(prog, &(*log)[0]);
+  }
+  nvrtcDestroyProgram(&prog);
+  return e == NVRTC_SUCCESS;
 }
 
 size_t jit_cache_size() {

@@ -17,5 +17,7 @@ struct JitResult {
 // Compile fbg_device.cuh + body for sm_103a and load it on the current device.
 JitResult jit_compile(const std::string& body, const char* kernel_name, int device);
 size_t jit_cache_size();
+// Compile only (no device needed); *log receives the NVRTC/ptxas messages.
+bool jit_check(const std::string& body, std::string* log);
 
 }  // namespace fbg

@@ -38,12 +38,13 @@ def small_mix(count, seed):
 
 
 @pytest.mark.parametrize("use_graph", [False, True])
+@pytest.mark.parametrize("specialize", [False, True])
 @pytest.mark.parametrize("max_item_units", [0, 1, 3])
-def test_batch_equals_oracle(use_graph, max_item_units):
+def test_batch_equals_oracle(use_graph, specialize, max_item_units):
     mix = small_mix(300, 17)
     want = [oracle.Theory(w.text, w.k).count() for w in mix]
     progs = [F.compile(w.text, w.k) for w in mix]
-    b = F.Batch(progs, max_item_units=max_item_units, use_graph=use_graph)
+    b = F.Batch(progs, max_item_units=max_item_units, use_graph=use_graph, specialize=specialize)
     for _ in range(3):                      # graph replays give the same counts
         b.run()
         got = b.results()
@@ -60,8 +61,28 @@ def test_batch_mix_matches_single_counts():
     b = F.Batch(progs)
     b.run()
     assert [int(x) for x in b.results()] == single
-    items, units, grid = b.info()
-    assert items >= len(sel) and units >= len(sel) and grid > 0
+    info = b.info()
+    assert info["items"] >= len(sel) and info["units"] >= len(sel) and info["grid"] > 0
+    # the n = 36 equivalence formulas carry the work: specialised
+    assert info["specialized"] >= 1
+    kinds = b.program_kinds()
+    assert all(kinds[i] == 1 for i, w in enumerate(sel) if w.n == 36)
+
+
+def test_hybrid_batch_mixes_specialised_and_interpreted():
+    """Two heavy programs specialised, many light ones interpreted, in one kernel."""
+    heavy = [W.transitive(5), W.equivalences(5)] * 3
+    light = small_mix(80, 9)
+    mix = heavy + light
+    progs = [F.compile(w.text, w.k) for w in mix]
+    b = F.Batch(progs, specialize=True)
+    for _ in range(2):
+        b.run()
+        got = [int(x) for x in b.results()]
+        assert got[:6] == [oracle.Theory(w.text, w.k).count_par(0, 1 << 25) for w in heavy]
+        assert got[6:] == [oracle.Theory(w.text, w.k).count() for w in light]
+    assert b.info()["specialized"] == 2
+    assert b.program_kinds()[:6] == [1] * 6
 
 
 def test_batch_single_program_and_errors():
