@@ -155,6 +155,7 @@ std::string batch_kernel_source(fbg_program* const* progs, int nprogs, std::vect
           "  bool alive0 = true;\n"
           "  fbg_u64 iters = 0;\n"
           "  FbgLaunch P = {};\n"
+          "  fbg_u64 lvl[16] = {0};\n"
           "  for (;;) {\n"
           "    if (threadIdx.x == 0) S.item = atomicAdd(item_ctr, 1ull);\n"
           "    __syncthreads();\n"
@@ -165,7 +166,7 @@ std::string batch_kernel_source(fbg_program* const* progs, int nprogs, std::vect
           "    fbg_u64 cnt = 0;\n"
           "    switch (fid[W.prog]) {\n";
   for (size_t gi = 0; gi < spec_lp.size(); gi++)
-    body += "      case " + std::to_string(gi) + ": cnt = fbg_bp" + std::to_string(gi) + "(W.unit_begin, W.unit_end); break;\n";
+    body += "      case " + std::to_string(gi) + ": cnt = fbg_bp" + std::to_string(gi) + "(W.unit_begin, W.unit_end, lvl); break;\n";
   body += "      default: process_item<0>(S, T, progs, W, cur, alive0, P, cnt, iters); break;\n"
           "    }\n"
           "    cnt = fbg_warp_sum(cnt);\n"

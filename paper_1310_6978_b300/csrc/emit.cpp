@@ -60,6 +60,8 @@ class SrcGen {
 
   std::string generate(int mode, int block, int minb);
   std::string generate_batch_fn(const std::string& fname);
+  std::string unit_fn_count(const std::string& fname);
+  std::string unit_fn_table(const std::string& fname);
 
  private:
   const LutProgram& p;
@@ -314,154 +316,18 @@ class SrcGen {
   }
 };
 
-std::string SrcGen::generate(int mode, int block, int minb) {
+// Per-unit device function of count mode: this thread's number of models over
+// the units [u0, u1); lvl[l] counts the executions of level l.  The kernels
+// and the batch kernel call it; keeping the unit fetch (with its barriers)
+// outside this function keeps the control flow the compiler sees simple.
+std::string SrcGen::unit_fn_count(const std::string& fname) {
   auto vars = used_vars();
   const int tvalid = 1 << (L.lane_bits + L.warp_bits);
   const int last = nl - 1;
-  const char* kname = mode == 0 ? "fbg_jit_count" : "fbg_jit_table";
-  o << "extern \"C\" __global__ void __launch_bounds__(" << block << ", " << minb << ") " << kname << "(FbgLaunch P) {\n";
+  o << "__device__ __noinline__ fbg_u64 " << fname << "(fbg_u64 u0, fbg_u64 u1, fbg_u64* lvl) {\n";
   o << "  const fbg_u32 tb = threadIdx.x;\n";
   o << "  const fbg_u32 tm = (tb < " << tvalid << "u) ? " << hex32(valid_mask()) << " : 0u;\n";
-  o << "  fbg_u64 lvl_iters[" << nl << "] = {0};\n";
-  var_words(vars[0], "tb", L.first_lane_pos(), "  ", false);
-  declare_level(0, "  ");
-  luts(0, "  ");
-  o << "  bool alive0 = true;\n";
-  if (p.levels[0].has_acc) o << "  alive0 = __any_sync(FBG_FULL, " << any_nonzero(p.levels[0].acc) << ");\n";
-  o << "  fbg_u64 total = 0;\n";
-  o << "  __shared__ fbg_u64 s_unit;\n";
-  o << "  for (;;) {\n";
-  o << "    const fbg_u64 u = fbg_next_unit(P, &s_unit);\n";
-  o << "    if (u >= P.unit_end) break;\n";
-  // tile index of this thread with every loop counter at zero (table mode)
-  auto tile_base = [&](int upto) {
-    std::string t = "(fbg_u64)tb";
-    for (int lv = 2; lv < upto; lv++) t += " | ((fbg_u64)i" + std::to_string(lv) + " << " + std::to_string(L.loop_pos(lv - 2) - 5 - L.r) + ")";
-    if (L.unit_bits) t += " | (u << " + std::to_string(L.first_unit_pos() - 5 - L.r) + ")";
-    return t;
-  };
-  if (mode == 0) {
-    o << "    if (!alive0) continue;\n";
-    o << "    lvl_iters[1]++;\n";
-    var_words(vars[1], "u", L.first_unit_pos(), "    ", true);
-    declare_level(1, "    ");
-    luts(1, "    ");
-    if (p.levels[1].has_acc && last > 1)
-      o << "    if (!__any_sync(FBG_FULL, " << any_nonzero(p.levels[1].acc) << ")) continue;\n";
-    o << "    fbg_u32 ucnt = 0;\n";
-    std::string ind = "    ";
-    for (int lv = 2; lv < nl; lv++) {
-      if (lv == unroll_lv) break;
-      std::string iv = "i" + std::to_string(lv);
-      o << ind << "for (fbg_u32 " << iv << " = 0; " << iv << " < " << (1u << L.loop_bits[(size_t)(lv - 2)]) << "u; ++" << iv << ") {\n";
-      ind += "  ";
-      o << ind << "lvl_iters[" << lv << "]++;\n";
-      var_words(vars[(size_t)lv], iv, L.loop_pos(lv - 2), ind, false);
-      declare_level(lv, ind);
-      luts(lv, ind);
-      if (p.levels[(size_t)lv].has_acc && lv < last)
-        o << ind << "if (!__any_sync(FBG_FULL, " << any_nonzero(p.levels[(size_t)lv].acc) << ")) continue;\n";
-    }
-    if (unroll_lv >= 0) {
-      o << ind << "lvl_iters[" << unroll_lv << "]++;\n";
-      for (int c = 0; c < (1 << unroll_bits); c++) {
-        for (auto& st : ustmt[(size_t)c]) o << ind << st << "\n";
-        for (int s = 0; s < nreg; s++) o << ind << "ucnt += __popc(" << operand(p.out, s, c) << " & tm);\n";
-      }
-    } else {
-      for (int s = 0; s < nreg; s++) o << ind << "ucnt += __popc(" << operand(p.out, s) << " & tm);\n";
-    }
-    for (int lv = (unroll_lv >= 0 ? unroll_lv - 1 : last); lv >= 2; lv--) {
-      ind.resize(ind.size() - 2);
-      o << ind << "}\n";
-    }
-    o << "    total += ucnt;\n";
-    o << "    if (P.unit_counts) {\n";
-    o << "      fbg_u64 w = fbg_warp_sum((fbg_u64)ucnt);\n";
-    o << "      if ((tb & 31u) == 0u && w) atomicAdd(P.unit_counts + (u - P.unit_begin), w);\n";
-    o << "    }\n";
-    o << "  }\n";
-    o << "  total = fbg_warp_sum(total);\n";
-    o << "  if ((tb & 31u) == 0u && total) atomicAdd(P.count, total);\n";
-  } else {
-    // truth table: every tile is stored; pruned levels store zeros
-    o << "    bool a1 = alive0;\n";
-    declare_level(1, "    ");
-    var_words(vars[1], "u", L.first_unit_pos(), "    ", true);
-    o << "    if (a1) {\n";
-    o << "      lvl_iters[1]++;\n";
-    luts(1, "      ");
-    if (p.levels[1].has_acc && last > 1) o << "      a1 = __any_sync(FBG_FULL, " << any_nonzero(p.levels[1].acc) << ");\n";
-    o << "    }\n";
-    std::string ind = "    ";
-    int prev = 1;
-    for (int lv = 2; lv < nl; lv++) {
-      if (lv == unroll_lv) break;
-      std::string iv = "i" + std::to_string(lv);
-      o << ind << "for (fbg_u32 " << iv << " = 0; " << iv << " < " << (1u << L.loop_bits[(size_t)(lv - 2)]) << "u; ++" << iv << ") {\n";
-      ind += "  ";
-      o << ind << "bool a" << lv << " = a" << (lv - 1) << ";\n";
-      declare_level(lv, ind);
-      var_words(vars[(size_t)lv], iv, L.loop_pos(lv - 2), ind, false);
-      o << ind << "if (a" << lv << ") {\n";
-      o << ind << "  lvl_iters[" << lv << "]++;\n";
-      luts(lv, ind + "  ");
-      if (p.levels[(size_t)lv].has_acc && lv < last)
-        o << ind << "  a" << lv << " = __any_sync(FBG_FULL, " << any_nonzero(p.levels[(size_t)lv].acc) << ");\n";
-      o << ind << "}\n";
-      prev = lv;
-    }
-    if (unroll_lv >= 0) {
-      const int sh = L.loop_pos(unroll_lv - 2) - 5 - L.r;
-      o << ind << "{\n";
-      o << ind << "  const fbg_u64 T = " << tile_base(unroll_lv) << ";\n";
-      o << ind << "  if (a" << prev << " && tm) {\n";
-      o << ind << "    lvl_iters[" << unroll_lv << "]++;\n";
-      for (int c = 0; c < (1 << unroll_bits); c++) {
-        for (auto& st : ustmt[(size_t)c]) o << ind << "    " << st << "\n";
-        std::vector<std::string> w;
-        for (int s = 0; s < nreg; s++) w.push_back("(" + operand(p.out, s, c) + " & tm)");
-        store(ind + "    ", "T | ((fbg_u64)" + std::to_string(c) + "u << " + std::to_string(sh) + ")", w);
-      }
-      o << ind << "  } else if (tm) {\n";
-      o << ind << "    for (fbg_u32 z = 0; z < " << (1u << unroll_bits) << "u; ++z) {\n";
-      std::vector<std::string> zw((size_t)nreg, "0u");
-      store(ind + "      ", "T | ((fbg_u64)z << " + std::to_string(sh) + ")", zw);
-      o << ind << "    }\n";
-      o << ind << "  }\n";
-      o << ind << "}\n";
-    } else {
-      o << ind << "const fbg_u32 keep = a" << prev << " ? tm : 0u;\n";
-      o << ind << "const fbg_u64 T = " << tile_base(nl) << ";\n";
-      std::vector<std::string> w;
-      for (int s = 0; s < nreg; s++) w.push_back("(" + operand(p.out, s) + " & keep)");
-      o << ind << "if (tm) {\n";
-      store(ind + "  ", "T", w);
-      o << ind << "}\n";
-    }
-    for (int lv = (unroll_lv >= 0 ? unroll_lv - 1 : last); lv >= 2; lv--) {
-      ind.resize(ind.size() - 2);
-      o << ind << "}\n";
-    }
-    o << "  }\n";
-  }
-  o << "  if (P.iters && (tb & 31u) == 0u) {\n";
-  o << "    for (int l = 0; l < " << nl << "; l++) if (lvl_iters[l]) atomicAdd(P.iters + l, lvl_iters[l]);\n";
-  o << "  }\n";
-  o << "}\n";
-  return o.str();
-}
-
-// Count over the units [u0, u1) for the calling block, returning this
-// thread's number of models: the body of fbg_jit_count as a device function,
-// called by the batch kernel for the work items of one program.
-std::string SrcGen::generate_batch_fn(const std::string& fname) {
-  auto vars = used_vars();
-  const int tvalid = 1 << (L.lane_bits + L.warp_bits);
-  const int last = nl - 1;
-  o << "__device__ __noinline__ fbg_u64 " << fname << "(fbg_u64 u0, fbg_u64 u1) {\n";
-  o << "  const fbg_u32 tb = threadIdx.x;\n";
-  o << "  const fbg_u32 tm = (tb < " << tvalid << "u) ? " << hex32(valid_mask()) << " : 0u;\n";
+  o << "  lvl[0]++;\n";
   var_words(vars[0], "tb", L.first_lane_pos(), "  ", false);
   declare_level(0, "  ");
   luts(0, "  ");
@@ -469,6 +335,7 @@ std::string SrcGen::generate_batch_fn(const std::string& fname) {
     o << "  if (!__any_sync(FBG_FULL, " << any_nonzero(p.levels[0].acc) << ")) return 0;\n";
   o << "  fbg_u64 total = 0;\n";
   o << "  for (fbg_u64 u = u0; u < u1; ++u) {\n";
+  o << "    lvl[1]++;\n";
   var_words(vars[1], "u", L.first_unit_pos(), "    ", true);
   declare_level(1, "    ");
   luts(1, "    ");
@@ -481,6 +348,7 @@ std::string SrcGen::generate_batch_fn(const std::string& fname) {
     std::string iv = "i" + std::to_string(lv);
     o << ind << "for (fbg_u32 " << iv << " = 0; " << iv << " < " << (1u << L.loop_bits[(size_t)(lv - 2)]) << "u; ++" << iv << ") {\n";
     ind += "  ";
+    o << ind << "lvl[" << lv << "]++;\n";
     var_words(vars[(size_t)lv], iv, L.loop_pos(lv - 2), ind, false);
     declare_level(lv, ind);
     luts(lv, ind);
@@ -488,6 +356,7 @@ std::string SrcGen::generate_batch_fn(const std::string& fname) {
       o << ind << "if (!__any_sync(FBG_FULL, " << any_nonzero(p.levels[(size_t)lv].acc) << ")) continue;\n";
   }
   if (unroll_lv >= 0) {
+    o << ind << "lvl[" << unroll_lv << "]++;\n";
     for (int c = 0; c < (1 << unroll_bits); c++) {
       for (auto& st : ustmt[(size_t)c]) o << ind << st << "\n";
       for (int s = 0; s < nreg; s++) o << ind << "ucnt += __popc(" << operand(p.out, s, c) << " & tm);\n";
@@ -505,6 +374,123 @@ std::string SrcGen::generate_batch_fn(const std::string& fname) {
   o << "}\n";
   return o.str();
 }
+
+// Per-unit device function of truth-table mode: stores every tile of unit u;
+// tiles under a level whose partial conjunction is zero store zeros.
+std::string SrcGen::unit_fn_table(const std::string& fname) {
+  auto vars = used_vars();
+  const int tvalid = 1 << (L.lane_bits + L.warp_bits);
+  const int last = nl - 1;
+  o << "__device__ __noinline__ void " << fname << "(fbg_u64 u, fbg_u32* table, fbg_u64* lvl) {\n";
+  o << "  const fbg_u32 tb = threadIdx.x;\n";
+  o << "  const fbg_u32 tm = (tb < " << tvalid << "u) ? " << hex32(valid_mask()) << " : 0u;\n";
+  var_words(vars[0], "tb", L.first_lane_pos(), "  ", false);
+  declare_level(0, "  ");
+  luts(0, "  ");
+  o << "  bool a1 = true;\n";
+  if (p.levels[0].has_acc && last > 0) o << "  a1 = __any_sync(FBG_FULL, " << any_nonzero(p.levels[0].acc) << ");\n";
+  declare_level(1, "  ");
+  var_words(vars[1], "u", L.first_unit_pos(), "  ", true);
+  o << "  if (a1) {\n";
+  o << "    lvl[1]++;\n";
+  luts(1, "    ");
+  if (p.levels[1].has_acc && last > 1) o << "    a1 = __any_sync(FBG_FULL, " << any_nonzero(p.levels[1].acc) << ");\n";
+  o << "  }\n";
+  auto tile_base = [&](int upto) {
+    std::string t = "(fbg_u64)tb";
+    for (int lv = 2; lv < upto; lv++) t += " | ((fbg_u64)i" + std::to_string(lv) + " << " + std::to_string(L.loop_pos(lv - 2) - 5 - L.r) + ")";
+    if (L.unit_bits) t += " | (u << " + std::to_string(L.first_unit_pos() - 5 - L.r) + ")";
+    return t;
+  };
+  std::string ind = "  ";
+  int prev = 1;
+  for (int lv = 2; lv < nl; lv++) {
+    if (lv == unroll_lv) break;
+    std::string iv = "i" + std::to_string(lv);
+    o << ind << "for (fbg_u32 " << iv << " = 0; " << iv << " < " << (1u << L.loop_bits[(size_t)(lv - 2)]) << "u; ++" << iv << ") {\n";
+    ind += "  ";
+    o << ind << "bool a" << lv << " = a" << (lv - 1) << ";\n";
+    declare_level(lv, ind);
+    var_words(vars[(size_t)lv], iv, L.loop_pos(lv - 2), ind, false);
+    o << ind << "if (a" << lv << ") {\n";
+    o << ind << "  lvl[" << lv << "]++;\n";
+    luts(lv, ind + "  ");
+    if (p.levels[(size_t)lv].has_acc && lv < last)
+      o << ind << "  a" << lv << " = __any_sync(FBG_FULL, " << any_nonzero(p.levels[(size_t)lv].acc) << ");\n";
+    o << ind << "}\n";
+    prev = lv;
+  }
+  if (unroll_lv >= 0) {
+    const int sh = L.loop_pos(unroll_lv - 2) - 5 - L.r;
+    o << ind << "{\n";
+    o << ind << "  const fbg_u64 T = " << tile_base(unroll_lv) << ";\n";
+    o << ind << "  if (a" << prev << " && tm) {\n";
+    o << ind << "    lvl[" << unroll_lv << "]++;\n";
+    for (int c = 0; c < (1 << unroll_bits); c++) {
+      for (auto& st : ustmt[(size_t)c]) o << ind << "    " << st << "\n";
+      std::vector<std::string> w;
+      for (int s = 0; s < nreg; s++) w.push_back("(" + operand(p.out, s, c) + " & tm)");
+      store(ind + "    ", "T | ((fbg_u64)" + std::to_string(c) + "u << " + std::to_string(sh) + ")", w);
+    }
+    o << ind << "  } else if (tm) {\n";
+    o << ind << "    for (fbg_u32 z = 0; z < " << (1u << unroll_bits) << "u; ++z) {\n";
+    std::vector<std::string> zw((size_t)nreg, "0u");
+    store(ind + "      ", "T | ((fbg_u64)z << " + std::to_string(sh) + ")", zw);
+    o << ind << "    }\n";
+    o << ind << "  }\n";
+    o << ind << "}\n";
+  } else {
+    o << ind << "const fbg_u32 keep = a" << prev << " ? tm : 0u;\n";
+    o << ind << "const fbg_u64 T = " << tile_base(nl) << ";\n";
+    std::vector<std::string> w;
+    for (int s = 0; s < nreg; s++) w.push_back("(" + operand(p.out, s) + " & keep)");
+    o << ind << "if (tm) {\n";
+    store(ind + "  ", "T", w);
+    o << ind << "}\n";
+  }
+  for (int lv = (unroll_lv >= 0 ? unroll_lv - 1 : last); lv >= 2; lv--) {
+    ind.resize(ind.size() - 2);
+    o << ind << "}\n";
+  }
+  o << "}\n";
+  return o.str();
+}
+
+std::string SrcGen::generate(int mode, int block, int minb) {
+  const char* kname = mode == 0 ? "fbg_jit_count" : "fbg_jit_table";
+  if (mode == 0) unit_fn_count("fbg_unit_count");
+  else unit_fn_table("fbg_unit_table");
+  o << "extern \"C\" __global__ void __launch_bounds__(" << block << ", " << minb << ") " << kname << "(FbgLaunch P) {\n";
+  o << "  fbg_u64 lvl[" << nl << "] = {0};\n";
+  o << "  fbg_u64 total = 0;\n";
+  o << "  __shared__ fbg_u64 s_unit;\n";
+  o << "  for (;;) {\n";
+  o << "    const fbg_u64 u = fbg_next_unit(P, &s_unit);\n";
+  o << "    if (u >= P.unit_end) break;\n";
+  if (mode == 0) {
+    o << "    const fbg_u64 c = fbg_unit_count(u, u + 1, lvl);\n";
+    o << "    total += c;\n";
+    o << "    if (P.unit_counts) {\n";
+    o << "      const fbg_u64 w = fbg_warp_sum(c);\n";
+    o << "      if ((threadIdx.x & 31u) == 0u && w) atomicAdd(P.unit_counts + (u - P.unit_begin), w);\n";
+    o << "    }\n";
+  } else {
+    o << "    fbg_unit_table(u, P.table, lvl);\n";
+  }
+  o << "  }\n";
+  if (mode == 0) {
+    o << "  total = fbg_warp_sum(total);\n";
+    o << "  if ((threadIdx.x & 31u) == 0u && total) atomicAdd(P.count, total);\n";
+  }
+  o << "  if (P.iters && (threadIdx.x & 31u) == 0u) {\n";
+  o << "    for (int l = 0; l < " << nl << "; l++) if (lvl[l]) atomicAdd(P.iters + l, lvl[l]);\n";
+  o << "  }\n";
+  o << "}\n";
+  return o.str();
+}
+
+// the count body as a device function for the batch kernel
+std::string SrcGen::generate_batch_fn(const std::string& fname) { return unit_fn_count(fname); }
 
 }  // namespace
 

@@ -27,6 +27,8 @@ PRELUDE = r'''
 struct dim3_ { unsigned x, y, z; };
 static dim3_ threadIdx;
 #define __global__
+#define __device__
+#define __noinline__
 #define __launch_bounds__(a, b)
 #define __shared__ static
 template <int LUT> static inline fbg_u32 fbg_lop3(fbg_u32 a, fbg_u32 b, fbg_u32 c) {
