@@ -302,15 +302,15 @@ class SrcGen {
 
   void store(const std::string& ind, const std::string& T, const std::vector<std::string>& w) {
     if (L.r == 0) {
-      o << ind << "reinterpret_cast<fbg_u64*>(P.table)[0] = (fbg_u64)" << w[0] << ";\n";
+      o << ind << "reinterpret_cast<fbg_u64*>(table)[0] = (fbg_u64)" << w[0] << ";\n";
     } else if (L.r == 1) {
-      o << ind << "reinterpret_cast<uint2*>(P.table)[" << T << "] = make_uint2(" << w[0] << ", " << w[1] << ");\n";
+      o << ind << "reinterpret_cast<uint2*>(table)[" << T << "] = make_uint2(" << w[0] << ", " << w[1] << ");\n";
     } else if (L.r == 2) {
-      o << ind << "reinterpret_cast<uint4*>(P.table)[" << T << "] = make_uint4(" << w[0] << ", " << w[1] << ", " << w[2]
+      o << ind << "reinterpret_cast<uint4*>(table)[" << T << "] = make_uint4(" << w[0] << ", " << w[1] << ", " << w[2]
         << ", " << w[3] << ");\n";
     } else {
       for (int q = 0; q < nreg / 4; q++)
-        o << ind << "reinterpret_cast<uint4*>(P.table)[(" << T << ") * " << nreg / 4 << " + " << q << "] = make_uint4("
+        o << ind << "reinterpret_cast<uint4*>(table)[(" << T << ") * " << nreg / 4 << " + " << q << "] = make_uint4("
           << w[4 * q] << ", " << w[4 * q + 1] << ", " << w[4 * q + 2] << ", " << w[4 * q + 3] << ");\n";
     }
   }
