@@ -229,6 +229,9 @@ fbg_status fbg_debug_dump(fbg_program *prog, int which, char *buf, size_t *len);
  */
 fbg_status fbg_debug_batch_source(fbg_program *const *progs, int nprogs, char *buf, size_t *len);
 fbg_status fbg_debug_nvrtc_compile(const char *body, char *log, size_t loglen);
+/* compile and link (without loading) the hybrid batch kernel of these programs;
+   *specialized receives the number of specialised programs */
+fbg_status fbg_debug_batch_build(fbg_program *const *progs, int nprogs, int *specialized, char *log, size_t loglen);
 
 /* NVRTC/ptxas log of the last specialised-kernel build (registers, spills) */
 const char *fbg_program_jit_log(fbg_program *prog);
@@ -245,9 +248,11 @@ const char *fbg_last_error(void);
  * must outlive the batch.  max_item_units bounds the units per queue item
  * (0 = automatic).  flags: FBG_BATCH_GRAPH captures memset + launch + result
  * copy in a CUDA graph on the first run and replays it afterwards;
- * FBG_BATCH_SPECIALIZE compiles the distinct programs that carry most of the
- * work (each >= 1% of the nominal work, at most 16) into straight-line device
- * functions of the one batch kernel, which interprets every other program.
+ * FBG_BATCH_SPECIALIZE compiles the distinct programs with n >= 20 that carry
+ * the most nominal work (at most 512) into straight-line device functions,
+ * separately and in parallel (relocatable device code, linked with
+ * nvJitLink), inside the one batch kernel, which interprets every other
+ * program.
  */
 enum { FBG_BATCH_GRAPH = 1, FBG_BATCH_SPECIALIZE = 2 };
 fbg_status fbg_batch_create(fbg_program *const *progs, int nprogs, uint64_t max_item_units, int flags,

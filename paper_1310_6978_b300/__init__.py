@@ -207,6 +207,17 @@ def batch_source(programs) -> str:
     return buf.value.decode()
 
 
+def batch_build_check(programs):
+    """fbg_debug_batch_build: compile and link the hybrid batch kernel without
+    a device; returns (ok, number of specialised programs, log)."""
+    L = _L()
+    arr = (ctypes.c_void_p * len(programs))(*[p.handle.value for p in programs])
+    spec = ctypes.c_int()
+    log = ctypes.create_string_buffer(1 << 16)
+    st = L.lib.fbg_debug_batch_build(arr, len(programs), ctypes.byref(spec), log, 1 << 16)
+    return st == L.FBG_OK, spec.value, log.value.decode(errors="replace")
+
+
 def nvrtc_check(body: str):
     """fbg_debug_nvrtc_compile: compile a kernel body with NVRTC (no device);
     returns (ok, log)."""

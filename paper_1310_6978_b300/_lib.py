@@ -95,6 +95,7 @@ _sig("fbg_batch_info", c_int, c_vp, ctypes.POINTER(c_u64), ctypes.POINTER(c_u64)
 _sig("fbg_batch_program_kinds", c_int, c_vp, ctypes.POINTER(c_int))
 _sig("fbg_debug_batch_source", c_int, ctypes.POINTER(c_vp), c_int, c_char_p, ctypes.POINTER(c_sz))
 _sig("fbg_debug_nvrtc_compile", c_int, c_char_p, c_char_p, c_sz)
+_sig("fbg_debug_batch_build", c_int, ctypes.POINTER(c_vp), c_int, ctypes.POINTER(c_int), c_char_p, c_sz)
 _sig("fbg_batch_free", None, c_vp)
 _sig("fbg_server_create", c_int, ctypes.POINTER(FbgServerOptions), ctypes.POINTER(c_vp))
 _sig("fbg_server_submit", c_int, c_vp, c_char_p, c_int, c_int, c_u64, ctypes.POINTER(c_u64))

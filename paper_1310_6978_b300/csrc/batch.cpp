@@ -10,16 +10,19 @@
 // With FBG_BATCH_GRAPH the memsets, the launch and the copy of the counts
 // to pinned host memory are captured once in a CUDA graph and replayed.
 //
-// With FBG_BATCH_SPECIALIZE the distinct programs that carry most of the
-// nominal work (each at least 1% of it, up to 16) are compiled by NVRTC into
-// straight-line device functions inside ONE persistent batch kernel; the
-// kernel's work-item loop calls a program's function when it has one and
-// interprets its bytecode otherwise.  If that compilation fails the batch
-// runs on the interpreter kernel alone.
+// With FBG_BATCH_SPECIALIZE the distinct programs with n >= 20 that carry
+// the most nominal work (up to 512) get straight-line device functions: each
+// is compiled separately by NVRTC as relocatable device code (in parallel,
+// cached per source), the dispatch kernel likewise, and nvJitLink links them
+// into ONE persistent batch kernel whose work-item loop calls a program's
+// function when it has one and interprets its bytecode otherwise.  Programs
+// whose compilation fails or misses the deadline are interpreted; if the
+// kernel itself cannot be built the batch runs on the interpreter kernel.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <map>
 #include <string>
@@ -97,31 +100,39 @@ fbg_status enqueue(fbg_batch* b, cudaStream_t st) {
 
 }  // namespace
 
-// Choice of the programs to specialise and the source of the batch kernel
-// (host only).  fid[i] receives program i's function id or -1.
-std::string batch_kernel_source(fbg_program* const* progs, int nprogs, std::vector<int>& fid,
-                                std::vector<LutProgram>& spec_lp, std::string* err) {
-  fid.assign((size_t)nprogs, -1);
-  spec_lp.clear();
+// at most this many distinct programs get a specialised function
+constexpr size_t kMaxSpecialized = 512;
+// specialised functions still compiling after this are dropped (interpreted)
+constexpr double kCompileDeadlineS = 180.0;
+
+struct BatchPlan {
+  std::vector<int> fid;                 // per program: function id or -1
+  std::vector<std::string> fn_name;     // per function
+  std::vector<std::string> fn_src;      // per function (relocatable device code)
+  std::vector<LutProgram> spec_lp;      // per function: its layout
+};
+
+// Choice of the programs to specialise (host only): distinct programs (by
+// text and domain) with n >= 20, ranked by nominal work (instances x 2^n x
+// program size), at most kMaxSpecialized.
+BatchPlan plan_batch(fbg_program* const* progs, int nprogs, std::string* err) {
+  BatchPlan plan;
+  plan.fid.assign((size_t)nprogs, -1);
   std::map<std::pair<std::string, int>, std::vector<int>> groups;
-  double total_cost = 0;
   std::vector<double> cost((size_t)nprogs);
   for (int i = 0; i < nprogs; i++) {
     size_t ins = progs[i]->ib[0].valid ? progs[i]->ib[0].code.ins.size() : (size_t)progs[i]->g.dag.size();
     cost[(size_t)i] = std::ldexp((double)std::max<size_t>(1, ins), progs[i]->n);
-    total_cost += cost[(size_t)i];
     groups[{progs[i]->text, progs[i]->k}].push_back(i);
   }
   std::vector<std::pair<double, const std::vector<int>*>> ranked;
   for (auto& g : groups) {
     double c = 0;
     for (int i : g.second) c += cost[(size_t)i];
-    if (progs[g.second[0]]->n >= 13 && c >= 0.01 * total_cost) ranked.push_back({c, &g.second});
+    if (progs[g.second[0]]->n >= 20) ranked.push_back({c, &g.second});
   }
   std::sort(ranked.begin(), ranked.end(), [](auto& x, auto& y) { return x.first > y.first; });
-  if (ranked.size() > 16) ranked.resize(16);
-  if (ranked.empty()) return "";
-  std::string body = "#include \"interp_device.cuh\"\n";
+  if (ranked.size() > kMaxSpecialized) ranked.resize(kMaxSpecialized);
   for (size_t gi = 0; gi < ranked.size(); gi++) {
     const fbg_program* p0 = progs[(*ranked[gi].second)[0]];
     LayoutParams lp;
@@ -129,18 +140,27 @@ std::string batch_kernel_source(fbg_program* const* progs, int nprogs, std::vect
     lp.warps_log2 = FBG_INTERP_WARPS_LOG2;   // the batch kernel's block shape
     lp.unit_bits_max = 13;
     lp.loop_level_bits = 2;
+    char nm[64];
+    std::snprintf(nm, sizeof nm, "fbg_bp_%016zx_%d", std::hash<std::string>()(p0->text), p0->k);
     try {
       Layout L = make_layout(p0->n, lp, search_order(p0->g));
-      spec_lp.push_back(lower_and_map(p0->g, L));
-      body += emit_batch_function(spec_lp.back(), "fbg_bp" + std::to_string(gi));
+      plan.spec_lp.push_back(lower_and_map(p0->g, L));
+      plan.fn_src.push_back("extern \"C\" " + emit_batch_function(plan.spec_lp.back(), nm));
+      plan.fn_name.push_back(nm);
     } catch (CompileError& e) {
       if (err) *err = e.msg;
-      fid.assign((size_t)nprogs, -1);
-      spec_lp.clear();
-      return "";
+      return BatchPlan{std::vector<int>((size_t)nprogs, -1), {}, {}, {}};
     }
-    for (int i : *ranked[gi].second) fid[(size_t)i] = (int)gi;
+    for (int i : *ranked[gi].second) plan.fid[(size_t)i] = (int)gi;
   }
+  return plan;
+}
+
+// the persistent batch kernel: calls the specialised functions listed in
+// `names` (by function id) and interprets every other program
+std::string batch_kernel_source(const std::vector<std::string>& names) {
+  std::string body = "#include \"interp_device.cuh\"\n";
+  for (auto& nm : names) body += "extern \"C\" __device__ fbg_u64 " + nm + "(fbg_u64 u0, fbg_u64 u1, fbg_u64* lvl);\n";
   body += "extern \"C\" __global__ void __launch_bounds__(" + std::to_string(FBG_INTERP_BLOCK) +
           ") fbg_batch_kernel(const FbgInterpProg* __restrict__ progs, const FbgWorkItem* __restrict__ items,"
           " fbg_u64 nitems, fbg_u64* item_ctr, fbg_u64* prog_counts, const int* __restrict__ fid) {\n"
@@ -165,8 +185,8 @@ std::string batch_kernel_source(fbg_program* const* progs, int nprogs, std::vect
           "    const FbgWorkItem W = items[item];\n"
           "    fbg_u64 cnt = 0;\n"
           "    switch (fid[W.prog]) {\n";
-  for (size_t gi = 0; gi < spec_lp.size(); gi++)
-    body += "      case " + std::to_string(gi) + ": cnt = fbg_bp" + std::to_string(gi) + "(W.unit_begin, W.unit_end, lvl); break;\n";
+  for (size_t gi = 0; gi < names.size(); gi++)
+    body += "      case " + std::to_string(gi) + ": cnt = " + names[gi] + "(W.unit_begin, W.unit_end, lvl); break;\n";
   body += "      default: process_item<0>(S, T, progs, W, cur, alive0, P, cnt, iters); break;\n"
           "    }\n"
           "    cnt = fbg_warp_sum(cnt);\n"
@@ -174,6 +194,37 @@ std::string batch_kernel_source(fbg_program* const* progs, int nprogs, std::vect
           "  }\n"
           "}\n";
   return body;
+}
+
+// compile the plan's functions (in parallel) and the batch kernel; drops the
+// functions that fail or miss the deadline; returns the relocatable cubins
+bool build_batch_cubins(BatchPlan& plan, std::vector<std::string>* cubins, std::string* log) {
+  std::vector<std::string> fn_cubins;
+  std::vector<bool> ok = jit_compile_rdc_many(plan.fn_src, &fn_cubins, kCompileDeadlineS, log);
+  std::vector<int> remap(plan.fn_src.size(), -1);
+  std::vector<std::string> names;
+  cubins->clear();
+  cubins->push_back(std::string());   // the kernel, below
+  std::vector<LutProgram> kept;
+  for (size_t f = 0; f < ok.size(); f++) {
+    if (!ok[f]) continue;
+    remap[f] = (int)names.size();
+    names.push_back(plan.fn_name[f]);
+    cubins->push_back(fn_cubins[f]);
+    kept.push_back(std::move(plan.spec_lp[f]));
+  }
+  for (auto& f : plan.fid) f = f >= 0 ? remap[(size_t)f] : -1;
+  plan.spec_lp.swap(kept);
+  plan.fn_name = names;
+  std::vector<std::string> kc;
+  std::string klog;
+  std::vector<bool> kok = jit_compile_rdc_many({batch_kernel_source(names)}, &kc, kCompileDeadlineS, &klog);
+  if (!kok[0]) {
+    if (log) *log += klog;
+    return false;
+  }
+  (*cubins)[0] = kc[0];
+  return true;
 }
 
 extern "C" {
@@ -220,19 +271,21 @@ fbg_status fbg_batch_create(fbg_program* const* progs, int nprogs, uint64_t max_
   std::vector<LutProgram> spec_lp;
   if (flags & FBG_BATCH_SPECIALIZE) {
     std::string err;
-    std::string body = batch_kernel_source(progs, nprogs, fid, spec_lp, &err);
+    BatchPlan plan = plan_batch(progs, nprogs, &err);
     b->jit_log = err;
-    if (!body.empty()) {
-      int dev = 0;
-      cudaGetDevice(&dev);
-      JitResult r = jit_compile(body, "fbg_batch_kernel", dev);
-      b->jit_log = r.log;
-      if (r.ok) {
-        b->kern = r.kernel;
-        b->specialized = (int)spec_lp.size();
-      } else {
-        std::fill(fid.begin(), fid.end(), -1);
-        spec_lp.clear();
+    if (!plan.fn_src.empty()) {
+      std::vector<std::string> cubins;
+      if (build_batch_cubins(plan, &cubins, &b->jit_log)) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        JitResult r = jit_link(cubins, "fbg_batch_kernel", dev);
+        if (!r.log.empty()) b->jit_log += r.log;
+        if (r.ok) {
+          b->kern = r.kernel;
+          b->specialized = (int)plan.fn_name.size();
+          fid = plan.fid;
+          spec_lp = std::move(plan.spec_lp);
+        }
       }
     }
   }
@@ -352,17 +405,33 @@ fbg_status fbg_batch_program_kinds(fbg_batch* b, int* specialized) {
 
 fbg_status fbg_debug_batch_source(fbg_program* const* progs, int nprogs, char* buf, size_t* len) {
   if (!progs || nprogs <= 0 || !len) return set_error(FBG_EINVAL, "bad argument");
-  std::vector<int> fid;
-  std::vector<LutProgram> spec_lp;
   std::string err;
-  std::string src = batch_kernel_source(progs, nprogs, fid, spec_lp, &err);
-  if (src.empty() && !err.empty()) return set_error(FBG_ETOOBIG, err);
+  BatchPlan plan = plan_batch(progs, nprogs, &err);
+  if (plan.fn_src.empty() && !err.empty()) return set_error(FBG_ETOOBIG, err);
+  std::string src = batch_kernel_source(plan.fn_name);
+  for (auto& f : plan.fn_src) src += f;
   if (buf) {
     if (*len < src.size() + 1) return set_error(FBG_EINVAL, "buffer too small");
     std::memcpy(buf, src.c_str(), src.size() + 1);
   }
   *len = src.size() + 1;
   return FBG_OK;
+}
+
+fbg_status fbg_debug_batch_build(fbg_program* const* progs, int nprogs, int* specialized, char* log, size_t loglen) {
+  if (!progs || nprogs <= 0) return set_error(FBG_EINVAL, "bad argument");
+  std::string err;
+  BatchPlan plan = plan_batch(progs, nprogs, &err);
+  std::vector<std::string> cubins;
+  bool ok = plan.fn_src.empty() || build_batch_cubins(plan, &cubins, &err);
+  if (ok && !cubins.empty()) ok = jit_link_check(cubins, &err);
+  if (specialized) *specialized = ok ? (int)plan.fn_name.size() : 0;
+  if (log && loglen) {
+    size_t n = std::min(loglen - 1, err.size());
+    std::memcpy(log, err.data(), n);
+    log[n] = 0;
+  }
+  return ok ? FBG_OK : set_error(FBG_EJIT, err);
 }
 
 void fbg_batch_free(fbg_batch* b) { delete b; }

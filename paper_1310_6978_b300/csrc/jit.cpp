@@ -2,6 +2,7 @@
 // process-wide cache keyed by the generated source, so identical programs
 // (same formula, layout and mode) are compiled once.
 #include <cuda_runtime.h>
+#include <nvJitLink.h>
 #include <nvrtc.h>
 
 #include <chrono>
@@ -11,6 +12,7 @@
 #include <mutex>
 #include <thread>
 #include <unordered_map>
+#include <vector>
 
 #include "jit.hpp"
 
@@ -148,6 +150,193 @@ bool jit_check(const std::string& body, std::string* log) {
   }
   nvrtcDestroyProgram(&prog);
   return e == NVRTC_SUCCESS;
+}
+
+
+// ------------------------------------------------- separate compilation --
+// Relocatable device code (-rdc=true) compiled by a pool of worker threads,
+// cached per source, then linked with nvJitLink into one cubin.
+
+namespace {
+
+std::mutex g_rdc_mu;
+std::unordered_map<std::string, std::string> g_rdc_cache;   // source -> relocatable cubin
+
+bool nvrtc_rdc(const std::string& src, std::string* cubin, std::string* log) {
+  const char* hdrs[3] = {fbg_device_header, fbg_interp_format_header, fbg_interp_device_header};
+  const char* names[3] = {"fbg_device.cuh", "interp_format.h", "interp_device.cuh"};
+  nvrtcProgram prog;
+  if (nvrtcCreateProgram(&prog, src.c_str(), "fbg_rdc.cu", 3, hdrs, names) != NVRTC_SUCCESS) return false;
+  const char* opts[] = {"-arch=sm_103a", "-std=c++17", "-rdc=true", "-lineinfo"};
+  nvrtcResult e = nvrtcCompileProgram(prog, 4, opts);
+  size_t logn = 0;
+  nvrtcGetProgramLogSize(prog, &logn);
+  if (log && logn > 1) {
+    log->resize(logn);
+    nvrtcGetProgramLog(prog, &(*log)[0]);
+  }
+  bool ok = e == NVRTC_SUCCESS;
+  if (ok) {
+    size_t n = 0;
+    nvrtcGetCUBINSize(prog, &n);
+    cubin->assign(n, '\0');
+    nvrtcGetCUBIN(prog, &(*cubin)[0]);
+  }
+  nvrtcDestroyProgram(&prog);
+  return ok;
+}
+
+}  // namespace
+
+std::vector<bool> jit_compile_rdc_many(const std::vector<std::string>& bodies, std::vector<std::string>* cubins,
+                                       double deadline_s, std::string* log) {
+  const size_t n = bodies.size();
+  cubins->assign(n, std::string());
+  std::vector<bool> ok(n, false);
+  struct Pool {
+    std::mutex mu;
+    std::condition_variable cv;
+    std::vector<std::string> src;
+    std::vector<std::string> out;
+    std::vector<int> state;   // 0 queued, 1 running, 2 done ok, 3 failed
+    size_t next = 0, finished = 0;
+    std::string log;
+  };
+  auto pool = std::make_shared<Pool>();
+  for (size_t i = 0; i < n; i++) {
+    std::string src = "#include \"fbg_device.cuh\"\n" + bodies[i];
+    std::lock_guard<std::mutex> lk(g_rdc_mu);
+    auto it = g_rdc_cache.find(src);
+    pool->src.push_back(src);
+    if (it != g_rdc_cache.end()) {
+      pool->out.push_back(it->second);
+      pool->state.push_back(2);
+      pool->finished++;
+    } else {
+      pool->out.push_back(std::string());
+      pool->state.push_back(0);
+    }
+  }
+  unsigned workers = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), 16u));
+  for (unsigned w = 0; w < workers; w++) {
+    std::thread([pool, n] {
+      for (;;) {
+        size_t i;
+        {
+          std::lock_guard<std::mutex> lk(pool->mu);
+          while (pool->next < n && pool->state[pool->next] != 0) pool->next++;
+          if (pool->next >= n) return;
+          i = pool->next++;
+          pool->state[i] = 1;
+        }
+        std::string cubin, lg;
+        bool good = nvrtc_rdc(pool->src[i], &cubin, &lg);
+        if (good) {
+          std::lock_guard<std::mutex> lk(g_rdc_mu);
+          g_rdc_cache.emplace(pool->src[i], cubin);
+        }
+        std::lock_guard<std::mutex> lk(pool->mu);
+        pool->out[i] = std::move(cubin);
+        pool->state[i] = good ? 2 : 3;
+        if (!good && pool->log.size() < 4096) pool->log += lg;
+        pool->finished++;
+        pool->cv.notify_all();
+      }
+    }).detach();
+  }
+  std::unique_lock<std::mutex> lk(pool->mu);
+  pool->cv.wait_for(lk, std::chrono::duration<double>(deadline_s), [&] { return pool->finished >= n; });
+  for (size_t i = 0; i < n; i++) {
+    if (pool->state[i] == 2) {
+      (*cubins)[i] = pool->out[i];
+      ok[i] = true;
+    }
+  }
+  if (log) *log = pool->log;
+  if (pool->finished < n && log) *log += "\nsome programs were still compiling at the deadline and run interpreted";
+  return ok;
+}
+
+JitResult jit_link(const std::vector<std::string>& cubins, const char* kernel_name, int device) {
+  JitResult r;
+  std::string key = std::to_string(device) + ":link:" + kernel_name;
+  for (auto& c : cubins) key += ":" + std::to_string(std::hash<std::string>()(c)) + "/" + std::to_string(c.size());
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) {
+      r.ok = true;
+      r.kernel = it->second.kern;
+      r.cached = true;
+      return r;
+    }
+  }
+  nvJitLinkHandle h;
+  const char* opts[] = {"-arch=sm_103a"};
+  if (nvJitLinkCreate(&h, 1, opts) != NVJITLINK_SUCCESS) {
+    r.log = "nvJitLinkCreate failed";
+    return r;
+  }
+  bool good = true;
+  for (size_t i = 0; i < cubins.size() && good; i++)
+    good = nvJitLinkAddData(h, NVJITLINK_INPUT_CUBIN, cubins[i].data(), cubins[i].size(), nullptr) == NVJITLINK_SUCCESS;
+  if (good) good = nvJitLinkComplete(h) == NVJITLINK_SUCCESS;
+  std::string linked;
+  if (good) {
+    size_t n = 0;
+    nvJitLinkGetLinkedCubinSize(h, &n);
+    linked.assign(n, '\0');
+    nvJitLinkGetLinkedCubin(h, &linked[0]);
+  } else {
+    size_t n = 0;
+    nvJitLinkGetErrorLogSize(h, &n);
+    std::string lg(n, '\0');
+    if (n) nvJitLinkGetErrorLog(h, &lg[0]);
+    r.log = "nvJitLink: " + lg;
+  }
+  nvJitLinkDestroy(&h);
+  if (!good) return r;
+  Entry ent;
+  cudaError_t ce = cudaLibraryLoadData(&ent.lib, linked.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+  if (ce != cudaSuccess) {
+    r.log = std::string("cudaLibraryLoadData: ") + cudaGetErrorString(ce);
+    return r;
+  }
+  ce = cudaLibraryGetKernel(&ent.kern, ent.lib, kernel_name);
+  if (ce != cudaSuccess) {
+    r.log = std::string("cudaLibraryGetKernel: ") + cudaGetErrorString(ce);
+    cudaLibraryUnload(ent.lib);
+    return r;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto ins = g_cache.emplace(key, ent);
+    if (!ins.second) {
+      cudaLibraryUnload(ent.lib);
+      ent = ins.first->second;
+    }
+  }
+  r.ok = true;
+  r.kernel = ent.kern;
+  return r;
+}
+
+bool jit_link_check(const std::vector<std::string>& cubins, std::string* log) {
+  nvJitLinkHandle h;
+  const char* opts[] = {"-arch=sm_103a"};
+  if (nvJitLinkCreate(&h, 1, opts) != NVJITLINK_SUCCESS) return false;
+  bool good = true;
+  for (size_t i = 0; i < cubins.size() && good; i++)
+    good = nvJitLinkAddData(h, NVJITLINK_INPUT_CUBIN, cubins[i].data(), cubins[i].size(), nullptr) == NVJITLINK_SUCCESS;
+  if (good) good = nvJitLinkComplete(h) == NVJITLINK_SUCCESS;
+  if (!good && log) {
+    size_t n = 0;
+    nvJitLinkGetErrorLogSize(h, &n);
+    log->assign(n, '\0');
+    if (n) nvJitLinkGetErrorLog(h, &(*log)[0]);
+  }
+  nvJitLinkDestroy(&h);
+  return good;
 }
 
 size_t jit_cache_size() {
