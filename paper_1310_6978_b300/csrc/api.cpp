@@ -201,6 +201,8 @@ fbg_status launch_count(fbg_program* p, cudaStream_t st, unsigned long long* dev
   if (jit) {
     JitBuild& b = p->jb[0];
     P.unit_end = b.nunits;
+    // a few fetches per resident block and unit: enough to balance pruned work
+    P.chunk = std::max<uint64_t>(1, b.nunits / ((uint64_t)b.grid * 16));
     void* args[] = {&P};
     CK(cudaLaunchKernel((const void*)b.kern, dim3((unsigned)b.grid), dim3((unsigned)b.block), args, 0, st));
   } else {
@@ -405,6 +407,7 @@ fbg_status fbg_truth_table(fbg_program* p, void* stream, uint64_t* dev_words, si
     JitBuild& b = p->jb[1];
     if (p->n < 6) CK(cudaMemsetAsync(dev_words, 0, 8, st));
     P.unit_end = b.nunits;
+    P.chunk = std::max<uint64_t>(1, b.nunits / ((uint64_t)b.grid * 16));
     void* args[] = {&P};
     CK(cudaLaunchKernel((const void*)b.kern, dim3((unsigned)b.grid), dim3((unsigned)b.block), args, 0, st));
   } else {

@@ -328,6 +328,8 @@ std::string SrcGen::unit_fn_count(const std::string& fname) {
   o << "  const fbg_u32 tb = threadIdx.x;\n";
   o << "  const fbg_u32 tm = (tb < " << tvalid << "u) ? " << hex32(valid_mask()) << " : 0u;\n";
   o << "  lvl[0]++;\n";
+  // level execution counters live in registers during the call
+  for (int lv = 1; lv < nl; lv++) o << "  fbg_u32 it" << lv << " = 0;\n";
   var_words(vars[0], "tb", L.first_lane_pos(), "  ", false);
   declare_level(0, "  ");
   luts(0, "  ");
@@ -335,7 +337,7 @@ std::string SrcGen::unit_fn_count(const std::string& fname) {
     o << "  if (!__any_sync(FBG_FULL, " << any_nonzero(p.levels[0].acc) << ")) return 0;\n";
   o << "  fbg_u64 total = 0;\n";
   o << "  for (fbg_u64 u = u0; u < u1; ++u) {\n";
-  o << "    lvl[1]++;\n";
+  o << "    it1++;\n";
   var_words(vars[1], "u", L.first_unit_pos(), "    ", true);
   declare_level(1, "    ");
   luts(1, "    ");
@@ -348,7 +350,7 @@ std::string SrcGen::unit_fn_count(const std::string& fname) {
     std::string iv = "i" + std::to_string(lv);
     o << ind << "for (fbg_u32 " << iv << " = 0; " << iv << " < " << (1u << L.loop_bits[(size_t)(lv - 2)]) << "u; ++" << iv << ") {\n";
     ind += "  ";
-    o << ind << "lvl[" << lv << "]++;\n";
+    o << ind << "it" << lv << "++;\n";
     var_words(vars[(size_t)lv], iv, L.loop_pos(lv - 2), ind, false);
     declare_level(lv, ind);
     luts(lv, ind);
@@ -356,7 +358,7 @@ std::string SrcGen::unit_fn_count(const std::string& fname) {
       o << ind << "if (!__any_sync(FBG_FULL, " << any_nonzero(p.levels[(size_t)lv].acc) << ")) continue;\n";
   }
   if (unroll_lv >= 0) {
-    o << ind << "lvl[" << unroll_lv << "]++;\n";
+    o << ind << "it" << unroll_lv << "++;\n";
     for (int c = 0; c < (1 << unroll_bits); c++) {
       for (auto& st : ustmt[(size_t)c]) o << ind << st << "\n";
       for (int s = 0; s < nreg; s++) o << ind << "ucnt += __popc(" << operand(p.out, s, c) << " & tm);\n";
@@ -370,6 +372,7 @@ std::string SrcGen::unit_fn_count(const std::string& fname) {
   }
   o << "    total += ucnt;\n";
   o << "  }\n";
+  for (int lv = 1; lv < nl; lv++) o << "  lvl[" << lv << "] += it" << lv << ";\n";
   o << "  return total;\n";
   o << "}\n";
   return o.str();
@@ -464,18 +467,24 @@ std::string SrcGen::generate(int mode, int block, int minb) {
   o << "  fbg_u64 lvl[" << nl << "] = {0};\n";
   o << "  fbg_u64 total = 0;\n";
   o << "  __shared__ fbg_u64 s_unit;\n";
+  o << "  const fbg_u64 chunk = P.chunk ? P.chunk : 1ull;\n";
   o << "  for (;;) {\n";
-  o << "    const fbg_u64 u = fbg_next_unit(P, &s_unit);\n";
+  o << "    const fbg_u64 u = fbg_next_units(P, &s_unit, chunk);\n";
   o << "    if (u >= P.unit_end) break;\n";
+  o << "    const fbg_u64 e = u + chunk < P.unit_end ? u + chunk : P.unit_end;\n";
   if (mode == 0) {
-    o << "    const fbg_u64 c = fbg_unit_count(u, u + 1, lvl);\n";
-    o << "    total += c;\n";
     o << "    if (P.unit_counts) {\n";
-    o << "      const fbg_u64 w = fbg_warp_sum(c);\n";
-    o << "      if ((threadIdx.x & 31u) == 0u && w) atomicAdd(P.unit_counts + (u - P.unit_begin), w);\n";
+    o << "      for (fbg_u64 v = u; v < e; ++v) {\n";
+    o << "        const fbg_u64 c = fbg_unit_count(v, v + 1, lvl);\n";
+    o << "        total += c;\n";
+    o << "        const fbg_u64 w = fbg_warp_sum(c);\n";
+    o << "        if ((threadIdx.x & 31u) == 0u && w) atomicAdd(P.unit_counts + (v - P.unit_begin), w);\n";
+    o << "      }\n";
+    o << "    } else {\n";
+    o << "      total += fbg_unit_count(u, e, lvl);\n";
     o << "    }\n";
   } else {
-    o << "    fbg_unit_table(u, P.table, lvl);\n";
+    o << "    for (fbg_u64 v = u; v < e; ++v) fbg_unit_table(v, P.table, lvl);\n";
   }
   o << "  }\n";
   if (mode == 0) {

@@ -18,6 +18,7 @@ struct FbgLaunch {
   fbg_u64* iters;          // optional: innermost-level iterations executed (+=)
   fbg_u64 cap;             // enumerate: capacity of `models`
   fbg_u64 unit_begin, unit_end;
+  fbg_u64 chunk;           // units fetched per counter increment (0 = 1)
 };
 
 #define FBG_FULL 0xffffffffu
@@ -45,6 +46,15 @@ __device__ __forceinline__ fbg_u32 fbg_genword(fbg_u64 coord, int bit) {
 // fetch the next unit for the whole block (dynamic, atomic counter)
 __device__ __forceinline__ fbg_u64 fbg_next_unit(const FbgLaunch& P, fbg_u64* s_unit) {
   if (threadIdx.x == 0) *s_unit = P.unit_begin + atomicAdd(P.unit_ctr, 1ull);
+  __syncthreads();
+  fbg_u64 u = *s_unit;
+  __syncthreads();
+  return u;
+}
+
+// fetch the next `chunk` units for the whole block
+__device__ __forceinline__ fbg_u64 fbg_next_units(const FbgLaunch& P, fbg_u64* s_unit, fbg_u64 chunk) {
+  if (threadIdx.x == 0) *s_unit = P.unit_begin + atomicAdd(P.unit_ctr, chunk);
   __syncthreads();
   fbg_u64 u = *s_unit;
   __syncthreads();

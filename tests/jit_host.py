@@ -52,6 +52,7 @@ static inline uint2 make_uint2(fbg_u32 a, fbg_u32 b) { return uint2{a, b}; }
 static inline uint4 make_uint4(fbg_u32 a, fbg_u32 b, fbg_u32 c, fbg_u32 d) { return uint4{a, b, c, d}; }
 static fbg_u64 g_next = 0;
 static inline fbg_u64 fbg_next_unit(const FbgLaunch& P, fbg_u64*) { return P.unit_begin + g_next++; }
+static inline fbg_u64 fbg_next_units(const FbgLaunch& P, fbg_u64*, fbg_u64 c) { fbg_u64 u = P.unit_begin + g_next; g_next += c; return u; }
 '''
 
 DRIVER = r'''
@@ -60,6 +61,7 @@ extern "C" int run(int mode, int block, unsigned long long nunits, unsigned long
   std::memset(&P, 0, sizeof P);
   unsigned long long cnt = 0, ctr = 0;
   P.count = &cnt; P.unit_ctr = &ctr; P.table = table; P.unit_begin = 0; P.unit_end = nunits;
+  P.chunk = nunits > 4 ? 3 : 1;   // ragged last chunk
   for (int w = 0; w < block / 32 || w == 0; w++) {
     for (int lane = 31; lane >= 0; lane--) {
       threadIdx.x = (unsigned)(w * 32 + lane);
