@@ -30,6 +30,13 @@
  *                                 S2/S3 = ordered tuples of distinct
  *                                 elements) scoping over the next unary term,
  *                                 optionally followed by '.'; '#' comments.
+ *   assume formula                killing variables (Sec. 3.3; the assumptions
+ *                                 of Sec. 4.2): a conjunction of literals,
+ *                                 possibly under A[..], fixes each letter
+ *                                 (atom 1, negated atom 0); later lines
+ *                                 override earlier ones.  Killed letters are
+ *                                 not variables: the free letters keep their
+ *                                 declaration order and n counts only them.
  *
  * Ownership and threads: the caller owns every device buffer and every CUDA
  * stream passed in (streams as cudaStream_t cast to void*, NULL = the legacy

@@ -49,6 +49,7 @@ def _load():
             lib.oracle_parse.restype = ctypes.c_int
             lib.oracle_free.argtypes = [vp]
             lib.oracle_num_vars.argtypes = [vp]
+            lib.oracle_num_letters.argtypes = [vp]
             lib.oracle_eval.argtypes = [vp, u64]
             lib.oracle_eval.restype = ctypes.c_int
             lib.oracle_range.argtypes = [vp, u64, u64, ctypes.POINTER(u64), vp, vp, u64, ctypes.POINTER(u64)]

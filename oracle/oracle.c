@@ -27,6 +27,10 @@
  *                                assoc) then <->; constants 0 1; quantifiers
  *                                A[i,j:S | i<j] / E[i:S2] scope over the next
  *                                unary term; an optional '.' may follow ']'.
+ *   assume formula              kill letters: a conjunction of literals,
+ *                                possibly quantified, fixes each letter
+ *                                (later lines override earlier ones); the
+ *                                remaining letters keep declaration order
  *   '#' starts a comment.
  * Sets: S = range(k) per bound name; S2/S3 = ordered tuples of 2/3 distinct
  * elements (the paper's perm(range(n),2) and perm(range(n),3), Sec. 4.2).
@@ -78,11 +82,16 @@ typedef struct Node {
 
 typedef struct oracle_prog {
   int k;
-  int nvars;
+  int nvars;                  /* free letters (declared minus killed) */
+  int nletters;               /* declared letters */
   int nfam;
   Family fam[OR_MAX_FAM];
   int naxioms;
   Node **axioms;
+  int nassume;
+  Node **assumes;             /* 'assume' lines, in order */
+  signed char fixed[64];      /* per declared letter: -1 free, else its killed value */
+  int bit_of[64];             /* per free letter: its bit in the assignment integer */
 } oracle_prog;
 
 /* ------------------------------------------------------------------ */
@@ -441,6 +450,8 @@ static void free_prog(oracle_prog *p) {
   if (!p) return;
   for (int i = 0; i < p->naxioms; i++) free_node(p->axioms[i]);
   free(p->axioms);
+  for (int i = 0; i < p->nassume; i++) free_node(p->assumes[i]);
+  free(p->assumes);
   for (int i = 0; i < p->nfam; i++) free(p->fam[i].bits);
   free(p);
 }
@@ -504,8 +515,13 @@ static int eval(Ctx *c, const Node *n) {
         for (int i = 0; i < f->arity; i++) lin = lin * c->p->k + tup[i];
         return f->bits[lin];
       }
-      /* h(mu_j): the letter with id v holds iff bit v of j is 1 */
-      return (int)((c->j >> (f->first_id + r)) & 1u);
+      /* h(mu_j): the free letter numbered v holds iff bit v of j is 1;
+         a killed letter (Sec. 3.3) has its assumed value */
+      {
+        int id = f->first_id + (int)r;
+        if (c->p->fixed[id] >= 0) return c->p->fixed[id];
+        return (int)((c->j >> c->p->bit_of[id]) & 1u);
+      }
     }
     case N_NOT: return !eval(c, n->a);
     case N_AND: return eval(c, n->a) && eval(c, n->b);
@@ -548,6 +564,45 @@ static int check_atoms(Ctx *c, const Node *n) {
   }
 }
 
+/* An assume line kills letters (Sec. 3.3; the assumptions dictionary of
+   Sec. 4.2): it must be a conjunction of literals, possibly under universal
+   quantifiers; each literal fixes its letter (atom: 1, negated atom: 0), and
+   a later assignment of the same letter replaces an earlier one. */
+static int apply_assume(Ctx *c, const Node *n, int value) {
+  switch (n->kind) {
+    case N_CONST: return n->value == 1 && value == 1;
+    case N_ATOM: {
+      const Family *f = &c->p->fam[n->fam];
+      if (f->is_const) return 0;
+      int tup[OR_MAX_ARITY];
+      for (int i = 0; i < n->nidx; i++) tup[i] = idx_value(c, n->idx[i]);
+      long r = tuple_rank(f, c->p->k, tup);
+      if (r < 0) return 0;
+      ((oracle_prog *)c->p)->fixed[f->first_id + r] = (signed char)value;
+      return 1;
+    }
+    case N_NOT:
+      if (n->a->kind != N_ATOM) return 0;
+      return apply_assume(c, n->a, !value);
+    case N_AND:
+      if (!value) return 0;
+      return apply_assume(c, n->a, 1) && apply_assume(c, n->b, 1);
+    case N_FORALL: {
+      if (!value) return 0;
+      int nb = n->nbound, ok = 1;
+      long combos = 1;
+      for (int i = 0; i < nb; i++) combos *= c->p->k;
+      for (long t = 0; t < combos && ok; t++) {
+        long r = t;
+        for (int i = nb - 1; i >= 0; i--) { c->env[n->first_slot + i] = (int)(r % c->p->k); r /= c->p->k; }
+        if (guard_ok(c, n)) ok = apply_assume(c, n->a, 1);
+      }
+      return ok;
+    }
+    default: return 0;
+  }
+}
+
 /* ------------------------------------------------------------------ */
 /* public interface (ctypes)                                            */
 
@@ -575,6 +630,12 @@ int oracle_parse(const char *text, int k, oracle_prog **out, char *err, int errl
       do { if (!parse_decl(&ps, 0)) break; } while (accept(&ps, ","));
     } else if (have && strcmp(word, "const") == 0 && (ps.s[ps.pos] == ' ' || ps.s[ps.pos] == '\t')) {
       parse_decl(&ps, 1);
+    } else if (have && strcmp(word, "assume") == 0 && (ps.s[ps.pos] == ' ' || ps.s[ps.pos] == '\t')) {
+      Node *f = parse_formula(&ps);
+      if (f) {
+        p->assumes = (Node **)realloc(p->assumes, sizeof(Node *) * (size_t)(p->nassume + 1));
+        p->assumes[p->nassume++] = f;
+      }
     } else {
       /* optional label:  name '=' formula   (but not '==') */
       if (have) {
@@ -594,11 +655,21 @@ int oracle_parse(const char *text, int k, oracle_prog **out, char *err, int errl
     skip_ws(&ps);
     if (ps.s[ps.pos] && ps.s[ps.pos] != '\n') set_err(&ps, "unexpected text after the end of a line");
   }
+  p->nletters = p->nvars;
+  for (int v = 0; v < 64; v++) p->fixed[v] = -1;
   if (!ps.err[0]) {
     Ctx c;
     memset(&c, 0, sizeof c);
     c.p = p;
-    for (int i = 0; i < p->naxioms; i++)
+    for (int i = 0; i < p->nassume && !ps.err[0]; i++)
+      if (!apply_assume(&c, p->assumes[i], 1))
+        snprintf(ps.err, sizeof ps.err, "assume line %d is not a conjunction of literals over declared letters", i + 1);
+    /* free letters keep their declaration order */
+    int nf = 0;
+    for (int v = 0; v < p->nletters; v++)
+      if (p->fixed[v] < 0) p->bit_of[v] = nf++;
+    p->nvars = nf;
+    for (int i = 0; i < p->naxioms && !ps.err[0]; i++)
       if (!check_atoms(&c, p->axioms[i])) { snprintf(ps.err, sizeof ps.err, "axiom %d names an undeclared tuple", i + 1); break; }
   }
   if (ps.err[0]) {
@@ -612,6 +683,7 @@ int oracle_parse(const char *text, int k, oracle_prog **out, char *err, int errl
 
 void oracle_free(oracle_prog *p) { free_prog(p); }
 int oracle_num_vars(const oracle_prog *p) { return p->nvars; }
+int oracle_num_letters(const oracle_prog *p) { return p->nletters; }
 
 /* the value of the theory (conjunction of axioms) under mu_j */
 int oracle_eval(const oracle_prog *p, uint64_t j) {

@@ -245,7 +245,7 @@ int fbg_num_vars(const fbg_program* p) { return p ? p->n : -1; }
 
 fbg_status fbg_var_name(const fbg_program* p, int i, char* buf, size_t len) {
   if (!p || !buf || i < 0 || i >= p->n) return set_error(FBG_EINVAL, "bad variable index");
-  const std::string& s = p->th.var_names[(size_t)i];
+  const std::string& s = p->th.var_names[(size_t)p->g.letter_of_var[(size_t)i]];
   if (len < s.size() + 1) return set_error(FBG_EINVAL, "buffer too small");
   std::memcpy(buf, s.c_str(), s.size() + 1);
   return FBG_OK;

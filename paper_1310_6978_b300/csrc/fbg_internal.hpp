@@ -57,10 +57,11 @@ struct Family {
 
 struct Theory {
   int k = 1;
-  int nvars = 0;
+  int nvars = 0;                       // declared letters
   std::vector<Family> fams;
   std::vector<std::unique_ptr<Ast>> axioms;
-  std::vector<std::string> var_names;  // "r(1,2)" per variable id
+  std::vector<std::unique_ptr<Ast>> assumes;   // 'assume' lines (killing, Sec. 3.3)
+  std::vector<std::string> var_names;  // "r(1,2)" per declared letter
 };
 
 Theory parse_theory(const std::string& text, int k);  // throws CompileError
@@ -101,7 +102,9 @@ class FormDag {
 struct Grounded {
   FormDag dag;
   int root = 1;
-  int nvars = 0;
+  int nvars = 0;                   // free letters (declared minus killed)
+  std::vector<int> letter_of_var;  // free letter -> declared letter id
+  std::vector<int> killed;         // per declared letter: -1 free, 0/1 killed value
 };
 
 Grounded ground(const Theory& th);   // the map * of Sec. 3.1

@@ -88,6 +88,8 @@ struct Grounder {
   const Theory& th;
   FormDag& dag;
   std::vector<int> env;
+  const std::vector<int>* killed = nullptr;      // per declared letter
+  const std::vector<int>* free_index = nullptr;  // per declared letter
 
   int idx(const IndexTerm& t) const { return t.slot < 0 ? t.value : env[(size_t)t.slot]; }
 
@@ -123,7 +125,58 @@ struct Grounder {
     if (f.is_const) return f.bits[(size_t)lin] ? 1 : 0;
     int rk = f.rank[(size_t)lin];
     if (rk < 0) throw CompileError{"'" + f.name + "' applied to a tuple outside its declaration"};
-    return dag.var(f.first_id + rk);
+    int id = f.first_id + rk;
+    if (killed && (*killed)[(size_t)id] >= 0) return (*killed)[(size_t)id] ? 1 : 0;
+    return dag.var(free_index ? (*free_index)[(size_t)id] : id);
+  }
+
+  // an assume line: a conjunction of literals, possibly under universal
+  // quantifiers; each literal fixes its letter, later ones replacing earlier
+  void assume(const Ast& e, bool value, std::vector<int>& fixed) {
+    switch (e.kind) {
+      case Ast::Const:
+        if (e.value == 1 && value) return;
+        break;
+      case Ast::Atom: {
+        const Family& f = th.fams[(size_t)e.family];
+        if (f.is_const) break;
+        long lin = 0;
+        for (auto& t : e.idx) {
+          int v = idx(t);
+          if (v < 0 || v >= th.k) throw CompileError{"index out of the domain in an assume line"};
+          lin = lin * th.k + v;
+        }
+        int rk = f.rank[(size_t)lin];
+        if (rk < 0) break;
+        fixed[(size_t)(f.first_id + rk)] = value ? 1 : 0;
+        return;
+      }
+      case Ast::Not:
+        if (e.a->kind != Ast::Atom) break;
+        assume(*e.a, !value, fixed);
+        return;
+      case Ast::And:
+        if (!value) break;
+        assume(*e.a, true, fixed);
+        assume(*e.b, true, fixed);
+        return;
+      case Ast::Forall: {
+        if (!value) break;
+        if ((int)env.size() < e.first_slot + e.nbound) env.resize((size_t)(e.first_slot + e.nbound));
+        std::vector<int> t((size_t)e.nbound, 0);
+        for (;;) {
+          for (int i = 0; i < e.nbound; i++) env[(size_t)(e.first_slot + i)] = t[(size_t)i];
+          if (guards_hold(e)) assume(*e.a, true, fixed);
+          int p = e.nbound - 1;
+          while (p >= 0 && ++t[(size_t)p] == th.k) t[(size_t)p--] = 0;
+          if (p < 0) break;
+        }
+        return;
+      }
+      default:
+        break;
+    }
+    throw CompileError{"an assume line must be a conjunction of literals over declared letters"};
   }
 
   int go(const Ast& e) {
@@ -159,8 +212,20 @@ struct Grounder {
 
 Grounded ground(const Theory& th) {
   Grounded g;
-  g.nvars = th.nvars;
   Grounder gr{th, g.dag, {}};
+  // killing variables (Sec. 3.3): assumed letters become constants and the
+  // free letters are renumbered in declaration order
+  g.killed.assign((size_t)th.nvars, -1);
+  for (auto& a : th.assumes) gr.assume(*a, true, g.killed);
+  std::vector<int> free_index((size_t)th.nvars, -1);
+  for (int v = 0; v < th.nvars; v++)
+    if (g.killed[(size_t)v] < 0) {
+      free_index[(size_t)v] = (int)g.letter_of_var.size();
+      g.letter_of_var.push_back(v);
+    }
+  g.nvars = (int)g.letter_of_var.size();
+  gr.killed = &g.killed;
+  gr.free_index = &free_index;
   std::vector<int> ax;
   for (auto& a : th.axioms) ax.push_back(gr.go(*a));
   g.root = g.dag.mk_and(ax);

@@ -286,6 +286,10 @@ class LineParser {
       else {
         do declaration(false); while (take(","));
       }
+    } else if (cur().kind == T_NAME && cur().text == "assume" && t_[p_ + 1].kind != T_END &&
+               !(t_[p_ + 1].kind == T_SYM && t_[p_ + 1].text != "(" && t_[p_ + 1].text != "~")) {
+      p_++;
+      th_.assumes.push_back(formula());
     } else {
       if (cur().kind == T_NAME && t_[p_ + 1].kind == T_SYM && t_[p_ + 1].text == "=") p_ += 2;  // label
       th_.axioms.push_back(formula());

@@ -223,3 +223,32 @@ def request_stream(count: int, rate_per_s: float, seed: int = 5,
         mode = "enumerate" if rng.uniform01() < enum_frac else "count"
         out.append(Request(rid, t, wl, mode, cap))
     return out
+
+
+# -- killing variables (Sec. 3.3) and the bounded posets of Sec. 5.2 ---------
+
+POSET_AXIOMS = [REFLEXIVE, ANTISYMMETRIC, TRANSITIVE]
+
+
+def posets_reflexivity_killed(k: int) -> Workload:
+    """Partial orders with the letters r(i,i) killed to 1 (the assumptions of
+    the SO.txt example, Sec. 4.2): k^2 - k free letters."""
+    text = "\n".join(["var r(S,S)", "assume A[i:S] r(i,i)", ANTISYMMETRIC, TRANSITIVE]) + "\n"
+    return Workload("poset_killed", k, text, k, k * k - k)
+
+
+def bounded_posets(k: int) -> Workload:
+    """Partial orders with a least and a greatest element (Sec. 5.2), k >= 2."""
+    text = "\n".join(["var r(S,S)", *POSET_AXIOMS, "E[x:S].A[y:S] r(x,y)", "E[x:S].A[y:S] r(y,x)"]) + "\n"
+    return Workload("bounded_poset", k, text, k, k * k)
+
+
+def bounded_posets_killed(k: int) -> Workload:
+    """The adequate family K of Sec. 5.2: 0 is the least and k-1 the greatest
+    element; eq. (conspa) kills 5k-6 letters (read with the greatest element
+    k-1: r(0,i)=1, r(j,0)=0 for j>=1, r(i,k-1)=1, r(k-1,l)=0 for l<=k-2,
+    r(i,i)=1), leaving (k-2)(k-3) free letters."""
+    kill = [f"assume A[i:S] r(0,i)", f"assume A[j:S | j>0] ~r(j,0)", f"assume A[i:S] r(i,{k - 1})",
+            f"assume A[l:S | l<{k - 1}] ~r({k - 1},l)", "assume A[i:S] r(i,i)"]
+    text = "\n".join(["var r(S,S)", *kill, ANTISYMMETRIC, TRANSITIVE]) + "\n"
+    return Workload("bounded_poset_killed", k, text, k, (k - 2) * (k - 3))
