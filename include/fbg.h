@@ -153,6 +153,13 @@ fbg_status fbg_count_async(fbg_program *prog, void *stream, uint64_t *dev_out);
  * Synchronises `stream`.
  */
 fbg_status fbg_count_units(fbg_program *prog, void *stream, uint64_t *dev_counts, uint64_t nunits);
+/*
+ * Models among the units [unit_begin, unit_end) of the count layout (clipped
+ * to the unit count of fbg_unit_vars): a long count split into chunks whose
+ * sums give fbg_count, e.g. to checkpoint and resume it.  Synchronises.
+ */
+fbg_status fbg_count_range(fbg_program *prog, void *stream, uint64_t unit_begin, uint64_t unit_end,
+                           uint64_t *out_count);
 fbg_status fbg_unit_vars(fbg_program *prog, int *vars, int max_vars, int *nvars, uint64_t *nunits);
 
 /*

@@ -80,3 +80,43 @@ uint64_t counter_triangle_free(int k) {
     }
   return tri_rec(0);
 }
+
+/* partial orders on k points: decide the pairs (i,j), i != j, in row-major
+   order (the diagonal is forced); reject a new pair that breaks
+   antisymmetry or transitivity among decided pairs */
+static int PK;
+static unsigned char PR[10][10], PD[10][10];
+
+static int poset_ok(int i, int j) {
+  if (PR[i][j] && PD[j][i] && PR[j][i]) return 0;
+  for (int x = 0; x < PK; x++) {
+    if (PD[j][x] && PD[i][x] && PR[i][j] && PR[j][x] && !PR[i][x]) return 0;
+    if (PD[x][i] && PD[x][j] && PR[x][i] && PR[i][j] && !PR[x][j]) return 0;
+    if (PD[i][x] && PD[x][j] && PR[i][x] && PR[x][j] && !PR[i][j]) return 0;
+  }
+  return 1;
+}
+
+static uint64_t poset_rec(int p) {
+  if (p == PK * PK) return 1;
+  int i = p / PK, j = p % PK;
+  if (i == j) return poset_rec(p + 1);
+  uint64_t total = 0;
+  PD[i][j] = 1;
+  for (int v = 0; v < 2; v++) {
+    PR[i][j] = (unsigned char)v;
+    if (poset_ok(i, j)) total += poset_rec(p + 1);
+  }
+  PD[i][j] = 0;
+  PR[i][j] = 0;
+  return total;
+}
+
+uint64_t counter_posets(int k) {
+  if (k < 0 || k > 9) return 0;
+  PK = k;
+  memset(PR, 0, sizeof PR);
+  memset(PD, 0, sizeof PD);
+  for (int i = 0; i < k; i++) PR[i][i] = PD[i][i] = 1;
+  return poset_rec(0);
+}

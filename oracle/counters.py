@@ -149,3 +149,9 @@ def count_triangle_free_backtrack(k: int) -> int:
     """Triangle-free labelled graphs on k vertices (k <= 11), backtracking in C."""
     from . import _load
     return int(_load().counter_triangle_free(k))
+
+
+def count_posets_c(k: int) -> int:
+    """Partial orders on k labelled points (k <= 9), backtracking in C."""
+    from . import _load
+    return int(_load().counter_posets(k))

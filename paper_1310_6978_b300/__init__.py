@@ -95,6 +95,12 @@ class Program:
         self._L.check(self._L.lib.fbg_unit_vars(self._h, vars_, 64, ctypes.byref(nv), ctypes.byref(nu)))
         return [vars_[i] for i in range(nv.value)], nu.value
 
+    def count_range(self, unit_begin: int, unit_end: int, stream=None) -> int:
+        """fbg_count_range: models among units [unit_begin, unit_end)."""
+        out = ctypes.c_uint64()
+        self._L.check(self._L.lib.fbg_count_range(self._h, _stream_ptr(stream), unit_begin, unit_end, ctypes.byref(out)))
+        return out.value
+
     def count_units(self, dev_counts, stream=None) -> None:
         self._L.check(self._L.lib.fbg_count_units(self._h, _stream_ptr(stream), _ptr(dev_counts), dev_counts.numel()))
 

@@ -76,6 +76,7 @@ _sig("fbg_program_stats", c_int, c_vp, ctypes.POINTER(FbgStats))
 _sig("fbg_count", c_int, c_vp, c_vp, ctypes.POINTER(c_u64))
 _sig("fbg_count_async", c_int, c_vp, c_vp, c_vp)
 _sig("fbg_count_noalloc", c_int, c_vp, c_vp, c_vp)
+_sig("fbg_count_range", c_int, c_vp, c_vp, c_u64, c_u64, ctypes.POINTER(c_u64))
 _sig("fbg_count_units", c_int, c_vp, c_vp, c_vp, c_u64)
 _sig("fbg_unit_vars", c_int, c_vp, ctypes.POINTER(c_int), c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_u64))
 _sig("fbg_truth_table", c_int, c_vp, c_vp, c_vp, c_sz)

@@ -182,12 +182,19 @@ fbg_status pick_engine(fbg_program* p, int mode, bool* use_jit) {
 constexpr size_t kScratchHead = 32;
 
 fbg_status launch_count(fbg_program* p, cudaStream_t st, unsigned long long* dev_count, unsigned long long* unit_counts,
-                        bool* used_jit) {
+                        bool* used_jit, uint64_t ubegin = 0, uint64_t uend = ~0ull) {
   bool jit = false;
   fbg_status s = pick_engine(p, 0, &jit);
   if (s != FBG_OK) return s;
   if (p->n > 63) return set_error(FBG_ETOOBIG, "counts need n <= 63");
-  s = ensure_scratch(p, kScratchHead);
+  size_t words = kScratchHead;
+  if (!jit) {   // room for the work items of a sub-range (interpreter)
+    const InterpBuild& ib = p->ib[0];
+    uint64_t e = std::min<uint64_t>(uend, ib.nunits);
+    if (e > ubegin && !(ubegin == 0 && e == ib.nunits))
+      words += ((e - ubegin) / ib.units_per_item + 2) * (sizeof(FbgWorkItem) / 8) + 1;
+  }
+  s = ensure_scratch(p, words);
   if (s != FBG_OK) return s;
   if (!dev_count) dev_count = p->d_scratch + 1;
   CK(cudaMemsetAsync(p->d_scratch, 0, kScratchHead * 8, st));
@@ -200,17 +207,39 @@ fbg_status launch_count(fbg_program* p, cudaStream_t st, unsigned long long* dev
   P.unit_begin = 0;
   if (jit) {
     JitBuild& b = p->jb[0];
-    P.unit_end = b.nunits;
+    uend = std::min<uint64_t>(uend, b.nunits);
+    if (ubegin > uend) return set_error(FBG_EINVAL, "empty or inverted unit range");
+    P.unit_begin = ubegin;
+    P.unit_end = uend;
     // a few fetches per resident block and unit: enough to balance pruned work
-    P.chunk = std::max<uint64_t>(1, b.nunits / ((uint64_t)b.grid * 16));
+    P.chunk = std::max<uint64_t>(1, (uend - ubegin) / ((uint64_t)b.grid * 16));
     void* args[] = {&P};
-    CK(cudaLaunchKernel((const void*)b.kern, dim3((unsigned)b.grid), dim3((unsigned)b.block), args, 0, st));
+    if (uend > ubegin)
+      CK(cudaLaunchKernel((const void*)b.kern, dim3((unsigned)b.grid), dim3((unsigned)b.block), args, 0, st));
   } else {
     InterpBuild& b = p->ib[0];
-    P.unit_end = b.nunits;
+    uend = std::min<uint64_t>(uend, b.nunits);
+    if (ubegin > uend) return set_error(FBG_EINVAL, "empty or inverted unit range");
     if (unit_counts && b.units_per_item != 1) return set_error(FBG_ETOOBIG, "too many units for per-unit counts");
-    CK(launch_interp(0, b.d_prog, b.d_items, b.nitems, p->d_scratch + 2, dev_count, unit_counts, P, b.code.nslots,
-                     b.grid, st));
+    P.unit_end = b.nunits;
+    if (ubegin == 0 && uend == b.nunits) {
+      CK(launch_interp(0, b.d_prog, b.d_items, b.nitems, p->d_scratch + 2, dev_count, unit_counts, P, b.code.nslots,
+                       b.grid, st));
+    } else if (uend > ubegin) {
+      // a sub-range: items aligned to the program's item grouping, clipped at the ends
+      std::vector<FbgWorkItem> items;
+      for (uint64_t u = ubegin; u < uend;) {
+        uint64_t e = std::min(uend, (u / b.units_per_item + 1) * b.units_per_item);
+        items.push_back(FbgWorkItem{0u, 0u, u, e});
+        u = e;
+      }
+      FbgWorkItem* d_items = reinterpret_cast<FbgWorkItem*>(p->d_scratch + kScratchHead);
+      CK(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(FbgWorkItem), cudaMemcpyHostToDevice, st));
+      int grid = (int)std::min<uint64_t>(items.size(), (uint64_t)b.grid);
+      CK(launch_interp(0, b.d_prog, d_items, items.size(), p->d_scratch + 2, dev_count, unit_counts, P, b.code.nslots,
+                       grid, st));
+      CK(cudaStreamSynchronize(st));   // the host item list goes out of scope
+    }
   }
   *used_jit = jit;
   return FBG_OK;
@@ -348,6 +377,19 @@ fbg_status fbg_count(fbg_program* p, void* stream, uint64_t* out_count) {
       es.lop3_nominal += nominal_execs * per;
     }
   }
+  return FBG_OK;
+}
+
+fbg_status fbg_count_range(fbg_program* p, void* stream, uint64_t unit_begin, uint64_t unit_end, uint64_t* out_count) {
+  if (!p || !out_count) return set_error(FBG_EINVAL, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  bool jit = false;
+  fbg_status s = launch_count(p, st, nullptr, nullptr, &jit, unit_begin, unit_end);
+  if (s != FBG_OK) return s;
+  unsigned long long c = 0;
+  CK(cudaMemcpyAsync(&c, p->d_scratch + 1, 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  *out_count = c;
   return FBG_OK;
 }
 

@@ -220,3 +220,9 @@ def test_backtracking_counters_match_brute_force_and_oracle():
         assert C.count_triangle_free_backtrack(k) == C.count_triangle_free(k)
     assert C.count_transitive_backtrack(5) == oracle.Theory(W.transitive(5).text, 5).count_par(0, 1 << 25)
     assert C.count_triangle_free_backtrack(7) == oracle.Theory(W.triangle_free(7).text, 7).count()
+
+
+def test_c_poset_counter_matches_brute_force_and_oracle():
+    for k in range(1, 5):
+        assert C.count_posets_c(k) == C.count_relations(k, "poset")
+    assert C.count_posets_c(5) == 4231
