@@ -22,6 +22,10 @@
  *                                increasing positions)
  *   const E(S,S) = 0110...       constant relation, bits over all tuples in
  *                                lexicographic order
+ *   fun m(S,S)                   function symbol with values in the domain
+ *                                (Sec. 3.1): letters m(a,b,u) = "m(a,b) = u",
+ *                                tuples (a,b,u) in lexicographic order; 'fun c'
+ *                                declares a constant symbol, letters c(u)
  *   [label =] formula            operators ~ & ^ | -> <-> with Python
  *                                precedence (~ > & > ^ > |) then -> (right
  *                                assoc) then <->; constants 0 1; quantifiers
@@ -30,7 +34,17 @@
  *   assume formula              kill letters: a conjunction of literals,
  *                                possibly quantified, fixes each letter
  *                                (later lines override earlier ones); the
- *                                remaining letters keep declaration order
+ *                                remaining letters keep declaration order.
+ *                                A literal m(a) = b fixes m(a,b) to 1 and
+ *                                m(a,b') to 0 for every b' != b; its negation
+ *                                fixes m(a,b) to 0.
+ * Terms: a numeral, a bound name, or m(t,..) for a declared function symbol.
+ * An equation t1 = t2 (or t1 != t2) is an atomic formula; relation atoms
+ * take terms as arguments (not in families declared with '<').
+ * Semantics of function symbols: mu_j defines a structure of the language
+ * only when every m(a..) has exactly one value u with m(a..,u) true (h of
+ * Sec. 3.2 reads F(a..) = b off mu(p_{Fa..b})); any other mu_j is not a model.
+ * Terms are then evaluated by looking up that value.
  *   '#' starts a comment.
  * Sets: S = range(k) per bound name; S2/S3 = ordered tuples of 2/3 distinct
  * elements (the paper's perm(range(n),2) and perm(range(n),3), Sec. 4.2).
@@ -47,8 +61,9 @@
 #define OR_MAX_ARITY 4
 #define OR_MAX_BOUND 32
 #define OR_MAX_FAM 64
+#define OR_MAX_LETTERS 4096         /* declared letters; at most 64 stay free */
 
-enum { N_CONST, N_ATOM, N_NOT, N_AND, N_OR, N_XOR, N_IMP, N_IFF, N_FORALL, N_EXISTS };
+enum { N_CONST, N_ATOM, N_NOT, N_AND, N_OR, N_XOR, N_IMP, N_IFF, N_FORALL, N_EXISTS, N_EQ };
 enum { CMP_LT, CMP_LE, CMP_GT, CMP_GE, CMP_EQ, CMP_NE };
 
 typedef struct {
@@ -56,6 +71,7 @@ typedef struct {
   int arity;
   int lt[OR_MAX_ARITY];       /* lt[p] = 1: position p < position p+1 */
   int is_const;
+  int is_fun;                 /* function symbol: arity = arguments + 1 (the value) */
   int first_id;               /* variables: id of the first tuple */
   int count;                  /* number of tuples in the family */
   unsigned char *bits;        /* constants: value per tuple, k^arity entries */
@@ -66,12 +82,22 @@ typedef struct { int slot; int value; } Idx;
 
 typedef struct { Idx l, r; int op; } Cmp;
 
+/* a term: an index (fam < 0) or a function symbol applied to terms */
+typedef struct Term {
+  int fam;
+  Idx idx;
+  int nargs;
+  struct Term *args[OR_MAX_ARITY];
+} Term;
+
 typedef struct Node {
   int kind;
   int value;                  /* N_CONST */
   int fam;                    /* N_ATOM */
   int nidx;
   Idx idx[OR_MAX_ARITY];
+  Term *targ[OR_MAX_ARITY];   /* N_ATOM: argument i is this term when non-NULL */
+  Term *lhs, *rhs;            /* N_EQ */
   struct Node *a, *b;         /* children */
   /* quantifiers */
   int nbound, first_slot;     /* bound names occupy slots first_slot.. */
@@ -90,8 +116,8 @@ typedef struct oracle_prog {
   Node **axioms;
   int nassume;
   Node **assumes;             /* 'assume' lines, in order */
-  signed char fixed[64];      /* per declared letter: -1 free, else its killed value */
-  int bit_of[64];             /* per free letter: its bit in the assignment integer */
+  signed char fixed[OR_MAX_LETTERS];  /* per declared letter: -1 free, else its killed value */
+  int bit_of[OR_MAX_LETTERS];         /* per free letter: its bit in the assignment integer */
 } oracle_prog;
 
 /* ------------------------------------------------------------------ */
@@ -163,10 +189,19 @@ static Node *new_node(int kind) {
   return n;
 }
 
+static void free_term(Term *t) {
+  if (!t) return;
+  for (int i = 0; i < t->nargs; i++) free_term(t->args[i]);
+  free(t);
+}
+
 static void free_node(Node *n) {
   if (!n) return;
   free_node(n->a);
   free_node(n->b);
+  for (int i = 0; i < OR_MAX_ARITY; i++) free_term(n->targ[i]);
+  free_term(n->lhs);
+  free_term(n->rhs);
   free(n);
 }
 
@@ -197,6 +232,61 @@ static int parse_idx(Parser *ps, Idx *out) {
   }
   set_err(ps, "expected index");
   return 0;
+}
+
+/* term: numeral | bound name | f(term, ..) for a function symbol f */
+static Term *parse_term(Parser *ps) {
+  Term *t = (Term *)calloc(1, sizeof(Term));
+  t->fam = -1;
+  char nm[64];
+  skip_ws(ps);
+  int save = ps->pos;
+  if (read_name(ps, nm)) {
+    int f = find_family(ps->p, nm);
+    if (find_bound(ps, nm) < 0 && f >= 0) {
+      const Family *F = &ps->p->fam[f];
+      if (!F->is_fun) { set_err(ps, "a relation symbol is not a term"); free(t); return NULL; }
+      t->fam = f;
+      if (F->arity > 1) {
+        if (!expect(ps, "(")) { free(t); return NULL; }
+        do {
+          if (t->nargs >= F->arity - 1) { set_err(ps, "too many arguments"); free_term(t); return NULL; }
+          Term *a = parse_term(ps);
+          if (!a) { free_term(t); return NULL; }
+          t->args[t->nargs++] = a;
+        } while (accept(ps, ","));
+        if (!expect(ps, ")")) { free_term(t); return NULL; }
+      }
+      if (t->nargs != F->arity - 1) { set_err(ps, "wrong number of arguments"); free_term(t); return NULL; }
+      return t;
+    }
+    ps->pos = save;
+  }
+  if (!parse_idx(ps, &t->idx)) { free(t); return NULL; }
+  return t;
+}
+
+/* '=' that is not '==' */
+static int accept_eq(Parser *ps) {
+  skip_ws(ps);
+  if (ps->s[ps->pos] == '=' && ps->s[ps->pos + 1] != '=') { ps->pos++; return 1; }
+  return 0;
+}
+
+/* the rest of an equation 't = u' / 't != u' after its left side */
+static Node *parse_equation(Parser *ps, Term *lhs) {
+  int neg = 0;
+  if (accept(ps, "!=")) neg = 1;
+  else if (!accept_eq(ps)) { set_err(ps, "expected '=' or '!=' after a term"); free_term(lhs); return NULL; }
+  Term *rhs = parse_term(ps);
+  if (!rhs) { free_term(lhs); return NULL; }
+  Node *e = new_node(N_EQ);
+  e->lhs = lhs;
+  e->rhs = rhs;
+  if (!neg) return e;
+  Node *n = new_node(N_NOT);
+  n->a = e;
+  return n;
 }
 
 static Node *parse_quant(Parser *ps, int forall) {
@@ -257,12 +347,21 @@ static Node *parse_primary(Parser *ps) {
   }
   int v;
   if (isdigit(c)) {
-    if (!read_int(ps, &v) || v > 1) { set_err(ps, "constants are 0 or 1"); return NULL; }
+    int save = ps->pos;
+    if (!read_int(ps, &v)) { set_err(ps, "bad numeral"); return NULL; }
+    skip_ws(ps);
+    if ((ps->s[ps->pos] == '=' && ps->s[ps->pos + 1] != '=') || (ps->s[ps->pos] == '!' && ps->s[ps->pos + 1] == '=')) {
+      ps->pos = save;
+      Term *t = parse_term(ps);
+      return t ? parse_equation(ps, t) : NULL;
+    }
+    if (v > 1) { set_err(ps, "constants are 0 or 1"); return NULL; }
     Node *n = new_node(N_CONST);
     n->value = v;
     return n;
   }
   char nm[64];
+  int start = ps->pos;
   if (!read_name(ps, nm)) { set_err(ps, "expected a term"); return NULL; }
   /* quantifier keyword: A or E directly followed by '[' */
   if ((strcmp(nm, "A") == 0 || strcmp(nm, "E") == 0) && peek(ps) == '[') {
@@ -270,6 +369,11 @@ static Node *parse_primary(Parser *ps) {
     return parse_quant(ps, nm[0] == 'A');
   }
   int f = find_family(ps->p, nm);
+  if (find_bound(ps, nm) >= 0 || (f >= 0 && ps->p->fam[f].is_fun)) {
+    ps->pos = start;
+    Term *t = parse_term(ps);
+    return t ? parse_equation(ps, t) : NULL;
+  }
   if (f < 0) { char m[128]; snprintf(m, sizeof m, "undeclared name '%s'", nm); set_err(ps, m); return NULL; }
   Node *n = new_node(N_ATOM);
   n->fam = f;
@@ -277,12 +381,19 @@ static Node *parse_primary(Parser *ps) {
     ps->pos++;
     do {
       if (n->nidx >= OR_MAX_ARITY) { set_err(ps, "too many indices"); free_node(n); return NULL; }
-      if (!parse_idx(ps, &n->idx[n->nidx])) { free_node(n); return NULL; }
+      Term *t = parse_term(ps);
+      if (!t) { free_node(n); return NULL; }
+      if (t->fam < 0) { n->idx[n->nidx] = t->idx; free(t); }
+      else n->targ[n->nidx] = t;
       n->nidx++;
     } while (accept(ps, ","));
     if (!expect(ps, ")")) { free_node(n); return NULL; }
   }
   if (n->nidx != ps->p->fam[f].arity) { set_err(ps, "wrong number of indices"); free_node(n); return NULL; }
+  for (int i = 0; i < n->nidx; i++)
+    if (n->targ[i])
+      for (int q = 0; q + 1 < ps->p->fam[f].arity; q++)
+        if (ps->p->fam[f].lt[q]) { set_err(ps, "function terms in a family declared with '<'"); free_node(n); return NULL; }
   return n;
 }
 
@@ -401,7 +512,7 @@ static long tuple_rank(const Family *f, int k, const int *tup) {
   return -1;
 }
 
-static int parse_decl(Parser *ps, int is_const) {
+static int parse_decl(Parser *ps, int is_const, int is_fun) {
   oracle_prog *p = ps->p;
   if (p->nfam >= OR_MAX_FAM) { set_err(ps, "too many declarations"); return 0; }
   Family *f = &p->fam[p->nfam];
@@ -413,14 +524,16 @@ static int parse_decl(Parser *ps, int is_const) {
     for (;;) {
       char d[64];
       if (!read_name(ps, d) || strcmp(d, "S") != 0) { set_err(ps, "declared positions range over S"); return 0; }
-      if (f->arity >= OR_MAX_ARITY) { set_err(ps, "arity too large"); return 0; }
+      if (f->arity >= OR_MAX_ARITY - (is_fun ? 1 : 0)) { set_err(ps, "arity too large"); return 0; }
       f->arity++;
       if (accept(ps, ",")) continue;
-      if (accept(ps, "<")) { f->lt[f->arity - 1] = 1; continue; }
+      if (!is_fun && accept(ps, "<")) { f->lt[f->arity - 1] = 1; continue; }
       break;
     }
     if (!expect(ps, ")")) return 0;
   }
+  if (is_fun) f->arity++;    /* the value position */
+  f->is_fun = is_fun;
   f->is_const = is_const;
   f->count = (int)family_size(f, p->k);
   if (is_const) {
@@ -439,7 +552,7 @@ static int parse_decl(Parser *ps, int is_const) {
     if (got != want) { set_err(ps, "constant has the wrong number of bits"); free(f->bits); f->bits = NULL; return 0; }
   } else {
     f->first_id = p->nvars;
-    if ((long)p->nvars + f->count > 64) { set_err(ps, "more than 64 variables"); return 0; }
+    if ((long)p->nvars + f->count > OR_MAX_LETTERS) { set_err(ps, "more than 4096 declared letters"); return 0; }
     p->nvars += f->count;
   }
   p->nfam++;
@@ -462,6 +575,51 @@ static void free_prog(oracle_prog *p) {
 typedef struct { const oracle_prog *p; uint64_t j; int env[OR_MAX_BOUND]; int bad; } Ctx;
 
 static int idx_value(const Ctx *c, Idx x) { return x.slot < 0 ? x.value : c->env[x.slot]; }
+
+/* h(mu_j): the free letter numbered v holds iff bit v of j is 1; a killed
+   letter (Sec. 3.3) has its assumed value */
+static int letter_value(const oracle_prog *p, uint64_t j, int id) {
+  if (p->fixed[id] >= 0) return p->fixed[id];
+  return (int)((j >> p->bit_of[id]) & 1u);
+}
+
+/* linear index of an argument tuple of a function symbol (values in range) */
+static long fun_base(const oracle_prog *p, const Family *f, const int *args) {
+  long lin = 0;
+  for (int i = 0; i + 1 < f->arity; i++) lin = lin * p->k + args[i];
+  return f->first_id + lin * p->k;
+}
+
+/* F^A(a..) = the b with mu_j(p_{Fa..b}) = 1; mu_j is known to be functional */
+static int term_value(Ctx *c, const Term *t) {
+  if (t->fam < 0) return idx_value(c, t->idx);
+  const Family *f = &c->p->fam[t->fam];
+  int args[OR_MAX_ARITY];
+  for (int i = 0; i < t->nargs; i++) args[i] = term_value(c, t->args[i]);
+  for (int i = 0; i < t->nargs; i++)
+    if (args[i] < 0 || args[i] >= c->p->k) { c->bad = 1; return 0; }
+  long base = fun_base(c->p, f, args);
+  for (int b = 0; b < c->p->k; b++)
+    if (letter_value(c->p, c->j, (int)(base + b))) return b;
+  c->bad = 1;
+  return 0;
+}
+
+/* mu_j defines a structure of the language: every function symbol has
+   exactly one value at every argument tuple */
+static int functional(const oracle_prog *p, uint64_t j) {
+  for (int fi = 0; fi < p->nfam; fi++) {
+    const Family *f = &p->fam[fi];
+    if (!f->is_fun) continue;
+    long tuples = f->count / p->k;
+    for (long t = 0; t < tuples; t++) {
+      int ones = 0;
+      for (int b = 0; b < p->k; b++) ones += letter_value(p, j, (int)(f->first_id + t * p->k + b));
+      if (ones != 1) return 0;
+    }
+  }
+  return 1;
+}
 
 static int eval(Ctx *c, const Node *n);
 
@@ -507,7 +665,7 @@ static int eval(Ctx *c, const Node *n) {
     case N_ATOM: {
       const Family *f = &c->p->fam[n->fam];
       int tup[OR_MAX_ARITY];
-      for (int i = 0; i < n->nidx; i++) tup[i] = idx_value(c, n->idx[i]);
+      for (int i = 0; i < n->nidx; i++) tup[i] = n->targ[i] ? term_value(c, n->targ[i]) : idx_value(c, n->idx[i]);
       long r = tuple_rank(f, c->p->k, tup);
       if (r < 0) { c->bad = 1; return 0; }
       if (f->is_const) {
@@ -515,14 +673,9 @@ static int eval(Ctx *c, const Node *n) {
         for (int i = 0; i < f->arity; i++) lin = lin * c->p->k + tup[i];
         return f->bits[lin];
       }
-      /* h(mu_j): the free letter numbered v holds iff bit v of j is 1;
-         a killed letter (Sec. 3.3) has its assumed value */
-      {
-        int id = f->first_id + (int)r;
-        if (c->p->fixed[id] >= 0) return c->p->fixed[id];
-        return (int)((c->j >> c->p->bit_of[id]) & 1u);
-      }
+      return letter_value(c->p, c->j, f->first_id + (int)r);
     }
+    case N_EQ: return term_value(c, n->lhs) == term_value(c, n->rhs);
     case N_NOT: return !eval(c, n->a);
     case N_AND: return eval(c, n->a) && eval(c, n->b);
     case N_OR: return eval(c, n->a) || eval(c, n->b);
@@ -535,15 +688,34 @@ static int eval(Ctx *c, const Node *n) {
   return 0;
 }
 
+/* every index inside a term names a domain element */
+static int check_term(Ctx *c, const Term *t) {
+  if (t->fam < 0) {
+    int v = idx_value(c, t->idx);
+    return v >= 0 && v < c->p->k;
+  }
+  for (int i = 0; i < t->nargs; i++)
+    if (!check_term(c, t->args[i])) return 0;
+  return 1;
+}
+
 /* every atom instance must name a declared tuple: checked by a full walk
    (no short-circuit) so that errors do not depend on j */
 static int check_atoms(Ctx *c, const Node *n) {
   switch (n->kind) {
     case N_CONST: return 1;
+    case N_EQ: return check_term(c, n->lhs) && check_term(c, n->rhs);
     case N_ATOM: {
       const Family *f = &c->p->fam[n->fam];
       int tup[OR_MAX_ARITY];
-      for (int i = 0; i < n->nidx; i++) tup[i] = idx_value(c, n->idx[i]);
+      for (int i = 0; i < n->nidx; i++) {
+        if (n->targ[i]) {
+          if (!check_term(c, n->targ[i])) return 0;
+          tup[i] = 0;   /* any element: '<' families take no function terms */
+        } else {
+          tup[i] = idx_value(c, n->idx[i]);
+        }
+      }
       return tuple_rank(f, c->p->k, tup) >= 0;
     }
     case N_NOT: return check_atoms(c, n->a);
@@ -575,14 +747,38 @@ static int apply_assume(Ctx *c, const Node *n, int value) {
       const Family *f = &c->p->fam[n->fam];
       if (f->is_const) return 0;
       int tup[OR_MAX_ARITY];
-      for (int i = 0; i < n->nidx; i++) tup[i] = idx_value(c, n->idx[i]);
+      for (int i = 0; i < n->nidx; i++) {
+        if (n->targ[i]) return 0;
+        tup[i] = idx_value(c, n->idx[i]);
+      }
       long r = tuple_rank(f, c->p->k, tup);
       if (r < 0) return 0;
       ((oracle_prog *)c->p)->fixed[f->first_id + r] = (signed char)value;
       return 1;
     }
+    case N_EQ: {
+      /* m(a..) = b with plain a.., b (either side): the value of m at a.. */
+      const Term *app = n->lhs->fam >= 0 ? n->lhs : n->rhs, *val = n->lhs->fam >= 0 ? n->rhs : n->lhs;
+      if (app->fam < 0 || val->fam >= 0) return 0;
+      const Family *f = &c->p->fam[app->fam];
+      int args[OR_MAX_ARITY];
+      for (int i = 0; i < app->nargs; i++) {
+        if (app->args[i]->fam >= 0) return 0;
+        args[i] = idx_value(c, app->args[i]->idx);
+        if (args[i] < 0 || args[i] >= c->p->k) return 0;
+      }
+      int b = idx_value(c, val->idx);
+      if (b < 0 || b >= c->p->k) return 0;
+      long base = fun_base(c->p, f, args);
+      oracle_prog *w = (oracle_prog *)c->p;
+      if (value)
+        for (int u = 0; u < c->p->k; u++) w->fixed[base + u] = (signed char)(u == b);
+      else
+        w->fixed[base + b] = 0;
+      return 1;
+    }
     case N_NOT:
-      if (n->a->kind != N_ATOM) return 0;
+      if (n->a->kind != N_ATOM && n->a->kind != N_EQ) return 0;
       return apply_assume(c, n->a, !value);
     case N_AND:
       if (!value) return 0;
@@ -627,9 +823,11 @@ int oracle_parse(const char *text, int k, oracle_prog **out, char *err, int errl
     char word[64];
     int have = read_name(&ps, word);
     if (have && strcmp(word, "var") == 0 && (ps.s[ps.pos] == ' ' || ps.s[ps.pos] == '\t')) {
-      do { if (!parse_decl(&ps, 0)) break; } while (accept(&ps, ","));
+      do { if (!parse_decl(&ps, 0, 0)) break; } while (accept(&ps, ","));
+    } else if (have && strcmp(word, "fun") == 0 && (ps.s[ps.pos] == ' ' || ps.s[ps.pos] == '\t')) {
+      do { if (!parse_decl(&ps, 0, 1)) break; } while (accept(&ps, ","));
     } else if (have && strcmp(word, "const") == 0 && (ps.s[ps.pos] == ' ' || ps.s[ps.pos] == '\t')) {
-      parse_decl(&ps, 1);
+      parse_decl(&ps, 1, 0);
     } else if (have && strcmp(word, "assume") == 0 && (ps.s[ps.pos] == ' ' || ps.s[ps.pos] == '\t')) {
       Node *f = parse_formula(&ps);
       if (f) {
@@ -637,10 +835,11 @@ int oracle_parse(const char *text, int k, oracle_prog **out, char *err, int errl
         p->assumes[p->nassume++] = f;
       }
     } else {
-      /* optional label:  name '=' formula   (but not '==') */
+      /* optional label:  name '=' formula   (but not '==', and not an
+         equation whose left side is a declared function symbol) */
       if (have) {
         skip_ws(&ps);
-        if (!(ps.s[ps.pos] == '=' && ps.s[ps.pos + 1] != '=')) ps.pos = save;
+        if (!(ps.s[ps.pos] == '=' && ps.s[ps.pos + 1] != '=') || find_family(p, word) >= 0) ps.pos = save;
         else ps.pos++;
       } else {
         ps.pos = save;
@@ -656,7 +855,7 @@ int oracle_parse(const char *text, int k, oracle_prog **out, char *err, int errl
     if (ps.s[ps.pos] && ps.s[ps.pos] != '\n') set_err(&ps, "unexpected text after the end of a line");
   }
   p->nletters = p->nvars;
-  for (int v = 0; v < 64; v++) p->fixed[v] = -1;
+  for (int v = 0; v < OR_MAX_LETTERS; v++) p->fixed[v] = -1;
   if (!ps.err[0]) {
     Ctx c;
     memset(&c, 0, sizeof c);
@@ -669,6 +868,7 @@ int oracle_parse(const char *text, int k, oracle_prog **out, char *err, int errl
     for (int v = 0; v < p->nletters; v++)
       if (p->fixed[v] < 0) p->bit_of[v] = nf++;
     p->nvars = nf;
+    if (nf > 64 && !ps.err[0]) snprintf(ps.err, sizeof ps.err, "more than 64 free variables");
     for (int i = 0; i < p->naxioms && !ps.err[0]; i++)
       if (!check_atoms(&c, p->axioms[i])) { snprintf(ps.err, sizeof ps.err, "axiom %d names an undeclared tuple", i + 1); break; }
   }
@@ -687,6 +887,7 @@ int oracle_num_letters(const oracle_prog *p) { return p->nletters; }
 
 /* the value of the theory (conjunction of axioms) under mu_j */
 int oracle_eval(const oracle_prog *p, uint64_t j) {
+  if (!functional(p, j)) return 0;
   Ctx c;
   memset(&c, 0, sizeof c);
   c.p = p;

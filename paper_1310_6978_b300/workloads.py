@@ -252,3 +252,53 @@ def bounded_posets_killed(k: int) -> Workload:
             f"assume A[l:S | l<{k - 1}] ~r({k - 1},l)", "assume A[i:S] r(i,i)"]
     text = "\n".join(["var r(S,S)", *kill, ANTISYMMETRIC, TRANSITIVE]) + "\n"
     return Workload("bounded_poset_killed", k, text, k, (k - 2) * (k - 3))
+
+
+# -- function symbols (Sec. 3.1: letters p_{F a_1..a_k b}) --------------------
+
+ASSOCIATIVE = "A[x,y,z:S] m(m(x,y),z) = m(x,m(y,z))"
+LEFT_CANCEL = "A[x,y,z:S] (m(x,y) = m(x,z) -> y = z)"
+RIGHT_CANCEL = "A[x,y,z:S] (m(y,x) = m(z,x) -> y = z)"
+
+
+def semigroups(k: int) -> Workload:
+    """Associative binary operations on k elements (letters m(a,b,u), k^3)."""
+    text = "\n".join(["fun m(S,S)", ASSOCIATIVE]) + "\n"
+    return Workload("semigroup", k, text, k, k ** 3)
+
+
+def latin_squares(k: int, first_row: bool = False) -> Workload:
+    """Quasigroups = Latin squares of order k (both cancellation laws); with
+    ``first_row`` the row m(0,j) = j is assumed, which kills k^2 letters."""
+    lines = ["fun m(S,S)"]
+    if first_row:
+        lines.append("assume A[j:S] m(0,j) = j")
+    lines += [LEFT_CANCEL, RIGHT_CANCEL]
+    return Workload("latin_row" if first_row else "latin", k, "\n".join(lines) + "\n", k,
+                    k ** 3 - (k * k if first_row else 0))
+
+
+def reduced_latin_squares(k: int) -> Workload:
+    """Latin squares with first row and column 0..k-1; letters that the
+    border rules out (m(i,j) = i or = j inside) are killed as well."""
+    lines = ["fun m(S,S)", "assume A[j:S] m(0,j) = j", "assume A[i:S] m(i,0) = i",
+             "assume A[i,j:S | i>0, j>0] (~(m(i,j) = i) & ~(m(i,j) = j))",
+             LEFT_CANCEL, RIGHT_CANCEL]
+    m = k - 1
+    free = m * (m - 1) * (k - 2) + m * (k - 1)
+    return Workload("latin_reduced", k, "\n".join(lines) + "\n", k, free)
+
+
+def groups_identity0(k: int) -> Workload:
+    """Groups on k elements with identity 0 (identity row and column killed):
+    associativity and a right inverse for every element."""
+    lines = ["fun m(S,S)", "assume A[x:S] (m(0,x) = x & m(x,0) = x)", ASSOCIATIVE,
+             "A[x:S] E[y:S] m(x,y) = 0"]
+    return Workload("group_e0", k, "\n".join(lines) + "\n", k, (k - 1) ** 2 * k)
+
+
+def groups(k: int) -> Workload:
+    """Groups on k elements: associativity, an identity and inverses."""
+    lines = ["fun m(S,S)", ASSOCIATIVE,
+             "E[e:S] (A[x:S] (m(e,x) = x & m(x,e) = x) & A[x:S] E[y:S] m(x,y) = e)"]
+    return Workload("group", k, "\n".join(lines) + "\n", k, k ** 3)
