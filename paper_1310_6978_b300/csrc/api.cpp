@@ -260,7 +260,7 @@ fbg_status fbg_compile(const char* formula, int domain_k, fbg_program** out) {
     p->g = ground(p->th);
   } catch (CompileError& e) {
     delete p;
-    bool big = e.msg.find("more than 64") != std::string::npos;
+    bool big = e.msg.find("more than") != std::string::npos;
     return set_error(big ? FBG_ETOOBIG : FBG_EPARSE, e.msg);
   }
   p->text = formula;

@@ -33,11 +33,20 @@ struct Guard {
   int op = 0;      // 0 <, 1 <=, 2 >, 3 >=, 4 ==, 5 !=
 };
 
+// a term: an index (family < 0) or a function symbol applied to terms
+struct Term {
+  int family = -1;
+  IndexTerm ix;
+  std::vector<Term> args;
+};
+
 struct Ast {
-  enum Kind { Const, Atom, Not, And, Or, Xor, Imp, Iff, Forall, Exists } kind = Const;
+  enum Kind { Const, Atom, Not, And, Or, Xor, Imp, Iff, Forall, Exists, Eq } kind = Const;
   int value = 0;                      // Const
   int family = -1;                    // Atom
-  std::vector<IndexTerm> idx;         // Atom
+  std::vector<IndexTerm> idx;         // Atom: plain arguments
+  std::vector<Term> targs;            // Atom: all arguments as terms, when one is a function term
+  Term lhs, rhs;                      // Eq
   std::unique_ptr<Ast> a, b;
   int first_slot = 0, nbound = 0;     // quantifiers
   bool distinct = false;              // S2 / S3
@@ -49,6 +58,7 @@ struct Family {
   int arity = 0;
   std::vector<bool> lt;               // lt[p]: position p < position p+1
   bool is_const = false;
+  bool is_fun = false;                // function symbol: the last position is the value
   int first_id = 0;                   // variables: id of the first tuple
   int count = 0;                      // number of admissible tuples
   std::vector<int> rank;              // linear tuple index -> rank or -1

@@ -6,7 +6,9 @@
 // S2 = perm(range(k),2) and S3 = perm(range(k),3), quantifiers separated by
 // '.', labels "e1 = ..." as in the BAequ4 example of Sec. 5.1.  Added here:
 // '->' and '<->', guards "A[a,b:S | a<b]", and 'var' / 'const' declarations
-// that fix the letters of the set P of Sec. 3.1 and their numbering.
+// that fix the letters of the set P of Sec. 3.1 and their numbering, and
+// 'fun' declarations of function symbols (letters p_{Fa..b}, named F(a..,b))
+// with terms F(t,..) and equations t = u / t != u as atomic formulas.
 #include <cctype>
 #include <cstring>
 
@@ -81,7 +83,7 @@ class LineParser {
   }
   bool at_end() const { return cur().kind == T_END; }
 
-  void declaration(bool is_const) {
+  void declaration(bool is_const, bool is_fun = false) {
     Family f;
     f.name = name();
     for (auto& g : th_.fams)
@@ -92,10 +94,15 @@ class LineParser {
         f.arity++;
         f.lt.push_back(false);
         if (take(",")) continue;
-        if (take("<")) { f.lt.back() = true; continue; }
+        if (!is_fun && take("<")) { f.lt.back() = true; continue; }
         break;
       }
       need(")");
+    }
+    if (is_fun) {   // the value position
+      f.arity++;
+      f.lt.push_back(false);
+      f.is_fun = true;
     }
     if (f.arity > 4) fail("arity above 4");
     long total = 1;
@@ -128,7 +135,7 @@ class LineParser {
       }
     } else {
       f.first_id = th_.nvars;
-      if (th_.nvars + f.count > 64) fail("more than 64 variables");
+      if (th_.nvars + f.count > 4096) fail("more than 4096 declared letters");
       th_.nvars += f.count;
       for (long lin = 0; lin < total; lin++) {
         if (f.rank[(size_t)lin] < 0) continue;
@@ -158,6 +165,59 @@ class LineParser {
     for (int i = (int)bound_.size() - 1; i >= 0; i--)
       if (bound_[i] == nm) { t.slot = i; return t; }
     fail("unbound index '" + nm + "'");
+  }
+
+  int bound_slot(const std::string& nm) const {
+    for (int i = (int)bound_.size() - 1; i >= 0; i--)
+      if (bound_[i] == nm) return i;
+    return -1;
+  }
+  int family_of(const std::string& nm) const {
+    for (int i = 0; i < (int)th_.fams.size(); i++)
+      if (th_.fams[i].name == nm) return i;
+    return -1;
+  }
+
+  // numeral | bound name | F(term, ..) for a function symbol F
+  Term term() {
+    Term t;
+    if (cur().kind == T_NAME && bound_slot(cur().text) < 0) {
+      int f = family_of(cur().text);
+      if (f >= 0) {
+        const Family& F = th_.fams[(size_t)f];
+        if (!F.is_fun) fail("a relation symbol is not a term");
+        p_++;
+        t.family = f;
+        if (F.arity > 1) {
+          need("(");
+          do t.args.push_back(term()); while (take(","));
+          need(")");
+        }
+        if ((int)t.args.size() != F.arity - 1) fail("'" + F.name + "' takes " + std::to_string(F.arity - 1) + " arguments");
+        return t;
+      }
+    }
+    t.ix = index_term();
+    return t;
+  }
+
+  std::unique_ptr<Ast> equation() {
+    auto e = std::make_unique<Ast>();
+    e->kind = Ast::Eq;
+    e->lhs = term();
+    bool neg = false;
+    if (take("!=")) neg = true;
+    else need("=");
+    e->rhs = term();
+    if (!neg) return e;
+    auto n = std::make_unique<Ast>();
+    n->kind = Ast::Not;
+    n->a = std::move(e);
+    return n;
+  }
+
+  bool at_equation_sign(size_t q) const {
+    return t_[q].kind == T_SYM && (t_[q].text == "=" || t_[q].text == "!=");
   }
 
   std::unique_ptr<Ast> quantifier(bool forall) {
@@ -205,6 +265,7 @@ class LineParser {
       return e;
     }
     if (cur().kind == T_NUM) {
+      if (at_equation_sign(p_ + 1)) return equation();
       std::string s = t_[p_++].text;
       if (s != "0" && s != "1") fail("constants are 0 or 1");
       auto e = std::make_unique<Ast>();
@@ -212,23 +273,38 @@ class LineParser {
       e->value = s[0] - '0';
       return e;
     }
-    std::string nm = name();
-    if ((nm == "A" || nm == "E") && is_sym("[")) {
-      p_++;
-      return quantifier(nm == "A");
+    if (cur().kind == T_NAME) {
+      const std::string& nm0 = cur().text;
+      if ((nm0 == "A" || nm0 == "E") && t_[p_ + 1].kind == T_SYM && t_[p_ + 1].text == "[") {
+        p_ += 2;
+        return quantifier(nm0 == "A");
+      }
+      int f0 = family_of(nm0);
+      if (bound_slot(nm0) >= 0 || (f0 >= 0 && th_.fams[(size_t)f0].is_fun)) return equation();
     }
-    int fam = -1;
-    for (int i = 0; i < (int)th_.fams.size(); i++)
-      if (th_.fams[i].name == nm) fam = i;
+    std::string nm = name();
+    int fam = family_of(nm);
     if (fam < 0) fail("undeclared name '" + nm + "'");
     auto e = std::make_unique<Ast>();
     e->kind = Ast::Atom;
     e->family = fam;
+    const Family& F = th_.fams[(size_t)fam];
+    bool any_fun = false;
+    std::vector<Term> args;
     if (take("(")) {
-      do e->idx.push_back(index_term()); while (take(","));
+      do {
+        args.push_back(term());
+        if (args.back().family >= 0) any_fun = true;
+        e->idx.push_back(args.back().ix);
+      } while (take(","));
       need(")");
     }
-    if ((int)e->idx.size() != th_.fams[fam].arity) fail("'" + nm + "' takes " + std::to_string(th_.fams[fam].arity) + " indices");
+    if ((int)args.size() != F.arity) fail("'" + nm + "' takes " + std::to_string(F.arity) + " indices");
+    if (any_fun) {
+      for (bool l : F.lt)
+        if (l) fail("function terms in a family declared with '<'");
+      e->targs = std::move(args);
+    }
     return e;
   }
 
@@ -279,19 +355,22 @@ class LineParser {
 
   void line() {
     if (at_end()) return;
-    if (cur().kind == T_NAME && (cur().text == "var" || cur().text == "const") && t_[p_ + 1].kind == T_NAME) {
-      bool c = cur().text == "const";
+    if (cur().kind == T_NAME && (cur().text == "var" || cur().text == "const" || cur().text == "fun") &&
+        t_[p_ + 1].kind == T_NAME) {
+      bool c = cur().text == "const", fn = cur().text == "fun";
       p_++;
       if (c) declaration(true);
       else {
-        do declaration(false); while (take(","));
+        do declaration(false, fn); while (take(","));
       }
     } else if (cur().kind == T_NAME && cur().text == "assume" && t_[p_ + 1].kind != T_END &&
                !(t_[p_ + 1].kind == T_SYM && t_[p_ + 1].text != "(" && t_[p_ + 1].text != "~")) {
       p_++;
       th_.assumes.push_back(formula());
     } else {
-      if (cur().kind == T_NAME && t_[p_ + 1].kind == T_SYM && t_[p_ + 1].text == "=") p_ += 2;  // label
+      // a label, unless the name is a declared symbol (then it is an equation)
+      if (cur().kind == T_NAME && t_[p_ + 1].kind == T_SYM && t_[p_ + 1].text == "=" && family_of(cur().text) < 0)
+        p_ += 2;
       th_.axioms.push_back(formula());
     }
     if (!at_end()) fail("unexpected '" + cur().text + "'");

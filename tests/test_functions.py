@@ -123,3 +123,14 @@ def test_assume_on_a_function_value_kills_its_row():
     with pytest.raises(oracle.OracleError):
         oracle.Theory("fun m(S,S)\nm(0,3) = 0\n", 3)
 
+
+
+def test_unlabelled_semigroups():
+    import paper_1310_6978_b300 as F
+    from paper_1310_6978_b300 import unlabelled as U
+    for k, labelled, unlabelled in ((2, 8, 5), (3, 113, 24)):
+        wl = W.semigroups(k)
+        models, total = oracle.Theory(wl.text, k).models(1 << 10)
+        prog = F.compile(wl.text, k)
+        sizes, _ = U.orbits(models, U.letter_permutations(prog, k))
+        assert total == labelled and sum(sizes) == labelled and len(sizes) == unlabelled

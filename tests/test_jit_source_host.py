@@ -14,7 +14,12 @@ import jit_host
 CASES = [W.BAEQU4, W.POSET3, W.posets(4), W.transitive(4), W.equivalences(4), W.triangle_free(6),
          W.automorphisms(4, 3), W.cnf3(14, 2), W.cnf3(18, 5), W.single_var(6, 5), W.minterm(3, 6),
          W.Workload("xor", 0, "var a, b, c, d, e, f, g, h\n(a ^ b ^ c) | (d & ~e) <-> (f -> g ^ h)\n", 1, 8),
-         W.Workload("unsat", 0, "var a, b, c, d, e, f, g\n(a & ~a) | (b & 0)\n", 1, 7)]
+         W.Workload("unsat", 0, "var a, b, c, d, e, f, g\n(a & ~a) | (b & 0)\n", 1, 7),
+         # function symbols (Sec. 3.1)
+         W.semigroups(2), W.latin_squares(3, first_row=True), W.reduced_latin_squares(4), W.groups(2),
+         W.Workload("image", 3, "var r(S)\nfun f(S)\nA[x:S] r(f(x))\n", 3, 12),
+         W.Workload("inj", 3, "fun f(S)\nA[x,y:S] (x != y -> f(x) != f(y))\n", 3, 9),
+         W.Workload("nested", 2, "var r(S,S)\nfun f(S), c\nA[x:S] (r(x, f(f(x))) | f(c) = x)\n", 2, 10)]
 
 LAYOUTS = [
     {},
