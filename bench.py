@@ -328,6 +328,21 @@ def run_serving(args, torch, F, L):
 
 # -------------------------------------------------------------------- ours --
 
+def max_over_ranks(t_local: float, world: int, device: str) -> float:
+    """The slowest rank's time (seconds): the job's time under replicas."""
+    import torch
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_all_ranks: int, t_max: float) -> float:
+    """Giga-units per second for the whole job: every rank's units over the
+    slowest rank's time."""
+    return units_all_ranks / t_max / 1e9
+
+
 def run_ours(args, rank, world):
     import torch
     import paper_1310_6978_b300 as F
@@ -381,13 +396,9 @@ def run_ours(args, rank, world):
             step_ms.append(evs[s][0][0].elapsed_time(evs[s][-1][1]))
         clk.stop()
     torch.cuda.synchronize()
-    t_local = sum(step_ms) / 1e3
-    t = torch.tensor([t_local], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    t_max = float(t.item())
+    t_max = max_over_ranks(sum(step_ms) / 1e3, world, "cuda")
     assign_per_step = sum(1 << w.n for w in wls)
-    value = world * assign_per_step * args.steps / t_max / 1e9
+    value = whole_job_rate(world * assign_per_step * args.steps, t_max)
 
     # executed work of the same kernels (level iteration counters), untimed
     executed = 0.0

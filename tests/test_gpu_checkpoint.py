@@ -53,3 +53,14 @@ def test_resume_after_interruption(tmp_path):
     # a checkpoint of another program is refused
     with pytest.raises(ValueError):
         checkpoint.count_resumable(F.compile(W.TRANSITIVE6.text, 6), path)
+
+
+def test_rank_slices_add_up():
+    """The unit slices that count_sharded gives each rank, counted one after
+    another on this GPU, add up to the count."""
+    from paper_1310_6978_b300.shard import unit_range
+    p = F.compile(W.triangle_free(9).text, 9)
+    total = p.count()
+    _, nunits = p.unit_vars()
+    for world in (2, 3, 8):
+        assert sum(p.count_range(*unit_range(nunits, r, world)) for r in range(world)) == total
