@@ -160,7 +160,7 @@ BatchPlan plan_batch(fbg_program* const* progs, int nprogs, std::string* err) {
 // `names` (by function id) and interprets every other program
 std::string batch_kernel_source(const std::vector<std::string>& names) {
   std::string body = "#include \"interp_device.cuh\"\n";
-  for (auto& nm : names) body += "extern \"C\" __device__ fbg_u64 " + nm + "(fbg_u64 u0, fbg_u64 u1, fbg_u64* lvl);\n";
+  for (auto& nm : names) body += "extern \"C\" __device__ fbg_u64 " + nm + "(fbg_u64 u0, fbg_u64 u1, fbg_u32 tb, fbg_u64* lvl);\n";
   body += "extern \"C\" __global__ void __launch_bounds__(" + std::to_string(FBG_INTERP_BLOCK) +
           ") fbg_batch_kernel(const FbgInterpProg* __restrict__ progs, const FbgWorkItem* __restrict__ items,"
           " fbg_u64 nitems, fbg_u64* item_ctr, fbg_u64* prog_counts, const int* __restrict__ fid) {\n"
@@ -186,7 +186,7 @@ std::string batch_kernel_source(const std::vector<std::string>& names) {
           "    fbg_u64 cnt = 0;\n"
           "    switch (fid[W.prog]) {\n";
   for (size_t gi = 0; gi < names.size(); gi++)
-    body += "      case " + std::to_string(gi) + ": cnt = " + names[gi] + "(W.unit_begin, W.unit_end, lvl); break;\n";
+    body += "      case " + std::to_string(gi) + ": cnt = " + names[gi] + "(W.unit_begin, W.unit_end, threadIdx.x, lvl); break;\n";
   body += "      default: process_item<0>(S, T, progs, W, cur, alive0, P, cnt, iters); break;\n"
           "    }\n"
           "    cnt = fbg_warp_sum(cnt);\n"

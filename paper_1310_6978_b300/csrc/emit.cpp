@@ -76,6 +76,86 @@ class SrcGen {
 
   bool in_unrolled(int lut) const { return unroll_lv >= 0 && p.luts[(size_t)lut].level == unroll_lv; }
 
+  // Counting the result words of one innermost execution.  POPC issues on
+  // the XU pipe at a quarter of the rate of lop3 on the ALU pipe; a full
+  // adder (xor3 and majority: two lop3) turns three words of one weight into
+  // one word of that weight and one of twice the weight, which trades one
+  // POPC for two lop3.  The accumulators ucnt, ucnt2, ucnt4, ucnt8 hold the
+  // popcounts of words of weight 1, 2, 4, 8.
+  struct CountState {
+    std::vector<std::string> pend[4];
+    int fa_left = 0;
+  };
+  int fa_id_ = 0;
+
+  // lanes beyond the valid range of a small program must not count; with
+  // all 32 lanes in use and n >= 5 every bit of every word is an assignment
+  bool need_thread_mask() const { return L.lane_bits < 5 || valid_mask() != 0xFFFFFFFFu; }
+
+  static std::string acc_name(int k) { return k == 0 ? "ucnt" : "ucnt" + std::to_string(1 << k); }
+
+  // full adders per innermost execution: balance ALU cycles (2 per warp lop3
+  // or add) against XU cycles (8 per warp POPC) for W words and A ALU ops
+  static int full_adder_budget(int W, long long A) {
+    long long f = (4LL * W - A + 3) / 6;
+    if (f < 0) f = 0;
+    if (f > W / 2) f = W / 2;
+    return (int)f;
+  }
+
+  void count_reduce(CountState& cs, const std::string& ind, bool last) {
+    for (;;) {
+      int k = -1;
+      if (cs.fa_left > 0)
+        for (int t = 0; t < 3 && k < 0; t++)
+          if (cs.pend[t].size() >= 3) k = t;
+      if (k < 0) break;
+      auto& v = cs.pend[k];
+      std::string a = v[v.size() - 3], b = v[v.size() - 2], c = v[v.size() - 1];
+      v.resize(v.size() - 3);
+      std::string sn = "fs" + std::to_string(fa_id_), cn = "fc" + std::to_string(fa_id_);
+      fa_id_++;
+      o << ind << "const fbg_u32 " << sn << " = fbg_lop3<0x96>(" << a << ", " << b << ", " << c << ");\n";
+      o << ind << "const fbg_u32 " << cn << " = fbg_lop3<0xe8>(" << a << ", " << b << ", " << c << ");\n";
+      v.push_back(sn);
+      cs.pend[k + 1].push_back(cn);
+      cs.fa_left--;
+    }
+    if (last || cs.fa_left == 0) {
+      for (int k = 0; k < 4; k++) {
+        for (auto& e : cs.pend[k]) o << ind << acc_name(k) << " += __popc(" << e << ");\n";
+        cs.pend[k].clear();
+      }
+    }
+  }
+
+  // the count of one innermost execution: words[c] are the result words of
+  // copy c (one copy when the innermost level is not unrolled), emitted after
+  // that copy's statements
+  void emit_counts(const std::vector<std::vector<std::string>>* stmts, const std::vector<std::vector<Sym>>& words,
+                   long long alu_ops, const std::string& ind) {
+    const bool masked = need_thread_mask();
+    int W = 0;
+    for (auto& ws : words)
+      for (const Sym& w : ws) W += w.is_const ? 0 : 1;
+    CountState cs;
+    cs.fa_left = masked ? 0 : full_adder_budget(W, alu_ops + W / 2 + 4);
+    for (size_t c = 0; c < words.size(); c++) {
+      if (stmts)
+        for (auto& st : (*stmts)[c]) o << ind << st << "\n";
+      for (const Sym& w : words[c]) {
+        if (masked) {
+          o << ind << "ucnt += __popc(" << expr(w) << " & tm);\n";
+        } else if (w.is_const) {
+          if (w.c) o << ind << "ucnt += " << __builtin_popcount(w.c) << "u;\n";
+        } else {
+          cs.pend[0].push_back(expr(w));
+        }
+      }
+      count_reduce(cs, ind, c + 1 == words.size());
+    }
+  }
+
   Sym operand_sym(const Val& v, int s, int copy) const {
     Sym x;
     if (v.kind == V_CONST) {
@@ -317,15 +397,15 @@ class SrcGen {
 };
 
 // Per-unit device function of count mode: this thread's number of models over
-// the units [u0, u1); lvl[l] counts the executions of level l.  The kernels
-// and the batch kernel call it; keeping the unit fetch (with its barriers)
-// outside this function keeps the control flow the compiler sees simple.
+// the units [u0, u1), the thread taking the lane and warp bits tb; lvl[l]
+// counts the executions of level l.  The kernels and the batch kernel call
+// it; keeping the work fetch outside this function keeps the control flow the
+// compiler sees simple.
 std::string SrcGen::unit_fn_count(const std::string& fname) {
   auto vars = used_vars();
   const int tvalid = 1 << (L.lane_bits + L.warp_bits);
   const int last = nl - 1;
-  o << "__device__ __noinline__ fbg_u64 " << fname << "(fbg_u64 u0, fbg_u64 u1, fbg_u64* lvl) {\n";
-  o << "  const fbg_u32 tb = threadIdx.x;\n";
+  o << "__device__ __noinline__ fbg_u64 " << fname << "(fbg_u64 u0, fbg_u64 u1, fbg_u32 tb, fbg_u64* lvl) {\n";
   o << "  const fbg_u32 tm = (tb < " << tvalid << "u) ? " << hex32(valid_mask()) << " : 0u;\n";
   o << "  lvl[0]++;\n";
   // level execution counters live in registers during the call
@@ -343,7 +423,7 @@ std::string SrcGen::unit_fn_count(const std::string& fname) {
   luts(1, "    ");
   if (p.levels[1].has_acc && last > 1)
     o << "    if (!__any_sync(FBG_FULL, " << any_nonzero(p.levels[1].acc) << ")) continue;\n";
-  o << "    fbg_u32 ucnt = 0;\n";
+  o << "    fbg_u32 ucnt = 0, ucnt2 = 0, ucnt4 = 0, ucnt8 = 0;\n";
   std::string ind = "    ";
   for (int lv = 2; lv < nl; lv++) {
     if (lv == unroll_lv) break;
@@ -359,18 +439,20 @@ std::string SrcGen::unit_fn_count(const std::string& fname) {
   }
   if (unroll_lv >= 0) {
     o << ind << "it" << unroll_lv << "++;\n";
-    for (int c = 0; c < (1 << unroll_bits); c++) {
-      for (auto& st : ustmt[(size_t)c]) o << ind << st << "\n";
-      for (int s = 0; s < nreg; s++) o << ind << "ucnt += __popc(" << operand(p.out, s, c) << " & tm);\n";
-    }
+    std::vector<std::vector<Sym>> words((size_t)(1 << unroll_bits));
+    for (int c = 0; c < (1 << unroll_bits); c++)
+      for (int s = 0; s < nreg; s++) words[(size_t)c].push_back(operand_sym(p.out, s, c));
+    emit_counts(&ustmt, words, ops[(size_t)unroll_lv], ind);
   } else {
-    for (int s = 0; s < nreg; s++) o << ind << "ucnt += __popc(" << operand(p.out, s) << " & tm);\n";
+    std::vector<std::vector<Sym>> words(1);
+    for (int s = 0; s < nreg; s++) words[0].push_back(operand_sym(p.out, s, -1));
+    emit_counts(nullptr, words, ops[(size_t)last], ind);
   }
   for (int lv = (unroll_lv >= 0 ? unroll_lv - 1 : last); lv >= 2; lv--) {
     ind.resize(ind.size() - 2);
     o << ind << "}\n";
   }
-  o << "    total += ucnt;\n";
+  o << "    total += (fbg_u64)ucnt + 2ull * ucnt2 + 4ull * ucnt4 + 8ull * ucnt8;\n";
   o << "  }\n";
   for (int lv = 1; lv < nl; lv++) o << "  lvl[" << lv << "] += it" << lv << ";\n";
   o << "  return total;\n";
@@ -459,38 +541,62 @@ std::string SrcGen::unit_fn_table(const std::string& fname) {
   return o.str();
 }
 
+// The kernels.  Count mode: the work items are (warp slice w, unit v) pairs,
+// w-major, so that a warp pulls its own items and never waits for the other
+// warps of its block; item t of the R = unit_end - unit_begin units is
+// w = t / R, v = unit_begin + t % R, and the warp evaluates it with the warp
+// bits of w.  Table mode: a block pulls whole units (its stores are dense and
+// the work per unit is even).
 std::string SrcGen::generate(int mode, int block, int minb) {
   const char* kname = mode == 0 ? "fbg_jit_count" : "fbg_jit_table";
   if (mode == 0) unit_fn_count("fbg_unit_count");
   else unit_fn_table("fbg_unit_table");
   o << "extern \"C\" __global__ void __launch_bounds__(" << block << ", " << minb << ") " << kname << "(FbgLaunch P) {\n";
+  if (mode == 0) {
+    o << "  fbg_u64 lvl[" << nl << "] = {0};\n";
+    o << "  fbg_u64 total = 0;\n";
+    o << "  const fbg_u32 lane = threadIdx.x & 31u;\n";
+    o << "  const fbg_u64 chunk = P.chunk ? P.chunk : 1ull;\n";
+    o << "  const fbg_u64 R = P.unit_end - P.unit_begin;\n";
+    o << "  const fbg_u64 items = R << " << L.warp_bits << ";\n";
+    o << "  for (;;) {\n";
+    o << "    fbg_u64 t = fbg_next_items_warp(P, chunk);\n";
+    o << "    if (t >= items) break;\n";
+    o << "    const fbg_u64 e = t + chunk < items ? t + chunk : items;\n";
+    o << "    while (t < e) {\n";
+    o << "      const fbg_u64 w = t / R, v0 = t - w * R;\n";
+    o << "      const fbg_u64 span = (e - t) < (R - v0) ? (e - t) : (R - v0);\n";
+    o << "      const fbg_u32 tb = lane | ((fbg_u32)w << 5);\n";
+    o << "      if (P.unit_counts) {\n";
+    o << "        for (fbg_u64 v = v0; v < v0 + span; ++v) {\n";
+    o << "          const fbg_u64 c = fbg_unit_count(P.unit_begin + v, P.unit_begin + v + 1, tb, lvl);\n";
+    o << "          total += c;\n";
+    o << "          const fbg_u64 ws = fbg_warp_sum(c);\n";
+    o << "          if (lane == 0u && ws) atomicAdd(P.unit_counts + v, ws);\n";
+    o << "        }\n";
+    o << "      } else {\n";
+    o << "        total += fbg_unit_count(P.unit_begin + v0, P.unit_begin + v0 + span, tb, lvl);\n";
+    o << "      }\n";
+    o << "      t += span;\n";
+    o << "    }\n";
+    o << "  }\n";
+    o << "  total = fbg_warp_sum(total);\n";
+    o << "  if (lane == 0u && total) atomicAdd(P.count, total);\n";
+    o << "  if (P.iters && lane == 0u) {\n";
+    o << "    for (int l = 0; l < " << nl << "; l++) if (lvl[l]) atomicAdd(P.iters + l, lvl[l]);\n";
+    o << "  }\n";
+    o << "}\n";
+    return o.str();
+  }
   o << "  fbg_u64 lvl[" << nl << "] = {0};\n";
-  o << "  fbg_u64 total = 0;\n";
   o << "  __shared__ fbg_u64 s_unit;\n";
   o << "  const fbg_u64 chunk = P.chunk ? P.chunk : 1ull;\n";
   o << "  for (;;) {\n";
   o << "    const fbg_u64 u = fbg_next_units(P, &s_unit, chunk);\n";
   o << "    if (u >= P.unit_end) break;\n";
   o << "    const fbg_u64 e = u + chunk < P.unit_end ? u + chunk : P.unit_end;\n";
-  if (mode == 0) {
-    o << "    if (P.unit_counts) {\n";
-    o << "      for (fbg_u64 v = u; v < e; ++v) {\n";
-    o << "        const fbg_u64 c = fbg_unit_count(v, v + 1, lvl);\n";
-    o << "        total += c;\n";
-    o << "        const fbg_u64 w = fbg_warp_sum(c);\n";
-    o << "        if ((threadIdx.x & 31u) == 0u && w) atomicAdd(P.unit_counts + (v - P.unit_begin), w);\n";
-    o << "      }\n";
-    o << "    } else {\n";
-    o << "      total += fbg_unit_count(u, e, lvl);\n";
-    o << "    }\n";
-  } else {
-    o << "    for (fbg_u64 v = u; v < e; ++v) fbg_unit_table(v, P.table, lvl);\n";
-  }
+  o << "    for (fbg_u64 v = u; v < e; ++v) fbg_unit_table(v, P.table, lvl);\n";
   o << "  }\n";
-  if (mode == 0) {
-    o << "  total = fbg_warp_sum(total);\n";
-    o << "  if ((threadIdx.x & 31u) == 0u && total) atomicAdd(P.count, total);\n";
-  }
   o << "  if (P.iters && (threadIdx.x & 31u) == 0u) {\n";
   o << "    for (int l = 0; l < " << nl << "; l++) if (lvl[l]) atomicAdd(P.iters + l, lvl[l]);\n";
   o << "  }\n";

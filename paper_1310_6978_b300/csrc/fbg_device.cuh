@@ -53,6 +53,15 @@ __device__ __forceinline__ fbg_u64 fbg_next_unit(const FbgLaunch& P, fbg_u64* s_
 }
 
 // fetch the next `chunk` units for the whole block
+// The next chunk of work items for the calling warp: lane 0 draws from the
+// counter and the other lanes receive the index; no block barrier, so a warp
+// never waits for the other warps of its block.
+__device__ __forceinline__ fbg_u64 fbg_next_items_warp(const FbgLaunch& P, fbg_u64 chunk) {
+  fbg_u64 i = 0;
+  if ((threadIdx.x & 31u) == 0u) i = atomicAdd(P.unit_ctr, chunk);
+  return __shfl_sync(0xffffffffu, i, 0);
+}
+
 __device__ __forceinline__ fbg_u64 fbg_next_units(const FbgLaunch& P, fbg_u64* s_unit, fbg_u64 chunk) {
   if (threadIdx.x == 0) *s_unit = P.unit_begin + atomicAdd(P.unit_ctr, chunk);
   __syncthreads();

@@ -1,7 +1,8 @@
 """Compile the generated CUDA source of the specialised kernels as host C++
 (test infrastructure).  The kernel body is straight-line integer code; the
 few device builtins it uses get host stand-ins here, and one "thread" runs at
-a time over all units.  Warp votes become per-thread votes (a thread skips
+a time over all units (count mode: the lanes of one warp over every
+(warp slice, unit) item).  Warp votes become per-thread votes (a thread skips
 only levels whose partial conjunction is zero for itself, so counts and
 tables are unchanged) and warp sums add over the lanes of a warp, run from
 lane 31 down to lane 0.  This checks the emitter (folding, loops, stores) on
@@ -53,6 +54,7 @@ static inline uint4 make_uint4(fbg_u32 a, fbg_u32 b, fbg_u32 c, fbg_u32 d) { ret
 static fbg_u64 g_next = 0;
 static inline fbg_u64 fbg_next_unit(const FbgLaunch& P, fbg_u64*) { return P.unit_begin + g_next++; }
 static inline fbg_u64 fbg_next_units(const FbgLaunch& P, fbg_u64*, fbg_u64 c) { fbg_u64 u = P.unit_begin + g_next; g_next += c; return u; }
+static inline fbg_u64 fbg_next_items_warp(const FbgLaunch&, fbg_u64 c) { fbg_u64 i = g_next; g_next += c; return i; }
 '''
 
 DRIVER = r'''
@@ -62,7 +64,9 @@ extern "C" int run(int mode, int block, unsigned long long nunits, unsigned long
   unsigned long long cnt = 0, ctr = 0;
   P.count = &cnt; P.unit_ctr = &ctr; P.table = table; P.unit_begin = 0; P.unit_end = nunits;
   P.chunk = nunits > 4 ? 3 : 1;   // ragged last chunk
-  for (int w = 0; w < block / 32 || w == 0; w++) {
+  // count mode: one warp's lanes see every (warp slice, unit) item; table
+  // mode: every thread of a block sees every unit
+  for (int w = 0; w < (mode == 0 ? 1 : block / 32) || w == 0; w++) {
     for (int lane = 31; lane >= 0; lane--) {
       threadIdx.x = (unsigned)(w * 32 + lane);
       if ((int)threadIdx.x >= block) continue;
