@@ -94,7 +94,9 @@ enum {
   FBG_OPT_LOOP_LEVEL_BITS = 6, /* bits per loop level (default 4) */
   FBG_OPT_SEARCH_ORDER = 7,    /* counts: 1 (default) heuristic variable order, 0 identity */
   FBG_OPT_MIN_BLOCKS = 8,      /* JIT: __launch_bounds__ min blocks per SM (default 2) */
-  FBG_OPT_STATS = 9            /* 1: record executed level iterations (fbg_exec_stats) */
+  FBG_OPT_STATS = 9            /* 1: kernels carry level counters and record executed level
+                                  iterations (fbg_exec_stats); changing it rebuilds the
+                                  kernels and drops a unit order (fbg_schedule_units) */
 };
 
 typedef struct {
@@ -234,6 +236,35 @@ fbg_status fbg_program_source(fbg_program *prog, int mode, char *buf, size_t *le
  * not evaluate anything.  *len receives the size; buf may be NULL.
  */
 fbg_status fbg_debug_dump(fbg_program *prog, int which, char *buf, size_t *len);
+
+/* Longest-first unit order (no counterpart in the paper).  The work of a
+ * unit of fbg_unit_vars depends on how much of its subspace the level
+ * conjunctions prune, and a few heavy units can keep a few SMs busy long
+ * after the rest are idle.  This call runs one count launch that times every
+ * item (unit, warp slice) on the GPU's nanosecond timer, sorts the items by
+ * time, longest first, and keeps that order on the device: later full-range
+ * counts of the program through fbg_count and fbg_count_async hand out items
+ * in it.  Results do not depend on the order.  The
+ * order is dropped when an option rebuilds the kernel.  Synchronises the
+ * stream; allocates 8 bytes per item temporarily and keeps 4 bytes per item.
+ * FBG_EINVAL when the program does not use the NVRTC engine, FBG_ETOOBIG
+ * above 2^26 items. */
+fbg_status fbg_schedule_units(fbg_program *prog, void *stream);
+
+/* Diagnostics (no counterpart in the paper): one count launch of the NVRTC
+ * engine that records, per unit u of fbg_unit_vars, dev_trace[2u] = the
+ * nanoseconds all warps spent on u (summed over warp slices) and
+ * dev_trace[2u+1] = the earliest start time of u on the GPU's nanosecond timer.
+ * dev_trace: device memory of 2 * nunits u64 words, caller-owned, written
+ * whole; nunits must equal the unit count.  Units are evaluated one at a time
+ * while tracing, so the launch is slower than fbg_count.  Synchronises the
+ * stream.  FBG_EINVAL when the program does not use the NVRTC engine. */
+fbg_status fbg_debug_unit_trace(fbg_program *prog, void *stream, uint64_t *dev_trace, uint64_t nunits);
+
+/* Diagnostics: the per-item times that fbg_schedule_units sorts.  dev_ns[u *
+ * S + w] = nanoseconds the warp spent on unit u, warp slice w (S = 2^warp
+ * bits of the layout, fbg_debug_dump); nitems must be nunits * S. */
+fbg_status fbg_debug_item_trace(fbg_program *prog, void *stream, uint64_t *dev_ns, uint64_t nitems);
 
 /*
  * Diagnostics without a device: the NVRTC source of the hybrid batch kernel

@@ -104,6 +104,23 @@ class Program:
     def count_units(self, dev_counts, stream=None) -> None:
         self._L.check(self._L.lib.fbg_count_units(self._h, _stream_ptr(stream), _ptr(dev_counts), dev_counts.numel()))
 
+    def schedule_units(self, stream=None) -> "Program":
+        """fbg_schedule_units: time every (unit, warp slice) item once and hand
+        items out longest first in later full-range counts."""
+        self._L.check(self._L.lib.fbg_schedule_units(self._h, _stream_ptr(stream)))
+        return self
+
+    def debug_item_trace(self, dev_ns, stream=None) -> None:
+        """fbg_debug_item_trace: nanoseconds per (unit, warp slice) item."""
+        self._L.check(self._L.lib.fbg_debug_item_trace(self._h, _stream_ptr(stream), _ptr(dev_ns), dev_ns.numel()))
+
+    def debug_unit_trace(self, dev_trace, stream=None) -> None:
+        """fbg_debug_unit_trace: per unit u, dev_trace[2u] = warp-nanoseconds
+        spent and dev_trace[2u+1] = earliest start (GPU timer, ns); dev_trace
+        holds 2 * nunits int64 words."""
+        self._L.check(self._L.lib.fbg_debug_unit_trace(self._h, _stream_ptr(stream), _ptr(dev_trace),
+                                                       dev_trace.numel() // 2))
+
     def table_words(self) -> int:
         return 1 if self.n <= 6 else 1 << (self.n - 6)
 

@@ -84,6 +84,7 @@ fbg_status ensure_scratch(fbg_program* p, size_t words) {
   if (p->d_scratch) cudaFree(p->d_scratch);
   p->d_scratch = nullptr;
   p->scratch_words = 0;
+  p->scratch_clean = false;
   CK(cudaMalloc(&p->d_scratch, words * sizeof(unsigned long long)));
   p->scratch_words = words;
   return FBG_OK;
@@ -140,7 +141,8 @@ fbg_status build_jit(fbg_program* p, int mode) {
     b.lp = lower_and_map(p->g, L);
     if (!p->opt_prune) strip_prune(b.lp);
     b.block = b.lp.layout.lane_bits < 5 ? 32 : 32 << b.lp.layout.warp_bits;
-    b.src = emit_cuda_source(b.lp, mode, b.block, (int)p->opt_min_blocks, &b.ops, &b.unrolled_level);
+    b.src = emit_cuda_source(b.lp, mode, b.block, (int)p->opt_min_blocks, &b.ops, &b.unrolled_level,
+                             p->opt_stats != 0);
   } catch (CompileError& e) {
     return set_error(FBG_ETOOBIG, e.msg);
   }
@@ -180,9 +182,14 @@ fbg_status pick_engine(fbg_program* p, int mode, bool* use_jit) {
 // scratch words: [0] unit counter [1] count [2] item counter [3] total
 // [4,20) level iterations, then two arrays of `units` words
 constexpr size_t kScratchHead = 32;
+// scratch head: [0] item counter, [1] count of fbg_count, [2] [3] interpreter
+// counters, [4..20) level iterations, [24] [25] running sum and finished
+// warps of self-resetting counts
+constexpr size_t kScratchAcc = 24, kScratchDone = 25;
 
 fbg_status launch_count(fbg_program* p, cudaStream_t st, unsigned long long* dev_count, unsigned long long* unit_counts,
-                        bool* used_jit, uint64_t ubegin = 0, uint64_t uend = ~0ull) {
+                        bool* used_jit, uint64_t ubegin = 0, uint64_t uend = ~0ull,
+                        unsigned long long* unit_trace = nullptr, unsigned long long* item_trace = nullptr) {
   bool jit = false;
   fbg_status s = pick_engine(p, 0, &jit);
   if (s != FBG_OK) return s;
@@ -197,10 +204,18 @@ fbg_status launch_count(fbg_program* p, cudaStream_t st, unsigned long long* dev
   s = ensure_scratch(p, words);
   if (s != FBG_OK) return s;
   if (!dev_count) dev_count = p->d_scratch + 1;
-  CK(cudaMemsetAsync(p->d_scratch, 0, kScratchHead * 8, st));
-  if (dev_count != p->d_scratch + 1) CK(cudaMemsetAsync(dev_count, 0, 8, st));
+  // a plain count of a non-empty range with the NVRTC engine resets its own
+  // counters and writes the total: no memset is needed once the head is clean
+  bool self_reset = false;
+  if (jit) {
+    const uint64_t e = std::min<uint64_t>(uend, p->jb[0].nunits);
+    self_reset = !unit_counts && !unit_trace && !item_trace && !p->opt_stats && e > ubegin;
+  }
+  if (!self_reset || !p->scratch_clean) CK(cudaMemsetAsync(p->d_scratch, 0, kScratchHead * 8, st));
+  if (!self_reset && dev_count != p->d_scratch + 1) CK(cudaMemsetAsync(dev_count, 0, 8, st));
+  p->scratch_clean = false;
   FbgLaunch P{};
-  P.count = dev_count;
+  P.count = self_reset ? nullptr : dev_count;
   P.unit_counts = unit_counts;
   P.unit_ctr = p->d_scratch + 0;
   P.iters = p->opt_stats ? p->d_scratch + 4 : nullptr;
@@ -211,11 +226,23 @@ fbg_status launch_count(fbg_program* p, cudaStream_t st, unsigned long long* dev
     if (ubegin > uend) return set_error(FBG_EINVAL, "empty or inverted unit range");
     P.unit_begin = ubegin;
     P.unit_end = uend;
+    P.unit_trace = unit_trace;
+    P.item_trace = item_trace;
+    // the measured order covers full-range counts without per-unit outputs
+    if (b.d_perm && ubegin == 0 && uend == b.nunits && !unit_counts && !unit_trace && !item_trace)
+      P.unit_perm = b.d_perm;
     // a few fetches per resident block and unit: enough to balance pruned work
     P.chunk = std::max<uint64_t>(1, (uend - ubegin) / ((uint64_t)b.grid * 16));
+    if (self_reset) {
+      P.acc = p->d_scratch + kScratchAcc;
+      P.done = p->d_scratch + kScratchDone;
+      P.out = dev_count;
+      P.nwarps = (fbg_u32)((uint64_t)b.grid * (uint64_t)b.block / 32);
+    }
     void* args[] = {&P};
     if (uend > ubegin)
       CK(cudaLaunchKernel((const void*)b.kern, dim3((unsigned)b.grid), dim3((unsigned)b.block), args, 0, st));
+    p->scratch_clean = self_reset;
   } else {
     InterpBuild& b = p->ib[0];
     uend = std::min<uint64_t>(uend, b.nunits);
@@ -310,7 +337,10 @@ fbg_status fbg_set_option(fbg_program* p, int option, int64_t v) {
       if (v < 1 || v > 32) return bad();
       p->opt_min_blocks = v;
       break;
-    case FBG_OPT_STATS: p->opt_stats = v ? 1 : 0; return FBG_OK;
+    case FBG_OPT_STATS:   // kernels carry level counters only while statistics are on
+      if (p->opt_stats == (v ? 1 : 0)) return FBG_OK;
+      p->opt_stats = v ? 1 : 0;
+      break;
     default: return set_error(FBG_EINVAL, "unknown option");
   }
   p->invalidate();
@@ -429,6 +459,89 @@ fbg_status fbg_count_units(fbg_program* p, void* stream, uint64_t* dev_counts, u
   return FBG_OK;
 }
 
+fbg_status fbg_schedule_units(fbg_program* p, void* stream) {
+  if (!p) return set_error(FBG_EINVAL, "null argument");
+  if (p->n > 63) return set_error(FBG_ETOOBIG, "counts need n <= 63");
+  bool jit = false;
+  fbg_status s = pick_engine(p, 0, &jit);
+  if (s != FBG_OK) return s;
+  if (!jit) return set_error(FBG_EINVAL, "unit schedules need the NVRTC engine");
+  JitBuild& b = p->jb[0];
+  const int wb = b.lp.layout.warp_bits;
+  const uint64_t items = b.nunits << wb;
+  if (items > (1ull << 26)) return set_error(FBG_ETOOBIG, "too many items to schedule");
+  cudaStream_t st = (cudaStream_t)stream;
+  s = ensure_scratch(p, kScratchHead);
+  if (s != FBG_OK) return s;
+  b.free_device();   // measure in the natural order
+  unsigned long long* d_tr = nullptr;
+  CK(cudaMalloc(&d_tr, items * 8));
+  std::vector<uint64_t> ns((size_t)items);
+  cudaError_t e = cudaMemsetAsync(d_tr, 0, items * 8, st);
+  if (e == cudaSuccess) {
+    s = launch_count(p, st, nullptr, nullptr, &jit, 0, ~0ull, nullptr, d_tr);
+    if (s == FBG_OK) e = cudaMemcpyAsync(ns.data(), d_tr, items * 8, cudaMemcpyDeviceToHost, st);
+    if (s == FBG_OK && e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  cudaFree(d_tr);
+  if (s != FBG_OK) return s;
+  if (e != cudaSuccess) return cuda_error(e, "fbg_schedule_units trace");
+  // longest processing time first; ties keep the natural (unit, slice) order
+  std::vector<unsigned> perm((size_t)items);
+  for (uint64_t t = 0; t < items; t++) perm[(size_t)t] = (unsigned)t;
+  std::stable_sort(perm.begin(), perm.end(), [&](unsigned x, unsigned y) { return ns[x] > ns[y]; });
+  unsigned* d_perm = nullptr;
+  CK(cudaMalloc(&d_perm, items * 4));
+  e = cudaMemcpyAsync(d_perm, perm.data(), items * 4, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaFree(d_perm);
+    return cuda_error(e, "fbg_schedule_units upload");
+  }
+  b.d_perm = d_perm;
+  return FBG_OK;
+}
+
+fbg_status fbg_debug_item_trace(fbg_program* p, void* stream, uint64_t* dev_ns, uint64_t nitems) {
+  if (!p || !dev_ns) return set_error(FBG_EINVAL, "null argument");
+  bool jit = false;
+  fbg_status s = pick_engine(p, 0, &jit);
+  if (s != FBG_OK) return s;
+  if (!jit) return set_error(FBG_EINVAL, "item traces need the NVRTC engine");
+  const JitBuild& b = p->jb[0];
+  const uint64_t items = b.nunits << b.lp.layout.warp_bits;
+  if (nitems != items) return set_error(FBG_EINVAL, "nitems must be " + std::to_string(items));
+  cudaStream_t st = (cudaStream_t)stream;
+  s = ensure_scratch(p, kScratchHead);
+  if (s != FBG_OK) return s;
+  CK(cudaMemsetAsync(dev_ns, 0, items * 8, st));
+  s = launch_count(p, st, nullptr, nullptr, &jit, 0, ~0ull, nullptr, (unsigned long long*)dev_ns);
+  if (s != FBG_OK) return s;
+  CK(cudaStreamSynchronize(st));
+  return FBG_OK;
+}
+
+fbg_status fbg_debug_unit_trace(fbg_program* p, void* stream, uint64_t* dev_trace, uint64_t nunits) {
+  if (!p || !dev_trace) return set_error(FBG_EINVAL, "null argument");
+  int vars[64], nv = 0;
+  uint64_t nu = 0;
+  fbg_status s = fbg_unit_vars(p, vars, 64, &nv, &nu);
+  if (s != FBG_OK) return s;
+  if (nunits != nu) return set_error(FBG_EINVAL, "nunits must be " + std::to_string(nu));
+  bool jit = false;
+  s = pick_engine(p, 0, &jit);
+  if (s != FBG_OK) return s;
+  if (!jit) return set_error(FBG_EINVAL, "unit traces need the NVRTC engine");
+  cudaStream_t st = (cudaStream_t)stream;
+  // durations 0, start times all-ones (the kernel takes the minimum)
+  CK(cudaMemsetAsync(dev_trace, 0xFF, nunits * 16, st));
+  CK(cudaMemset2DAsync(dev_trace, 16, 0, 8, nunits, st));
+  s = launch_count(p, st, nullptr, nullptr, &jit, 0, ~0ull, (unsigned long long*)dev_trace);
+  if (s != FBG_OK) return s;
+  CK(cudaStreamSynchronize(st));
+  return FBG_OK;
+}
+
 fbg_status fbg_truth_table(fbg_program* p, void* stream, uint64_t* dev_words, size_t nwords) {
   if (!p || !dev_words) return set_error(FBG_EINVAL, "null argument");
   if (p->n > 40) return set_error(FBG_ETOOBIG, "truth tables need n <= 40");
@@ -441,6 +554,7 @@ fbg_status fbg_truth_table(fbg_program* p, void* stream, uint64_t* dev_words, si
   s = ensure_scratch(p, kScratchHead);
   if (s != FBG_OK) return s;
   CK(cudaMemsetAsync(p->d_scratch, 0, kScratchHead * 8, st));
+  p->scratch_clean = false;
   FbgLaunch P{};
   P.table = (fbg_u32*)dev_words;
   P.unit_ctr = p->d_scratch + 0;
@@ -476,6 +590,7 @@ fbg_status fbg_enumerate_models(fbg_program* p, void* stream, uint64_t* dev_mode
   unsigned long long* unit_counts = p->d_scratch + kScratchHead;
   unsigned long long* offsets = unit_counts + b.nunits;
   CK(cudaMemsetAsync(p->d_scratch, 0, (kScratchHead + b.nunits) * 8, st));
+  p->scratch_clean = false;
   FbgLaunch P{};
   P.unit_ctr = p->d_scratch + 0;
   P.unit_begin = 0;

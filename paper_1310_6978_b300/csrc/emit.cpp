@@ -43,8 +43,10 @@ struct Sym {
 // generator words are constants, so the copy is folded further.
 class SrcGen {
  public:
-  explicit SrcGen(const LutProgram& prog)
-      : p(prog), L(prog.layout), nreg(1 << prog.layout.r), nl(prog.layout.nlevels()) {
+  // counters: count level executions (lvl[]) for fbg_exec_stats; a kernel
+  // built without them spends no instructions or registers on them
+  explicit SrcGen(const LutProgram& prog, bool counters = true)
+      : p(prog), L(prog.layout), nreg(1 << prog.layout.r), nl(prog.layout.nlevels()), counters_(counters) {
     if (nl > 2 && L.loop_bits.back() <= 5) {
       unroll_lv = nl - 1;
       unroll_bits = L.loop_bits.back();
@@ -67,6 +69,7 @@ class SrcGen {
   const LutProgram& p;
   const Layout& L;
   int nreg, nl;
+  bool counters_;
   int unroll_bits = 0, unroll_base = 0;
   std::vector<std::vector<Sym>> sym;                  // [lut][s], levels other than unroll_lv
   std::vector<std::vector<std::string>> code;         // real lop3 calls of those
@@ -407,9 +410,11 @@ std::string SrcGen::unit_fn_count(const std::string& fname) {
   const int last = nl - 1;
   o << "__device__ __noinline__ fbg_u64 " << fname << "(fbg_u64 u0, fbg_u64 u1, fbg_u32 tb, fbg_u64* lvl) {\n";
   o << "  const fbg_u32 tm = (tb < " << tvalid << "u) ? " << hex32(valid_mask()) << " : 0u;\n";
-  o << "  lvl[0]++;\n";
-  // level execution counters live in registers during the call
-  for (int lv = 1; lv < nl; lv++) o << "  fbg_u32 it" << lv << " = 0;\n";
+  if (counters_) {
+    o << "  lvl[0]++;\n";
+    // level execution counters live in registers during the call
+    for (int lv = 1; lv < nl; lv++) o << "  fbg_u32 it" << lv << " = 0;\n";
+  }
   var_words(vars[0], "tb", L.first_lane_pos(), "  ", false);
   declare_level(0, "  ");
   luts(0, "  ");
@@ -417,7 +422,7 @@ std::string SrcGen::unit_fn_count(const std::string& fname) {
     o << "  if (!__any_sync(FBG_FULL, " << any_nonzero(p.levels[0].acc) << ")) return 0;\n";
   o << "  fbg_u64 total = 0;\n";
   o << "  for (fbg_u64 u = u0; u < u1; ++u) {\n";
-  o << "    it1++;\n";
+  if (counters_) o << "    it1++;\n";
   var_words(vars[1], "u", L.first_unit_pos(), "    ", true);
   declare_level(1, "    ");
   luts(1, "    ");
@@ -430,7 +435,7 @@ std::string SrcGen::unit_fn_count(const std::string& fname) {
     std::string iv = "i" + std::to_string(lv);
     o << ind << "for (fbg_u32 " << iv << " = 0; " << iv << " < " << (1u << L.loop_bits[(size_t)(lv - 2)]) << "u; ++" << iv << ") {\n";
     ind += "  ";
-    o << ind << "it" << lv << "++;\n";
+    if (counters_) o << ind << "it" << lv << "++;\n";
     var_words(vars[(size_t)lv], iv, L.loop_pos(lv - 2), ind, false);
     declare_level(lv, ind);
     luts(lv, ind);
@@ -438,7 +443,7 @@ std::string SrcGen::unit_fn_count(const std::string& fname) {
       o << ind << "if (!__any_sync(FBG_FULL, " << any_nonzero(p.levels[(size_t)lv].acc) << ")) continue;\n";
   }
   if (unroll_lv >= 0) {
-    o << ind << "it" << unroll_lv << "++;\n";
+    if (counters_) o << ind << "it" << unroll_lv << "++;\n";
     std::vector<std::vector<Sym>> words((size_t)(1 << unroll_bits));
     for (int c = 0; c < (1 << unroll_bits); c++)
       for (int s = 0; s < nreg; s++) words[(size_t)c].push_back(operand_sym(p.out, s, c));
@@ -454,7 +459,8 @@ std::string SrcGen::unit_fn_count(const std::string& fname) {
   }
   o << "    total += (fbg_u64)ucnt + 2ull * ucnt2 + 4ull * ucnt4 + 8ull * ucnt8;\n";
   o << "  }\n";
-  for (int lv = 1; lv < nl; lv++) o << "  lvl[" << lv << "] += it" << lv << ";\n";
+  if (counters_)
+    for (int lv = 1; lv < nl; lv++) o << "  lvl[" << lv << "] += it" << lv << ";\n";
   o << "  return total;\n";
   o << "}\n";
   return o.str();
@@ -541,12 +547,15 @@ std::string SrcGen::unit_fn_table(const std::string& fname) {
   return o.str();
 }
 
-// The kernels.  Count mode: the work items are (warp slice w, unit v) pairs,
-// w-major, so that a warp pulls its own items and never waits for the other
-// warps of its block; item t of the R = unit_end - unit_begin units is
-// w = t / R, v = unit_begin + t % R, and the warp evaluates it with the warp
-// bits of w.  Table mode: a block pulls whole units (its stores are dense and
-// the work per unit is even).
+// The kernels.  Count mode: the work items are (warp slice w, unit v) pairs
+// that a warp pulls by itself, never waiting for the other warps of its
+// block; the warp evaluates an item with the warp bits of w.  Without an
+// order the items go out w-major (item t of the R = unit_end - unit_begin
+// units is w = t / R, v = t % R) in chunks of consecutive units, which one
+// call evaluates with its thread-level values computed once; with an order
+// (P.unit_perm, longest measured items first) item t is P.unit_perm[t].
+// Table mode: a block pulls whole units (its stores are dense and the work
+// per unit is even).
 std::string SrcGen::generate(int mode, int block, int minb) {
   const char* kname = mode == 0 ? "fbg_jit_count" : "fbg_jit_table";
   if (mode == 0) unit_fn_count("fbg_unit_count");
@@ -563,16 +572,31 @@ std::string SrcGen::generate(int mode, int block, int minb) {
     o << "    fbg_u64 t = fbg_next_items_warp(P, chunk);\n";
     o << "    if (t >= items) break;\n";
     o << "    const fbg_u64 e = t + chunk < items ? t + chunk : items;\n";
+    o << "    if (P.unit_perm) {\n";
+    o << "      for (; t < e; ++t) {\n";
+    o << "        const fbg_u32 it = P.unit_perm[t];\n";
+    o << "        const fbg_u64 v = it >> " << L.warp_bits << ";\n";
+    o << "        const fbg_u32 tb = lane | ((it & " << ((1u << L.warp_bits) - 1u) << "u) << 5);\n";
+    o << "        total += fbg_unit_count(P.unit_begin + v, P.unit_begin + v + 1, tb, lvl);\n";
+    o << "      }\n";
+    o << "      continue;\n";
+    o << "    }\n";
     o << "    while (t < e) {\n";
     o << "      const fbg_u64 w = t / R, v0 = t - w * R;\n";
     o << "      const fbg_u64 span = (e - t) < (R - v0) ? (e - t) : (R - v0);\n";
     o << "      const fbg_u32 tb = lane | ((fbg_u32)w << 5);\n";
-    o << "      if (P.unit_counts) {\n";
+    o << "      if (P.unit_counts || P.unit_trace || P.item_trace) {\n";
     o << "        for (fbg_u64 v = v0; v < v0 + span; ++v) {\n";
+    o << "          const fbg_u64 t0 = (P.unit_trace || P.item_trace) ? fbg_globaltimer() : 0ull;\n";
     o << "          const fbg_u64 c = fbg_unit_count(P.unit_begin + v, P.unit_begin + v + 1, tb, lvl);\n";
     o << "          total += c;\n";
     o << "          const fbg_u64 ws = fbg_warp_sum(c);\n";
-    o << "          if (lane == 0u && ws) atomicAdd(P.unit_counts + v, ws);\n";
+    o << "          if (lane == 0u && ws && P.unit_counts) atomicAdd(P.unit_counts + v, ws);\n";
+    o << "          if (lane == 0u && P.unit_trace) {\n";
+    o << "            atomicAdd(P.unit_trace + 2 * v, fbg_globaltimer() - t0);\n";
+    o << "            atomicMin(P.unit_trace + 2 * v + 1, t0);\n";
+    o << "          }\n";
+    o << "          if (lane == 0u && P.item_trace) P.item_trace[(v << " << L.warp_bits << ") | w] = fbg_globaltimer() - t0;\n";
     o << "        }\n";
     o << "      } else {\n";
     o << "        total += fbg_unit_count(P.unit_begin + v0, P.unit_begin + v0 + span, tb, lvl);\n";
@@ -581,7 +605,11 @@ std::string SrcGen::generate(int mode, int block, int minb) {
     o << "    }\n";
     o << "  }\n";
     o << "  total = fbg_warp_sum(total);\n";
-    o << "  if (lane == 0u && total) atomicAdd(P.count, total);\n";
+    o << "  if (P.done) {\n";
+    o << "    if (lane == 0u) fbg_finish_count(P, total);\n";
+    o << "  } else if (lane == 0u && total) {\n";
+    o << "    atomicAdd(P.count, total);\n";
+    o << "  }\n";
     o << "  if (P.iters && lane == 0u) {\n";
     o << "    for (int l = 0; l < " << nl << "; l++) if (lvl[l]) atomicAdd(P.iters + l, lvl[l]);\n";
     o << "  }\n";
@@ -610,13 +638,13 @@ std::string SrcGen::generate_batch_fn(const std::string& fname) { return unit_fn
 }  // namespace
 
 std::string emit_batch_function(const LutProgram& p, const std::string& fname) {
-  SrcGen g(p);
+  SrcGen g(p, false);
   return g.generate_batch_fn(fname);
 }
 
 std::string emit_cuda_source(const LutProgram& p, int mode, int block, int minblocks,
-                             std::vector<long long>* ops_per_level, int* unrolled_level) {
-  SrcGen g(p);
+                             std::vector<long long>* ops_per_level, int* unrolled_level, bool counters) {
+  SrcGen g(p, counters);
   std::string src = g.generate(mode, block, minblocks);
   if (ops_per_level) *ops_per_level = g.ops;
   if (unrolled_level) *unrolled_level = g.unroll_lv;

@@ -16,7 +16,8 @@ namespace fbg {
 // level whose 2^b iterations are emitted as one folded straight-line block
 // (one "execution" of that level covers all its iterations), or -1.
 std::string emit_cuda_source(const LutProgram& p, int mode, int block, int minblocks,
-                             std::vector<long long>* ops_per_level = nullptr, int* unrolled_level = nullptr);
+                             std::vector<long long>* ops_per_level = nullptr, int* unrolled_level = nullptr,
+                             bool counters = true);
 
 // device function `fname(u0, u1)`: this thread's model count over the units
 // [u0, u1) of p's layout (the count body, for the batch kernel)

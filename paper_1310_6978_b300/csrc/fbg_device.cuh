@@ -19,6 +19,16 @@ struct FbgLaunch {
   fbg_u64 cap;             // enumerate: capacity of `models`
   fbg_u64 unit_begin, unit_end;
   fbg_u64 chunk;           // units fetched per counter increment (0 = 1)
+  fbg_u64* unit_trace;     // optional diagnostics (count mode): per unit (index u - unit_begin)
+                           // [2u] += warp-nanoseconds spent, [2u+1] = min start time (ns)
+  fbg_u64* item_trace;     // optional (count mode): nanoseconds of item (unit u, warp slice w)
+                           // at index (u - unit_begin) * slices + w
+  const fbg_u32* unit_perm;  // optional (count mode, full range): the order in which items are
+                             // handed out, each entry u << warp_bits | w
+  fbg_u64* acc;            // self-resetting count (count mode, when done is set): running sum,
+  fbg_u64* done;           //   warps finished, the destination of the total, warps in the grid;
+  fbg_u64* out;            //   acc, done and unit_ctr are zero before the launch and after it
+  fbg_u32 nwarps;
 };
 
 #define FBG_FULL 0xffffffffu
@@ -53,6 +63,29 @@ __device__ __forceinline__ fbg_u64 fbg_next_unit(const FbgLaunch& P, fbg_u64* s_
 }
 
 // fetch the next `chunk` units for the whole block
+// the global nanosecond timer (diagnostics only)
+__device__ __forceinline__ fbg_u64 fbg_globaltimer() {
+  fbg_u64 t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Self-resetting count, which needs no memset before a launch: every warp
+// adds its total to *acc and then counts itself done; the warp that finishes
+// last writes the sum to *out and zeroes acc, done and the item counter for
+// the next launch.  No warp waits for another (call from one lane per warp).
+__device__ __forceinline__ void fbg_finish_count(const FbgLaunch& P, fbg_u64 total) {
+  if (total) atomicAdd(P.acc, total);
+  __threadfence();
+  if (atomicAdd(P.done, 1ull) == (fbg_u64)P.nwarps - 1ull) {
+    __threadfence();
+    *P.out = atomicAdd(P.acc, 0ull);
+    *P.acc = 0ull;
+    *P.unit_ctr = 0ull;
+    *P.done = 0ull;
+  }
+}
+
 // The next chunk of work items for the calling warp: lane 0 draws from the
 // counter and the other lanes receive the index; no block barrier, so a warp
 // never waits for the other warps of its block.

@@ -42,6 +42,11 @@ struct JitBuild {
   cudaKernel_t kern = nullptr;   // owned by the process-wide JIT cache
   int block = 256, grid = 1;
   uint64_t nunits = 1;
+  unsigned* d_perm = nullptr;    // item order of full-range counts (fbg_schedule_units), or null
+  void free_device() {
+    if (d_perm) cudaFree(d_perm);
+    d_perm = nullptr;
+  }
 };
 
 fbg_status set_error(fbg_status s, const std::string& m);
@@ -62,6 +67,7 @@ struct fbg_program {
   fbg::InterpBuild ib[2];   // [0] count layout, [1] identity layout (tables, model lists)
   fbg::JitBuild jb[2];      // [0] count kernel, [1] truth-table kernel
   unsigned long long* d_scratch = nullptr;
+  bool scratch_clean = false;   // counters of self-resetting count launches are zero
   size_t scratch_words = 0;
   fbg_exec_stats last{};
   std::string jit_log;
@@ -71,10 +77,14 @@ struct fbg_program {
       b.free_device();
       b = fbg::InterpBuild{};
     }
-    for (auto& b : jb) b = fbg::JitBuild{};
+    for (auto& b : jb) {
+      b.free_device();
+      b = fbg::JitBuild{};
+    }
   }
   ~fbg_program() {
     for (auto& b : ib) b.free_device();
+    for (auto& b : jb) b.free_device();
     if (d_scratch) cudaFree(d_scratch);
   }
 };

@@ -47,6 +47,20 @@ static inline fbg_u64 fbg_warp_sum(fbg_u64 v) {
   return v;
 }
 static inline unsigned long long atomicAdd(unsigned long long* p, unsigned long long v) { auto o = *p; *p += v; return o; }
+static inline unsigned long long atomicMin(unsigned long long* p, unsigned long long v) { auto o = *p; if (v < o) *p = v; return o; }
+static inline fbg_u64 fbg_globaltimer() { return 0; }
+static inline void __threadfence() {}
+static inline void fbg_finish_count(const FbgLaunch& P, fbg_u64 total) {
+  if (total) atomicAdd(P.acc, total);
+  __threadfence();
+  if (atomicAdd(P.done, 1ull) == (fbg_u64)P.nwarps - 1ull) {
+    __threadfence();
+    *P.out = atomicAdd(P.acc, 0ull);
+    *P.acc = 0ull;
+    *P.unit_ctr = 0ull;
+    *P.done = 0ull;
+  }
+}
 struct uint2 { fbg_u32 x, y; };
 struct uint4 { fbg_u32 x, y, z, w; };
 static inline uint2 make_uint2(fbg_u32 a, fbg_u32 b) { return uint2{a, b}; }
@@ -58,9 +72,13 @@ static inline fbg_u64 fbg_next_items_warp(const FbgLaunch&, fbg_u64 c) { fbg_u64
 '''
 
 DRIVER = r'''
-extern "C" int run(int mode, int block, unsigned long long nunits, unsigned long long* count, unsigned* table) {
+extern "C" int run(int mode, int block, unsigned long long nunits, unsigned long long* count, unsigned* table,
+                   const unsigned* perm, int self_reset) {
   FbgLaunch P;
   std::memset(&P, 0, sizeof P);
+  P.unit_perm = perm;
+  unsigned long long acc = 0, done = 0, out = ~0ull;
+  if (self_reset) { P.acc = &acc; P.done = &done; P.out = &out; P.nwarps = 1; }
   unsigned long long cnt = 0, ctr = 0;
   P.count = &cnt; P.unit_ctr = &ctr; P.table = table; P.unit_begin = 0; P.unit_end = nunits;
   P.chunk = nunits > 4 ? 3 : 1;   // ragged last chunk
@@ -74,7 +92,8 @@ extern "C" int run(int mode, int block, unsigned long long nunits, unsigned long
       if (mode == 0) fbg_jit_count(P); else fbg_jit_table(P);
     }
   }
-  *count = cnt;
+  *count = self_reset ? out : cnt;
+  if (self_reset && (acc || done || cnt)) return 1;   // counters must be left zero
   return 0;
 }
 '''
@@ -95,14 +114,23 @@ def build_kernel(src: str, mode: int) -> ctypes.CDLL:
         subprocess.check_call(["g++", "-O1", "-std=c++17", "-shared", "-fPIC", "-w", "-o", so + ".tmp", cpp])
         os.replace(so + ".tmp", so)
     lib = ctypes.CDLL(so)
-    lib.run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_void_p]
+    lib.run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_void_p,
+                        ctypes.c_void_p, ctypes.c_int]
     return lib
 
 
-def run_count(src: str, block: int, nunits: int) -> int:
+def run_count(src: str, block: int, nunits: int, perm=None, self_reset: bool = False) -> int:
+    """Count; ``perm`` (uint32 array, entries unit << warp_bits | slice) is
+    the item order of a scheduled launch; ``self_reset`` runs the protocol in
+    which the last warp writes the total and zeroes the counters."""
     lib = build_kernel(src, 0)
     c = ctypes.c_ulonglong()
-    lib.run(0, block, nunits, ctypes.byref(c), None)
+    pp = None
+    if perm is not None:
+        perm = np.ascontiguousarray(perm, dtype=np.uint32)
+        pp = perm.ctypes.data_as(ctypes.c_void_p)
+    rc = lib.run(0, block, nunits, ctypes.byref(c), None, pp, 1 if self_reset else 0)
+    assert rc == 0, "counters not reset"
     return c.value
 
 
@@ -110,5 +138,5 @@ def run_table(src: str, block: int, nunits: int, nwords: int) -> np.ndarray:
     lib = build_kernel(src, 1)
     t = np.zeros(nwords, dtype=np.uint64)
     c = ctypes.c_ulonglong()
-    lib.run(1, block, nunits, ctypes.byref(c), t.ctypes.data_as(ctypes.c_void_p))
+    lib.run(1, block, nunits, ctypes.byref(c), t.ctypes.data_as(ctypes.c_void_p), None, 0)
     return t

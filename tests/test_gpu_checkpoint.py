@@ -64,3 +64,67 @@ def test_rank_slices_add_up():
     _, nunits = p.unit_vars()
     for world in (2, 3, 8):
         assert sum(p.count_range(*unit_range(nunits, r, world)) for r in range(world)) == total
+
+
+@pytest.mark.parametrize("wl", [W.TRANSITIVE6, W.TRIFREE9, W.AUT6, W.posets(5)], ids=lambda w: w.family)
+def test_scheduled_counts_unchanged(wl):
+    """fbg_schedule_units reorders the items, longest measured first; counts,
+    unit ranges and per-unit counts stay the same, and an option change drops
+    the order."""
+    import torch
+    p = F.compile(wl.text, wl.k)
+    want = p.count()
+    _, nunits = p.unit_vars()
+    per_unit = torch.zeros(nunits, dtype=torch.int64, device="cuda")
+    p.count_units(per_unit)
+    p.schedule_units()
+    out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for _ in range(3):
+        p.count_async(out)
+        assert int(out.item()) == want
+    assert p.count() == want
+    assert p.count_range(0, nunits // 2) + p.count_range(nunits // 2, nunits) == want
+    again = torch.zeros_like(per_unit)
+    p.count_units(again)
+    assert torch.equal(again, per_unit)
+    tr = torch.zeros(2 * nunits, dtype=torch.int64, device="cuda")
+    p.debug_unit_trace(tr)
+    t = tr.cpu().view(-1, 2)
+    assert int(t[:, 0].sum()) > 0 and int(t[:, 1].min()) >= 0
+    p.set_option(L.OPT_MIN_BLOCKS, 1)
+    assert p.count() == want
+
+
+def test_counts_interleaved_with_tables_and_model_lists():
+    """Plain counts reset their own counters; tables, model lists, unit
+    counts, statistics and ranges in between must not disturb them."""
+    import numpy as np
+    import torch
+    import oracle
+    wl = W.posets(5)
+    th = oracle.Theory(wl.text, wl.k)
+    want = th.count()
+    p = F.compile(wl.text, wl.k)
+    out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    words = torch.zeros(p.table_words(), dtype=torch.int64, device="cuda")
+    models = torch.zeros(8192, dtype=torch.int64, device="cuda")
+    _, nunits = p.unit_vars()
+    per_unit = torch.zeros(nunits, dtype=torch.int64, device="cuda")
+    for r in range(3):
+        assert p.count() == want
+        p.truth_table(words)
+        p.count_async(out)
+        assert int(out.item()) == want
+        assert p.enumerate_models(models) == (want, want)
+        assert p.count() == want
+        p.count_units(per_unit)
+        assert int(per_unit.sum()) == want
+        p.count_async(out)
+        p.count_async(out)
+        assert int(out.item()) == want
+        assert p.count_range(0, nunits // 3) + p.count_range(nunits // 3, nunits) == want
+        p.set_option(L.OPT_STATS, 1)
+        assert p.count() == want
+        p.set_option(L.OPT_STATS, 0)
+        assert p.count() == want
+    assert np.array_equal(words.cpu().numpy().view(np.uint64), th.table())

@@ -43,5 +43,10 @@ def test_generated_source_matches_oracle(wl, li):
         src = p.source(mode)
         if mode == 0:
             assert jit_host.run_count(src, block, nunits) == th.count()
+            # a scheduled launch: every (unit, warp slice) item once, in a shuffled order
+            items = nunits << d["warp_bits"]
+            perm = np.random.default_rng(items).permutation(items).astype(np.uint32)
+            assert jit_host.run_count(src, block, nunits, perm) == th.count()
+            assert jit_host.run_count(src, block, nunits, perm, self_reset=True) == th.count()
         else:
             assert np.array_equal(jit_host.run_table(src, block, nunits, p.table_words()), th.table())
