@@ -88,7 +88,7 @@ fbg_status enqueue(fbg_batch* b, cudaStream_t st) {
     unsigned long long nitems = b->nitems;
     const int* fid = b->d_fid;
     void* args[] = {(void*)&progs, (void*)&items, (void*)&nitems, (void*)&item_ctr, (void*)&counts, (void*)&fid};
-    CKB(cudaLaunchKernel((const void*)b->kern, dim3((unsigned)b->grid), dim3(FBG_INTERP_BLOCK), args,
+    CKB(cudaLaunchKernel((const void*)b->kern, dim3((unsigned)b->grid), dim3(FBG_INTERP_THREADS), args,
                          interp_smem_bytes(b->nslots), st));
   } else {
     CKB(launch_interp(0, b->d_progs, b->d_items, b->nitems, b->d_counts + np, b->d_counts, nullptr, P, b->nslots,
@@ -161,16 +161,14 @@ BatchPlan plan_batch(fbg_program* const* progs, int nprogs, std::string* err) {
 std::string batch_kernel_source(const std::vector<std::string>& names) {
   std::string body = "#include \"interp_device.cuh\"\n";
   for (auto& nm : names) body += "extern \"C\" __device__ fbg_u64 " + nm + "(fbg_u64 u0, fbg_u64 u1, fbg_u32 tb, fbg_u64* lvl);\n";
-  body += "extern \"C\" __global__ void __launch_bounds__(" + std::to_string(FBG_INTERP_BLOCK) +
+  body += "extern \"C\" __global__ void __launch_bounds__(" + std::to_string(FBG_INTERP_THREADS) +
           ") fbg_batch_kernel(const FbgInterpProg* __restrict__ progs, const FbgWorkItem* __restrict__ items,"
           " fbg_u64 nitems, fbg_u64* item_ctr, fbg_u64* prog_counts, const int* __restrict__ fid) {\n"
           "  using namespace fbg_interp;\n"
           "  extern __shared__ fbg_u64 dyn_slots[];\n"
           "  __shared__ Shared S;\n"
           "  Thread T;\n"
-          "  T.slots = dyn_slots + threadIdx.x;\n"
-          "  T.acc = 0;\n"
-          "  T.coords = 0;\n"
+          "  init_thread(T, dyn_slots);\n"
           "  unsigned cur = 0xFFFFFFFFu;\n"
           "  bool alive0 = true;\n"
           "  fbg_u64 iters = 0;\n"
@@ -186,7 +184,8 @@ std::string batch_kernel_source(const std::vector<std::string>& names) {
           "    fbg_u64 cnt = 0;\n"
           "    switch (fid[W.prog]) {\n";
   for (size_t gi = 0; gi < names.size(); gi++)
-    body += "      case " + std::to_string(gi) + ": cnt = " + names[gi] + "(W.unit_begin, W.unit_end, threadIdx.x, lvl); break;\n";
+    body += "      case " + std::to_string(gi) + ": cnt = " + names[gi] + "(W.unit_begin, W.unit_end, threadIdx.x, lvl) + " +
+            names[gi] + "(W.unit_begin, W.unit_end, threadIdx.x + 32u, lvl); break;\n";
   body += "      default: process_item<0>(S, T, progs, W, cur, alive0, P, cnt, iters); break;\n"
           "    }\n"
           "    cnt = fbg_warp_sum(cnt);\n"
@@ -306,7 +305,7 @@ fbg_status fbg_batch_create(fbg_program* const* progs, int nprogs, uint64_t max_
     size_t smem = interp_smem_bytes(b->nslots);
     cudaKernelSetAttributeForDevice(b->kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem, dev);
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)b->kern, FBG_INTERP_BLOCK, smem) == cudaSuccess &&
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)b->kern, FBG_INTERP_THREADS, smem) == cudaSuccess &&
         nb > 0)
       per_sm = nb;
   }

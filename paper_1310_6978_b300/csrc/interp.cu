@@ -15,15 +15,14 @@ using namespace fbg_interp;
 namespace {
 
 template <int MODE>
-__global__ void __launch_bounds__(B) interp_kernel(const FbgInterpProg* __restrict__ progs,
+__global__ void __launch_bounds__(NT) interp_kernel(const FbgInterpProg* __restrict__ progs,
                                                    const FbgWorkItem* __restrict__ items, fbg_u64 nitems,
                                                    fbg_u64* item_ctr, fbg_u64* prog_counts, fbg_u64* item_counts,
                                                    FbgLaunch P) {
   extern __shared__ fbg_u64 dyn_slots[];
   __shared__ Shared S;
   Thread T;
-  T.slots = dyn_slots + threadIdx.x;
-  T.acc = 0;
+  init_thread(T, dyn_slots);
   unsigned cur = 0xFFFFFFFFu;
   bool alive0 = true;
   fbg_u64 iters = 0;
@@ -100,11 +99,11 @@ cudaError_t launch_interp(int mode, const FbgInterpProg* progs, const FbgWorkIte
   cudaError_t e = ensure_smem(mode, smem);
   if (e != cudaSuccess) return e;
   if (mode == 0)
-    interp_kernel<0><<<grid, B, smem, stream>>>(progs, items, nitems, item_ctr, prog_counts, item_counts, P);
+    interp_kernel<0><<<grid, NT, smem, stream>>>(progs, items, nitems, item_ctr, prog_counts, item_counts, P);
   else if (mode == 1)
-    interp_kernel<1><<<grid, B, smem, stream>>>(progs, items, nitems, item_ctr, prog_counts, item_counts, P);
+    interp_kernel<1><<<grid, NT, smem, stream>>>(progs, items, nitems, item_ctr, prog_counts, item_counts, P);
   else
-    interp_kernel<2><<<grid, B, smem, stream>>>(progs, items, nitems, item_ctr, prog_counts, item_counts, P);
+    interp_kernel<2><<<grid, NT, smem, stream>>>(progs, items, nitems, item_ctr, prog_counts, item_counts, P);
   return cudaGetLastError();
 }
 
@@ -118,9 +117,9 @@ int interp_blocks_per_sm(int mode, unsigned nslots) {
   int nb = 0;
   size_t smem = interp_smem_bytes(nslots);
   if (ensure_smem(mode, smem) != cudaSuccess) return 0;
-  if (mode == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, interp_kernel<0>, B, smem);
-  else if (mode == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, interp_kernel<1>, B, smem);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, interp_kernel<2>, B, smem);
+  if (mode == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, interp_kernel<0>, NT, smem);
+  else if (mode == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, interp_kernel<1>, NT, smem);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, interp_kernel<2>, NT, smem);
   return nb;
 }
 

@@ -2,10 +2,12 @@
 // nvcc-compiled kernels (interp.cu) and the NVRTC-compiled batch kernel that
 // mixes interpreted and specialised programs.  Evaluates the LUT bytecode of
 // interp_format.h on 64-bit tiles: the bitwise evaluation of Sec. 2.3 with
-// 64-bit blocks.  Each thread owns one tile per innermost iteration; values
-// live in a per-thread column of shared memory plus an accumulator register;
-// loop levels run as an odometer; a level whose partial conjunction is zero
-// for a whole warp (for model lists: the whole block) skips its inner levels.
+// 64-bit blocks.  A block is one warp; each thread owns two tiles per
+// innermost iteration (the layout's threads lane and lane + 32), so every
+// decoded instruction does the work of both (two independent data paths per
+// instruction); values live in per-thread columns of shared memory plus an
+// accumulator register; loop levels run as an odometer; a level whose partial
+// conjunction is zero for the whole warp skips its inner levels.
 #pragma once
 
 #include "fbg_device.cuh"
@@ -22,11 +24,27 @@ __device__ __forceinline__ fbg_u64 lop3_pair(fbg_u64 a, fbg_u64 b, fbg_u64 c) {
   return ((fbg_u64)hi << 32) | lo;
 }
 
-// lop3 needs its truth table as an immediate: dispatch on the (warp-uniform) LUT
-__device__ __forceinline__ fbg_u64 lop3_dyn(unsigned lut, fbg_u64 a, fbg_u64 b, fbg_u64 c) {
+constexpr int B = FBG_INTERP_BLOCK;          // tiles per block (the layout's threads), slot stride
+constexpr int NT = FBG_INTERP_THREADS;       // threads per block
+constexpr int NTILE = B / NT;                // tiles per thread
+static_assert(NT == 32 && NTILE == 2, "one warp per block, two tiles per thread");
+constexpr int MAX_CONST_SMEM = FBG_INTERP_MAX_CONSTS;
+
+// the two tiles of a thread: tile k is the layout's thread lane + 32 k
+struct Pair {
+  fbg_u64 v[NTILE];
+};
+
+// lop3 needs its truth table as an immediate: dispatch on the (warp-uniform)
+// LUT once per instruction for both tiles
+__device__ __forceinline__ Pair lop3_dyn(unsigned lut, const Pair& a, const Pair& b, const Pair& c) {
+  Pair d;
   switch (lut) {
-#define FBG_C(x) \
-  case (x): return lop3_pair<(x)>(a, b, c);
+#define FBG_C(x)                                   \
+  case (x):                                        \
+    d.v[0] = lop3_pair<(x)>(a.v[0], b.v[0], c.v[0]); \
+    d.v[1] = lop3_pair<(x)>(a.v[1], b.v[1], c.v[1]); \
+    return d;
 #define FBG_C4(x) FBG_C(x) FBG_C((x) + 1) FBG_C((x) + 2) FBG_C((x) + 3)
 #define FBG_C16(x) FBG_C4(x) FBG_C4((x) + 4) FBG_C4((x) + 8) FBG_C4((x) + 12)
 #define FBG_C64(x) FBG_C16(x) FBG_C16((x) + 16) FBG_C16((x) + 32) FBG_C16((x) + 48)
@@ -36,44 +54,72 @@ __device__ __forceinline__ fbg_u64 lop3_dyn(unsigned lut, fbg_u64 a, fbg_u64 b, 
 #undef FBG_C4
 #undef FBG_C
   }
-  return 0;
+  d.v[0] = d.v[1] = 0;
+  return d;
 }
-
-constexpr int B = FBG_INTERP_BLOCK;
-constexpr int MAX_CONST_SMEM = FBG_INTERP_MAX_CONSTS;
 
 struct Shared {
   FbgInterpProg prog;
   fbg_u64 consts[MAX_CONST_SMEM];
   fbg_u64 unit;
   fbg_u64 item;
-  fbg_u32 warp_tot[B / 32];
 };
 
 struct Thread {
-  fbg_u64* slots;       // this thread's column
-  fbg_u64 acc;
-  fbg_u64 coords;       // tile coordinates: bit positions >= 6 of j
+  fbg_u64* slots;       // this thread's column: tile k of slot s at slots[s * B + k * NT]
+  Pair acc;
+  fbg_u64 coords[NTILE];   // tile coordinates: bit positions >= 6 of j
 };
 
-__device__ __forceinline__ fbg_u64 fetch(const Shared& S, const Thread& T, unsigned op) {
-  if (op == FBG_OP_ACC) return T.acc;
-  if (op & FBG_OP_VAR) return ((T.coords >> (op & 63u)) & 1ull) ? ~0ull : 0ull;
-  if (op & FBG_OP_CONST) return S.consts[op & 0x3FFFu];
-  return T.slots[(unsigned long long)op * B];
+__device__ __forceinline__ void init_thread(Thread& T, fbg_u64* dyn_slots) {
+  T.slots = dyn_slots + threadIdx.x;
+  T.acc.v[0] = T.acc.v[1] = 0;
+  T.coords[0] = T.coords[1] = 0;
 }
 
+__device__ __forceinline__ void set_thread_coords(Thread& T, fbg_u64 upper) {
+#pragma unroll
+  for (int k = 0; k < NTILE; k++) T.coords[k] = ((fbg_u64)(threadIdx.x + k * NT) << 6) | upper;
+}
+
+__device__ __forceinline__ Pair fetch(const Shared& S, const Thread& T, unsigned op) {
+  Pair r;
+  if (op == FBG_OP_ACC) return T.acc;
+  if (op & FBG_OP_VAR) {
+#pragma unroll
+    for (int k = 0; k < NTILE; k++) r.v[k] = ((T.coords[k] >> (op & 63u)) & 1ull) ? ~0ull : 0ull;
+    return r;
+  }
+  if (op & FBG_OP_CONST) {
+    r.v[0] = r.v[1] = S.consts[op & 0x3FFFu];
+    return r;
+  }
+#pragma unroll
+  for (int k = 0; k < NTILE; k++) r.v[k] = T.slots[(unsigned long long)op * B + k * NT];
+  return r;
+}
+
+// instructions of one level; the next instruction word is loaded while the
+// current one executes
 __device__ __forceinline__ void exec_level(const Shared& S, Thread& T, const FbgInterpLevel& L) {
   const fbg_u64* ins = S.prog.ins;
-  for (unsigned i = L.ins_begin; i < L.ins_end; i++) {
-    fbg_u64 w = __ldg(ins + i);
-    unsigned lut = (unsigned)(w & 0xFF), dst = (unsigned)((w >> 8) & 0xFF);
-    fbg_u64 a = fetch(S, T, (unsigned)((w >> 16) & 0xFFFF));
-    fbg_u64 b = fetch(S, T, (unsigned)((w >> 32) & 0xFFFF));
-    fbg_u64 c = fetch(S, T, (unsigned)(w >> 48));
-    fbg_u64 d = lop3_dyn(lut, a, b, c);
-    if (dst == FBG_DST_ACC) T.acc = d;
-    else T.slots[(unsigned long long)dst * B] = d;
+  unsigned i = L.ins_begin;
+  if (i >= L.ins_end) return;
+  fbg_u64 w = __ldg(ins + i);
+  for (; i < L.ins_end; i++) {
+    const fbg_u64 next = i + 1 < L.ins_end ? __ldg(ins + i + 1) : 0ull;
+    const unsigned lut = (unsigned)(w & 0xFF), dst = (unsigned)((w >> 8) & 0xFF);
+    const Pair a = fetch(S, T, (unsigned)((w >> 16) & 0xFFFF));
+    const Pair b = fetch(S, T, (unsigned)((w >> 32) & 0xFFFF));
+    const Pair c = fetch(S, T, (unsigned)(w >> 48));
+    const Pair d = lop3_dyn(lut, a, b, c);
+    if (dst == FBG_DST_ACC) {
+      T.acc = d;
+    } else {
+#pragma unroll
+      for (int k = 0; k < NTILE; k++) T.slots[(unsigned long long)dst * B + k * NT] = d.v[k];
+    }
+    w = next;
   }
 }
 
@@ -81,7 +127,8 @@ __device__ __forceinline__ void exec_level(const Shared& S, Thread& T, const Fbg
 template <int MODE>
 __device__ __forceinline__ bool level_alive(const Shared& S, const Thread& T, const FbgInterpLevel& L) {
   if (!L.has_acc) return true;
-  bool mine = fetch(S, T, L.acc_op) != 0ull;
+  const Pair v = fetch(S, T, L.acc_op);
+  const bool mine = (v.v[0] | v.v[1]) != 0ull;
   if (MODE == 2) return __syncthreads_or(mine) != 0;
   return __any_sync(FBG_FULL, mine);
 }
@@ -90,16 +137,28 @@ __device__ __forceinline__ void load_prog(Shared& S, const FbgInterpProg* progs,
   __syncthreads();
   if (threadIdx.x == 0) S.prog = progs[p];
   __syncthreads();
-  for (unsigned i = threadIdx.x; i < S.prog.nconst && i < MAX_CONST_SMEM; i += B) S.consts[i] = S.prog.consts[i];
+  for (unsigned i = threadIdx.x; i < S.prog.nconst && i < MAX_CONST_SMEM; i += NT) S.consts[i] = S.prog.consts[i];
   __syncthreads();
+}
+
+// inclusive prefix sum over the warp's lanes
+__device__ __forceinline__ unsigned warp_incl(unsigned c) {
+  const unsigned lane = threadIdx.x & 31u;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned y = __shfl_up_sync(FBG_FULL, c, o);
+    if (lane >= (unsigned)o) c += y;
+  }
+  return c;
 }
 
 template <int MODE>
 __device__ void run_unit(Shared& S, Thread& T, fbg_u64 u, const FbgLaunch& P, fbg_u64& cnt, fbg_u64& iters) {
   const FbgInterpProg& G = S.prog;
-  const unsigned tb = threadIdx.x;
-  const bool tvalid = tb < G.tvalid;
-  T.coords = ((fbg_u64)tb << 6) | (G.unit_bits ? (u << G.first_unit_pos) : 0ull);
+  bool tvalid[NTILE];
+#pragma unroll
+  for (int k = 0; k < NTILE; k++) tvalid[k] = threadIdx.x + k * NT < G.tvalid;
+  set_thread_coords(T, G.unit_bits ? (u << G.first_unit_pos) : 0ull);
   fbg_u64 base = 0;
   if (MODE == 2) base = P.unit_offsets[u - P.unit_begin];
   exec_level(S, T, G.lev[1]);
@@ -112,8 +171,9 @@ __device__ void run_unit(Shared& S, Thread& T, fbg_u64 u, const FbgLaunch& P, fb
     bool leaf = false;
     if (lv < nl) {
       const FbgInterpLevel& L = G.lev[lv];
-      fbg_u64 m = ((1ull << L.bits) - 1ull) << L.pos;
-      T.coords = (T.coords & ~m) | ((fbg_u64)it[lv] << L.pos);
+      const fbg_u64 m = ((1ull << L.bits) - 1ull) << L.pos;
+#pragma unroll
+      for (int k = 0; k < NTILE; k++) T.coords[k] = (T.coords[k] & ~m) | ((fbg_u64)it[lv] << L.pos);
       exec_level(S, T, L);
       bool alive = level_alive<MODE>(S, T, L);
       if (alive && lv + 1 < nl) {
@@ -126,38 +186,38 @@ __device__ void run_unit(Shared& S, Thread& T, fbg_u64 u, const FbgLaunch& P, fb
       leaf = true;   // no loop levels: the unit level is innermost
     }
     if (leaf) {
-      fbg_u64 word = tvalid ? (fetch(S, T, G.out_op) & G.vmask) : 0ull;
-      if (MODE == 0) {
-        cnt += (fbg_u64)__popcll(word);
-      } else if (MODE == 1) {
-        if (tvalid) reinterpret_cast<fbg_u64*>(P.table)[T.coords >> 6] = word;
-      } else {
-        // ordered compaction across the block: tiles ascend with threadIdx
-        unsigned c = (unsigned)__popcll(word);
-        unsigned incl = c;
+      const Pair o = fetch(S, T, G.out_op);
+      fbg_u64 word[NTILE];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          unsigned y = __shfl_up_sync(FBG_FULL, incl, o);
-          if ((tb & 31) >= (unsigned)o) incl += y;
+      for (int k = 0; k < NTILE; k++) word[k] = tvalid[k] ? (o.v[k] & G.vmask) : 0ull;
+      if (MODE == 0) {
+        cnt += (fbg_u64)(__popcll(word[0]) + __popcll(word[1]));
+      } else if (MODE == 1) {
+#pragma unroll
+        for (int k = 0; k < NTILE; k++)
+          if (tvalid[k]) reinterpret_cast<fbg_u64*>(P.table)[T.coords[k] >> 6] = word[k];
+      } else {
+        // ordered compaction: tiles ascend with lane + 32 k, so all tiles 0
+        // of the warp precede all tiles 1
+        fbg_u64 off = base;
+#pragma unroll
+        for (int k = 0; k < NTILE; k++) {
+          const unsigned c = (unsigned)__popcll(word[k]);
+          const unsigned incl = warp_incl(c);
+          const unsigned total = __shfl_sync(FBG_FULL, incl, 31);
+          fbg_u64 o2 = off + incl - c;
+          fbg_u64 wd = word[k];
+          while (wd) {
+            int b = __ffsll((long long)wd) - 1;
+            wd &= wd - 1;
+            if (o2 < P.cap) P.models[o2] = T.coords[k] | (fbg_u64)b;
+            o2++;
+          }
+          off += total;
         }
-        if ((tb & 31) == 31) S.warp_tot[tb >> 5] = incl;
-        __syncthreads();
-        unsigned before = 0, total = 0;
-        for (int w = 0; w < B / 32; w++) {
-          if (w < (int)(tb >> 5)) before += S.warp_tot[w];
-          total += S.warp_tot[w];
-        }
-        __syncthreads();
-        fbg_u64 off = base + before + incl - c;
-        while (word) {
-          int b = __ffsll((long long)word) - 1;
-          word &= word - 1;
-          if (off < P.cap) P.models[off] = T.coords | (fbg_u64)b;
-          off++;
-        }
-        base += total;
+        base = off;
       }
-      if ((tb & 31) == 0) iters++;
+      if ((threadIdx.x & 31) == 0) iters += NTILE;
     }
     if (lv < 2 || nl <= 2) break;
     // odometer advance
@@ -174,7 +234,7 @@ __device__ __forceinline__ void process_item(Shared& S, Thread& T, const FbgInte
   if (W.prog != cur) {
     load_prog(S, progs, W.prog);
     cur = W.prog;
-    T.coords = (fbg_u64)threadIdx.x << 6;
+    set_thread_coords(T, 0ull);
     exec_level(S, T, S.prog.lev[0]);
     alive0 = level_alive<MODE>(S, T, S.prog.lev[0]);
   }

@@ -9,7 +9,8 @@
 #pragma once
 
 #define FBG_INTERP_MAX_LEVELS 10
-#define FBG_INTERP_BLOCK 64
+#define FBG_INTERP_BLOCK 64          // tiles per block: the layout's threads (5 lane bits, 1 warp bit)
+#define FBG_INTERP_THREADS 32        // threads per block; each evaluates BLOCK / THREADS tiles
 #define FBG_INTERP_WARPS_LOG2 1
 #define FBG_INTERP_MAX_SLOTS 160
 #define FBG_INTERP_MAX_CONSTS 512   // constant table entries staged in shared memory
