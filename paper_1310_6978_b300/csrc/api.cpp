@@ -179,12 +179,11 @@ fbg_status pick_engine(fbg_program* p, int mode, bool* use_jit) {
   return build_interp(p, mode == 0 ? 0 : 1);
 }
 
-// scratch words: [0] unit counter [1] count [2] item counter [3] total
-// [4,20) level iterations, then two arrays of `units` words
-constexpr size_t kScratchHead = 32;
 // scratch head: [0] item counter, [1] count of fbg_count, [2] [3] interpreter
-// counters, [4..20) level iterations, [24] [25] running sum and finished
-// warps of self-resetting counts
+// item counter and total, [4..20) level iterations, [24] [25] running sum and
+// finished warps of self-resetting counts; then, for model lists and
+// interpreter sub-ranges, arrays after the head
+constexpr size_t kScratchHead = 32;
 constexpr size_t kScratchAcc = 24, kScratchDone = 25;
 
 fbg_status launch_count(fbg_program* p, cudaStream_t st, unsigned long long* dev_count, unsigned long long* unit_counts,
