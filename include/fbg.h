@@ -267,15 +267,16 @@ fbg_status fbg_debug_unit_trace(fbg_program *prog, void *stream, uint64_t *dev_t
 fbg_status fbg_debug_item_trace(fbg_program *prog, void *stream, uint64_t *dev_ns, uint64_t nitems);
 
 /*
- * Diagnostics without a device: the NVRTC source of the hybrid batch kernel
- * for these programs ("" when none would be specialised), and an NVRTC
+ * Diagnostics without a device: the NVRTC sources of the specialised count
+ * kernels a batch of these programs would build, one after another ("" when
+ * none would be specialised), and an NVRTC
  * compile of a kernel body (the library's device headers are available to it)
  * with the library's options; log receives the NVRTC/ptxas messages.
  */
 fbg_status fbg_debug_batch_source(fbg_program *const *progs, int nprogs, char *buf, size_t *len);
 fbg_status fbg_debug_nvrtc_compile(const char *body, char *log, size_t loglen);
-/* compile and link (without loading) the hybrid batch kernel of these programs;
-   *specialized receives the number of specialised programs */
+/* compile (without loading) the specialised kernels a batch of these programs
+   would build; *specialized receives the number that compile */
 fbg_status fbg_debug_batch_build(fbg_program *const *progs, int nprogs, int *specialized, char *log, size_t loglen);
 
 /* NVRTC/ptxas log of the last specialised-kernel build (registers, spills) */
@@ -288,16 +289,18 @@ const char *fbg_last_error(void);
 
 /*
  * Batch (the inner loop of the counting procedure of Sec. 3.4 runs over many
- * reduced formulas): count many programs in one persistent launch fed by a
- * device work queue of (program, unit range) items, largest first.  Programs
- * must outlive the batch.  max_item_units bounds the units per queue item
- * (0 = automatic).  flags: FBG_BATCH_GRAPH captures memset + launch + result
- * copy in a CUDA graph on the first run and replays it afterwards;
+ * reduced formulas): count many programs together.  Interpreted programs share
+ * one persistent interpreter launch fed by a device work queue of (program,
+ * unit range) items, largest first.  Programs must outlive the batch.
+ * max_item_units bounds the units per queue item (0 = automatic).  flags:
+ * FBG_BATCH_GRAPH captures the whole run (memset, launches, result copy) in a
+ * CUDA graph on the first run and replays it afterwards;
  * FBG_BATCH_SPECIALIZE compiles the distinct programs with n >= 20 that carry
- * the most nominal work (at most 512) into straight-line device functions,
- * separately and in parallel (relocatable device code, linked with
- * nvJitLink), inside the one batch kernel, which interprets every other
- * program.
+ * the most nominal work (at most 512) into specialised count kernels (NVRTC,
+ * in parallel, 180 s deadline); each instance of such a program is one
+ * self-resetting launch of its kernel, the launches spread longest first (by
+ * one timed launch per kernel at creation) over eight side streams, the
+ * interpreter launch on a ninth; every other program is interpreted.
  */
 enum { FBG_BATCH_GRAPH = 1, FBG_BATCH_SPECIALIZE = 2 };
 fbg_status fbg_batch_create(fbg_program *const *progs, int nprogs, uint64_t max_item_units, int flags,
@@ -346,6 +349,10 @@ fbg_status fbg_server_drain(fbg_server *srv, double timeout_s);
 /* release a finished request's result memory */
 fbg_status fbg_server_release(fbg_server *srv, uint64_t request_id);
 fbg_status fbg_server_stats(fbg_server *srv, uint64_t *ticks, uint64_t *launches, double *busy_s);
+/* diagnostics: seconds the server thread spent admitting requests (building
+   their interpreter programs), in count ticks (launch to completion) and on
+   model lists */
+fbg_status fbg_server_profile(fbg_server *srv, double *admit_s, double *count_s, double *enum_s);
 void fbg_server_free(fbg_server *srv);
 
 #ifdef __cplusplus

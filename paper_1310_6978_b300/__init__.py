@@ -220,7 +220,7 @@ class Batch:
 
 
 def batch_source(programs) -> str:
-    """fbg_debug_batch_source: NVRTC source of the hybrid batch kernel."""
+    """fbg_debug_batch_source: NVRTC sources of the batch's specialised kernels."""
     L = _L()
     arr = (ctypes.c_void_p * len(programs))(*[p.handle.value for p in programs])
     n = ctypes.c_size_t()
@@ -231,8 +231,8 @@ def batch_source(programs) -> str:
 
 
 def batch_build_check(programs):
-    """fbg_debug_batch_build: compile and link the hybrid batch kernel without
-    a device; returns (ok, number of specialised programs, log)."""
+    """fbg_debug_batch_build: compile the batch's specialised kernels without a
+    device; returns (ok, number that compile, log)."""
     L = _L()
     arr = (ctypes.c_void_p * len(programs))(*[p.handle.value for p in programs])
     spec = ctypes.c_int()
@@ -294,4 +294,7 @@ class Server:
     def stats(self):
         t, l, b = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_double()
         self._L.check(self._L.lib.fbg_server_stats(self._h, ctypes.byref(t), ctypes.byref(l), ctypes.byref(b)))
-        return {"ticks": t.value, "launches": l.value, "busy_s": b.value}
+        a, c, e = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._L.check(self._L.lib.fbg_server_profile(self._h, ctypes.byref(a), ctypes.byref(c), ctypes.byref(e)))
+        return {"ticks": t.value, "launches": l.value, "busy_s": b.value, "admit_s": a.value, "count_s": c.value,
+                "enum_s": e.value}

@@ -107,6 +107,8 @@ _sig("fbg_server_poll", c_int, c_vp, c_u64, ctypes.POINTER(FbgResult))
 _sig("fbg_server_drain", c_int, c_vp, ctypes.c_double)
 _sig("fbg_server_release", c_int, c_vp, c_u64)
 _sig("fbg_server_stats", c_int, c_vp, ctypes.POINTER(c_u64), ctypes.POINTER(c_u64), ctypes.POINTER(ctypes.c_double))
+_sig("fbg_server_profile", c_int, c_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+     ctypes.POINTER(ctypes.c_double))
 _sig("fbg_server_free", None, c_vp)
 
 

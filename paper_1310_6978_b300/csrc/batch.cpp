@@ -1,23 +1,27 @@
-// batch.cpp -- many programs counted in one persistent launch.
+// batch.cpp -- many programs counted together.
 //
 // The counting procedure of Sec. 3.4 evaluates a whole family of reduced
-// formulas; here any set of compiled programs is counted together.  Every
-// program's unit range is cut into work items (program, unit range); the
-// items are sorted by nominal cost (assignments x instructions), largest
-// first, and blocks of the interpreter kernel pull them from a device
-// counter, so large and small formulas share one launch without a tail of
-// idle SMs.  Per-program partial counts are accumulated in device memory.
-// With FBG_BATCH_GRAPH the memsets, the launch and the copy of the counts
-// to pinned host memory are captured once in a CUDA graph and replayed.
+// formulas; here any set of compiled programs is counted together.
 //
-// With FBG_BATCH_SPECIALIZE the distinct programs with n >= 20 that carry
-// the most nominal work (up to 512) get straight-line device functions: each
-// is compiled separately by NVRTC as relocatable device code (in parallel,
-// cached per source), the dispatch kernel likewise, and nvJitLink links them
-// into ONE persistent batch kernel whose work-item loop calls a program's
-// function when it has one and interprets its bytecode otherwise.  Programs
-// whose compilation fails or misses the deadline are interpreted; if the
-// kernel itself cannot be built the batch runs on the interpreter kernel.
+// Interpreted programs: every program's unit range is cut into work items
+// (program, unit range); the items are sorted by nominal cost (assignments x
+// instructions), largest first, and the warps of ONE interpreter launch pull
+// them from a device counter, so large and small formulas share the launch
+// without a tail of idle SMs.  Per-program counts accumulate in device memory.
+//
+// With FBG_BATCH_SPECIALIZE the distinct programs with n >= 20 that carry the
+// most nominal work (up to 512) get their own specialised count kernel (the
+// one a single program uses, built by NVRTC in parallel, cached per source).
+// Each instance of such a program is one launch of its kernel with its own
+// four counter words (self-resetting: no memset between runs); the launches
+// are spread over eight side streams longest first, by a time measured once
+// per kernel when the batch is created, and the interpreter launch takes a
+// stream of its own, so short kernels fill the SMs that long ones leave idle.
+// Programs whose compilation fails or misses the deadline are interpreted.
+//
+// With FBG_BATCH_GRAPH the memset, the fork, all launches, the join and the
+// copy of the counts to pinned host memory are captured once in a CUDA graph
+// and replayed.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,11 +40,27 @@
 
 using namespace fbg;
 
+namespace {
+
+// a specialised count kernel shared by the instances of one distinct program
+struct SpecKernel {
+  cudaKernel_t kern = nullptr;
+  int grid = 1, block = 32;
+  uint64_t nunits = 1, chunk = 1;
+  unsigned nwarps = 1;
+  float ms = 0.f;   // one launch, measured when the batch is created
+};
+
+constexpr int kSideStreams = 8;
+constexpr size_t kInstWords = 4;   // item counter, running sum, finished warps, pad
+
+}  // namespace
+
 struct fbg_batch {
   std::vector<fbg_program*> progs;
   FbgInterpProg* d_progs = nullptr;
   FbgWorkItem* d_items = nullptr;
-  unsigned long long* d_counts = nullptr;   // [nprogs] counts, then the item counter
+  unsigned long long* d_counts = nullptr;   // [nprogs] counts, then the interpreter's item counter
   unsigned long long* h_counts = nullptr;   // pinned
   uint64_t nitems = 0, units = 0;
   unsigned nslots = 1;
@@ -48,21 +68,25 @@ struct fbg_batch {
   bool use_graph = false;
   // specialised programs
   int specialized = 0;
-  int* d_fid = nullptr;                     // per program: function id or -1
-  std::vector<int> fid;
-  cudaKernel_t kern = nullptr;              // hybrid kernel, or null: interpreter kernel
+  std::vector<int> fid;                     // per program: kernel id or -1
+  std::vector<SpecKernel> spec;
+  unsigned long long* d_inst = nullptr;     // kInstWords counter words per program
+  std::vector<std::vector<int>> lanes;      // per side stream: the programs launched there
+  std::vector<cudaStream_t> side;           // side streams (kSideStreams + 1 for the interpreter)
+  std::vector<cudaEvent_t> ev;              // fork + one join event per side stream
   std::string jit_log;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  cudaStream_t graph_stream = nullptr;
   ~fbg_batch() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    for (cudaStream_t s : side) cudaStreamDestroy(s);
     if (d_progs) cudaFree(d_progs);
     if (d_items) cudaFree(d_items);
     if (d_counts) cudaFree(d_counts);
     if (h_counts) cudaFreeHost(h_counts);
-    if (d_fid) cudaFree(d_fid);
+    if (d_inst) cudaFree(d_inst);
   }
 };
 
@@ -74,25 +98,48 @@ struct fbg_batch {
 
 namespace {
 
+// one self-resetting launch of a specialised kernel for program i
+cudaError_t launch_spec(const fbg_batch* b, int i, cudaStream_t st) {
+  const SpecKernel& k = b->spec[(size_t)b->fid[(size_t)i]];
+  unsigned long long* w = b->d_inst + (size_t)i * kInstWords;
+  FbgLaunch P{};
+  P.unit_ctr = w + 0;
+  P.acc = w + 1;
+  P.done = w + 2;
+  P.out = b->d_counts + i;
+  P.nwarps = k.nwarps;
+  P.unit_begin = 0;
+  P.unit_end = k.nunits;
+  P.chunk = k.chunk;
+  void* args[] = {&P};
+  return cudaLaunchKernel((const void*)k.kern, dim3((unsigned)k.grid), dim3((unsigned)k.block), args, 0, st);
+}
+
 fbg_status enqueue(fbg_batch* b, cudaStream_t st) {
   const size_t np = b->progs.size();
   CKB(cudaMemsetAsync(b->d_counts, 0, (np + 1) * 8, st));
   FbgLaunch P{};
   P.unit_begin = 0;
   P.unit_end = ~0ull;
-  if (b->kern) {
-    unsigned long long* item_ctr = b->d_counts + np;
-    unsigned long long* counts = b->d_counts;
-    const FbgInterpProg* progs = b->d_progs;
-    const FbgWorkItem* items = b->d_items;
-    unsigned long long nitems = b->nitems;
-    const int* fid = b->d_fid;
-    void* args[] = {(void*)&progs, (void*)&items, (void*)&nitems, (void*)&item_ctr, (void*)&counts, (void*)&fid};
-    CKB(cudaLaunchKernel((const void*)b->kern, dim3((unsigned)b->grid), dim3(FBG_INTERP_THREADS), args,
-                         interp_smem_bytes(b->nslots), st));
+  if (b->side.empty()) {
+    if (b->nitems)
+      CKB(launch_interp(0, b->d_progs, b->d_items, b->nitems, b->d_counts + np, b->d_counts, nullptr, P, b->nslots,
+                        b->grid, st));
   } else {
-    CKB(launch_interp(0, b->d_progs, b->d_items, b->nitems, b->d_counts + np, b->d_counts, nullptr, P, b->nslots,
-                      b->grid, st));
+    // fork: every side stream waits for the memset
+    CKB(cudaEventRecord(b->ev[0], st));
+    for (size_t s = 0; s < b->side.size(); s++) CKB(cudaStreamWaitEvent(b->side[s], b->ev[0], 0));
+    cudaStream_t is = b->side.back();
+    if (b->nitems)
+      CKB(launch_interp(0, b->d_progs, b->d_items, b->nitems, b->d_counts + np, b->d_counts, nullptr, P, b->nslots,
+                        b->grid, is));
+    for (size_t s = 0; s < b->lanes.size(); s++)
+      for (int i : b->lanes[s]) CKB(launch_spec(b, i, b->side[s]));
+    // join
+    for (size_t s = 0; s < b->side.size(); s++) {
+      CKB(cudaEventRecord(b->ev[s + 1], b->side[s]));
+      CKB(cudaStreamWaitEvent(st, b->ev[s + 1], 0));
+    }
   }
   CKB(cudaMemcpyAsync(b->h_counts, b->d_counts, np * 8, cudaMemcpyDeviceToHost, st));
   return FBG_OK;
@@ -100,21 +147,22 @@ fbg_status enqueue(fbg_batch* b, cudaStream_t st) {
 
 }  // namespace
 
-// at most this many distinct programs get a specialised function
+// at most this many distinct programs get a specialised kernel
 constexpr size_t kMaxSpecialized = 512;
-// specialised functions still compiling after this are dropped (interpreted)
+// specialised kernels still compiling after this are dropped (interpreted)
 constexpr double kCompileDeadlineS = 180.0;
 
 struct BatchPlan {
-  std::vector<int> fid;                 // per program: function id or -1
-  std::vector<std::string> fn_name;     // per function
-  std::vector<std::string> fn_src;      // per function (relocatable device code)
-  std::vector<LutProgram> spec_lp;      // per function: its layout
+  std::vector<int> fid;                 // per program: kernel id or -1
+  std::vector<std::string> src;         // per kernel: complete NVRTC source
+  std::vector<LutProgram> lp;           // per kernel: its layout and LUTs
+  std::vector<int> block;               // per kernel: threads per block
 };
 
 // Choice of the programs to specialise (host only): distinct programs (by
 // text and domain) with n >= 20, ranked by nominal work (instances x 2^n x
-// program size), at most kMaxSpecialized.
+// program size), at most kMaxSpecialized; each gets the count kernel of a
+// single program (4 warps per block, 4 words per thread, 2-bit loop levels).
 BatchPlan plan_batch(fbg_program* const* progs, int nprogs, std::string* err) {
   BatchPlan plan;
   plan.fid.assign((size_t)nprogs, -1);
@@ -137,16 +185,16 @@ BatchPlan plan_batch(fbg_program* const* progs, int nprogs, std::string* err) {
     const fbg_program* p0 = progs[(*ranked[gi].second)[0]];
     LayoutParams lp;
     lp.r_max = 2;
-    lp.warps_log2 = FBG_INTERP_WARPS_LOG2;   // the batch kernel's block shape
+    lp.warps_log2 = 2;
     lp.unit_bits_max = 13;
     lp.loop_level_bits = 2;
-    char nm[64];
-    std::snprintf(nm, sizeof nm, "fbg_bp_%016zx_%d", std::hash<std::string>()(p0->text), p0->k);
     try {
       Layout L = make_layout(p0->n, lp, search_order(p0->g));
-      plan.spec_lp.push_back(lower_and_map(p0->g, L));
-      plan.fn_src.push_back("extern \"C\" " + emit_batch_function(plan.spec_lp.back(), nm));
-      plan.fn_name.push_back(nm);
+      LutProgram prog = lower_and_map(p0->g, L);
+      int block = prog.layout.lane_bits < 5 ? 32 : 32 << prog.layout.warp_bits;
+      plan.src.push_back(emit_cuda_source(prog, 0, block, 2, nullptr, nullptr, false));
+      plan.block.push_back(block);
+      plan.lp.push_back(std::move(prog));
     } catch (CompileError& e) {
       if (err) *err = e.msg;
       return BatchPlan{std::vector<int>((size_t)nprogs, -1), {}, {}, {}};
@@ -154,76 +202,6 @@ BatchPlan plan_batch(fbg_program* const* progs, int nprogs, std::string* err) {
     for (int i : *ranked[gi].second) plan.fid[(size_t)i] = (int)gi;
   }
   return plan;
-}
-
-// the persistent batch kernel: calls the specialised functions listed in
-// `names` (by function id) and interprets every other program
-std::string batch_kernel_source(const std::vector<std::string>& names) {
-  std::string body = "#include \"interp_device.cuh\"\n";
-  for (auto& nm : names) body += "extern \"C\" __device__ fbg_u64 " + nm + "(fbg_u64 u0, fbg_u64 u1, fbg_u32 tb, fbg_u64* lvl);\n";
-  body += "extern \"C\" __global__ void __launch_bounds__(" + std::to_string(FBG_INTERP_THREADS) +
-          ") fbg_batch_kernel(const FbgInterpProg* __restrict__ progs, const FbgWorkItem* __restrict__ items,"
-          " fbg_u64 nitems, fbg_u64* item_ctr, fbg_u64* prog_counts, const int* __restrict__ fid) {\n"
-          "  using namespace fbg_interp;\n"
-          "  extern __shared__ fbg_u64 dyn_slots[];\n"
-          "  __shared__ Shared S;\n"
-          "  Thread T;\n"
-          "  init_thread(T, dyn_slots);\n"
-          "  unsigned cur = 0xFFFFFFFFu;\n"
-          "  bool alive0 = true;\n"
-          "  fbg_u64 iters = 0;\n"
-          "  FbgLaunch P = {};\n"
-          "  fbg_u64 lvl[16] = {0};\n"
-          "  for (;;) {\n"
-          "    if (threadIdx.x == 0) S.item = atomicAdd(item_ctr, 1ull);\n"
-          "    __syncthreads();\n"
-          "    const fbg_u64 item = S.item;\n"
-          "    __syncthreads();\n"
-          "    if (item >= nitems) break;\n"
-          "    const FbgWorkItem W = items[item];\n"
-          "    fbg_u64 cnt = 0;\n"
-          "    switch (fid[W.prog]) {\n";
-  for (size_t gi = 0; gi < names.size(); gi++)
-    body += "      case " + std::to_string(gi) + ": cnt = " + names[gi] + "(W.unit_begin, W.unit_end, threadIdx.x, lvl) + " +
-            names[gi] + "(W.unit_begin, W.unit_end, threadIdx.x + 32u, lvl); break;\n";
-  body += "      default: process_item<0>(S, T, progs, W, cur, alive0, P, cnt, iters); break;\n"
-          "    }\n"
-          "    cnt = fbg_warp_sum(cnt);\n"
-          "    if ((threadIdx.x & 31u) == 0u && cnt) atomicAdd(prog_counts + W.prog, cnt);\n"
-          "  }\n"
-          "}\n";
-  return body;
-}
-
-// compile the plan's functions (in parallel) and the batch kernel; drops the
-// functions that fail or miss the deadline; returns the relocatable cubins
-bool build_batch_cubins(BatchPlan& plan, std::vector<std::string>* cubins, std::string* log) {
-  std::vector<std::string> fn_cubins;
-  std::vector<bool> ok = jit_compile_rdc_many(plan.fn_src, &fn_cubins, kCompileDeadlineS, log);
-  std::vector<int> remap(plan.fn_src.size(), -1);
-  std::vector<std::string> names;
-  cubins->clear();
-  cubins->push_back(std::string());   // the kernel, below
-  std::vector<LutProgram> kept;
-  for (size_t f = 0; f < ok.size(); f++) {
-    if (!ok[f]) continue;
-    remap[f] = (int)names.size();
-    names.push_back(plan.fn_name[f]);
-    cubins->push_back(fn_cubins[f]);
-    kept.push_back(std::move(plan.spec_lp[f]));
-  }
-  for (auto& f : plan.fid) f = f >= 0 ? remap[(size_t)f] : -1;
-  plan.spec_lp.swap(kept);
-  plan.fn_name = names;
-  std::vector<std::string> kc;
-  std::string klog;
-  std::vector<bool> kok = jit_compile_rdc_many({batch_kernel_source(names)}, &kc, kCompileDeadlineS, &klog);
-  if (!kok[0]) {
-    if (log) *log += klog;
-    return false;
-  }
-  (*cubins)[0] = kc[0];
-  return true;
 }
 
 extern "C" {
@@ -236,12 +214,6 @@ fbg_status fbg_batch_create(fbg_program* const* progs, int nprogs, uint64_t max_
   b->progs.assign(progs, progs + nprogs);
   b->use_graph = (flags & FBG_BATCH_GRAPH) != 0;
   std::vector<FbgInterpProg> descs((size_t)nprogs);
-  struct Item {
-    FbgWorkItem w;
-    double cost;
-  };
-  std::vector<Item> items;
-  uint64_t total_units = 0;
   for (int i = 0; i < nprogs; i++) {
     fbg_program* p = progs[i];
     if (!p) {
@@ -262,66 +234,69 @@ fbg_status fbg_batch_create(fbg_program* const* progs, int nprogs, uint64_t max_
     G.ins = ib.d_ins;
     G.consts = ib.d_consts;
     descs[(size_t)i] = G;
-    b->nslots = std::max(b->nslots, ib.code.nslots);
-    total_units += ib.nunits;
   }
-  // specialised functions for the distinct programs that carry the work
-  std::vector<int> fid((size_t)nprogs, -1);
-  std::vector<LutProgram> spec_lp;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  // specialised kernels for the distinct programs that carry the work
+  b->fid.assign((size_t)nprogs, -1);
   if (flags & FBG_BATCH_SPECIALIZE) {
     std::string err;
     BatchPlan plan = plan_batch(progs, nprogs, &err);
     b->jit_log = err;
-    if (!plan.fn_src.empty()) {
-      std::vector<std::string> cubins;
-      if (build_batch_cubins(plan, &cubins, &b->jit_log)) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        JitResult r = jit_link(cubins, "fbg_batch_kernel", dev);
-        if (!r.log.empty()) b->jit_log += r.log;
-        if (r.ok) {
-          b->kern = r.kernel;
-          b->specialized = (int)plan.fn_name.size();
-          fid = plan.fid;
-          spec_lp = std::move(plan.spec_lp);
-        }
-      }
+    std::vector<JitResult> built = jit_compile_many(plan.src, "fbg_jit_count", dev, kCompileDeadlineS, &b->jit_log);
+    std::vector<int> remap(plan.src.size(), -1);
+    for (size_t k = 0; k < built.size(); k++) {
+      if (!built[k].ok) continue;
+      SpecKernel sk;
+      sk.kern = built[k].kernel;
+      sk.block = plan.block[k];
+      int per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)sk.kern, sk.block, 0) != cudaSuccess ||
+          per_sm <= 0)
+        per_sm = 1;
+      sk.nunits = 1ull << plan.lp[k].layout.unit_bits;
+      sk.grid = (int)std::min<uint64_t>(sk.nunits, (uint64_t)device_sms() * (uint64_t)per_sm);
+      sk.chunk = std::max<uint64_t>(1, sk.nunits / ((uint64_t)sk.grid * 16));
+      sk.nwarps = (unsigned)((uint64_t)sk.grid * (uint64_t)sk.block / 32);
+      remap[k] = (int)b->spec.size();
+      b->spec.push_back(sk);
+    }
+    for (int i = 0; i < nprogs; i++)
+      if (plan.fid[(size_t)i] >= 0) b->fid[(size_t)i] = remap[(size_t)plan.fid[(size_t)i]];
+    b->specialized = (int)b->spec.size();
+  }
+  // interpreter items for the other programs
+  struct Item {
+    FbgWorkItem w;
+    double cost;
+  };
+  std::vector<Item> items;
+  uint64_t interp_units = 0, total_units = 0;
+  for (int i = 0; i < nprogs; i++) {
+    const int f = b->fid[(size_t)i];
+    if (f >= 0) {
+      total_units += b->spec[(size_t)f].nunits;
+    } else {
+      b->nslots = std::max(b->nslots, progs[i]->ib[0].code.nslots);
+      interp_units += progs[i]->ib[0].nunits;
     }
   }
-  b->fid = fid;
-  // units of each program in the layout its items are evaluated in
-  std::vector<uint64_t> nunits((size_t)nprogs);
-  total_units = 0;
-  for (int i = 0; i < nprogs; i++) {
-    nunits[(size_t)i] = fid[(size_t)i] >= 0 ? (1ull << spec_lp[(size_t)fid[(size_t)i]].layout.unit_bits)
-                                              : progs[i]->ib[0].nunits;
-    total_units += nunits[(size_t)i];
-  }
-  // item size: about 8 items per resident block, never more than max_item_units
+  total_units += interp_units;
   int per_sm = interp_blocks_per_sm(0, b->nslots);
-  if (b->kern) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    size_t smem = interp_smem_bytes(b->nslots);
-    cudaKernelSetAttributeForDevice(b->kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem, dev);
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, (const void*)b->kern, FBG_INTERP_THREADS, smem) == cudaSuccess &&
-        nb > 0)
-      per_sm = nb;
-  }
   if (per_sm <= 0) {
     delete b;
     return set_error(FBG_ETOOBIG, "batch programs do not fit in shared memory");
   }
+  // item size: about 8 items per resident block, never more than max_item_units
   uint64_t resident = (uint64_t)device_sms() * (uint64_t)per_sm;
   uint64_t target_items = resident * 8;
-  uint64_t auto_units = std::max<uint64_t>(1, total_units / std::max<uint64_t>(1, target_items));
+  uint64_t auto_units = std::max<uint64_t>(1, interp_units / std::max<uint64_t>(1, target_items));
   uint64_t chunk = max_item_units ? max_item_units : auto_units;
   for (int i = 0; i < nprogs; i++) {
+    if (b->fid[(size_t)i] >= 0) continue;
     const InterpBuild& ib = progs[i]->ib[0];
-    uint64_t nu = nunits[(size_t)i];
-    double unit_cost = (double)std::max<size_t>(1, ib.code.ins.size()) *
-                       std::ldexp(1.0, progs[i]->n) / (double)nu;
+    uint64_t nu = ib.nunits;
+    double unit_cost = (double)std::max<size_t>(1, ib.code.ins.size()) * std::ldexp(1.0, progs[i]->n) / (double)nu;
     for (uint64_t u = 0; u < nu; u += chunk) {
       uint64_t e = std::min(nu, u + chunk);
       items.push_back(Item{FbgWorkItem{(unsigned)i, 0u, u, e}, unit_cost * (double)(e - u)});
@@ -333,19 +308,70 @@ fbg_status fbg_batch_create(fbg_program* const* progs, int nprogs, uint64_t max_
   for (auto& it : items) w.push_back(it.w);
   b->nitems = w.size();
   b->units = total_units;
-  b->grid = (int)std::min<uint64_t>(b->nitems, resident);
+  b->grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(b->nitems, resident));
   cudaError_t e;
-  if ((e = cudaMalloc(&b->d_fid, (size_t)nprogs * sizeof(int))) != cudaSuccess ||
-      (e = cudaMemcpy(b->d_fid, fid.data(), (size_t)nprogs * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMalloc(&b->d_progs, descs.size() * sizeof(FbgInterpProg))) != cudaSuccess ||
-      (e = cudaMalloc(&b->d_items, w.size() * sizeof(FbgWorkItem))) != cudaSuccess ||
+  if ((e = cudaMalloc(&b->d_progs, descs.size() * sizeof(FbgInterpProg))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_items, std::max<size_t>(1, w.size()) * sizeof(FbgWorkItem))) != cudaSuccess ||
       (e = cudaMalloc(&b->d_counts, ((size_t)nprogs + 1) * 8)) != cudaSuccess ||
       (e = cudaMallocHost(&b->h_counts, (size_t)nprogs * 8)) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_inst, (size_t)nprogs * kInstWords * 8)) != cudaSuccess ||
+      (e = cudaMemset(b->d_inst, 0, (size_t)nprogs * kInstWords * 8)) != cudaSuccess ||
       (e = cudaMemcpy(b->d_progs, descs.data(), descs.size() * sizeof(FbgInterpProg), cudaMemcpyHostToDevice)) !=
           cudaSuccess ||
-      (e = cudaMemcpy(b->d_items, w.data(), w.size() * sizeof(FbgWorkItem), cudaMemcpyHostToDevice)) != cudaSuccess) {
+      (w.size() && (e = cudaMemcpy(b->d_items, w.data(), w.size() * sizeof(FbgWorkItem), cudaMemcpyHostToDevice)) !=
+                       cudaSuccess)) {
     delete b;
     return cuda_error(e, "batch setup");
+  }
+  if (!b->spec.empty()) {
+    // one timed launch per kernel (after one untimed), on a private stream
+    cudaStream_t ts = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    std::vector<int> first(b->spec.size(), -1);
+    for (int i = 0; i < nprogs; i++)
+      if (b->fid[(size_t)i] >= 0 && first[(size_t)b->fid[(size_t)i]] < 0) first[(size_t)b->fid[(size_t)i]] = i;
+    e = cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (size_t k = 0; k < b->spec.size() && e == cudaSuccess; k++) {
+      e = launch_spec(b, first[k], ts);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, ts);
+      if (e == cudaSuccess) e = launch_spec(b, first[k], ts);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, ts);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&b->spec[k].ms, e0, e1);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (ts) cudaStreamDestroy(ts);
+    if (e != cudaSuccess) {
+      delete b;
+      return cuda_error(e, "batch kernel timing");
+    }
+    // longest processing time first over the side streams
+    std::vector<int> order;
+    for (int i = 0; i < nprogs; i++)
+      if (b->fid[(size_t)i] >= 0) order.push_back(i);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+      return b->spec[(size_t)b->fid[(size_t)x]].ms > b->spec[(size_t)b->fid[(size_t)y]].ms;
+    });
+    b->lanes.assign(kSideStreams, {});
+    std::vector<double> load(kSideStreams, 0.0);
+    for (int i : order) {
+      size_t s = (size_t)(std::min_element(load.begin(), load.end()) - load.begin());
+      b->lanes[s].push_back(i);
+      load[s] += b->spec[(size_t)b->fid[(size_t)i]].ms;
+    }
+    b->side.assign(kSideStreams + 1, nullptr);
+    b->ev.assign(kSideStreams + 2, nullptr);
+    for (auto& s : b->side)
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    for (auto& ev : b->ev)
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      delete b;
+      return cuda_error(e, "batch streams");
+    }
   }
   *out = b;
   return FBG_OK;
@@ -406,9 +432,9 @@ fbg_status fbg_debug_batch_source(fbg_program* const* progs, int nprogs, char* b
   if (!progs || nprogs <= 0 || !len) return set_error(FBG_EINVAL, "bad argument");
   std::string err;
   BatchPlan plan = plan_batch(progs, nprogs, &err);
-  if (plan.fn_src.empty() && !err.empty()) return set_error(FBG_ETOOBIG, err);
-  std::string src = batch_kernel_source(plan.fn_name);
-  for (auto& f : plan.fn_src) src += f;
+  if (plan.src.empty() && !err.empty()) return set_error(FBG_ETOOBIG, err);
+  std::string src;
+  for (size_t k = 0; k < plan.src.size(); k++) src += "// specialised count kernel " + std::to_string(k) + "\n" + plan.src[k];
   if (buf) {
     if (*len < src.size() + 1) return set_error(FBG_EINVAL, "buffer too small");
     std::memcpy(buf, src.c_str(), src.size() + 1);
@@ -421,10 +447,17 @@ fbg_status fbg_debug_batch_build(fbg_program* const* progs, int nprogs, int* spe
   if (!progs || nprogs <= 0) return set_error(FBG_EINVAL, "bad argument");
   std::string err;
   BatchPlan plan = plan_batch(progs, nprogs, &err);
-  std::vector<std::string> cubins;
-  bool ok = plan.fn_src.empty() || build_batch_cubins(plan, &cubins, &err);
-  if (ok && !cubins.empty()) ok = jit_link_check(cubins, &err);
-  if (specialized) *specialized = ok ? (int)plan.fn_name.size() : 0;
+  int good = 0;
+  bool ok = true;
+  for (auto& src : plan.src) {
+    std::string lg;
+    if (jit_check(src, &lg)) good++;
+    else {
+      ok = false;
+      if (err.size() < 4096) err += lg;
+    }
+  }
+  if (specialized) *specialized = good;
   if (log && loglen) {
     size_t n = std::min(loglen - 1, err.size());
     std::memcpy(log, err.data(), n);

@@ -162,13 +162,15 @@ namespace {
 std::mutex g_rdc_mu;
 std::unordered_map<std::string, std::string> g_rdc_cache;   // source -> relocatable cubin
 
-bool nvrtc_rdc(const std::string& src, std::string* cubin, std::string* log) {
+// one NVRTC compilation to a cubin: relocatable (for nvJitLink) or complete
+bool nvrtc_cubin(const std::string& src, bool rdc, std::string* cubin, std::string* log) {
   const char* hdrs[3] = {fbg_device_header, fbg_interp_format_header, fbg_interp_device_header};
   const char* names[3] = {"fbg_device.cuh", "interp_format.h", "interp_device.cuh"};
   nvrtcProgram prog;
-  if (nvrtcCreateProgram(&prog, src.c_str(), "fbg_rdc.cu", 3, hdrs, names) != NVRTC_SUCCESS) return false;
-  const char* opts[] = {"-arch=sm_103a", "-std=c++17", "-rdc=true", "-lineinfo"};
-  nvrtcResult e = nvrtcCompileProgram(prog, 4, opts);
+  if (nvrtcCreateProgram(&prog, src.c_str(), rdc ? "fbg_rdc.cu" : "fbg_jit.cu", 3, hdrs, names) != NVRTC_SUCCESS)
+    return false;
+  const char* opts[] = {"-arch=sm_103a", "-std=c++17", "-lineinfo", "-rdc=true"};
+  nvrtcResult e = nvrtcCompileProgram(prog, rdc ? 4 : 3, opts);
   size_t logn = 0;
   nvrtcGetProgramLogSize(prog, &logn);
   if (log && logn > 1) {
@@ -186,10 +188,16 @@ bool nvrtc_rdc(const std::string& src, std::string* cubin, std::string* log) {
   return ok;
 }
 
-}  // namespace
+// a pool of worker threads compiles the sources not yet cached (rdc: the
+// relocatable cache, else the cubin cache); sources still compiling at the
+// deadline are reported as not ok (their compiles finish in the background)
+std::mutex g_cubin_mu;
+std::unordered_map<std::string, std::string> g_cubin_cache;   // source -> complete cubin
 
-std::vector<bool> jit_compile_rdc_many(const std::vector<std::string>& bodies, std::vector<std::string>* cubins,
-                                       double deadline_s, std::string* log) {
+std::vector<bool> compile_many(const std::vector<std::string>& bodies, bool rdc, std::vector<std::string>* cubins,
+                               double deadline_s, std::string* log) {
+  std::mutex& cmu = rdc ? g_rdc_mu : g_cubin_mu;
+  std::unordered_map<std::string, std::string>& cache = rdc ? g_rdc_cache : g_cubin_cache;
   const size_t n = bodies.size();
   cubins->assign(n, std::string());
   std::vector<bool> ok(n, false);
@@ -205,10 +213,10 @@ std::vector<bool> jit_compile_rdc_many(const std::vector<std::string>& bodies, s
   auto pool = std::make_shared<Pool>();
   for (size_t i = 0; i < n; i++) {
     std::string src = "#include \"fbg_device.cuh\"\n" + bodies[i];
-    std::lock_guard<std::mutex> lk(g_rdc_mu);
-    auto it = g_rdc_cache.find(src);
+    std::lock_guard<std::mutex> lk(cmu);
+    auto it = cache.find(src);
     pool->src.push_back(src);
-    if (it != g_rdc_cache.end()) {
+    if (it != cache.end()) {
       pool->out.push_back(it->second);
       pool->state.push_back(2);
       pool->finished++;
@@ -219,7 +227,7 @@ std::vector<bool> jit_compile_rdc_many(const std::vector<std::string>& bodies, s
   }
   unsigned workers = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), 16u));
   for (unsigned w = 0; w < workers; w++) {
-    std::thread([pool, n] {
+    std::thread([pool, n, rdc, &cmu, &cache] {
       for (;;) {
         size_t i;
         {
@@ -230,10 +238,10 @@ std::vector<bool> jit_compile_rdc_many(const std::vector<std::string>& bodies, s
           pool->state[i] = 1;
         }
         std::string cubin, lg;
-        bool good = nvrtc_rdc(pool->src[i], &cubin, &lg);
+        bool good = nvrtc_cubin(pool->src[i], rdc, &cubin, &lg);
         if (good) {
-          std::lock_guard<std::mutex> lk(g_rdc_mu);
-          g_rdc_cache.emplace(pool->src[i], cubin);
+          std::lock_guard<std::mutex> lk(cmu);
+          cache.emplace(pool->src[i], cubin);
         }
         std::lock_guard<std::mutex> lk(pool->mu);
         pool->out[i] = std::move(cubin);
@@ -255,6 +263,71 @@ std::vector<bool> jit_compile_rdc_many(const std::vector<std::string>& bodies, s
   if (log) *log = pool->log;
   if (pool->finished < n && log) *log += "\nsome programs were still compiling at the deadline and run interpreted";
   return ok;
+}
+
+// load a complete cubin (cached by key) and look up `kernel_name`
+JitResult load_cubin(const std::string& key, const std::string& cubin, const char* kernel_name) {
+  JitResult r;
+  Entry ent;
+  cudaError_t ce = cudaLibraryLoadData(&ent.lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+  if (ce != cudaSuccess) {
+    r.log = std::string("cudaLibraryLoadData: ") + cudaGetErrorString(ce);
+    return r;
+  }
+  ce = cudaLibraryGetKernel(&ent.kern, ent.lib, kernel_name);
+  if (ce != cudaSuccess) {
+    r.log = std::string("cudaLibraryGetKernel: ") + cudaGetErrorString(ce);
+    cudaLibraryUnload(ent.lib);
+    return r;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto ins = g_cache.emplace(key, ent);
+    if (!ins.second) {
+      cudaLibraryUnload(ent.lib);
+      ent = ins.first->second;
+    }
+  }
+  r.ok = true;
+  r.kernel = ent.kern;
+  return r;
+}
+
+}  // namespace
+
+std::vector<bool> jit_compile_rdc_many(const std::vector<std::string>& bodies, std::vector<std::string>* cubins,
+                                       double deadline_s, std::string* log) {
+  return compile_many(bodies, true, cubins, deadline_s, log);
+}
+
+std::vector<JitResult> jit_compile_many(const std::vector<std::string>& bodies, const char* kernel_name, int device,
+                                        double deadline_s, std::string* log) {
+  const size_t n = bodies.size();
+  std::vector<JitResult> res(n);
+  std::vector<std::string> todo;
+  std::vector<size_t> where;
+  for (size_t i = 0; i < n; i++) {
+    std::string key = std::to_string(device) + ":" + kernel_name + ":#include \"fbg_device.cuh\"\n" + bodies[i];
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) {
+      res[i].ok = true;
+      res[i].cached = true;
+      res[i].kernel = it->second.kern;
+    } else {
+      todo.push_back(bodies[i]);
+      where.push_back(i);
+    }
+  }
+  if (todo.empty()) return res;
+  std::vector<std::string> cubins;
+  std::vector<bool> ok = compile_many(todo, false, &cubins, deadline_s, log);
+  for (size_t t = 0; t < todo.size(); t++) {
+    if (!ok[t]) continue;
+    std::string key = std::to_string(device) + ":" + kernel_name + ":#include \"fbg_device.cuh\"\n" + todo[t];
+    res[where[t]] = load_cubin(key, cubins[t], kernel_name);
+  }
+  return res;
 }
 
 JitResult jit_link(const std::vector<std::string>& cubins, const char* kernel_name, int device) {

@@ -23,6 +23,10 @@ size_t jit_cache_size();
 // deadline_s are reported as not ok (their compiles finish in the background).
 std::vector<bool> jit_compile_rdc_many(const std::vector<std::string>& bodies, std::vector<std::string>* cubins,
                                        double deadline_s, std::string* log);
+// Complete kernels for many sources at once (same pool and deadline), each
+// loaded on this device and cached like jit_compile; failures are not ok.
+std::vector<JitResult> jit_compile_many(const std::vector<std::string>& bodies, const char* kernel_name, int device,
+                                        double deadline_s, std::string* log);
 // Link relocatable cubins with nvJitLink and load `kernel_name` on this device.
 JitResult jit_link(const std::vector<std::string>& cubins, const char* kernel_name, int device);
 bool jit_link_check(const std::vector<std::string>& cubins, std::string* log);

@@ -83,6 +83,7 @@ struct fbg_server {
   // statistics
   std::atomic<uint64_t> ticks{0}, launches{0};
   double busy_s = 0;
+  double admit_s = 0, count_s = 0, enum_s = 0;   // server-thread time by activity
   fbg_status fatal = FBG_OK;
 
   void run();
@@ -147,6 +148,7 @@ void fbg_server::tick() {
   std::vector<Request*> count_reqs, enum_reqs;
   {
     std::unique_lock<std::mutex> lk(mu);
+    const double ta = now_s();
     // admission by device memory and free slots, in arrival order
     while (!pending.empty()) {
       Request* r = pending.front();
@@ -159,8 +161,10 @@ void fbg_server::tick() {
       fbg_status s = admit_locked(r);
       if (s != FBG_OK) finish(r, s);
     }
+    admit_s += now_s() - ta;
     for (Request* r : active) (r->mode == FBG_MODE_COUNT ? count_reqs : enum_reqs).push_back(r);
   }
+  const double tc = now_s();
   // one launch over a share of every admitted count request
   if (!count_reqs.empty()) {
     uint64_t budget = opt.tick_units;
@@ -206,6 +210,8 @@ void fbg_server::tick() {
     }
     active.erase(std::remove_if(active.begin(), active.end(), [](Request* r) { return r->done; }), active.end());
   }
+  count_s += now_s() - tc;
+  const double te = now_s();
   // model lists: ordered two-pass evaluation, one request after another
   for (Request* r : enum_reqs) {
     size_t cap = (size_t)r->cap;
@@ -229,6 +235,7 @@ void fbg_server::tick() {
     finish(r, s);
     active.erase(std::remove(active.begin(), active.end(), r), active.end());
   }
+  enum_s += now_s() - te;
   ticks++;
   busy_s += now_s() - t0;
 }
@@ -347,6 +354,15 @@ fbg_status fbg_server_stats(fbg_server* s, uint64_t* ticks, uint64_t* launches, 
   if (ticks) *ticks = s->ticks.load();
   if (launches) *launches = s->launches.load();
   if (busy_s) *busy_s = s->busy_s;
+  return FBG_OK;
+}
+
+fbg_status fbg_server_profile(fbg_server* s, double* admit_s, double* count_s, double* enum_s) {
+  if (!s) return set_error(FBG_EINVAL, "null server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (admit_s) *admit_s = s->admit_s;
+  if (count_s) *count_s = s->count_s;
+  if (enum_s) *enum_s = s->enum_s;
   return FBG_OK;
 }
 

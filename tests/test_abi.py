@@ -75,12 +75,12 @@ def test_option_validation():
         assert ei.value.status == L.FBG_EINVAL
 
 
-def test_hybrid_batch_kernel_compiles_and_links_without_a_device():
+def test_batch_specialised_kernels_compile_without_a_device():
     from paper_1310_6978_b300 import workloads as W
     mix = [W.transitive(5), W.equivalences(5), W.cnf3(22, 4), W.cnf3(21, 5)] * 2 + [W.cnf3(12, 1), W.POSET3]
     progs = [F.compile(w.text, w.k) for w in mix]
     ok, spec, log = F.batch_build_check(progs)
     assert ok, log
-    assert spec == 4          # the four distinct programs with n >= 20
+    assert spec == 4          # one kernel per distinct program with n >= 20
     src = F.batch_source(progs)
-    assert src.count("case ") == 4 and "fbg_batch_kernel" in src
+    assert src.count("fbg_jit_count(FbgLaunch P)") == 4 and "fbg_finish_count" in src

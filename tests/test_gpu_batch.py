@@ -69,8 +69,9 @@ def test_batch_mix_matches_single_counts():
     assert all(kinds[i] == 1 for i, w in enumerate(sel) if w.n == 36)
 
 
-def test_hybrid_batch_mixes_specialised_and_interpreted():
-    """Two heavy programs specialised, many light ones interpreted, in one kernel."""
+def test_batch_mixes_specialised_and_interpreted():
+    """Two heavy programs on specialised kernels (three instances each, on
+    side streams), many light ones in the interpreter launch."""
     heavy = [W.transitive(5), W.equivalences(5)] * 3
     light = small_mix(80, 9)
     mix = heavy + light
