@@ -141,6 +141,77 @@ def cpu_oracle_rate(wls, seconds_budget: float, seed: int = 7):
     return done / dt, cores, f"{chunks} random subcubes of 2^22 assignments (22 free letters) over the three n=36 formulas, {dt:.1f} s"
 
 
+def cpu_single_thread_rate(wls, seconds_budget: float = 3.0, seed: int = 11):
+    """The oracle on one host thread, same kind of sample (2^20-assignment
+    subcubes)."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(seed)
+    done, chunks = 0, 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds_budget or chunks < len(wls):
+        wl = wls[chunks % len(wls)]
+        th = oracle.Theory(wl.text, wl.k)
+        fixed = [int(v) for v in rng.choice(wl.n, wl.n - 20, replace=False)]
+        mask = sum(1 << v for v in fixed)
+        th.count_cube(mask, int(rng.integers(0, 1 << 62)) & mask)
+        done += 1 << 20
+        chunks += 1
+    return done / (time.perf_counter() - t0)
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def run_small(torch, F, stream):
+    """Posets on 3 points (n = 9, 19 models, 8-word table): latency of the
+    public calls (host round trip) and device time of back-to-back launches."""
+    from paper_1310_6978_b300 import workloads as W
+    wl = W.POSET3
+    p = F.compile(wl.text, wl.k)
+    table = torch.zeros(p.table_words(), dtype=torch.int64, device="cuda")
+    out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    assert p.count(stream) == 19
+    p.truth_table(table, stream)
+    stream.synchronize()
+    host_us = []
+    for _ in range(200):
+        t0 = time.perf_counter()
+        c = p.count(stream)
+        host_us.append((time.perf_counter() - t0) * 1e6)
+    assert c == 19
+    host_us.sort()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 200
+    with torch.cuda.stream(stream):
+        for _ in range(5):
+            p.count_async(out, stream=stream)
+        e0.record(stream)
+        for _ in range(reps):
+            p.count_async(out, stream=stream)
+        e1.record(stream)
+        e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        for _ in range(reps):
+            p.truth_table(table, stream)
+        e3.record(stream)
+    stream.synchronize()
+    assert int(out.item()) == 19
+    return {"workload": "posets on 3 points (n=9): count 19, 8-word table",
+            "count_call_us_p50": host_us[len(host_us) // 2], "count_call_us_p99": host_us[int(0.99 * len(host_us))],
+            "count_launch_us": e0.elapsed_time(e1) * 1e3 / reps, "table_launch_us": e2.elapsed_time(e3) * 1e3 / reps,
+            "basis": "call = fbg_count incl. launch, sync and copy of the count to the host; launch = CUDA-event "
+                     "time per launch over 200 back-to-back launches"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -451,6 +522,7 @@ def run_ours(args, rank, world):
                  "lop3_tops": bex / bt / 1e12, "frac": bex / bt / peak_lop3}
 
     table_leg = {} if args.quick else run_table(args, torch, F, L, load_peaks())
+    small_leg = {} if args.quick else run_small(torch, F, stream)
     batched = {} if args.quick or args.no_batch else run_batched(args, torch, F, L)
     serving = {} if args.quick or args.no_serve else run_serving(args, torch, F, L)
 
@@ -468,7 +540,9 @@ def run_ours(args, rank, world):
     cpu = {}
     if world == 1 and not args.no_cpu:
         rate, cores, sample = cpu_oracle_rate(wls, args.cpu_seconds)
-        cpu = {"value": rate / 1e9, "unit": "Gassign/s", "cores": cores, "kind": "oracle", "sample": sample}
+        one = cpu_single_thread_rate(wls)
+        cpu = {"value": rate / 1e9, "unit": "Gassign/s", "cores": cores, "kind": "oracle", "sample": sample,
+               "single_thread_value": one / 1e9, "cpu_model": cpu_model(), "extrapolated": True}
     peaks = load_peaks()
     line = {
         "metric": "model-count throughput at n=36 (Gassign/s)",
@@ -487,6 +561,7 @@ def run_ours(args, rank, world):
         "nominal_lop3_ratio": executed / nominal if nominal else None,
         "brute_force": brute,
         "truth_table": table_leg,
+        "small_poset3": small_leg,
         "batched": batched,
         "serving": serving,
         "clocks": clocks,

@@ -2,10 +2,10 @@
 // nvcc-compiled kernels (interp.cu) and the NVRTC-compiled batch kernel that
 // mixes interpreted and specialised programs.  Evaluates the LUT bytecode of
 // interp_format.h on 64-bit tiles: the bitwise evaluation of Sec. 2.3 with
-// 64-bit blocks.  A block is one warp; each thread owns two tiles per
-// innermost iteration (the layout's threads lane and lane + 32), so every
-// decoded instruction does the work of both (two independent data paths per
-// instruction); values live in per-thread columns of shared memory plus an
+// 64-bit blocks.  A block is one warp; each thread owns B / 32 tiles per
+// innermost iteration (the layout's threads lane, lane + 32, ...), so every
+// decoded instruction does the work of all of them (independent data paths
+// per instruction); values live in per-thread columns of shared memory plus an
 // accumulator register; loop levels run as an odometer; a level whose partial
 // conjunction is zero for the whole warp skips its inner levels.
 #pragma once
@@ -27,10 +27,10 @@ __device__ __forceinline__ fbg_u64 lop3_pair(fbg_u64 a, fbg_u64 b, fbg_u64 c) {
 constexpr int B = FBG_INTERP_BLOCK;          // tiles per block (the layout's threads), slot stride
 constexpr int NT = FBG_INTERP_THREADS;       // threads per block
 constexpr int NTILE = B / NT;                // tiles per thread
-static_assert(NT == 32 && NTILE == 2, "one warp per block, two tiles per thread");
+static_assert(NT == 32 && NTILE * NT == B, "one warp per block, B / 32 tiles per thread");
 constexpr int MAX_CONST_SMEM = FBG_INTERP_MAX_CONSTS;
 
-// the two tiles of a thread: tile k is the layout's thread lane + 32 k
+// the tiles of a thread: tile k is the layout's thread lane + 32 k
 struct Pair {
   fbg_u64 v[NTILE];
 };
@@ -40,10 +40,9 @@ struct Pair {
 __device__ __forceinline__ Pair lop3_dyn(unsigned lut, const Pair& a, const Pair& b, const Pair& c) {
   Pair d;
   switch (lut) {
-#define FBG_C(x)                                   \
-  case (x):                                        \
-    d.v[0] = lop3_pair<(x)>(a.v[0], b.v[0], c.v[0]); \
-    d.v[1] = lop3_pair<(x)>(a.v[1], b.v[1], c.v[1]); \
+#define FBG_C(x)                                                               \
+  case (x):                                                                    \
+    _Pragma("unroll") for (int k = 0; k < NTILE; k++) d.v[k] = lop3_pair<(x)>(a.v[k], b.v[k], c.v[k]); \
     return d;
 #define FBG_C4(x) FBG_C(x) FBG_C((x) + 1) FBG_C((x) + 2) FBG_C((x) + 3)
 #define FBG_C16(x) FBG_C4(x) FBG_C4((x) + 4) FBG_C4((x) + 8) FBG_C4((x) + 12)
@@ -54,7 +53,8 @@ __device__ __forceinline__ Pair lop3_dyn(unsigned lut, const Pair& a, const Pair
 #undef FBG_C4
 #undef FBG_C
   }
-  d.v[0] = d.v[1] = 0;
+#pragma unroll
+  for (int k = 0; k < NTILE; k++) d.v[k] = 0;
   return d;
 }
 
@@ -73,8 +73,11 @@ struct Thread {
 
 __device__ __forceinline__ void init_thread(Thread& T, fbg_u64* dyn_slots) {
   T.slots = dyn_slots + threadIdx.x;
-  T.acc.v[0] = T.acc.v[1] = 0;
-  T.coords[0] = T.coords[1] = 0;
+#pragma unroll
+  for (int k = 0; k < NTILE; k++) {
+    T.acc.v[k] = 0;
+    T.coords[k] = 0;
+  }
 }
 
 __device__ __forceinline__ void set_thread_coords(Thread& T, fbg_u64 upper) {
@@ -91,7 +94,9 @@ __device__ __forceinline__ Pair fetch(const Shared& S, const Thread& T, unsigned
     return r;
   }
   if (op & FBG_OP_CONST) {
-    r.v[0] = r.v[1] = S.consts[op & 0x3FFFu];
+    const fbg_u64 c = S.consts[op & 0x3FFFu];
+#pragma unroll
+    for (int k = 0; k < NTILE; k++) r.v[k] = c;
     return r;
   }
 #pragma unroll
@@ -128,7 +133,10 @@ template <int MODE>
 __device__ __forceinline__ bool level_alive(const Shared& S, const Thread& T, const FbgInterpLevel& L) {
   if (!L.has_acc) return true;
   const Pair v = fetch(S, T, L.acc_op);
-  const bool mine = (v.v[0] | v.v[1]) != 0ull;
+  fbg_u64 any = 0;
+#pragma unroll
+  for (int k = 0; k < NTILE; k++) any |= v.v[k];
+  const bool mine = any != 0ull;
   if (MODE == 2) return __syncthreads_or(mine) != 0;
   return __any_sync(FBG_FULL, mine);
 }
@@ -191,7 +199,8 @@ __device__ void run_unit(Shared& S, Thread& T, fbg_u64 u, const FbgLaunch& P, fb
 #pragma unroll
       for (int k = 0; k < NTILE; k++) word[k] = tvalid[k] ? (o.v[k] & G.vmask) : 0ull;
       if (MODE == 0) {
-        cnt += (fbg_u64)(__popcll(word[0]) + __popcll(word[1]));
+#pragma unroll
+        for (int k = 0; k < NTILE; k++) cnt += (fbg_u64)__popcll(word[k]);
       } else if (MODE == 1) {
 #pragma unroll
         for (int k = 0; k < NTILE; k++)

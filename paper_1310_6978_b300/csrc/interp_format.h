@@ -9,7 +9,10 @@
 #pragma once
 
 #define FBG_INTERP_MAX_LEVELS 10
-#define FBG_INTERP_BLOCK 64          // tiles per block: the layout's threads (5 lane bits, 1 warp bit)
+// tiles per block: the layout's threads (5 lane bits, 1 warp bit).  Two
+// tiles per thread halve the decode and dispatch work per bit; four were
+// measured slower (the larger slot file in shared memory costs occupancy).
+#define FBG_INTERP_BLOCK 64
 #define FBG_INTERP_THREADS 32        // threads per block; each evaluates BLOCK / THREADS tiles
 #define FBG_INTERP_WARPS_LOG2 1
 #define FBG_INTERP_MAX_SLOTS 160

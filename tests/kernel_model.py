@@ -109,14 +109,14 @@ def lut_program_prune_sound(d: dict) -> bool:
 # ------------------------------------------------------------- interpreter --
 
 OP_CONST, OP_VAR, OP_ACC, DST_ACC = 0x4000, 0x8000, 0xFFFF, 255
-BLOCK = 64
+BLOCK = 64   # tiles of a block: one warp of 32 threads, two tiles each
 
 
 class InterpModel:
-    """Literal model of interp_kernel: one block of 64 threads (2 warps) runs
-    the units in order; loop levels as an odometer; per-warp (count, table)
-    or per-block (enumerate) prune votes; slots and the accumulator as in the
-    kernel."""
+    """Literal model of interp_kernel: one block (one warp holding all 64
+    tiles) runs the units in order; loop levels as an odometer; the prune
+    vote covers the whole warp, so every tile; slots and the accumulator as
+    in the kernel."""
 
     def __init__(self, d: dict):
         self.d = d
@@ -155,9 +155,7 @@ class InterpModel:
     def alive(self, lv, mode):
         has, op = self.levels[lv][4], self.levels[lv][5]
         mine = np.ones(BLOCK, dtype=bool) if not has else (self.fetch(op) != 0)
-        if mode == 2:
-            return np.full(BLOCK, bool(mine.any()))
-        return np.repeat(mine.reshape(-1, 32).any(axis=1), 32)   # warp vote
+        return np.full(BLOCK, bool(mine.any()))   # one warp holds every tile
 
     def run(self, mode, cap=0, unit_offsets=None):
         d = self.d
