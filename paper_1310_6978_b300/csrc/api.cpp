@@ -133,6 +133,16 @@ fbg_status build_interp(fbg_program* p, int which) {
   return FBG_OK;
 }
 
+// the items a full-range count hands out, uploaded in the given order
+fbg_status upload_items(JitBuild& b, const std::vector<unsigned>& items) {
+  b.free_device();
+  CK(cudaMalloc(&b.d_perm, std::max<size_t>(1, items.size()) * sizeof(unsigned)));
+  if (!items.empty())
+    CK(cudaMemcpy(b.d_perm, items.data(), items.size() * sizeof(unsigned), cudaMemcpyHostToDevice));
+  b.nperm = items.size();
+  return FBG_OK;
+}
+
 fbg_status build_jit(fbg_program* p, int mode) {
   JitBuild& b = p->jb[mode];
   if (b.valid) return FBG_OK;
@@ -158,6 +168,25 @@ fbg_status build_jit(fbg_program* p, int mode) {
   if (per_sm <= 0) per_sm = 1;
   b.nunits = 1ull << b.lp.layout.unit_bits;
   b.grid = (int)std::min<uint64_t>(b.nunits, (uint64_t)device_sms() * (uint64_t)per_sm);
+  if (mode == 0 && p->opt_prune) {
+    // units whose unit-only conjuncts are false have no models: full-range
+    // counts skip them when that removes at least a quarter of the units
+    b.alive = alive_units(p->g, b.lp.layout);
+    uint64_t live = 0;
+    for (uint8_t a : b.alive) live += a;
+    if (!b.alive.empty() && live * 4 <= b.nunits * 3) {
+      const int wb = b.lp.layout.warp_bits;
+      std::vector<unsigned> items;
+      items.reserve((size_t)(live << wb));
+      for (uint64_t u = 0; u < b.nunits; u++)
+        if (b.alive[(size_t)u])
+          for (unsigned w = 0; w < (1u << wb); w++) items.push_back((unsigned)(u << wb) | w);
+      fbg_status s = upload_items(b, items);
+      if (s != FBG_OK) return s;
+    } else {
+      b.alive.clear();
+    }
+  }
   b.valid = true;
   return FBG_OK;
 }
@@ -227,11 +256,15 @@ fbg_status launch_count(fbg_program* p, cudaStream_t st, unsigned long long* dev
     P.unit_end = uend;
     P.unit_trace = unit_trace;
     P.item_trace = item_trace;
-    // the measured order covers full-range counts without per-unit outputs
-    if (b.d_perm && ubegin == 0 && uend == b.nunits && !unit_counts && !unit_trace && !item_trace)
-      P.unit_perm = b.d_perm;
     // a few fetches per resident block and unit: enough to balance pruned work
     P.chunk = std::max<uint64_t>(1, (uend - ubegin) / ((uint64_t)b.grid * 16));
+    // the item list (live units, measured order) covers full-range counts
+    // without per-unit outputs
+    if (b.d_perm && ubegin == 0 && uend == b.nunits && !unit_counts && !unit_trace && !item_trace) {
+      P.unit_perm = b.d_perm;
+      P.nperm = b.nperm;
+      P.chunk = std::max<uint64_t>(1, b.nperm / ((uint64_t)b.grid * (uint64_t)(b.block / 32) * 16));
+    }
     if (self_reset) {
       P.acc = p->d_scratch + kScratchAcc;
       P.done = p->d_scratch + kScratchDone;
@@ -485,20 +518,14 @@ fbg_status fbg_schedule_units(fbg_program* p, void* stream) {
   cudaFree(d_tr);
   if (s != FBG_OK) return s;
   if (e != cudaSuccess) return cuda_error(e, "fbg_schedule_units trace");
-  // longest processing time first; ties keep the natural (unit, slice) order
-  std::vector<unsigned> perm((size_t)items);
-  for (uint64_t t = 0; t < items; t++) perm[(size_t)t] = (unsigned)t;
+  // longest processing time first; ties keep the natural (unit, slice)
+  // order; units without models (b.alive) stay out
+  std::vector<unsigned> perm;
+  perm.reserve((size_t)items);
+  for (uint64_t t = 0; t < items; t++)
+    if (b.alive.empty() || b.alive[(size_t)(t >> wb)]) perm.push_back((unsigned)t);
   std::stable_sort(perm.begin(), perm.end(), [&](unsigned x, unsigned y) { return ns[x] > ns[y]; });
-  unsigned* d_perm = nullptr;
-  CK(cudaMalloc(&d_perm, items * 4));
-  e = cudaMemcpyAsync(d_perm, perm.data(), items * 4, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) {
-    cudaFree(d_perm);
-    return cuda_error(e, "fbg_schedule_units upload");
-  }
-  b.d_perm = d_perm;
-  return FBG_OK;
+  return upload_items(b, perm);
 }
 
 fbg_status fbg_debug_item_trace(fbg_program* p, void* stream, uint64_t* dev_ns, uint64_t nitems) {
@@ -691,7 +718,21 @@ fbg_status fbg_debug_dump(fbg_program* p, int which, char* buf, size_t* len) {
     val_json(lp.out);
     o << ", \"const_acc\": [";
     for (size_t j = 0; j < lp.const_acc.w.size(); j++) o << (j ? ", " : "") << lp.const_acc.w[j];
-    o << "]}";
+    o << "]";
+    if (which == 0 && p->opt_prune) {   // units the count kernel hands out (all when absent)
+      std::vector<uint8_t> alive = alive_units(p->g, lp.layout);
+      if (!alive.empty()) {
+        o << ", \"alive_units\": [";
+        bool first = true;
+        for (size_t u = 0; u < alive.size(); u++)
+          if (alive[u]) {
+            o << (first ? "" : ", ") << u;
+            first = false;
+          }
+        o << "]";
+      }
+    }
+    o << "}";
   } else {
     InterpCode code;
     LutProgram lp;

@@ -48,6 +48,8 @@ struct SpecKernel {
   int grid = 1, block = 32;
   uint64_t nunits = 1, chunk = 1;
   unsigned nwarps = 1;
+  unsigned* d_items = nullptr;   // live (unit, slice) items, or null: all
+  uint64_t nitems = 0;
   float ms = 0.f;   // one launch, measured when the batch is created
 };
 
@@ -87,6 +89,8 @@ struct fbg_batch {
     if (d_counts) cudaFree(d_counts);
     if (h_counts) cudaFreeHost(h_counts);
     if (d_inst) cudaFree(d_inst);
+    for (SpecKernel& k : spec)
+      if (k.d_items) cudaFree(k.d_items);
   }
 };
 
@@ -111,6 +115,10 @@ cudaError_t launch_spec(const fbg_batch* b, int i, cudaStream_t st) {
   P.unit_begin = 0;
   P.unit_end = k.nunits;
   P.chunk = k.chunk;
+  if (k.d_items) {
+    P.unit_perm = k.d_items;
+    P.nperm = k.nitems;
+  }
   void* args[] = {&P};
   return cudaLaunchKernel((const void*)k.kern, dim3((unsigned)k.grid), dim3((unsigned)k.block), args, 0, st);
 }
@@ -157,6 +165,8 @@ struct BatchPlan {
   std::vector<std::string> src;         // per kernel: complete NVRTC source
   std::vector<LutProgram> lp;           // per kernel: its layout and LUTs
   std::vector<int> block;               // per kernel: threads per block
+  std::vector<std::vector<unsigned>> live;   // per kernel: live items (when filtered)
+  std::vector<char> filtered;                 // per kernel: 1 = hand out `live` only
 };
 
 // Choice of the programs to specialise (host only): distinct programs (by
@@ -194,10 +204,25 @@ BatchPlan plan_batch(fbg_program* const* progs, int nprogs, std::string* err) {
       int block = prog.layout.lane_bits < 5 ? 32 : 32 << prog.layout.warp_bits;
       plan.src.push_back(emit_cuda_source(prog, 0, block, 2, nullptr, nullptr, false));
       plan.block.push_back(block);
+      // units whose unit-only conjuncts are false have no models: left out
+      // when that removes at least a quarter of them
+      std::vector<uint8_t> alive = alive_units(p0->g, prog.layout);
+      std::vector<unsigned> live;
+      uint64_t nlive = 0;
+      for (uint8_t a : alive) nlive += a;
+      const bool filter = !alive.empty() && nlive * 4 <= alive.size() * 3;
+      if (filter) {
+        const int wb = prog.layout.warp_bits;
+        for (size_t u = 0; u < alive.size(); u++)
+          if (alive[u])
+            for (unsigned w = 0; w < (1u << wb); w++) live.push_back((unsigned)(u << wb) | w);
+      }
+      plan.live.push_back(std::move(live));
+      plan.filtered.push_back(filter ? 1 : 0);
       plan.lp.push_back(std::move(prog));
     } catch (CompileError& e) {
       if (err) *err = e.msg;
-      return BatchPlan{std::vector<int>((size_t)nprogs, -1), {}, {}, {}};
+      return BatchPlan{std::vector<int>((size_t)nprogs, -1), {}, {}, {}, {}, {}};
     }
     for (int i : *ranked[gi].second) plan.fid[(size_t)i] = (int)gi;
   }
@@ -258,6 +283,19 @@ fbg_status fbg_batch_create(fbg_program* const* progs, int nprogs, uint64_t max_
       sk.grid = (int)std::min<uint64_t>(sk.nunits, (uint64_t)device_sms() * (uint64_t)per_sm);
       sk.chunk = std::max<uint64_t>(1, sk.nunits / ((uint64_t)sk.grid * 16));
       sk.nwarps = (unsigned)((uint64_t)sk.grid * (uint64_t)sk.block / 32);
+      const std::vector<unsigned>& live = plan.live[k];
+      if (plan.filtered[k]) {
+        // live items only (possibly none); on failure all items run
+        if (cudaMalloc(&sk.d_items, std::max<size_t>(1, live.size()) * sizeof(unsigned)) == cudaSuccess &&
+            (live.empty() || cudaMemcpy(sk.d_items, live.data(), live.size() * sizeof(unsigned),
+                                        cudaMemcpyHostToDevice) == cudaSuccess)) {
+          sk.nitems = live.size();
+          sk.chunk = std::max<uint64_t>(1, sk.nitems / ((uint64_t)sk.nwarps * 16));
+        } else if (sk.d_items) {
+          cudaFree(sk.d_items);
+          sk.d_items = nullptr;
+        }
+      }
       remap[k] = (int)b->spec.size();
       b->spec.push_back(sk);
     }

@@ -567,7 +567,7 @@ std::string SrcGen::generate(int mode, int block, int minb) {
     o << "  const fbg_u32 lane = threadIdx.x & 31u;\n";
     o << "  const fbg_u64 chunk = P.chunk ? P.chunk : 1ull;\n";
     o << "  const fbg_u64 R = P.unit_end - P.unit_begin;\n";
-    o << "  const fbg_u64 items = R << " << L.warp_bits << ";\n";
+    o << "  const fbg_u64 items = P.unit_perm ? P.nperm : (R << " << L.warp_bits << ");\n";
     o << "  for (;;) {\n";
     o << "    fbg_u64 t = fbg_next_items_warp(P, chunk);\n";
     o << "    if (t >= items) break;\n";

@@ -23,8 +23,9 @@ struct FbgLaunch {
                            // [2u] += warp-nanoseconds spent, [2u+1] = min start time (ns)
   fbg_u64* item_trace;     // optional (count mode): nanoseconds of item (unit u, warp slice w)
                            // at index (u - unit_begin) * slices + w
-  const fbg_u32* unit_perm;  // optional (count mode, full range): the order in which items are
-                             // handed out, each entry u << warp_bits | w
+  const fbg_u32* unit_perm;  // optional (count mode, full range): the items handed out, in order,
+                             // each entry u << warp_bits | w (units with no models may be left out)
+  fbg_u64 nperm;             // number of entries of unit_perm
   fbg_u64* acc;            // self-resetting count (count mode, when done is set): running sum,
   fbg_u64* done;           //   warps finished, the destination of the total, warps in the grid;
   fbg_u64* out;            //   acc, done and unit_ctr are zero before the launch and after it

@@ -137,6 +137,88 @@ std::vector<int> search_order(const Grounded& g) {
   return order;
 }
 
+// The unit-only conjuncts are evaluated bitwise over all 2^unit_bits units
+// at once: unit bit b is a free generator over the unit index (bit u of its
+// word vector is bit b of u, Sec. 2.2-2.3), so each DAG node costs one pass
+// over 2^unit_bits / 64 words.
+std::vector<uint8_t> alive_units(const Grounded& g, const Layout& L) {
+  const int ub = L.unit_bits;
+  if (ub <= 0 || ub > 16) return {};
+  const FormDag& d = g.dag;
+  std::vector<uint64_t> sup = supports(d);
+  uint64_t umask = 0;
+  std::vector<int> ubit(64, -1);
+  for (int b = 0; b < ub; b++) {
+    const int v = L.var_of_pos[(size_t)(L.first_unit_pos() + b)];
+    umask |= 1ull << v;
+    ubit[(size_t)v] = b;
+  }
+  std::vector<int> keep;
+  const FNode& root = d.node(g.root);
+  if (root.op == FAND) {
+    for (int c : root.kids)
+      if ((sup[(size_t)c] & ~umask) == 0) keep.push_back(c);
+  } else if ((sup[(size_t)g.root] & ~umask) == 0) {
+    keep.push_back(g.root);
+  }
+  if (keep.empty()) return {};
+  const uint64_t U = 1ull << ub;
+  const size_t W = U >= 64 ? (size_t)(U / 64) : 1;
+  const uint64_t tail = U >= 64 ? ~0ull : ((1ull << U) - 1ull);
+  static const uint64_t pat[6] = {0xAAAAAAAAAAAAAAAAull, 0xCCCCCCCCCCCCCCCCull, 0xF0F0F0F0F0F0F0F0ull,
+                                  0xFF00FF00FF00FF00ull, 0xFFFF0000FFFF0000ull, 0xFFFFFFFF00000000ull};
+  // nodes under the kept conjuncts, children first (a child's id is smaller)
+  std::vector<char> need((size_t)d.size(), 0);
+  std::vector<int> stack(keep.begin(), keep.end());
+  while (!stack.empty()) {
+    int x = stack.back();
+    stack.pop_back();
+    if (need[(size_t)x]) continue;
+    need[(size_t)x] = 1;
+    for (int c : d.node(x).kids) stack.push_back(c);
+  }
+  std::vector<std::vector<uint64_t>> val((size_t)d.size());
+  for (int x = 0; x < d.size(); x++) {
+    if (!need[(size_t)x]) continue;
+    const FNode& f = d.node(x);
+    std::vector<uint64_t>& out = val[(size_t)x];
+    out.assign(W, 0);
+    switch (f.op) {
+      case F0: break;
+      case F1: std::fill(out.begin(), out.end(), ~0ull); break;
+      case FVAR: {
+        const int b = ubit[(size_t)f.var];
+        for (size_t w = 0; w < W; w++)
+          out[w] = b < 6 ? pat[b] : (((w >> (b - 6)) & 1) ? ~0ull : 0ull);
+        break;
+      }
+      case FNOT:
+        for (size_t w = 0; w < W; w++) out[w] = ~val[(size_t)f.kids[0]][w];
+        break;
+      case FAND:
+        std::fill(out.begin(), out.end(), ~0ull);
+        for (int c : f.kids)
+          for (size_t w = 0; w < W; w++) out[w] &= val[(size_t)c][w];
+        break;
+      case FOR:
+        for (int c : f.kids)
+          for (size_t w = 0; w < W; w++) out[w] |= val[(size_t)c][w];
+        break;
+      case FXOR:
+        for (size_t w = 0; w < W; w++) out[w] = val[(size_t)f.kids[0]][w] ^ val[(size_t)f.kids[1]][w];
+        break;
+    }
+  }
+  std::vector<uint8_t> alive((size_t)U, 0);
+  for (uint64_t u = 0; u < U; u++) {
+    bool ok = ((tail >> (u & 63)) & 1) != 0;
+    for (int c : keep)
+      if (!((val[(size_t)c][(size_t)(u >> 6)] >> (u & 63)) & 1)) ok = false;
+    alive[(size_t)u] = ok ? 1 : 0;
+  }
+  return alive;
+}
+
 uint32_t rmask_of(const LutProgram& p, const Val& v) {
   if (v.kind == V_LUT) return p.luts[(size_t)v.id].rmask;
   if (v.kind == V_VAR) return 0;

@@ -42,10 +42,13 @@ struct JitBuild {
   cudaKernel_t kern = nullptr;   // owned by the process-wide JIT cache
   int block = 256, grid = 1;
   uint64_t nunits = 1;
-  unsigned* d_perm = nullptr;    // item order of full-range counts (fbg_schedule_units), or null
+  unsigned* d_perm = nullptr;    // items of full-range counts, in order, or null (all, natural order)
+  uint64_t nperm = 0;
+  std::vector<uint8_t> alive;    // per unit: 0 = no models (unit-only conjuncts false), empty = all
   void free_device() {
     if (d_perm) cudaFree(d_perm);
     d_perm = nullptr;
+    nperm = 0;
   }
 };
 

@@ -73,10 +73,11 @@ static inline fbg_u64 fbg_next_items_warp(const FbgLaunch&, fbg_u64 c) { fbg_u64
 
 DRIVER = r'''
 extern "C" int run(int mode, int block, unsigned long long nunits, unsigned long long* count, unsigned* table,
-                   const unsigned* perm, int self_reset) {
+                   const unsigned* perm, unsigned long long nperm, int self_reset) {
   FbgLaunch P;
   std::memset(&P, 0, sizeof P);
   P.unit_perm = perm;
+  P.nperm = nperm;
   unsigned long long acc = 0, done = 0, out = ~0ull;
   if (self_reset) { P.acc = &acc; P.done = &done; P.out = &out; P.nwarps = 1; }
   unsigned long long cnt = 0, ctr = 0;
@@ -115,21 +116,23 @@ def build_kernel(src: str, mode: int) -> ctypes.CDLL:
         os.replace(so + ".tmp", so)
     lib = ctypes.CDLL(so)
     lib.run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_void_p,
-                        ctypes.c_void_p, ctypes.c_int]
+                        ctypes.c_void_p, ctypes.c_ulonglong, ctypes.c_int]
     return lib
 
 
 def run_count(src: str, block: int, nunits: int, perm=None, self_reset: bool = False) -> int:
     """Count; ``perm`` (uint32 array, entries unit << warp_bits | slice) is
-    the item order of a scheduled launch; ``self_reset`` runs the protocol in
-    which the last warp writes the total and zeroes the counters."""
+    the list of items a launch hands out, in order (a scheduled launch, or
+    only the live units); ``self_reset`` runs the protocol in which the last
+    warp writes the total and zeroes the counters."""
     lib = build_kernel(src, 0)
     c = ctypes.c_ulonglong()
-    pp = None
+    pp, npp = None, 0
     if perm is not None:
         perm = np.ascontiguousarray(perm, dtype=np.uint32)
-        pp = perm.ctypes.data_as(ctypes.c_void_p)
-    rc = lib.run(0, block, nunits, ctypes.byref(c), None, pp, 1 if self_reset else 0)
+        pp = perm.ctypes.data_as(ctypes.c_void_p) if len(perm) else ctypes.c_void_p(8)
+        npp = len(perm)
+    rc = lib.run(0, block, nunits, ctypes.byref(c), None, pp, npp, 1 if self_reset else 0)
     assert rc == 0, "counters not reset"
     return c.value
 
@@ -138,5 +141,5 @@ def run_table(src: str, block: int, nunits: int, nwords: int) -> np.ndarray:
     lib = build_kernel(src, 1)
     t = np.zeros(nwords, dtype=np.uint64)
     c = ctypes.c_ulonglong()
-    lib.run(1, block, nunits, ctypes.byref(c), t.ctypes.data_as(ctypes.c_void_p), None, 0)
+    lib.run(1, block, nunits, ctypes.byref(c), t.ctypes.data_as(ctypes.c_void_p), None, 0, 0)
     return t

@@ -37,7 +37,8 @@ def test_generated_source_matches_oracle(wl, li):
     for k, v in LAYOUTS[li].items():
         p.set_option(k, v)
     for mode in (0, 1):
-        d = p.debug_dump(mode)["layout"]
+        d0 = p.debug_dump(mode)
+        d = d0["layout"]
         block = 32 if d["lane_bits"] < 5 else 32 << d["warp_bits"]
         nunits = 1 << d["unit_bits"]
         src = p.source(mode)
@@ -48,5 +49,10 @@ def test_generated_source_matches_oracle(wl, li):
             perm = np.random.default_rng(items).permutation(items).astype(np.uint32)
             assert jit_host.run_count(src, block, nunits, perm) == th.count()
             assert jit_host.run_count(src, block, nunits, perm, self_reset=True) == th.count()
+            # only the units whose unit-only conjuncts hold (the list full-range counts use)
+            if "alive_units" in d0:
+                live = np.array([(u << d["warp_bits"]) | w for u in d0["alive_units"]
+                                 for w in range(1 << d["warp_bits"])], dtype=np.uint32)
+                assert jit_host.run_count(src, block, nunits, live, self_reset=True) == th.count()
         else:
             assert np.array_equal(jit_host.run_table(src, block, nunits, p.table_words()), th.table())
