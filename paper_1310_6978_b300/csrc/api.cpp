@@ -169,18 +169,17 @@ fbg_status build_jit(fbg_program* p, int mode) {
   b.nunits = 1ull << b.lp.layout.unit_bits;
   b.grid = (int)std::min<uint64_t>(b.nunits, (uint64_t)device_sms() * (uint64_t)per_sm);
   if (mode == 0 && p->opt_prune) {
-    // units whose unit-only conjuncts are false have no models: full-range
-    // counts skip them when that removes at least a quarter of the units
-    b.alive = alive_units(p->g, b.lp.layout);
+    // items on which a conjunct over unit and warp letters is false have no
+    // models: full-range counts skip them when that removes at least a
+    // quarter of the items
+    b.alive = alive_items(p->g, b.lp.layout);
     uint64_t live = 0;
     for (uint8_t a : b.alive) live += a;
-    if (!b.alive.empty() && live * 4 <= b.nunits * 3) {
-      const int wb = b.lp.layout.warp_bits;
+    if (!b.alive.empty() && live * 4 <= b.alive.size() * 3) {
       std::vector<unsigned> items;
-      items.reserve((size_t)(live << wb));
-      for (uint64_t u = 0; u < b.nunits; u++)
-        if (b.alive[(size_t)u])
-          for (unsigned w = 0; w < (1u << wb); w++) items.push_back((unsigned)(u << wb) | w);
+      items.reserve((size_t)live);
+      for (size_t t = 0; t < b.alive.size(); t++)
+        if (b.alive[t]) items.push_back((unsigned)t);
       fbg_status s = upload_items(b, items);
       if (s != FBG_OK) return s;
     } else {
@@ -523,7 +522,7 @@ fbg_status fbg_schedule_units(fbg_program* p, void* stream) {
   std::vector<unsigned> perm;
   perm.reserve((size_t)items);
   for (uint64_t t = 0; t < items; t++)
-    if (b.alive.empty() || b.alive[(size_t)(t >> wb)]) perm.push_back((unsigned)t);
+    if (b.alive.empty() || b.alive[(size_t)t]) perm.push_back((unsigned)t);
   std::stable_sort(perm.begin(), perm.end(), [&](unsigned x, unsigned y) { return ns[x] > ns[y]; });
   return upload_items(b, perm);
 }
@@ -720,13 +719,13 @@ fbg_status fbg_debug_dump(fbg_program* p, int which, char* buf, size_t* len) {
     for (size_t j = 0; j < lp.const_acc.w.size(); j++) o << (j ? ", " : "") << lp.const_acc.w[j];
     o << "]";
     if (which == 0 && p->opt_prune) {   // units the count kernel hands out (all when absent)
-      std::vector<uint8_t> alive = alive_units(p->g, lp.layout);
+      std::vector<uint8_t> alive = alive_items(p->g, lp.layout);
       if (!alive.empty()) {
-        o << ", \"alive_units\": [";
+        o << ", \"alive_items\": [";
         bool first = true;
-        for (size_t u = 0; u < alive.size(); u++)
-          if (alive[u]) {
-            o << (first ? "" : ", ") << u;
+        for (size_t t = 0; t < alive.size(); t++)
+          if (alive[t]) {
+            o << (first ? "" : ", ") << t;
             first = false;
           }
         o << "]";

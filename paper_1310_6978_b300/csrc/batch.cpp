@@ -206,17 +206,14 @@ BatchPlan plan_batch(fbg_program* const* progs, int nprogs, std::string* err) {
       plan.block.push_back(block);
       // units whose unit-only conjuncts are false have no models: left out
       // when that removes at least a quarter of them
-      std::vector<uint8_t> alive = alive_units(p0->g, prog.layout);
+      std::vector<uint8_t> alive = alive_items(p0->g, prog.layout);
       std::vector<unsigned> live;
       uint64_t nlive = 0;
       for (uint8_t a : alive) nlive += a;
       const bool filter = !alive.empty() && nlive * 4 <= alive.size() * 3;
-      if (filter) {
-        const int wb = prog.layout.warp_bits;
-        for (size_t u = 0; u < alive.size(); u++)
-          if (alive[u])
-            for (unsigned w = 0; w < (1u << wb); w++) live.push_back((unsigned)(u << wb) | w);
-      }
+      if (filter)
+        for (size_t t = 0; t < alive.size(); t++)
+          if (alive[t]) live.push_back((unsigned)t);
       plan.live.push_back(std::move(live));
       plan.filtered.push_back(filter ? 1 : 0);
       plan.lp.push_back(std::move(prog));

@@ -157,10 +157,11 @@ struct LayoutParams {
 Layout make_layout(int n, const LayoutParams& prm, const std::vector<int>& order_top_first);
 std::vector<int> identity_order(int n);                          // top position first
 std::vector<int> search_order(const Grounded& g);                // count-mode heuristic
-// Per unit of layout L (1 byte each): 0 when a top-level conjunct whose
-// letters all sit in unit positions is false on that unit, so the unit has
-// no models; empty when there is no such conjunct or more than 16 unit bits.
-std::vector<uint8_t> alive_units(const Grounded& g, const Layout& L);
+// Per work item (unit u, warp slice w) of layout L, index u << warp_bits | w
+// (1 byte each): 0 when a top-level conjunct whose letters all sit in unit
+// and warp positions is false on that item, so the item has no models;
+// empty when there is no such conjunct or more than 20 unit + warp bits.
+std::vector<uint8_t> alive_items(const Grounded& g, const Layout& L);
 
 // ------------------------------------------------------------ LUT program --
 

@@ -137,19 +137,20 @@ std::vector<int> search_order(const Grounded& g) {
   return order;
 }
 
-// The unit-only conjuncts are evaluated bitwise over all 2^unit_bits units
-// at once: unit bit b is a free generator over the unit index (bit u of its
-// word vector is bit b of u, Sec. 2.2-2.3), so each DAG node costs one pass
-// over 2^unit_bits / 64 words.
-std::vector<uint8_t> alive_units(const Grounded& g, const Layout& L) {
-  const int ub = L.unit_bits;
-  if (ub <= 0 || ub > 16) return {};
+// The conjuncts over unit and warp letters are evaluated bitwise over all
+// 2^(unit bits + warp bits) items at once: item bit b is a free generator
+// over the item index (bit t of its word vector is bit b of t, Sec. 2.2-2.3),
+// so each DAG node costs one pass over 2^(unit + warp bits) / 64 words.
+std::vector<uint8_t> alive_items(const Grounded& g, const Layout& L) {
+  const int wb = L.warp_bits, ub = L.unit_bits + wb;
+  if (L.unit_bits <= 0 || ub > 20) return {};
   const FormDag& d = g.dag;
   std::vector<uint64_t> sup = supports(d);
   uint64_t umask = 0;
   std::vector<int> ubit(64, -1);
   for (int b = 0; b < ub; b++) {
-    const int v = L.var_of_pos[(size_t)(L.first_unit_pos() + b)];
+    const int pos = b < wb ? L.first_lane_pos() + L.lane_bits + b : L.first_unit_pos() + (b - wb);
+    const int v = L.var_of_pos[(size_t)pos];
     umask |= 1ull << v;
     ubit[(size_t)v] = b;
   }

@@ -44,7 +44,7 @@ struct JitBuild {
   uint64_t nunits = 1;
   unsigned* d_perm = nullptr;    // items of full-range counts, in order, or null (all, natural order)
   uint64_t nperm = 0;
-  std::vector<uint8_t> alive;    // per unit: 0 = no models (unit-only conjuncts false), empty = all
+  std::vector<uint8_t> alive;    // per (unit, warp slice) item: 0 = no models, empty = all live
   void free_device() {
     if (d_perm) cudaFree(d_perm);
     d_perm = nullptr;

@@ -49,10 +49,9 @@ def test_generated_source_matches_oracle(wl, li):
             perm = np.random.default_rng(items).permutation(items).astype(np.uint32)
             assert jit_host.run_count(src, block, nunits, perm) == th.count()
             assert jit_host.run_count(src, block, nunits, perm, self_reset=True) == th.count()
-            # only the units whose unit-only conjuncts hold (the list full-range counts use)
-            if "alive_units" in d0:
-                live = np.array([(u << d["warp_bits"]) | w for u in d0["alive_units"]
-                                 for w in range(1 << d["warp_bits"])], dtype=np.uint32)
+            # only the items whose unit and warp conjuncts hold (the list full-range counts use)
+            if "alive_items" in d0:
+                live = np.array(d0["alive_items"], dtype=np.uint32)
                 assert jit_host.run_count(src, block, nunits, live, self_reset=True) == th.count()
         else:
             assert np.array_equal(jit_host.run_table(src, block, nunits, p.table_words()), th.table())
