@@ -495,6 +495,7 @@ def run_ours(args, rank, world):
         nominal += es.lop3_nominal
         p.set_option(L.OPT_STATS, 0)
     kern_s = sum(step_ms) / args.steps / 1e3   # the three concurrent count launches of a step
+    lop3_probe = F.probe_lop3_rate(stream)      # independent lop3 chains: the measured roof
     clocks = clk.summary()
     peak_lop3 = SM_COUNT * LOP3_LANES_PER_CLK_SM * 2032e6
 
@@ -559,6 +560,8 @@ def run_ours(args, rank, world):
                               "(in-kernel level counters, untimed run) / CUDA-event step time on the launching "
                               "stream; peak = 148 SM x 64 lanes/clk x 2032 MHz"},
         "nominal_lop3_ratio": executed / nominal if nominal else None,
+        "alu_probe": {"lop3_tops": lop3_probe, "of_nominal_peak": lop3_probe / (peak_lop3 / 1e12),
+                      "basis": "fbg_probe_lop3_rate: 16 independent lop3.b32 chains per thread, CUDA events"},
         "brute_force": brute,
         "truth_table": table_leg,
         "small_poset3": small_leg,

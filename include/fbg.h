@@ -279,6 +279,12 @@ fbg_status fbg_debug_nvrtc_compile(const char *body, char *log, size_t loglen);
    would build; *specialized receives the number that compile */
 fbg_status fbg_debug_batch_build(fbg_program *const *progs, int nprogs, int *specialized, char *log, size_t loglen);
 
+/* The integer-logic roof, measured (no counterpart in the paper): one launch
+ * of a kernel in which every thread runs 16 independent lop3.b32 chains, no
+ * memory traffic; *tops = lop3.b32 lane-operations per second / 1e12.
+ * Synchronises the stream. */
+fbg_status fbg_probe_lop3_rate(void *stream, double *tops);
+
 /* NVRTC/ptxas log of the last specialised-kernel build (registers, spills) */
 const char *fbg_program_jit_log(fbg_program *prog);
 

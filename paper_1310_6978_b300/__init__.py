@@ -219,6 +219,14 @@ class Batch:
         return {"items": items.value, "units": units.value, "grid": grid.value, "specialized": spec.value}
 
 
+def probe_lop3_rate(stream=None) -> float:
+    """fbg_probe_lop3_rate: measured lop3.b32 issue rate of this GPU (T/s)."""
+    L = _L()
+    t = ctypes.c_double()
+    L.check(L.lib.fbg_probe_lop3_rate(_stream_ptr(stream), ctypes.byref(t)))
+    return t.value
+
+
 def batch_source(programs) -> str:
     """fbg_debug_batch_source: NVRTC sources of the batch's specialised kernels."""
     L = _L()

@@ -80,6 +80,7 @@ _sig("fbg_count_range", c_int, c_vp, c_vp, c_u64, c_u64, ctypes.POINTER(c_u64))
 _sig("fbg_count_units", c_int, c_vp, c_vp, c_vp, c_u64)
 _sig("fbg_debug_unit_trace", c_int, c_vp, c_vp, c_vp, c_u64)
 _sig("fbg_schedule_units", c_int, c_vp, c_vp)
+_sig("fbg_probe_lop3_rate", c_int, c_vp, ctypes.POINTER(ctypes.c_double))
 _sig("fbg_debug_item_trace", c_int, c_vp, c_vp, c_vp, c_u64)
 _sig("fbg_unit_vars", c_int, c_vp, ctypes.POINTER(c_int), c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_u64))
 _sig("fbg_truth_table", c_int, c_vp, c_vp, c_vp, c_sz)
