@@ -109,15 +109,32 @@ fbg_status build_interp(fbg_program* p, int which) {
   // work items: single units while that keeps the queue short, else ranges
   uint64_t per = 1;
   while (b.nunits / per > 65536) per <<= 1;
+  b.live.clear();
+  if (which == 0 && p->opt_prune && per == 1) {
+    // units on which a conjunct over unit and warp letters is false have no
+    // models: counts leave them out when that removes a quarter of them
+    std::vector<uint8_t> alive = alive_items(p->g, b.lp.layout);
+    const int wb = b.lp.layout.warp_bits;
+    std::vector<uint32_t> live;
+    for (uint64_t u = 0; !alive.empty() && u < b.nunits; u++) {
+      bool any = false;
+      for (int w = 0; w < (1 << wb); w++) any = any || alive[(size_t)((u << wb) | (uint64_t)w)];
+      if (any) live.push_back((uint32_t)u);
+    }
+    if (!alive.empty() && live.size() * 4 <= b.nunits * 3) b.live = std::move(live);
+  }
   std::vector<FbgWorkItem> items;
-  for (uint64_t u = 0; u < b.nunits; u += per) items.push_back(FbgWorkItem{0u, 0u, u, std::min(b.nunits, u + per)});
+  if (per == 1)
+    b.append_items(items, 0u, 0, b.live_units(), 1);
+  else
+    for (uint64_t u = 0; u < b.nunits; u += per) items.push_back(FbgWorkItem{0u, 0u, u, std::min(b.nunits, u + per)});
   b.units_per_item = per;
   b.nitems = items.size();
   b.free_device();
   CK(cudaMalloc(&b.d_ins, std::max<size_t>(1, b.code.ins.size()) * 8));
   CK(cudaMalloc(&b.d_consts, std::max<size_t>(1, b.code.consts.size()) * 8));
   CK(cudaMalloc(&b.d_prog, sizeof(FbgInterpProg)));
-  CK(cudaMalloc(&b.d_items, items.size() * sizeof(FbgWorkItem)));
+  CK(cudaMalloc(&b.d_items, std::max<size_t>(1, items.size()) * sizeof(FbgWorkItem)));
   if (!b.code.ins.empty()) CK(cudaMemcpy(b.d_ins, b.code.ins.data(), b.code.ins.size() * 8, cudaMemcpyHostToDevice));
   if (!b.code.consts.empty())
     CK(cudaMemcpy(b.d_consts, b.code.consts.data(), b.code.consts.size() * 8, cudaMemcpyHostToDevice));
@@ -125,10 +142,11 @@ fbg_status build_interp(fbg_program* p, int which) {
   G.ins = b.d_ins;
   G.consts = b.d_consts;
   CK(cudaMemcpy(b.d_prog, &G, sizeof G, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(b.d_items, items.data(), items.size() * sizeof(FbgWorkItem), cudaMemcpyHostToDevice));
+  if (!items.empty())
+    CK(cudaMemcpy(b.d_items, items.data(), items.size() * sizeof(FbgWorkItem), cudaMemcpyHostToDevice));
   int per_sm = interp_blocks_per_sm(which == 0 ? 0 : 2, b.code.nslots);
   if (per_sm <= 0) return set_error(FBG_ETOOBIG, "interpreter program does not fit in shared memory");
-  b.grid = (int)std::min<uint64_t>(b.nitems, (uint64_t)device_sms() * (uint64_t)per_sm);
+  b.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(b.nitems, (uint64_t)device_sms() * (uint64_t)per_sm));
   b.valid = true;
   return FBG_OK;
 }

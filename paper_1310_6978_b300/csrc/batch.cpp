@@ -313,7 +313,7 @@ fbg_status fbg_batch_create(fbg_program* const* progs, int nprogs, uint64_t max_
       total_units += b->spec[(size_t)f].nunits;
     } else {
       b->nslots = std::max(b->nslots, progs[i]->ib[0].code.nslots);
-      interp_units += progs[i]->ib[0].nunits;
+      interp_units += progs[i]->ib[0].live_units();
     }
   }
   total_units += interp_units;
@@ -330,12 +330,16 @@ fbg_status fbg_batch_create(fbg_program* const* progs, int nprogs, uint64_t max_
   for (int i = 0; i < nprogs; i++) {
     if (b->fid[(size_t)i] >= 0) continue;
     const InterpBuild& ib = progs[i]->ib[0];
-    uint64_t nu = ib.nunits;
-    double unit_cost = (double)std::max<size_t>(1, ib.code.ins.size()) * std::ldexp(1.0, progs[i]->n) / (double)nu;
-    for (uint64_t u = 0; u < nu; u += chunk) {
-      uint64_t e = std::min(nu, u + chunk);
-      items.push_back(Item{FbgWorkItem{(unsigned)i, 0u, u, e}, unit_cost * (double)(e - u)});
+    double unit_cost = (double)std::max<size_t>(1, ib.code.ins.size()) * std::ldexp(1.0, progs[i]->n) / (double)ib.nunits;
+    // runs of live units (all units when none was left out), at most `chunk` each
+    std::vector<FbgWorkItem> runs;
+    if (ib.units_per_item == 1) {
+      ib.append_items(runs, (unsigned)i, 0, ib.live_units(), chunk);
+    } else {
+      for (uint64_t u = 0; u < ib.nunits; u += chunk)
+        runs.push_back(FbgWorkItem{(unsigned)i, 0u, u, std::min(ib.nunits, u + chunk)});
     }
+    for (const FbgWorkItem& r : runs) items.push_back(Item{r, unit_cost * (double)(r.unit_end - r.unit_begin)});
   }
   std::stable_sort(items.begin(), items.end(), [](const Item& x, const Item& y) { return x.cost > y.cost; });
   std::vector<FbgWorkItem> w;

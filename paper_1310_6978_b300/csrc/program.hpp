@@ -22,6 +22,24 @@ struct InterpBuild {
   FbgWorkItem* d_items = nullptr;
   uint64_t nitems = 0, nunits = 0, units_per_item = 1;
   int grid = 1;
+  // count layout: the units that can have models, ascending (empty = all);
+  // units on which a conjunct over unit and warp letters is false are left out
+  std::vector<uint32_t> live;
+  uint64_t live_units() const { return live.empty() ? nunits : (uint64_t)live.size(); }
+  uint64_t unit_at(uint64_t i) const { return live.empty() ? i : (uint64_t)live[(size_t)i]; }
+  // work items over the live units with positions [lo, hi): runs of
+  // consecutive units, at most max_units each
+  void append_items(std::vector<FbgWorkItem>& out, unsigned prog, uint64_t lo, uint64_t hi,
+                    uint64_t max_units) const {
+    uint64_t i = lo;
+    while (i < hi) {
+      const uint64_t u0 = unit_at(i);
+      uint64_t len = 1;
+      while (i + len < hi && len < max_units && unit_at(i + len) == u0 + len) len++;
+      out.push_back(FbgWorkItem{prog, 0u, u0, u0 + len});
+      i += len;
+    }
+  }
   void free_device() {
     if (d_prog) cudaFree(d_prog);
     if (d_ins) cudaFree(d_ins);

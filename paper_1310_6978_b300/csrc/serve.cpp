@@ -128,7 +128,7 @@ fbg_status fbg_server::admit_locked(Request* r) {
     const InterpBuild& b = r->prog->ib[0];
     r->slot = free_slots.back();
     free_slots.pop_back();
-    r->nunits = b.nunits;
+    r->nunits = b.live_units();   // positions in the program's list of live units
     r->next_unit = 0;
     FbgInterpProg G = b.code.prog;
     G.ins = b.d_ins;
@@ -172,15 +172,23 @@ void fbg_server::tick() {
     uint64_t n = 0, units = 0;
     unsigned nslots = 1;
     for (Request* r : count_reqs) {
+      if (n >= item_cap) break;   // the rest waits for the next tick
       uint64_t take = std::min<uint64_t>(r->nunits - r->next_unit, share);
-      // at most 8 units per item so that blocks share large requests
-      uint64_t need = (take + 7) / 8;
-      if (n + need > item_cap) break;   // the rest waits for the next tick
-      for (uint64_t u = r->next_unit; u < r->next_unit + take; u += 8)
-        h_items[n++] = FbgWorkItem{(unsigned)r->slot, 0u, u, std::min(r->next_unit + take, u + 8)};
-      r->next_unit += take;
-      units += take;
-      nslots = std::max(nslots, r->prog->ib[0].code.nslots);
+      // runs of consecutive live units, at most 8 units per item so that
+      // blocks share large requests, while the tick's item buffer has room
+      const InterpBuild& ib = r->prog->ib[0];
+      uint64_t i = r->next_unit;
+      const uint64_t end = r->next_unit + take;
+      while (i < end && n < item_cap) {
+        const uint64_t u0 = ib.unit_at(i);
+        uint64_t len = 1;
+        while (i + len < end && len < 8 && ib.unit_at(i + len) == u0 + len) len++;
+        h_items[n++] = FbgWorkItem{(unsigned)r->slot, 0u, u0, u0 + len};
+        i += len;
+      }
+      units += i - r->next_unit;
+      r->next_unit = i;
+      nslots = std::max(nslots, ib.code.nslots);
     }
     (void)units;
     cudaError_t e = cudaMemcpyAsync(d_items, h_items, n * sizeof(FbgWorkItem), cudaMemcpyHostToDevice, stream);
