@@ -586,7 +586,7 @@ def main():
     ap.add_argument("--quick", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
-    ap.add_argument("--only", default="", choices=["", "table", "batch"], help="run one leg alone (profiling)")
+    ap.add_argument("--only", default="", choices=["", "table", "batch", "serve"], help="run one leg alone (profiling)")
     ap.add_argument("--batch-formulas", type=int, default=4096)
     ap.add_argument("--autotune", action="store_true", help="tune kernel shapes missing from the cache")
     ap.add_argument("--tune-out", default="", help="write the updated shape cache here")
@@ -604,7 +604,12 @@ def main():
         import torch
         import paper_1310_6978_b300 as F
         from paper_1310_6978_b300 import _lib as L
-        leg = run_table(args, torch, F, L, load_peaks()) if args.only == "table" else run_batched(args, torch, F, L)
+        if args.only == "table":
+            leg = run_table(args, torch, F, L, load_peaks())
+        elif args.only == "batch":
+            leg = run_batched(args, torch, F, L)
+        else:
+            leg = run_serving(args, torch, F, L)
         print(json.dumps(leg), flush=True)
         return
     if args.impl == "reference":
