@@ -110,9 +110,10 @@ fbg_status build_interp(fbg_program* p, int which) {
   uint64_t per = 1;
   while (b.nunits / per > 65536) per <<= 1;
   b.live.clear();
-  if (which == 0 && p->opt_prune && per == 1) {
+  if (p->opt_prune && per == 1) {
     // units on which a conjunct over unit and warp letters is false have no
-    // models: counts leave them out when that removes a quarter of them
+    // models: counts, tables (zeroed before the launch) and model lists leave
+    // them out when that removes a quarter of them
     std::vector<uint8_t> alive = alive_items(p->g, b.lp.layout);
     const int wb = b.lp.layout.warp_bits;
     std::vector<uint32_t> live;

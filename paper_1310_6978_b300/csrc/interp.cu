@@ -17,7 +17,7 @@ namespace {
 template <int MODE>
 __global__ void __launch_bounds__(NT) interp_kernel(const FbgInterpProg* __restrict__ progs,
                                                    const FbgWorkItem* __restrict__ items, fbg_u64 nitems,
-                                                   fbg_u64* item_ctr, fbg_u64* prog_counts, fbg_u64* item_counts,
+                                                   fbg_u64* item_ctr, fbg_u64* prog_counts, fbg_u64* unit_counts,
                                                    FbgLaunch P) {
   extern __shared__ fbg_u64 dyn_slots[];
   __shared__ Shared S;
@@ -39,7 +39,8 @@ __global__ void __launch_bounds__(NT) interp_kernel(const FbgInterpProg* __restr
       cnt = fbg_warp_sum(cnt);
       if ((threadIdx.x & 31) == 0 && cnt) {
         if (prog_counts) atomicAdd(prog_counts + W.prog, cnt);
-        if (item_counts) atomicAdd(item_counts + item, cnt);
+        // per-unit counts: items of one unit each (the caller ensures it)
+        if (unit_counts) atomicAdd(unit_counts + (W.unit_begin - P.unit_begin), cnt);
       }
     }
   }
@@ -93,17 +94,17 @@ static cudaError_t ensure_smem(int mode, size_t smem) {
 
 cudaError_t launch_interp(int mode, const FbgInterpProg* progs, const FbgWorkItem* items, unsigned long long nitems,
                           unsigned long long* item_ctr, unsigned long long* prog_counts,
-                          unsigned long long* item_counts, const FbgLaunch& P, unsigned nslots, int grid,
+                          unsigned long long* unit_counts, const FbgLaunch& P, unsigned nslots, int grid,
                           cudaStream_t stream) {
   size_t smem = interp_smem_bytes(nslots);
   cudaError_t e = ensure_smem(mode, smem);
   if (e != cudaSuccess) return e;
   if (mode == 0)
-    interp_kernel<0><<<grid, NT, smem, stream>>>(progs, items, nitems, item_ctr, prog_counts, item_counts, P);
+    interp_kernel<0><<<grid, NT, smem, stream>>>(progs, items, nitems, item_ctr, prog_counts, unit_counts, P);
   else if (mode == 1)
-    interp_kernel<1><<<grid, NT, smem, stream>>>(progs, items, nitems, item_ctr, prog_counts, item_counts, P);
+    interp_kernel<1><<<grid, NT, smem, stream>>>(progs, items, nitems, item_ctr, prog_counts, unit_counts, P);
   else
-    interp_kernel<2><<<grid, NT, smem, stream>>>(progs, items, nitems, item_ctr, prog_counts, item_counts, P);
+    interp_kernel<2><<<grid, NT, smem, stream>>>(progs, items, nitems, item_ctr, prog_counts, unit_counts, P);
   return cudaGetLastError();
 }
 

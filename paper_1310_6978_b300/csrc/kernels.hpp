@@ -11,7 +11,7 @@ namespace fbg {
 size_t interp_smem_bytes(unsigned nslots);
 cudaError_t launch_interp(int mode, const FbgInterpProg* progs, const FbgWorkItem* items, unsigned long long nitems,
                           unsigned long long* item_ctr, unsigned long long* prog_counts,
-                          unsigned long long* item_counts, const FbgLaunch& P, unsigned nslots, int grid,
+                          unsigned long long* unit_counts, const FbgLaunch& P, unsigned nslots, int grid,
                           cudaStream_t stream);
 cudaError_t launch_scan(const unsigned long long* in, unsigned long long* out, unsigned long long n,
                         unsigned long long* total, cudaStream_t stream);

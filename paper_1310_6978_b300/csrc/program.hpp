@@ -22,8 +22,8 @@ struct InterpBuild {
   FbgWorkItem* d_items = nullptr;
   uint64_t nitems = 0, nunits = 0, units_per_item = 1;
   int grid = 1;
-  // count layout: the units that can have models, ascending (empty = all);
-  // units on which a conjunct over unit and warp letters is false are left out
+  // the units that can have models, ascending (empty = all); units on which a
+  // conjunct over unit and warp letters is false are left out
   std::vector<uint32_t> live;
   uint64_t live_units() const { return live.empty() ? nunits : (uint64_t)live.size(); }
   uint64_t unit_at(uint64_t i) const { return live.empty() ? i : (uint64_t)live[(size_t)i]; }
