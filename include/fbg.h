@@ -94,9 +94,12 @@ enum {
   FBG_OPT_LOOP_LEVEL_BITS = 6, /* bits per loop level (default 4) */
   FBG_OPT_SEARCH_ORDER = 7,    /* counts: 1 (default) heuristic variable order, 0 identity */
   FBG_OPT_MIN_BLOCKS = 8,      /* JIT: __launch_bounds__ min blocks per SM (default 2) */
-  FBG_OPT_STATS = 9            /* 1: kernels carry level counters and record executed level
+  FBG_OPT_STATS = 9,           /* 1: kernels carry level counters and record executed level
                                   iterations (fbg_exec_stats); changing it rebuilds the
                                   kernels and drops a unit order (fbg_schedule_units) */
+  FBG_OPT_INNER_BITS = 10,     /* JIT: bits of the innermost loop level, which is emitted
+                                  unrolled with its generator words folded as constants
+                                  (0 = default: as the other levels; 1..5) */
 };
 
 typedef struct {
@@ -218,6 +221,7 @@ typedef struct {
   double best_ms;
   int trials;
   int regs_log2, warps_log2, min_blocks, loop_level_bits, unit_bits;
+  int inner_bits;
 } fbg_tune_result;
 fbg_status fbg_autotune(fbg_program *prog, void *stream, int mode, int reps, fbg_tune_result *out);
 

@@ -140,13 +140,15 @@ class Program:
         r = self._L.FbgTuneResult()
         self._L.check(self._L.lib.fbg_autotune(self._h, _stream_ptr(stream), mode, reps, ctypes.byref(r)))
         return {"best_ms": r.best_ms, "trials": r.trials, "regs_log2": r.regs_log2, "warps_log2": r.warps_log2,
-                "min_blocks": r.min_blocks, "loop_level_bits": r.loop_level_bits, "unit_bits": r.unit_bits}
+                "min_blocks": r.min_blocks, "loop_level_bits": r.loop_level_bits, "unit_bits": r.unit_bits,
+                "inner_bits": r.inner_bits}
 
     def apply_shape(self, shape: dict) -> "Program":
         """Set the kernel-shape options recorded by ``autotune``."""
         L = self._L
         for key, opt in (("regs_log2", L.OPT_REGS_LOG2), ("warps_log2", L.OPT_WARPS_LOG2),
                          ("min_blocks", L.OPT_MIN_BLOCKS), ("loop_level_bits", L.OPT_LOOP_LEVEL_BITS),
+                         ("inner_bits", L.OPT_INNER_BITS),
                          ("unit_bits", L.OPT_UNIT_BITS)):
             if key in shape:
                 self.set_option(opt, shape[key])

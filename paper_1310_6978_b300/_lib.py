@@ -29,7 +29,7 @@ STATUS_NAMES = ["FBG_OK", "FBG_EINVAL", "FBG_EPARSE", "FBG_ETOOBIG", "FBG_ENOMEM
 
 ENGINE_AUTO, ENGINE_JIT, ENGINE_INTERP = 0, 1, 2
 OPT_ENGINE, OPT_PRUNE, OPT_REGS_LOG2, OPT_WARPS_LOG2, OPT_UNIT_BITS, OPT_LOOP_LEVEL_BITS, OPT_SEARCH_ORDER, \
-    OPT_MIN_BLOCKS, OPT_STATS = range(1, 10)
+    OPT_MIN_BLOCKS, OPT_STATS, OPT_INNER_BITS = range(1, 11)
 MODE_COUNT, MODE_ENUMERATE = 0, 1
 BATCH_GRAPH, BATCH_SPECIALIZE = 1, 2
 
@@ -47,7 +47,7 @@ class FbgExecStats(ctypes.Structure):
 
 class FbgTuneResult(ctypes.Structure):
     _fields_ = [("best_ms", ctypes.c_double), ("trials", c_int), ("regs_log2", c_int), ("warps_log2", c_int),
-                ("min_blocks", c_int), ("loop_level_bits", c_int), ("unit_bits", c_int)]
+                ("min_blocks", c_int), ("loop_level_bits", c_int), ("unit_bits", c_int), ("inner_bits", c_int)]
 
 
 class FbgServerOptions(ctypes.Structure):

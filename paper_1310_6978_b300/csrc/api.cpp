@@ -67,6 +67,7 @@ LayoutParams jit_params(const fbg_program* p) {
   lp.warps_log2 = (int)p->opt_warps_log2;
   lp.unit_bits_max = (int)p->opt_unit_bits;
   lp.loop_level_bits = (int)p->opt_loop_level_bits;
+  lp.inner_bits = (int)p->opt_inner_bits;
   return lp;
 }
 
@@ -386,6 +387,10 @@ fbg_status fbg_set_option(fbg_program* p, int option, int64_t v) {
     case FBG_OPT_MIN_BLOCKS:
       if (v < 1 || v > 32) return bad();
       p->opt_min_blocks = v;
+      break;
+    case FBG_OPT_INNER_BITS:
+      if (v < 0 || v > 5) return bad();
+      p->opt_inner_bits = v;
       break;
     case FBG_OPT_STATS:   // kernels carry level counters only while statistics are on
       if (p->opt_stats == (v ? 1 : 0)) return FBG_OK;

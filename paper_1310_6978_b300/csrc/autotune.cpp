@@ -86,6 +86,7 @@ extern "C" fbg_status fbg_autotune(fbg_program* p, void* stream, int mode, int r
       {FBG_OPT_MIN_BLOCKS, {1, 2, 3}},
       {FBG_OPT_WARPS_LOG2, {2, 3, 4}},
       {FBG_OPT_UNIT_BITS, {10, 12, 13, 14}},
+      {FBG_OPT_INNER_BITS, {0, 1, 3, 4}},
   };
   auto get = [&](int opt) -> int64_t {
     switch (opt) {
@@ -93,6 +94,7 @@ extern "C" fbg_status fbg_autotune(fbg_program* p, void* stream, int mode, int r
       case FBG_OPT_REGS_LOG2: return p->opt_regs_log2;
       case FBG_OPT_MIN_BLOCKS: return p->opt_min_blocks;
       case FBG_OPT_WARPS_LOG2: return p->opt_warps_log2;
+      case FBG_OPT_INNER_BITS: return p->opt_inner_bits;
       default: return p->opt_unit_bits;
     }
   };
@@ -130,5 +132,6 @@ extern "C" fbg_status fbg_autotune(fbg_program* p, void* stream, int mode, int r
   out->min_blocks = (int)p->opt_min_blocks;
   out->loop_level_bits = (int)p->opt_loop_level_bits;
   out->unit_bits = (int)p->opt_unit_bits;
+  out->inner_bits = (int)p->opt_inner_bits;
   return err;
 }

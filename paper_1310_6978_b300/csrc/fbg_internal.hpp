@@ -152,6 +152,7 @@ struct LayoutParams {
   int unit_bits_max = 13;
   int loop_level_bits = 4;
   int loop_bits_max = 16;
+  int inner_bits = 0;        // innermost loop level's bits (0 = loop_level_bits)
 };
 
 Layout make_layout(int n, const LayoutParams& prm, const std::vector<int>& order_top_first);

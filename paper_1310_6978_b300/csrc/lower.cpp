@@ -59,11 +59,16 @@ Layout make_layout(int n, const LayoutParams& prm, const std::vector<int>& order
     if (rem - units - loops > 0) units = rem - loops;   // everything else becomes units
     L.unit_bits = units;
     int lb = std::max(1, prm.loop_level_bits);
+    // the innermost level may have its own width; the others split the rest
+    // from the top
+    int inner = prm.inner_bits > 0 ? std::min(prm.inner_bits, loops) : 0;
+    loops -= inner;
     while (loops > 0) {
       int b = std::min(lb, loops);
       L.loop_bits.push_back(b);
       loops -= b;
     }
+    if (inner > 0) L.loop_bits.push_back(inner);
   }
   L.pos_of_var.assign((size_t)n, 0);
   L.var_of_pos.assign((size_t)n, 0);

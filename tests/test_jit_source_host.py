@@ -26,6 +26,7 @@ LAYOUTS = [
     {L.OPT_REGS_LOG2: 1, L.OPT_WARPS_LOG2: 0, L.OPT_UNIT_BITS: 1, L.OPT_LOOP_LEVEL_BITS: 1},
     {L.OPT_REGS_LOG2: 3, L.OPT_WARPS_LOG2: 1, L.OPT_UNIT_BITS: 2, L.OPT_LOOP_LEVEL_BITS: 2},
     {L.OPT_PRUNE: 0, L.OPT_WARPS_LOG2: 0, L.OPT_UNIT_BITS: 1, L.OPT_LOOP_LEVEL_BITS: 2},
+    {L.OPT_REGS_LOG2: 2, L.OPT_WARPS_LOG2: 1, L.OPT_UNIT_BITS: 2, L.OPT_LOOP_LEVEL_BITS: 1, L.OPT_INNER_BITS: 3},
 ]
 
 
