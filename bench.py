@@ -212,20 +212,42 @@ def run_small(torch, F, stream):
                      "time per launch over 200 back-to-back launches"}
 
 
+def oracle_step(wls, bits, rng):
+    """One reference step: one random subcube of 2^bits assignments per
+    formula, counted by the oracle on all host cores; returns seconds."""
+    import oracle
+    t0 = time.perf_counter()
+    for wl in wls:
+        th = oracle.Theory(wl.text, wl.k)
+        fixed = [int(v) for v in rng.choice(wl.n, wl.n - bits, replace=False)]
+        mask = sum(1 << v for v in fixed)
+        th.count_cube_par(mask, int(rng.integers(0, 1 << 62)) & mask)
+    return time.perf_counter() - t0
+
+
 def run_reference(args, rank, world):
+    """The oracle as it stands on the same metric; each step is a bounded
+    sample (one subcube per formula) sized so that warm-up and timed steps
+    together take about --ref-total-seconds."""
     if rank != 0:
         return
+    import numpy as np
+    import oracle
     wls = workloads()
-    steps = []
+    rng = np.random.default_rng(7)
+    probe = oracle_step(wls, 16, rng) / (3 << 16)            # seconds per assignment
+    per_step = max(0.002, args.ref_total_seconds / max(1, args.steps + args.warmup))
+    bits = int(min(22, max(10, np.floor(np.log2(max(1.0, per_step / probe / 3))))))
     for _ in range(args.warmup):
-        cpu_oracle_rate(wls, 0.5)
-    for _ in range(args.steps):
-        rate, cores, sample = cpu_oracle_rate(wls, args.ref_seconds)
-        steps.append(rate)
-    rate = sorted(steps)[len(steps) // 2]
+        oracle_step(wls, bits, rng)
+    times = [oracle_step(wls, bits, rng) for _ in range(args.steps)]
+    rate = 3 * (1 << bits) / sorted(times)[len(times) // 2]
+    cores = oracle.max_threads()
+    sample = (f"per step one random subcube of 2^{bits} assignments of each of the three n=36 formulas, "
+              f"{args.steps} timed steps (median)")
     line = {"metric": "model-count throughput at n=36 (Gassign/s)", "value": rate / 1e9, "unit": "Gassign/s",
             "impl": "reference", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 3 * (1 << 22) / rate * 1e3, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 3 * (1 << bits) / rate * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": "count n=36: transitive k=6, triangle-free k=9, Aut(G(6,1/2)) seed 3",
                        "engine": "CPU oracle (model checking per assignment)", "flush_l2": False},
@@ -593,7 +615,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=3000)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--ref-seconds", type=float, default=4.0)
+    ap.add_argument("--ref-total-seconds", type=float, default=90.0,
+                    help="reference arm: seconds for all its warm-up and timed steps together")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
