@@ -448,8 +448,8 @@ def run_ours(args, rank, world):
     progs = [F.compile(w.text, w.k) for w in wls]
     stream = torch.cuda.Stream()
     cache = tuning.load()
-    shapes = [tuning.ensure(p, 0, cache, tune=args.autotune, stream=stream) for p in progs]
-    if args.autotune and args.tune_out:
+    shapes = [tuning.ensure(p, 0, cache, tune=args.autotune, stream=stream, refine=args.retune) for p in progs]
+    if (args.autotune or args.retune) and args.tune_out:
         tuning.save(cache, args.tune_out)
     for p in progs:                       # longest-first item order (setup, untimed)
         p.schedule_units(stream=stream)
@@ -611,6 +611,7 @@ def main():
     ap.add_argument("--only", default="", choices=["", "table", "batch", "serve"], help="run one leg alone (profiling)")
     ap.add_argument("--batch-formulas", type=int, default=4096)
     ap.add_argument("--autotune", action="store_true", help="tune kernel shapes missing from the cache")
+    ap.add_argument("--retune", action="store_true", help="tune again from the cached shapes, keep the better")
     ap.add_argument("--tune-out", default="", help="write the updated shape cache here")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=3000)

@@ -33,14 +33,21 @@ def save(cache: dict, path: str) -> None:
     os.replace(tmp, path)
 
 
-def ensure(prog, mode: int = 0, cache: dict | None = None, tune: bool = False, stream=None, reps: int = 3):
+def ensure(prog, mode: int = 0, cache: dict | None = None, tune: bool = False, stream=None, reps: int = 3,
+           refine: bool = False):
     """Apply the cached shape of ``prog`` (a Program) if there is one; else,
-    with ``tune``, run the autotuner and record its choice in ``cache``.
-    Returns the shape applied (or None)."""
+    with ``tune``, run the autotuner and record its choice in ``cache``.  With
+    ``refine`` the autotuner also runs on a cached shape, starting from it.  Returns the shape applied (or None)."""
     cache = load() if cache is None else cache
     kk = key(prog.text, prog.k, mode)
-    if kk in cache:
+    if kk in cache and not refine:
         prog.apply_shape(cache[kk])
+        return cache[kk]
+    if kk in cache:
+        # the search starts from (and times) the cached shape, so its result
+        # is at least as fast on this GPU
+        prog.apply_shape(cache[kk])
+        cache[kk] = prog.autotune(mode, reps, stream)
         return cache[kk]
     if not tune:
         return None
