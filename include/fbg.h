@@ -148,7 +148,11 @@ fbg_status fbg_program_stats(fbg_program *prog, fbg_stats *out);
 fbg_status fbg_count(fbg_program *prog, void *stream, uint64_t *out_count);
 
 /* as fbg_count, but writes the count to device memory dev_out (8 bytes,
-   caller-owned, overwritten) and returns without synchronising */
+   caller-owned, overwritten) and returns without synchronising.  One launch,
+   no memset: the kernel's last warp writes *dev_out and zeroes the program's
+   counters.  Launches of one program share those counters, so they must not
+   overlap: issue them on one stream (or order them with events); different
+   programs may run concurrently on different streams. */
 fbg_status fbg_count_async(fbg_program *prog, void *stream, uint64_t *dev_out);
 
 /*
