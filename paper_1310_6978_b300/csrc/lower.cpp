@@ -215,13 +215,12 @@ std::vector<uint8_t> alive_items(const Grounded& g, const Layout& L) {
         break;
     }
   }
+  // the AND of the kept conjuncts, word by word, then one byte per item
+  std::vector<uint64_t> all(W, tail);
+  for (int c : keep)
+    for (size_t w = 0; w < W; w++) all[w] &= val[(size_t)c][w];
   std::vector<uint8_t> alive((size_t)U, 0);
-  for (uint64_t u = 0; u < U; u++) {
-    bool ok = ((tail >> (u & 63)) & 1) != 0;
-    for (int c : keep)
-      if (!((val[(size_t)c][(size_t)(u >> 6)] >> (u & 63)) & 1)) ok = false;
-    alive[(size_t)u] = ok ? 1 : 0;
-  }
+  for (uint64_t u = 0; u < U; u++) alive[(size_t)u] = (uint8_t)((all[(size_t)(u >> 6)] >> (u & 63)) & 1);
   return alive;
 }
 
