@@ -509,12 +509,14 @@ def run_ours(args, rank, world):
     # executed work of the same kernels (level iteration counters), untimed
     executed = 0.0
     nominal = 0.0
+    uniform = 0.0
     for p in progs:
         p.set_option(L.OPT_STATS, 1)
         p.count()
         es = p.exec_stats()
         executed += es.lop3_executed
         nominal += es.lop3_nominal
+        uniform += es.lop3_uniform
         p.set_option(L.OPT_STATS, 0)
     kern_s = sum(step_ms) / args.steps / 1e3   # the three concurrent count launches of a step
     lop3_probe = F.probe_lop3_rate(stream)      # independent lop3 chains: the measured roof
@@ -578,9 +580,11 @@ def run_ours(args, rank, world):
                    "shapes": shapes},
         "roofline": {"bound": "alu", "achieved": executed / kern_s / 1e12, "peak": peak_lop3 / 1e12,
                      "unit": "Tlop3/s", "frac": executed / kern_s / peak_lop3, "traffic": None,
-                     "basis": "executed lop3.b32 lane-ops of the step's three concurrent fbg_jit_count launches "
-                              "(in-kernel level counters, untimed run) / CUDA-event step time on the launching "
-                              "stream; peak = 148 SM x 64 lanes/clk x 2032 MHz"},
+                     "basis": "executed lane-varying lop3.b32 lane-ops of the step's three concurrent "
+                              "fbg_jit_count launches (in-kernel level counters, untimed run) / CUDA-event step "
+                              "time on the launching stream; peak = 148 SM x 64 lanes/clk x 2032 MHz; lop3 whose "
+                              "inputs are all warp-uniform (uniform datapath) are not counted",
+                     "uniform_lop3_warp_ops_per_step": uniform},
         "nominal_lop3_ratio": executed / nominal if nominal else None,
         "alu_probe": {"lop3_tops": lop3_probe, "of_nominal_peak": lop3_probe / (peak_lop3 / 1e12),
                       "basis": "fbg_probe_lop3_rate: 16 independent lop3.b32 chains per thread, CUDA events"},

@@ -117,9 +117,12 @@ typedef struct {
 
 typedef struct {
   uint64_t level_iters[16]; /* warp-level executions of each level in the last count */
-  double lop3_executed;     /* lop3.b32 lane operations those executions issued */
+  double lop3_executed;     /* lop3.b32 lane operations those executions issued whose inputs vary
+                               across lanes (the vector ALU pipe's work) */
   double lop3_nominal;      /* lane operations without pruning: every word evaluated */
   int engine;               /* engine that ran */
+  double lop3_uniform;      /* warp operations of lop3 whose inputs are all warp-uniform (constants
+                               and loop counters; the compiler may run them on the uniform pipe) */
 } fbg_exec_stats;
 
 /*

@@ -42,7 +42,7 @@ class FbgStats(ctypes.Structure):
 
 class FbgExecStats(ctypes.Structure):
     _fields_ = [("level_iters", c_u64 * 16), ("lop3_executed", ctypes.c_double),
-                ("lop3_nominal", ctypes.c_double), ("engine", c_int)]
+                ("lop3_nominal", ctypes.c_double), ("engine", c_int), ("lop3_uniform", ctypes.c_double)]
 
 
 class FbgTuneResult(ctypes.Structure):

@@ -172,7 +172,7 @@ fbg_status build_jit(fbg_program* p, int mode) {
     if (!p->opt_prune) strip_prune(b.lp);
     b.block = b.lp.layout.lane_bits < 5 ? 32 : 32 << b.lp.layout.warp_bits;
     b.src = emit_cuda_source(b.lp, mode, b.block, (int)p->opt_min_blocks, &b.ops, &b.unrolled_level,
-                             p->opt_stats != 0);
+                             p->opt_stats != 0, &b.uops);
   } catch (CompileError& e) {
     return set_error(FBG_ETOOBIG, e.msg);
   }
@@ -457,9 +457,10 @@ fbg_status fbg_count(fbg_program* p, void* stream, uint64_t* out_count) {
       double per = jit ? (double)p->jb[0].ops[(size_t)lv] * 32.0
                        : (double)(lp.levels[(size_t)lv].lut_end - lp.levels[(size_t)lv].lut_begin) * 64.0;
       es.lop3_executed += (double)host[4 + lv] * per;
+      if (jit) es.lop3_uniform += (double)host[4 + lv] * (double)p->jb[0].uops[(size_t)lv];
       if (lv >= 2 && !(jit && lv == p->jb[0].unrolled_level)) execs *= (double)(1u << L.loop_bits[(size_t)(lv - 2)]);
       double nominal_execs = lv == 0 ? 0.0 : execs;
-      es.lop3_nominal += nominal_execs * per;
+      es.lop3_nominal += nominal_execs * (jit ? (double)(p->jb[0].ops[(size_t)lv] + p->jb[0].uops[(size_t)lv]) * 32.0 : per);
     }
   }
   return FBG_OK;

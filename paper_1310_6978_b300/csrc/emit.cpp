@@ -7,6 +7,8 @@
 #include <cstring>
 #include <map>
 #include <sstream>
+#include <unordered_map>
+#include <unordered_set>
 
 #include "emit.hpp"
 
@@ -30,6 +32,9 @@ struct Sym {
   uint32_t c = 0;
   std::string name;
   bool neg = false;
+  // provably the same in every lane: built only from constants and loop
+  // counters (the compiler may run such lop3 on the uniform datapath)
+  bool uni = true;
   bool operator==(const Sym& o) const {
     return is_const == o.is_const && (is_const ? c == o.c : (name == o.name && neg == o.neg));
   }
@@ -53,11 +58,13 @@ class SrcGen {
       unroll_base = L.loop_pos(nl - 3);
     }
     ops.assign((size_t)nl, 0);
+    uops.assign((size_t)nl, 0);
     fold_base();
     if (unroll_lv >= 0) fold_unrolled();
   }
 
-  std::vector<long long> ops;   // lop3.b32 per thread per execution of each level
+  std::vector<long long> ops;   // lop3.b32 per thread per execution of each level (lane-varying)
+  std::vector<long long> uops;  // warp-uniform lop3 per warp per execution of each level
   int unroll_lv = -1;
 
   std::string generate(int mode, int block, int minb);
@@ -75,6 +82,17 @@ class SrcGen {
   std::vector<std::vector<std::string>> code;         // real lop3 calls of those
   std::vector<std::vector<std::vector<Sym>>> usym;    // [copy][lut - first][s]
   std::vector<std::vector<std::string>> ustmt;        // [copy] statements
+  std::vector<std::vector<std::string>> ustmt_name;   // [copy] the value each statement defines
+  // every lop3 call emitted by folding: its name, the values it reads, its
+  // level and whether it is warp-uniform; live_ holds those the kernel needs
+  struct CallInfo {
+    std::vector<std::string> deps;
+    int level = 0;
+    bool uni = false;
+  };
+  std::unordered_map<std::string, CallInfo> calls_;
+  std::unordered_set<std::string> live_;
+  bool is_live(const std::string& name) const { return live_.count(name) != 0; }
   std::ostringstream o;
 
   bool in_unrolled(int lut) const { return unroll_lv >= 0 && p.luts[(size_t)lut].level == unroll_lv; }
@@ -170,6 +188,7 @@ class SrcGen {
       } else {
         x.is_const = false;
         x.name = "V" + std::to_string(v.id);
+        x.uni = L.level_of_pos(v.id) >= 2;   // loop counters are uniform; thread and unit bits are not
       }
     } else {
       size_t r = (size_t)((uint32_t)s & p.luts[(size_t)v.id].rmask);
@@ -239,8 +258,11 @@ class SrcGen {
       kf--;
     }
     Sym out;
-    bool all_imm = true;
-    for (auto& x : fs) all_imm &= x.is_const;
+    bool all_imm = true, uni = true;
+    for (auto& x : fs) {
+      all_imm &= x.is_const;
+      uni &= x.uni;
+    }
     if (kf == 0) {
       out.c = g[0] ? 0xFFFFFFFFu : 0u;
     } else if (all_imm) {
@@ -265,6 +287,7 @@ class SrcGen {
       std::string c3 = "fbg_lop3<" + std::to_string(tt) + ">(" + expr(fs[0]) + ", " + expr(fs[kf > 1 ? 1 : 0]) + ", " +
                        expr(fs[kf > 2 ? 2 : 0]) + ")";
       out.is_const = false;
+      out.uni = uni;
       auto it = cse.find(c3);
       if (it != cse.end()) {
         out.name = it->second;
@@ -272,6 +295,12 @@ class SrcGen {
         cse.emplace(c3, name);
         out.name = name;
         *call = c3;
+        CallInfo ci;
+        for (auto& x : fs)
+          if (!x.is_const) ci.deps.push_back(x.name);
+        ci.level = copy >= 0 ? unroll_lv : lu.level;
+        ci.uni = uni;
+        calls_[name] = std::move(ci);
       }
     }
     return out;
@@ -296,10 +325,7 @@ class SrcGen {
         if (((uint32_t)s & lu.rmask) != (uint32_t)s) continue;
         std::string call;
         sym[i][(size_t)s] = fold_one(lu, s, -1, "L" + std::to_string(i) + "_" + std::to_string(s), cse, &call);
-        if (!call.empty()) {
-          code[i][(size_t)s] = call;
-          ops[(size_t)lu.level]++;
-        }
+        if (!call.empty()) code[i][(size_t)s] = call;
       }
     }
   }
@@ -309,6 +335,7 @@ class SrcGen {
     const int copies = 1 << unroll_bits;
     usym.assign((size_t)copies, {});
     ustmt.assign((size_t)copies, {});
+    ustmt_name.assign((size_t)copies, {});
     std::map<std::string, std::string> cse;   // shared: the copies are one straight-line block
     for (int c = 0; c < copies; c++) {
       usym[(size_t)c].assign((size_t)(li.lut_end - li.lut_begin), std::vector<Sym>((size_t)nreg));
@@ -321,7 +348,7 @@ class SrcGen {
           usym[(size_t)c][(size_t)(i - li.lut_begin)][(size_t)s] = v;
           if (!call.empty()) {
             ustmt[(size_t)c].push_back("const fbg_u32 " + nm + " = " + call + ";");
-            ops[(size_t)unroll_lv]++;
+            ustmt_name[(size_t)c].push_back(nm);
           }
         }
       }
@@ -346,18 +373,70 @@ class SrcGen {
     return byl;
   }
 
+  static std::string lut_name(int i, int s) { return "L" + std::to_string(i) + "_" + std::to_string(s); }
+
+  // The values the kernel needs: the result words of every copy and the
+  // partial conjunctions of the levels whose warp vote is emitted (mode 0:
+  // count, 1: table), and all they read.  Calls nothing reads are dead (with
+  // pruning off, the level conjunctions feed no vote); they are neither
+  // emitted nor counted in ops / uops.
+  void mark_live(int mode) {
+    const int last = nl - 1;
+    std::vector<std::string> stack;
+    auto root = [&](const Val& v, int copy) {
+      for (int s = 0; s < nreg; s++) {
+        Sym x = operand_sym(v, s, copy);
+        if (!x.is_const) stack.push_back(x.name);
+      }
+    };
+    if (unroll_lv >= 0)
+      for (int c = 0; c < (1 << unroll_bits); c++) root(p.out, c);
+    else
+      root(p.out, -1);
+    if (p.levels[0].has_acc && (mode == 0 || last > 0)) root(p.levels[0].acc, -1);
+    if (nl > 1 && p.levels[1].has_acc && last > 1) root(p.levels[1].acc, -1);
+    for (int lv = 2; lv < last; lv++)
+      if (lv != unroll_lv && p.levels[(size_t)lv].has_acc) root(p.levels[(size_t)lv].acc, -1);
+    live_.clear();
+    while (!stack.empty()) {
+      std::string nm = stack.back();
+      stack.pop_back();
+      auto it = calls_.find(nm);
+      if (it == calls_.end() || live_.count(nm)) continue;
+      live_.insert(nm);
+      for (auto& d : it->second.deps) stack.push_back(d);
+    }
+    ops.assign((size_t)nl, 0);
+    uops.assign((size_t)nl, 0);
+    for (auto& nm : live_) {
+      const CallInfo& ci = calls_[nm];
+      (ci.uni ? uops : ops)[(size_t)ci.level]++;
+    }
+  }
+
+  // the statements of the unrolled copies that define live values
+  std::vector<std::vector<std::string>> live_ustmt() const {
+    std::vector<std::vector<std::string>> out(ustmt.size());
+    for (size_t c = 0; c < ustmt.size(); c++)
+      for (size_t t = 0; t < ustmt[c].size(); t++)
+        if (is_live(ustmt_name[c][t])) out[c].push_back(ustmt[c][t]);
+    return out;
+  }
+
   void declare_level(int lv, const std::string& ind) {
     const LevelInfo& li = p.levels[(size_t)lv];
     for (int i = li.lut_begin; i < li.lut_end; i++)
       for (int s = 0; s < nreg; s++)
-        if (!code[(size_t)i][(size_t)s].empty()) o << ind << "fbg_u32 L" << i << "_" << s << ";\n";
+        if (!code[(size_t)i][(size_t)s].empty() && is_live(lut_name(i, s)))
+          o << ind << "fbg_u32 " << lut_name(i, s) << ";\n";
   }
 
   void luts(int lv, const std::string& ind) {
     const LevelInfo& li = p.levels[(size_t)lv];
     for (int i = li.lut_begin; i < li.lut_end; i++)
       for (int s = 0; s < nreg; s++)
-        if (!code[(size_t)i][(size_t)s].empty()) o << ind << "L" << i << "_" << s << " = " << code[(size_t)i][(size_t)s] << ";\n";
+        if (!code[(size_t)i][(size_t)s].empty() && is_live(lut_name(i, s)))
+          o << ind << lut_name(i, s) << " = " << code[(size_t)i][(size_t)s] << ";\n";
   }
 
   std::string any_nonzero(const Val& v) const {
@@ -406,6 +485,7 @@ class SrcGen {
 // it; keeping the work fetch outside this function keeps the control flow the
 // compiler sees simple.
 std::string SrcGen::unit_fn_count(const std::string& fname) {
+  mark_live(0);
   auto vars = used_vars();
   const int tvalid = 1 << (L.lane_bits + L.warp_bits);
   const int last = nl - 1;
@@ -450,7 +530,8 @@ std::string SrcGen::unit_fn_count(const std::string& fname) {
     std::vector<std::vector<Sym>> words((size_t)(1 << unroll_bits));
     for (int c = 0; c < (1 << unroll_bits); c++)
       for (int s = 0; s < nreg; s++) words[(size_t)c].push_back(operand_sym(p.out, s, c));
-    emit_counts(&ustmt, words, ops[(size_t)unroll_lv], ind);
+    const std::vector<std::vector<std::string>> lst = live_ustmt();
+    emit_counts(&lst, words, ops[(size_t)unroll_lv], ind);
   } else {
     std::vector<std::vector<Sym>> words(1);
     for (int s = 0; s < nreg; s++) words[0].push_back(operand_sym(p.out, s, -1));
@@ -472,6 +553,7 @@ std::string SrcGen::unit_fn_count(const std::string& fname) {
 // Per-unit device function of truth-table mode: stores every tile of unit u;
 // tiles under a level whose partial conjunction is zero store zeros.
 std::string SrcGen::unit_fn_table(const std::string& fname) {
+  mark_live(1);
   auto vars = used_vars();
   const int tvalid = 1 << (L.lane_bits + L.warp_bits);
   const int last = nl - 1;
@@ -520,8 +602,9 @@ std::string SrcGen::unit_fn_table(const std::string& fname) {
     o << ind << "  const fbg_u64 T = " << tile_base(unroll_lv) << ";\n";
     o << ind << "  if (a" << prev << " && tm) {\n";
     o << ind << "    lvl[" << unroll_lv << "]++;\n";
+    const std::vector<std::vector<std::string>> lst = live_ustmt();
     for (int c = 0; c < (1 << unroll_bits); c++) {
-      for (auto& st : ustmt[(size_t)c]) o << ind << "    " << st << "\n";
+      for (auto& st : lst[(size_t)c]) o << ind << "    " << st << "\n";
       std::vector<std::string> w;
       for (int s = 0; s < nreg; s++) w.push_back("(" + operand(p.out, s, c) + " & tm)");
       store(ind + "    ", "T | ((fbg_u64)" + std::to_string(c) + "u << " + std::to_string(sh) + ")", w);
@@ -646,10 +729,12 @@ std::string emit_batch_function(const LutProgram& p, const std::string& fname) {
 }
 
 std::string emit_cuda_source(const LutProgram& p, int mode, int block, int minblocks,
-                             std::vector<long long>* ops_per_level, int* unrolled_level, bool counters) {
+                             std::vector<long long>* ops_per_level, int* unrolled_level, bool counters,
+                             std::vector<long long>* uniform_ops_per_level) {
   SrcGen g(p, counters);
   std::string src = g.generate(mode, block, minblocks);
   if (ops_per_level) *ops_per_level = g.ops;
+  if (uniform_ops_per_level) *uniform_ops_per_level = g.uops;
   if (unrolled_level) *unrolled_level = g.unroll_lv;
   return src;
 }

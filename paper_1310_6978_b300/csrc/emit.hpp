@@ -17,7 +17,7 @@ namespace fbg {
 // (one "execution" of that level covers all its iterations), or -1.
 std::string emit_cuda_source(const LutProgram& p, int mode, int block, int minblocks,
                              std::vector<long long>* ops_per_level = nullptr, int* unrolled_level = nullptr,
-                             bool counters = true);
+                             bool counters = true, std::vector<long long>* uniform_ops_per_level = nullptr);
 
 // device function `fname(u0, u1)`: this thread's model count over the units
 // [u0, u1) of p's layout (the count body, for the batch kernel)

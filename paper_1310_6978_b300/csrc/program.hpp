@@ -55,7 +55,8 @@ struct JitBuild {
   bool valid = false;
   LutProgram lp;
   std::string src, log;
-  std::vector<long long> ops;    // lop3.b32 per thread per level execution (after folding)
+  std::vector<long long> ops;    // lane-varying lop3.b32 per thread per level execution (after folding)
+  std::vector<long long> uops;   // warp-uniform lop3 per warp per level execution
   int unrolled_level = -1;       // loop level emitted unrolled (one execution = all iterations)
   cudaKernel_t kern = nullptr;   // owned by the process-wide JIT cache
   int block = 256, grid = 1;
