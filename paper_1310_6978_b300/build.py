@@ -24,11 +24,8 @@ SOURCES = ["parse.cpp", "ground.cpp", "lower.cpp", "emit.cpp", "jit.cpp", "api.c
 
 
 def _embed_header() -> str:
-    """Device headers as text, for NVRTC: fbg_device_header (fbg_device.cuh),
-    fbg_interp_format_header (interp_format.h), fbg_interp_device_header
-    (interp_device.cuh)."""
-    parts = [("fbg_device_header", "fbg_device.cuh"), ("fbg_interp_format_header", "interp_format.h"),
-             ("fbg_interp_device_header", "interp_device.cuh")]
+    """The device header as text, for NVRTC: fbg_device_header (fbg_device.cuh)."""
+    parts = [("fbg_device_header", "fbg_device.cuh")]
     body = "// generated by build.py from the device headers\nnamespace fbg {\n"
     for sym, fn in parts:
         src = open(os.path.join(CSRC, fn)).read()
@@ -76,7 +73,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     newest = max(os.path.getmtime(o) for o in objs)
     if force or not os.path.exists(SO) or os.path.getmtime(SO) < newest:
         tmp = SO + f".tmp{os.getpid()}"
-        cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lnvrtc", "-lnvJitLink", "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
+        cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lnvrtc", "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

@@ -2,7 +2,6 @@
 // process-wide cache keyed by the generated source, so identical programs
 // (same formula, layout and mode) are compiled once.
 #include <cuda_runtime.h>
-#include <nvJitLink.h>
 #include <nvrtc.h>
 
 #include <chrono>
@@ -20,8 +19,6 @@ namespace fbg {
 
 // device headers as text (generated by the build from the .cuh / .h files)
 extern const char fbg_device_header[];
-extern const char fbg_interp_format_header[];
-extern const char fbg_interp_device_header[];
 
 namespace {
 
@@ -62,10 +59,10 @@ JitResult jit_compile(const std::string& body, const char* kernel_name, int devi
   std::thread([job, src] {
     std::string cubin, log;
     bool ok = false;
-    const char* hdrs[3] = {fbg_device_header, fbg_interp_format_header, fbg_interp_device_header};
-    const char* names[3] = {"fbg_device.cuh", "interp_format.h", "interp_device.cuh"};
+    const char* hdrs[1] = {fbg_device_header};
+    const char* names[1] = {"fbg_device.cuh"};
     nvrtcProgram prog;
-    nvrtcResult e = nvrtcCreateProgram(&prog, src.c_str(), "fbg_jit.cu", 3, hdrs, names);
+    nvrtcResult e = nvrtcCreateProgram(&prog, src.c_str(), "fbg_jit.cu", 1, hdrs, names);
     if (e != NVRTC_SUCCESS) {
       log = std::string("nvrtcCreateProgram: ") + nvrtcGetErrorString(e);
     } else {
@@ -136,10 +133,10 @@ JitResult jit_compile(const std::string& body, const char* kernel_name, int devi
 
 bool jit_check(const std::string& body, std::string* log) {
   std::string src = "#include \"fbg_device.cuh\"\n" + body;
-  const char* hdrs[3] = {fbg_device_header, fbg_interp_format_header, fbg_interp_device_header};
-  const char* names[3] = {"fbg_device.cuh", "interp_format.h", "interp_device.cuh"};
+  const char* hdrs[1] = {fbg_device_header};
+  const char* names[1] = {"fbg_device.cuh"};
   nvrtcProgram prog;
-  if (nvrtcCreateProgram(&prog, src.c_str(), "fbg_jit.cu", 3, hdrs, names) != NVRTC_SUCCESS) return false;
+  if (nvrtcCreateProgram(&prog, src.c_str(), "fbg_jit.cu", 1, hdrs, names) != NVRTC_SUCCESS) return false;
   const char* opts[] = {"-arch=sm_103a", "-std=c++17", "-lineinfo", "--ptxas-options=-v"};
   nvrtcResult e = nvrtcCompileProgram(prog, 4, opts);
   size_t logn = 0;
@@ -153,24 +150,21 @@ bool jit_check(const std::string& body, std::string* log) {
 }
 
 
-// ------------------------------------------------- separate compilation --
-// Relocatable device code (-rdc=true) compiled by a pool of worker threads,
-// cached per source, then linked with nvJitLink into one cubin.
+// ---------------------------------------------------- many at once --
+// A pool of worker threads compiles many sources (the batch's specialised
+// kernels), each cached per source like jit_compile.
 
 namespace {
 
-std::mutex g_rdc_mu;
-std::unordered_map<std::string, std::string> g_rdc_cache;   // source -> relocatable cubin
 
-// one NVRTC compilation to a cubin: relocatable (for nvJitLink) or complete
-bool nvrtc_cubin(const std::string& src, bool rdc, std::string* cubin, std::string* log) {
-  const char* hdrs[3] = {fbg_device_header, fbg_interp_format_header, fbg_interp_device_header};
-  const char* names[3] = {"fbg_device.cuh", "interp_format.h", "interp_device.cuh"};
+// one NVRTC compilation to a cubin
+bool nvrtc_cubin(const std::string& src, std::string* cubin, std::string* log) {
+  const char* hdrs[1] = {fbg_device_header};
+  const char* names[1] = {"fbg_device.cuh"};
   nvrtcProgram prog;
-  if (nvrtcCreateProgram(&prog, src.c_str(), rdc ? "fbg_rdc.cu" : "fbg_jit.cu", 3, hdrs, names) != NVRTC_SUCCESS)
-    return false;
-  const char* opts[] = {"-arch=sm_103a", "-std=c++17", "-lineinfo", "-rdc=true"};
-  nvrtcResult e = nvrtcCompileProgram(prog, rdc ? 4 : 3, opts);
+  if (nvrtcCreateProgram(&prog, src.c_str(), "fbg_jit.cu", 1, hdrs, names) != NVRTC_SUCCESS) return false;
+  const char* opts[] = {"-arch=sm_103a", "-std=c++17", "-lineinfo"};
+  nvrtcResult e = nvrtcCompileProgram(prog, 3, opts);
   size_t logn = 0;
   nvrtcGetProgramLogSize(prog, &logn);
   if (log && logn > 1) {
@@ -188,16 +182,16 @@ bool nvrtc_cubin(const std::string& src, bool rdc, std::string* cubin, std::stri
   return ok;
 }
 
-// a pool of worker threads compiles the sources not yet cached (rdc: the
-// relocatable cache, else the cubin cache); sources still compiling at the
-// deadline are reported as not ok (their compiles finish in the background)
+// the sources not yet cached are compiled by the pool; sources still
+// compiling at the deadline are reported as not ok (their compiles finish in
+// the background)
 std::mutex g_cubin_mu;
-std::unordered_map<std::string, std::string> g_cubin_cache;   // source -> complete cubin
+std::unordered_map<std::string, std::string> g_cubin_cache;   // source -> cubin
 
-std::vector<bool> compile_many(const std::vector<std::string>& bodies, bool rdc, std::vector<std::string>* cubins,
+std::vector<bool> compile_many(const std::vector<std::string>& bodies, std::vector<std::string>* cubins,
                                double deadline_s, std::string* log) {
-  std::mutex& cmu = rdc ? g_rdc_mu : g_cubin_mu;
-  std::unordered_map<std::string, std::string>& cache = rdc ? g_rdc_cache : g_cubin_cache;
+  std::mutex& cmu = g_cubin_mu;
+  std::unordered_map<std::string, std::string>& cache = g_cubin_cache;
   const size_t n = bodies.size();
   cubins->assign(n, std::string());
   std::vector<bool> ok(n, false);
@@ -227,7 +221,7 @@ std::vector<bool> compile_many(const std::vector<std::string>& bodies, bool rdc,
   }
   unsigned workers = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), 16u));
   for (unsigned w = 0; w < workers; w++) {
-    std::thread([pool, n, rdc, &cmu, &cache] {
+    std::thread([pool, n, &cmu, &cache] {
       for (;;) {
         size_t i;
         {
@@ -238,7 +232,7 @@ std::vector<bool> compile_many(const std::vector<std::string>& bodies, bool rdc,
           pool->state[i] = 1;
         }
         std::string cubin, lg;
-        bool good = nvrtc_cubin(pool->src[i], rdc, &cubin, &lg);
+        bool good = nvrtc_cubin(pool->src[i], &cubin, &lg);
         if (good) {
           std::lock_guard<std::mutex> lk(cmu);
           cache.emplace(pool->src[i], cubin);
@@ -295,11 +289,6 @@ JitResult load_cubin(const std::string& key, const std::string& cubin, const cha
 
 }  // namespace
 
-std::vector<bool> jit_compile_rdc_many(const std::vector<std::string>& bodies, std::vector<std::string>* cubins,
-                                       double deadline_s, std::string* log) {
-  return compile_many(bodies, true, cubins, deadline_s, log);
-}
-
 std::vector<JitResult> jit_compile_many(const std::vector<std::string>& bodies, const char* kernel_name, int device,
                                         double deadline_s, std::string* log) {
   const size_t n = bodies.size();
@@ -321,95 +310,13 @@ std::vector<JitResult> jit_compile_many(const std::vector<std::string>& bodies, 
   }
   if (todo.empty()) return res;
   std::vector<std::string> cubins;
-  std::vector<bool> ok = compile_many(todo, false, &cubins, deadline_s, log);
+  std::vector<bool> ok = compile_many(todo, &cubins, deadline_s, log);
   for (size_t t = 0; t < todo.size(); t++) {
     if (!ok[t]) continue;
     std::string key = std::to_string(device) + ":" + kernel_name + ":#include \"fbg_device.cuh\"\n" + todo[t];
     res[where[t]] = load_cubin(key, cubins[t], kernel_name);
   }
   return res;
-}
-
-JitResult jit_link(const std::vector<std::string>& cubins, const char* kernel_name, int device) {
-  JitResult r;
-  std::string key = std::to_string(device) + ":link:" + kernel_name;
-  for (auto& c : cubins) key += ":" + std::to_string(std::hash<std::string>()(c)) + "/" + std::to_string(c.size());
-  {
-    std::lock_guard<std::mutex> lk(g_mu);
-    auto it = g_cache.find(key);
-    if (it != g_cache.end()) {
-      r.ok = true;
-      r.kernel = it->second.kern;
-      r.cached = true;
-      return r;
-    }
-  }
-  nvJitLinkHandle h;
-  const char* opts[] = {"-arch=sm_103a"};
-  if (nvJitLinkCreate(&h, 1, opts) != NVJITLINK_SUCCESS) {
-    r.log = "nvJitLinkCreate failed";
-    return r;
-  }
-  bool good = true;
-  for (size_t i = 0; i < cubins.size() && good; i++)
-    good = nvJitLinkAddData(h, NVJITLINK_INPUT_CUBIN, cubins[i].data(), cubins[i].size(), nullptr) == NVJITLINK_SUCCESS;
-  if (good) good = nvJitLinkComplete(h) == NVJITLINK_SUCCESS;
-  std::string linked;
-  if (good) {
-    size_t n = 0;
-    nvJitLinkGetLinkedCubinSize(h, &n);
-    linked.assign(n, '\0');
-    nvJitLinkGetLinkedCubin(h, &linked[0]);
-  } else {
-    size_t n = 0;
-    nvJitLinkGetErrorLogSize(h, &n);
-    std::string lg(n, '\0');
-    if (n) nvJitLinkGetErrorLog(h, &lg[0]);
-    r.log = "nvJitLink: " + lg;
-  }
-  nvJitLinkDestroy(&h);
-  if (!good) return r;
-  Entry ent;
-  cudaError_t ce = cudaLibraryLoadData(&ent.lib, linked.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
-  if (ce != cudaSuccess) {
-    r.log = std::string("cudaLibraryLoadData: ") + cudaGetErrorString(ce);
-    return r;
-  }
-  ce = cudaLibraryGetKernel(&ent.kern, ent.lib, kernel_name);
-  if (ce != cudaSuccess) {
-    r.log = std::string("cudaLibraryGetKernel: ") + cudaGetErrorString(ce);
-    cudaLibraryUnload(ent.lib);
-    return r;
-  }
-  {
-    std::lock_guard<std::mutex> lk(g_mu);
-    auto ins = g_cache.emplace(key, ent);
-    if (!ins.second) {
-      cudaLibraryUnload(ent.lib);
-      ent = ins.first->second;
-    }
-  }
-  r.ok = true;
-  r.kernel = ent.kern;
-  return r;
-}
-
-bool jit_link_check(const std::vector<std::string>& cubins, std::string* log) {
-  nvJitLinkHandle h;
-  const char* opts[] = {"-arch=sm_103a"};
-  if (nvJitLinkCreate(&h, 1, opts) != NVJITLINK_SUCCESS) return false;
-  bool good = true;
-  for (size_t i = 0; i < cubins.size() && good; i++)
-    good = nvJitLinkAddData(h, NVJITLINK_INPUT_CUBIN, cubins[i].data(), cubins[i].size(), nullptr) == NVJITLINK_SUCCESS;
-  if (good) good = nvJitLinkComplete(h) == NVJITLINK_SUCCESS;
-  if (!good && log) {
-    size_t n = 0;
-    nvJitLinkGetErrorLogSize(h, &n);
-    log->assign(n, '\0');
-    if (n) nvJitLinkGetErrorLog(h, &(*log)[0]);
-  }
-  nvJitLinkDestroy(&h);
-  return good;
 }
 
 size_t jit_cache_size() {

@@ -18,18 +18,11 @@ struct JitResult {
 // Compile fbg_device.cuh + body for sm_103a and load it on the current device.
 JitResult jit_compile(const std::string& body, const char* kernel_name, int device);
 size_t jit_cache_size();
-// Relocatable device code for many sources at once: a pool of worker threads
-// compiles the sources not yet cached; sources still compiling after
-// deadline_s are reported as not ok (their compiles finish in the background).
-std::vector<bool> jit_compile_rdc_many(const std::vector<std::string>& bodies, std::vector<std::string>* cubins,
-                                       double deadline_s, std::string* log);
-// Complete kernels for many sources at once (same pool and deadline), each
-// loaded on this device and cached like jit_compile; failures are not ok.
+// Kernels for many sources at once: a pool of worker threads compiles them
+// (sources still compiling after deadline_s are not ok); each is loaded on
+// this device and cached like jit_compile.
 std::vector<JitResult> jit_compile_many(const std::vector<std::string>& bodies, const char* kernel_name, int device,
                                         double deadline_s, std::string* log);
-// Link relocatable cubins with nvJitLink and load `kernel_name` on this device.
-JitResult jit_link(const std::vector<std::string>& cubins, const char* kernel_name, int device);
-bool jit_link_check(const std::vector<std::string>& cubins, std::string* log);
 // Compile only (no device needed); *log receives the NVRTC/ptxas messages.
 bool jit_check(const std::string& body, std::string* log);
 
