@@ -128,3 +128,22 @@ def test_counts_interleaved_with_tables_and_model_lists():
         p.set_option(L.OPT_STATS, 0)
         assert p.count() == want
     assert np.array_equal(words.cpu().numpy().view(np.uint64), th.table())
+
+
+def test_item_trace_covers_every_item():
+    """fbg_debug_item_trace times each (unit, warp slice) item of a natural
+    launch; the wrong buffer size is refused."""
+    import torch
+    p = F.compile(W.TRIFREE9.text, 9)
+    want = p.count()
+    lay = p.debug_dump(0)["layout"]
+    _, nunits = p.unit_vars()
+    nitems = nunits << lay["warp_bits"]
+    ns = torch.zeros(nitems, dtype=torch.int64, device="cuda")
+    p.debug_item_trace(ns)
+    t = ns.cpu()
+    # every item is timed (the timer's resolution may round the shortest to 0)
+    assert int(t.sum()) > 0 and int((t > 0).sum()) * 2 >= nitems and int((t >= 0).sum()) == nitems
+    assert p.count() == want
+    with pytest.raises(L.FbgError):
+        p.debug_item_trace(torch.zeros(nitems + 1, dtype=torch.int64, device="cuda"))
