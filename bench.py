@@ -30,6 +30,13 @@ SM_COUNT = 148
 LOP3_LANES_PER_CLK_SM = 64      # measured issue rate of lop3.b32 per SM per clock (sm_103a)
 
 
+# DRAM bytes (read + write) per launch from one ncu capture of the current
+# kernels (profiles/fbg_jit_count_n36.md, profiles/fbg_jit_table_cnf32.md):
+# the three count launches of a step, and one truth-table launch.
+TRAFFIC_COUNT_STEP = 50_944 + 99_840 + 68_096
+TRAFFIC_TABLE_LAUNCH = 478_839_808 + 70_400
+
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -295,7 +302,7 @@ def run_table(args, torch, F, L, peaks):
     return {"workload": "3-CNF n=32 m=136 seed 1, full truth table", "shape": shape, "value": (1 << 32) / t / 1e9, "unit": "Gassign/s",
             "ms": t * 1e3, "bytes_written": nbytes, "count": cnt, "popcount_equals_count": True,
             "roofline": {"bound": "hbm", "achieved": nbytes / t / 1e9, "peak": peak, "unit": "GB/s",
-                         "frac": (nbytes / t / 1e9) / peak if peak else None, "traffic": None,
+                         "frac": (nbytes / t / 1e9) / peak if peak else None, "traffic": TRAFFIC_TABLE_LAUNCH,
                          "basis": "algorithmic bytes = 2^32/8 written per launch; peak = measured copy GB/s"}}
 
 
@@ -579,7 +586,7 @@ def run_ours(args, rank, world):
                    "flush_l2": True, "parallelism": f"replicas x{world}", "counts": expected,
                    "shapes": shapes},
         "roofline": {"bound": "alu", "achieved": executed / kern_s / 1e12, "peak": peak_lop3 / 1e12,
-                     "unit": "Tlop3/s", "frac": executed / kern_s / peak_lop3, "traffic": None,
+                     "unit": "Tlop3/s", "frac": executed / kern_s / peak_lop3, "traffic": TRAFFIC_COUNT_STEP,
                      "basis": "executed lane-varying lop3.b32 lane-ops of the step's three concurrent "
                               "fbg_jit_count launches (in-kernel level counters, untimed run) / CUDA-event step "
                               "time on the launching stream; peak = 148 SM x 64 lanes/clk x 2032 MHz; lop3 whose "
