@@ -145,7 +145,7 @@ class SrcGen {
     if (last || cs.fa_left == 0) {
       for (int k = 0; k < 4; k++) {
         for (auto& e : cs.pend[k])
-          o << ind << acc_name(k) << " += __popc(" << e << ");\n";
+          o << ind << acc_name(k) << " = fbg_madd(" << acc_name(k) << ", __popc(" << e << "), one);\n";
         cs.pend[k].clear();
       }
     }
@@ -491,6 +491,8 @@ std::string SrcGen::unit_fn_count(const std::string& fname) {
   const int last = nl - 1;
   o << "__device__ __noinline__ fbg_u64 " << fname << "(fbg_u64 u0, fbg_u64 u1, fbg_u32 tb, fbg_u64* lvl) {\n";
   o << "  const fbg_u32 tm = (tb < " << tvalid << "u) ? " << hex32(valid_mask()) << " : 0u;\n";
+  // a 1 the compiler cannot see (tb < 2^31 always): count adds become IMAD
+  o << "  const fbg_u32 one = (tb >> 31) | 1u;\n";
   if (counters_) {
     o << "  lvl[0]++;\n";
     // level execution counters live in registers during the call

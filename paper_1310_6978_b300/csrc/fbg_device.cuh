@@ -64,6 +64,15 @@ __device__ __forceinline__ fbg_u64 fbg_next_unit(const FbgLaunch& P, fbg_u64* s_
 }
 
 // fetch the next `chunk` units for the whole block
+// a + b * one as an integer multiply-add: with `one` a runtime 1 the
+// compiler cannot fold, the add issues on the FMA pipe instead of the ALU
+// pipe that the lop3 work saturates
+__device__ __forceinline__ fbg_u32 fbg_madd(fbg_u32 a, fbg_u32 b, fbg_u32 one) {
+  fbg_u32 d;
+  asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(b), "r"(one), "r"(a));
+  return d;
+}
+
 // the global nanosecond timer (diagnostics only)
 __device__ __forceinline__ fbg_u64 fbg_globaltimer() {
   fbg_u64 t;

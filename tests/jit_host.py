@@ -39,6 +39,7 @@ template <int LUT> static inline fbg_u32 fbg_lop3(fbg_u32 a, fbg_u32 b, fbg_u32 
   return r;
 }
 static inline int __popc(fbg_u32 x) { return __builtin_popcount(x); }
+static inline fbg_u32 fbg_madd(fbg_u32 a, fbg_u32 b, fbg_u32 one) { return a + b * one; }
 static inline bool __any_sync(unsigned, bool p) { return p; }
 static fbg_u64 g_warp_acc = 0;
 static inline fbg_u64 fbg_warp_sum(fbg_u64 v) {
