@@ -100,6 +100,11 @@ enum {
   FBG_OPT_INNER_BITS = 10,     /* JIT: bits of the innermost loop level, which is emitted
                                   unrolled with its generator words folded as constants
                                   (0 = default: as the other levels; 1..5) */
+  FBG_OPT_SPLIT_ITEMS = 11,    /* 1: fbg_schedule_units hands a long item out as up to 16
+                                  pieces over the first loop level; 0 (default): whole items.
+                                  Pieces shorten a lone launch whose longest items end it
+                                  late; launches that share the GPU already fill that tail.
+                                  Read by the next fbg_schedule_units; no rebuild */
 };
 
 typedef struct {
@@ -252,14 +257,17 @@ fbg_status fbg_debug_dump(fbg_program *prog, int which, char *buf, size_t *len);
  * unit of fbg_unit_vars depends on how much of its subspace the level
  * conjunctions prune, and a few heavy units can keep a few SMs busy long
  * after the rest are idle.  This call runs one count launch that times every
- * item (unit, warp slice) on the GPU's nanosecond timer, sorts the items by
- * time, longest first, and keeps that order on the device: later full-range
+ * item (unit, warp slice) on the GPU's nanosecond timer, with
+ * FBG_OPT_SPLIT_ITEMS splits each item that takes longer than half the mean
+ * load of a warp into 2, 4, 8 or 16 pieces over the values of the first loop
+ * level (only when that level is a runtime loop), sorts the items and pieces by time,
+ * longest first, and keeps that order on the device: later full-range
  * counts of the program through fbg_count and fbg_count_async hand out items
- * in it.  Results do not depend on the order.  The
+ * in it.  Results do not depend on the order or the pieces.  The
  * order is dropped when an option rebuilds the kernel.  Synchronises the
- * stream; allocates 8 bytes per item temporarily and keeps 4 bytes per item.
- * FBG_EINVAL when the program does not use the NVRTC engine, FBG_ETOOBIG
- * above 2^26 items. */
+ * stream; allocates 8 bytes per item temporarily and keeps 4 bytes per item
+ * or piece.  FBG_EINVAL when the program does not use the NVRTC engine,
+ * FBG_ETOOBIG above 2^24 items. */
 fbg_status fbg_schedule_units(fbg_program *prog, void *stream);
 
 /* Diagnostics (no counterpart in the paper): one count launch of the NVRTC

@@ -29,7 +29,7 @@ STATUS_NAMES = ["FBG_OK", "FBG_EINVAL", "FBG_EPARSE", "FBG_ETOOBIG", "FBG_ENOMEM
 
 ENGINE_AUTO, ENGINE_JIT, ENGINE_INTERP = 0, 1, 2
 OPT_ENGINE, OPT_PRUNE, OPT_REGS_LOG2, OPT_WARPS_LOG2, OPT_UNIT_BITS, OPT_LOOP_LEVEL_BITS, OPT_SEARCH_ORDER, \
-    OPT_MIN_BLOCKS, OPT_STATS, OPT_INNER_BITS = range(1, 11)
+    OPT_MIN_BLOCKS, OPT_STATS, OPT_INNER_BITS, OPT_SPLIT_ITEMS = range(1, 12)
 MODE_COUNT, MODE_ENUMERATE = 0, 1
 BATCH_GRAPH, BATCH_SPECIALIZE = 1, 2
 

@@ -392,6 +392,9 @@ fbg_status fbg_set_option(fbg_program* p, int option, int64_t v) {
       if (v < 0 || v > 5) return bad();
       p->opt_inner_bits = v;
       break;
+    case FBG_OPT_SPLIT_ITEMS:   // read by the next fbg_schedule_units; kernels stay valid
+      p->opt_split_items = v ? 1 : 0;
+      return FBG_OK;
     case FBG_OPT_STATS:   // kernels carry level counters only while statistics are on
       if (p->opt_stats == (v ? 1 : 0)) return FBG_OK;
       p->opt_stats = v ? 1 : 0;
@@ -525,7 +528,7 @@ fbg_status fbg_schedule_units(fbg_program* p, void* stream) {
   JitBuild& b = p->jb[0];
   const int wb = b.lp.layout.warp_bits;
   const uint64_t items = b.nunits << wb;
-  if (items > (1ull << 26)) return set_error(FBG_ETOOBIG, "too many items to schedule");
+  if (items > (1ull << 24)) return set_error(FBG_ETOOBIG, "too many items to schedule");
   cudaStream_t st = (cudaStream_t)stream;
   s = ensure_scratch(p, kScratchHead);
   if (s != FBG_OK) return s;
@@ -542,13 +545,38 @@ fbg_status fbg_schedule_units(fbg_program* p, void* stream) {
   cudaFree(d_tr);
   if (s != FBG_OK) return s;
   if (e != cudaSuccess) return cuda_error(e, "fbg_schedule_units trace");
-  // longest processing time first; ties keep the natural (unit, slice)
-  // order; units without models (b.alive) stay out
-  std::vector<unsigned> perm;
-  perm.reserve((size_t)items);
+  // units without models (b.alive) stay out
+  std::vector<unsigned> live;
+  live.reserve((size_t)items);
+  double sum = 0;
   for (uint64_t t = 0; t < items; t++)
-    if (b.alive.empty() || b.alive[(size_t)t]) perm.push_back((unsigned)t);
-  std::stable_sort(perm.begin(), perm.end(), [&](unsigned x, unsigned y) { return ns[x] > ns[y]; });
+    if (b.alive.empty() || b.alive[(size_t)t]) {
+      live.push_back((unsigned)t);
+      sum += (double)ns[(size_t)t];
+    }
+  // An item longer than half the mean load of a warp would end the launch
+  // late on its own: it is handed out as 2^s pieces over the first loop level
+  // (each estimated at its share of the item's time).
+  const int smax = p->opt_split_items ? top_loop_split_bits(b.lp.layout) : 0;
+  const double warps = (double)b.grid * (double)(b.block / 32);
+  const double target = sum / warps / 2.0;
+  struct Piece {
+    unsigned code;
+    double t;
+  };
+  std::vector<Piece> pieces;
+  pieces.reserve(live.size());
+  for (unsigned t : live) {
+    const double d = (double)ns[t];
+    int sb = 0;
+    while (sb < smax && d / (double)(1u << sb) > target) sb++;
+    for (unsigned q = 0; q < (1u << sb); q++)
+      pieces.push_back(Piece{t | ((unsigned)sb << 28) | (q << 24), d / (double)(1u << sb)});
+  }
+  // longest processing time first; ties keep the natural (unit, slice, piece) order
+  std::stable_sort(pieces.begin(), pieces.end(), [](const Piece& x, const Piece& y) { return x.t > y.t; });
+  std::vector<unsigned> perm(pieces.size());
+  for (size_t i = 0; i < pieces.size(); i++) perm[i] = pieces[i].code;
   return upload_items(b, perm);
 }
 
@@ -694,7 +722,8 @@ fbg_status fbg_debug_dump(fbg_program* p, int which, char* buf, size_t* len) {
   std::ostringstream o;
   auto layout_json = [&](const Layout& L) {
     o << "\"layout\": {\"n\": " << L.n << ", \"r\": " << L.r << ", \"lane_bits\": " << L.lane_bits
-      << ", \"warp_bits\": " << L.warp_bits << ", \"unit_bits\": " << L.unit_bits << ", \"loop_bits\": [";
+      << ", \"warp_bits\": " << L.warp_bits << ", \"unit_bits\": " << L.unit_bits
+      << ", \"split_bits\": " << top_loop_split_bits(L) << ", \"loop_bits\": [";
     for (size_t i = 0; i < L.loop_bits.size(); i++) o << (i ? ", " : "") << L.loop_bits[i];
     o << "], \"loop_pos\": [";
     for (size_t i = 0; i < L.loop_bits.size(); i++) o << (i ? ", " : "") << L.loop_pos((int)i);
@@ -756,6 +785,9 @@ fbg_status fbg_debug_dump(fbg_program* p, int which, char* buf, size_t* len) {
         o << "]";
       }
     }
+    // entries of the item list full-range counts hand out now (live items,
+    // or the items and pieces of fbg_schedule_units)
+    if (which == 0 && p->jb[0].valid && p->jb[0].d_perm) o << ", \"item_list_entries\": " << p->jb[0].nperm;
     o << "}";
   } else {
     InterpCode code;

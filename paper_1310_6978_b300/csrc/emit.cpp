@@ -40,6 +40,19 @@ struct Sym {
   }
 };
 
+// The innermost loop level is emitted unrolled when it has at most 5 bits.
+static bool innermost_unrolled(const Layout& L) { return L.nlevels() > 2 && L.loop_bits.back() <= 5; }
+
+}  // namespace
+
+int top_loop_split_bits(const Layout& L) {
+  if (L.nlevels() <= 2) return 0;
+  if (L.nlevels() == 3 && innermost_unrolled(L)) return 0;   // the first loop level is the unrolled one
+  return std::min(L.loop_bits[0], 4);
+}
+
+namespace {
+
 // Source generator.  Every LUT register is folded: all-zero/all-one inputs
 // fix their bit, negated inputs flip, repeated inputs merge; a function of at
 // most one input becomes a constant or an alias, identical operations inside
@@ -51,8 +64,9 @@ class SrcGen {
   // counters: count level executions (lvl[]) for fbg_exec_stats; a kernel
   // built without them spends no instructions or registers on them
   explicit SrcGen(const LutProgram& prog, bool counters = true)
-      : p(prog), L(prog.layout), nreg(1 << prog.layout.r), nl(prog.layout.nlevels()), counters_(counters) {
-    if (nl > 2 && L.loop_bits.back() <= 5) {
+      : p(prog), L(prog.layout), nreg(1 << prog.layout.r), nl(prog.layout.nlevels()), counters_(counters),
+        split_bits(top_loop_split_bits(prog.layout)) {
+    if (innermost_unrolled(L)) {
       unroll_lv = nl - 1;
       unroll_bits = L.loop_bits.back();
       unroll_base = L.loop_pos(nl - 3);
@@ -66,9 +80,9 @@ class SrcGen {
   std::vector<long long> ops;   // lop3.b32 per thread per execution of each level (lane-varying)
   std::vector<long long> uops;  // warp-uniform lop3 per warp per execution of each level
   int unroll_lv = -1;
+  const int split_bits;   // pieces of an item: up to 2^split_bits over the first loop level
 
   std::string generate(int mode, int block, int minb);
-  std::string generate_batch_fn(const std::string& fname);
   std::string unit_fn_count(const std::string& fname);
   std::string unit_fn_table(const std::string& fname);
 
@@ -481,15 +495,17 @@ class SrcGen {
 
 // Per-unit device function of count mode: this thread's number of models over
 // the units [u0, u1), the thread taking the lane and warp bits tb; lvl[l]
-// counts the executions of level l.  The kernels and the batch kernel call
-// it; keeping the work fetch outside this function keeps the control flow the
-// compiler sees simple.
+// counts the executions of level l; when the first loop level is a runtime
+// loop (top_loop_split_bits > 0) it runs over [lo2, hi2) only, so that one
+// heavy item can be handed out as several pieces.  Keeping the work fetch
+// outside this function keeps the control flow the compiler sees simple.
 std::string SrcGen::unit_fn_count(const std::string& fname) {
   mark_live(0);
   auto vars = used_vars();
   const int tvalid = 1 << (L.lane_bits + L.warp_bits);
   const int last = nl - 1;
-  o << "__device__ __noinline__ fbg_u64 " << fname << "(fbg_u64 u0, fbg_u64 u1, fbg_u32 tb, fbg_u64* lvl) {\n";
+  o << "__device__ __noinline__ fbg_u64 " << fname
+    << "(fbg_u64 u0, fbg_u64 u1, fbg_u32 tb, fbg_u64* lvl, fbg_u32 lo2, fbg_u32 hi2) {\n";
   o << "  const fbg_u32 tm = (tb < " << tvalid << "u) ? " << hex32(valid_mask()) << " : 0u;\n";
   // a 1 the compiler cannot see (tb < 2^31 always): count adds become IMAD
   o << "  const fbg_u32 one = (tb >> 31) | 1u;\n";
@@ -516,7 +532,10 @@ std::string SrcGen::unit_fn_count(const std::string& fname) {
   for (int lv = 2; lv < nl; lv++) {
     if (lv == unroll_lv) break;
     std::string iv = "i" + std::to_string(lv);
-    o << ind << "for (fbg_u32 " << iv << " = 0; " << iv << " < " << (1u << L.loop_bits[(size_t)(lv - 2)]) << "u; ++" << iv << ") {\n";
+    if (lv == 2)
+      o << ind << "for (fbg_u32 " << iv << " = lo2; " << iv << " < hi2; ++" << iv << ") {\n";
+    else
+      o << ind << "for (fbg_u32 " << iv << " = 0; " << iv << " < " << (1u << L.loop_bits[(size_t)(lv - 2)]) << "u; ++" << iv << ") {\n";
     ind += "  ";
     if (counters_) o << ind << "it" << lv << "++;\n";
     var_words(vars[(size_t)lv], iv, L.loop_pos(lv - 2), ind, false);
@@ -654,6 +673,8 @@ std::string SrcGen::generate(int mode, int block, int minb) {
     o << "  const fbg_u64 chunk = P.chunk ? P.chunk : 1ull;\n";
     o << "  const fbg_u64 R = P.unit_end - P.unit_begin;\n";
     o << "  const fbg_u64 items = P.unit_perm ? P.nperm : (R << " << L.warp_bits << ");\n";
+    // the whole first loop level (unused when it is not a runtime loop)
+    o << "  const fbg_u32 full2 = " << (split_bits > 0 ? (1u << L.loop_bits[0]) : 0u) << "u;\n";
     o << "  for (;;) {\n";
     o << "    fbg_u64 t = fbg_next_items_warp(P, chunk);\n";
     o << "    if (t >= items) break;\n";
@@ -661,9 +682,18 @@ std::string SrcGen::generate(int mode, int block, int minb) {
     o << "    if (P.unit_perm) {\n";
     o << "      for (; t < e; ++t) {\n";
     o << "        const fbg_u32 it = P.unit_perm[t];\n";
-    o << "        const fbg_u64 v = it >> " << L.warp_bits << ";\n";
-    o << "        const fbg_u32 tb = lane | ((it & " << ((1u << L.warp_bits) - 1u) << "u) << 5);\n";
-    o << "        total += fbg_unit_count(P.unit_begin + v, P.unit_begin + v + 1, tb, lvl);\n";
+    o << "        const fbg_u32 base = it & 0xFFFFFFu;\n";
+    o << "        const fbg_u64 v = base >> " << L.warp_bits << ";\n";
+    o << "        const fbg_u32 tb = lane | ((base & " << ((1u << L.warp_bits) - 1u) << "u) << 5);\n";
+    if (split_bits > 0) {
+      // piece q of 2^s of the first loop level (s <= split_bits)
+      o << "        const fbg_u32 s = (it >> 28) < " << split_bits << "u ? (it >> 28) : " << split_bits << "u;\n";
+      o << "        const fbg_u32 q = (it >> 24) & ((1u << s) - 1u);\n";
+      o << "        const fbg_u32 w2 = full2 >> s;\n";
+      o << "        total += fbg_unit_count(P.unit_begin + v, P.unit_begin + v + 1, tb, lvl, q * w2, q * w2 + w2);\n";
+    } else {
+      o << "        total += fbg_unit_count(P.unit_begin + v, P.unit_begin + v + 1, tb, lvl, 0u, full2);\n";
+    }
     o << "      }\n";
     o << "      continue;\n";
     o << "    }\n";
@@ -674,7 +704,7 @@ std::string SrcGen::generate(int mode, int block, int minb) {
     o << "      if (P.unit_counts || P.unit_trace || P.item_trace) {\n";
     o << "        for (fbg_u64 v = v0; v < v0 + span; ++v) {\n";
     o << "          const fbg_u64 t0 = (P.unit_trace || P.item_trace) ? fbg_globaltimer() : 0ull;\n";
-    o << "          const fbg_u64 c = fbg_unit_count(P.unit_begin + v, P.unit_begin + v + 1, tb, lvl);\n";
+    o << "          const fbg_u64 c = fbg_unit_count(P.unit_begin + v, P.unit_begin + v + 1, tb, lvl, 0u, full2);\n";
     o << "          total += c;\n";
     o << "          const fbg_u64 ws = fbg_warp_sum(c);\n";
     o << "          if (lane == 0u && ws && P.unit_counts) atomicAdd(P.unit_counts + v, ws);\n";
@@ -685,7 +715,7 @@ std::string SrcGen::generate(int mode, int block, int minb) {
     o << "          if (lane == 0u && P.item_trace) P.item_trace[(v << " << L.warp_bits << ") | w] = fbg_globaltimer() - t0;\n";
     o << "        }\n";
     o << "      } else {\n";
-    o << "        total += fbg_unit_count(P.unit_begin + v0, P.unit_begin + v0 + span, tb, lvl);\n";
+    o << "        total += fbg_unit_count(P.unit_begin + v0, P.unit_begin + v0 + span, tb, lvl, 0u, full2);\n";
     o << "      }\n";
     o << "      t += span;\n";
     o << "    }\n";
@@ -718,15 +748,7 @@ std::string SrcGen::generate(int mode, int block, int minb) {
   return o.str();
 }
 
-// the count body as a device function for the batch kernel
-std::string SrcGen::generate_batch_fn(const std::string& fname) { return unit_fn_count(fname); }
-
 }  // namespace
-
-std::string emit_batch_function(const LutProgram& p, const std::string& fname) {
-  SrcGen g(p, false);
-  return g.generate_batch_fn(fname);
-}
 
 std::string emit_cuda_source(const LutProgram& p, int mode, int block, int minblocks,
                              std::vector<long long>* ops_per_level, int* unrolled_level, bool counters,

@@ -19,9 +19,11 @@ std::string emit_cuda_source(const LutProgram& p, int mode, int block, int minbl
                              std::vector<long long>* ops_per_level = nullptr, int* unrolled_level = nullptr,
                              bool counters = true, std::vector<long long>* uniform_ops_per_level = nullptr);
 
-// device function `fname(u0, u1)`: this thread's model count over the units
-// [u0, u1) of p's layout (the count body, for the batch kernel)
-std::string emit_batch_function(const LutProgram& p, const std::string& fname);
+// Count-mode item pieces: an entry of the item list (FbgLaunch::unit_perm) is
+// item | s << 28 | q << 24 (item < 2^24): piece q of 2^s equal ranges of the
+// first loop level.  The largest s the kernel of layout L takes (0: items
+// are not split -- the first loop level is absent or emitted unrolled).
+int top_loop_split_bits(const Layout& L);
 
 struct InterpCode {
   FbgInterpProg prog;                 // device pointers left null

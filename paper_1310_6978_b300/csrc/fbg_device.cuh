@@ -24,7 +24,9 @@ struct FbgLaunch {
   fbg_u64* item_trace;     // optional (count mode): nanoseconds of item (unit u, warp slice w)
                            // at index (u - unit_begin) * slices + w
   const fbg_u32* unit_perm;  // optional (count mode, full range): the items handed out, in order,
-                             // each entry u << warp_bits | w (units with no models may be left out)
+                             // each entry u << warp_bits | w (< 2^24; units with no models may be
+                             // left out), plus s << 28 | q << 24: piece q of 2^s of the values of
+                             // the first loop level (s = 0: the whole item)
   fbg_u64 nperm;             // number of entries of unit_perm
   fbg_u64* acc;            // self-resetting count (count mode, when done is set): running sum,
   fbg_u64* done;           //   warps finished, the destination of the total, warps in the grid;

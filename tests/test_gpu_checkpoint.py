@@ -147,3 +147,40 @@ def test_item_trace_covers_every_item():
     assert p.count() == want
     with pytest.raises(L.FbgError):
         p.debug_item_trace(torch.zeros(nitems + 1, dtype=torch.int64, device="cuda"))
+
+
+@pytest.mark.parametrize("wl,opts,want", [
+    (W.posets(5), {L.OPT_UNIT_BITS: 2}, 4231),
+    (W.posets(5), {L.OPT_UNIT_BITS: 0, L.OPT_LOOP_LEVEL_BITS: 3}, 4231),
+    (W.TRANSITIVE6, {}, 9415189),
+    (W.TRIFREE9, {}, 246348115),
+], ids=["posets5_u2", "posets5_u0", "transitive6", "trifree9"])
+def test_split_items_keep_counts(wl, opts, want):
+    """fbg_schedule_units hands long items out as pieces over the first loop
+    level; counts equal the known counts with and without pieces."""
+    import torch
+    p = F.compile(wl.text, wl.k)
+    for k, v in opts.items():
+        p.set_option(k, v)
+    p.set_option(L.OPT_SPLIT_ITEMS, 1)
+    d = p.debug_dump(0)
+    lay = d["layout"]
+    assert lay["split_bits"] > 0
+    items = (1 << lay["unit_bits"]) << lay["warp_bits"]
+    live = len(d["alive_items"]) if "alive_items" in d else items
+    assert p.count() == want
+    p.schedule_units()
+    split = p.debug_dump(0)["item_list_entries"]
+    assert split >= live
+    assert split <= live << lay["split_bits"]
+    if items < 1000:   # fewer items than warps: every item the timer saw is split
+        assert split > live
+    out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for _ in range(3):
+        p.count_async(out)
+        assert int(out.item()) == want
+    assert p.count() == want
+    p.set_option(L.OPT_SPLIT_ITEMS, 0)
+    p.schedule_units()
+    assert p.debug_dump(0)["item_list_entries"] == live
+    assert p.count() == want

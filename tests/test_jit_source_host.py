@@ -54,5 +54,24 @@ def test_generated_source_matches_oracle(wl, li):
             if "alive_items" in d0:
                 live = np.array(d0["alive_items"], dtype=np.uint32)
                 assert jit_host.run_count(src, block, nunits, live, self_reset=True) == th.count()
+            # items handed out as pieces over the first loop level (entry
+            # item | s << 28 | q << 24): every item in 2^s pieces, and a mix
+            sb = d["split_bits"]
+            if sb:
+                for s in sorted({1, sb}):
+                    whole = np.repeat(np.arange(items, dtype=np.uint32), 1 << s)
+                    q = np.tile(np.arange(1 << s, dtype=np.uint32), items)
+                    split = whole | np.uint32(s << 28) | (q << np.uint32(24))
+                    split = split[np.random.default_rng(s).permutation(len(split))]
+                    assert jit_host.run_count(src, block, nunits, split, self_reset=True) == th.count()
+                ent = []
+                for t in range(items):
+                    if t % 3:
+                        ent.append(t)
+                    else:
+                        ent += [t | (sb << 28) | (q << 24) for q in range(1 << sb)]
+                assert jit_host.run_count(src, block, nunits, np.array(ent[::-1], dtype=np.uint32)) == th.count()
+            else:
+                assert len(d["loop_bits"]) <= 1
         else:
             assert np.array_equal(jit_host.run_table(src, block, nunits, p.table_words()), th.table())
