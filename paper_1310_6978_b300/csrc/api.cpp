@@ -278,21 +278,26 @@ fbg_status launch_count(fbg_program* p, cudaStream_t st, unsigned long long* dev
     // a few fetches per resident block and unit: enough to balance pruned work
     P.chunk = std::max<uint64_t>(1, (uend - ubegin) / ((uint64_t)b.grid * 16));
     // the item list (live units, measured order) covers full-range counts
-    // without per-unit outputs
+    // without per-unit outputs; a list shorter than the grid's warps gets
+    // only the blocks it needs (every warp of a launch draws from the item
+    // counter and reports to the finish counter once)
+    uint64_t grid = (uint64_t)b.grid;
     if (b.d_perm && ubegin == 0 && uend == b.nunits && !unit_counts && !unit_trace && !item_trace) {
       P.unit_perm = b.d_perm;
       P.nperm = b.nperm;
-      P.chunk = std::max<uint64_t>(1, b.nperm / ((uint64_t)b.grid * (uint64_t)(b.block / 32) * 16));
+      const uint64_t wpb = (uint64_t)(b.block / 32);
+      grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, (b.nperm + wpb - 1) / wpb));
+      P.chunk = std::max<uint64_t>(1, b.nperm / (grid * wpb * 16));
     }
     if (self_reset) {
       P.acc = p->d_scratch + kScratchAcc;
       P.done = p->d_scratch + kScratchDone;
       P.out = dev_count;
-      P.nwarps = (fbg_u32)((uint64_t)b.grid * (uint64_t)b.block / 32);
+      P.nwarps = (fbg_u32)(grid * (uint64_t)b.block / 32);
     }
     void* args[] = {&P};
     if (uend > ubegin)
-      CK(cudaLaunchKernel((const void*)b.kern, dim3((unsigned)b.grid), dim3((unsigned)b.block), args, 0, st));
+      CK(cudaLaunchKernel((const void*)b.kern, dim3((unsigned)grid), dim3((unsigned)b.block), args, 0, st));
     p->scratch_clean = self_reset;
   } else {
     InterpBuild& b = p->ib[0];

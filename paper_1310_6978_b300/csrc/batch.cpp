@@ -287,6 +287,10 @@ fbg_status fbg_batch_create(fbg_program* const* progs, int nprogs, uint64_t max_
             (live.empty() || cudaMemcpy(sk.d_items, live.data(), live.size() * sizeof(unsigned),
                                         cudaMemcpyHostToDevice) == cudaSuccess)) {
           sk.nitems = live.size();
+          // only the blocks a short list needs
+          const uint64_t wpb = (uint64_t)(sk.block / 32);
+          sk.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)sk.grid, (sk.nitems + wpb - 1) / wpb));
+          sk.nwarps = (unsigned)((uint64_t)sk.grid * wpb);
           sk.chunk = std::max<uint64_t>(1, sk.nitems / ((uint64_t)sk.nwarps * 16));
         } else if (sk.d_items) {
           cudaFree(sk.d_items);
