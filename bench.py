@@ -33,7 +33,7 @@ LOP3_LANES_PER_CLK_SM = 64      # measured issue rate of lop3.b32 per SM per clo
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernels (profiles/fbg_jit_count_n36.md, profiles/fbg_jit_table_cnf32.md):
 # the three count launches of a step, and one truth-table launch.
-TRAFFIC_COUNT_STEP = 48_384 + 98_816 + 67_840
+TRAFFIC_COUNT_STEP = 48_384 + 103_936 + 67_328
 TRAFFIC_TABLE_LAUNCH = 478_839_808 + 70_400
 
 
