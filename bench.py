@@ -34,6 +34,10 @@ LOP3_LANES_PER_CLK_SM = 64      # measured issue rate of lop3.b32 per SM per clo
 # kernels (profiles/fbg_jit_count_n36.md, profiles/fbg_jit_table_cnf32.md):
 # the three count launches of a step, and one truth-table launch.
 TRAFFIC_COUNT_STEP = 48_384 + 103_936 + 67_328
+# Vector-pipe LOP3 warp instructions of the three count launches of a step in
+# the same capture (sass__inst_executed_per_opcode; the formulas' LUTs and the
+# full adders of the popcount, not the ULOP3 of the uniform datapath).
+NCU_VECTOR_LOP3_STEP = 9_460_222 + 21_021_412 + 32_735
 TRAFFIC_TABLE_LAUNCH = 478_839_808 + 70_400
 
 
@@ -597,8 +601,14 @@ def run_ours(args, rank, world):
                      "basis": "executed lane-varying lop3.b32 lane-ops of the step's three concurrent "
                               "fbg_jit_count launches (in-kernel level counters, untimed run) / CUDA-event step "
                               "time on the launching stream; peak = 148 SM x 64 lanes/clk x 2032 MHz; lop3 whose "
-                              "inputs are all warp-uniform (uniform datapath) are not counted",
-                     "uniform_lop3_warp_ops_per_step": uniform},
+                              "inputs are all warp-uniform (constants, unit letters, loop counters: the uniform datapath) are not counted",
+                     "uniform_lop3_warp_ops_per_step": uniform,
+                     "ncu_cross_check": {
+                         "vector_lop3_warp_instructions_per_step": NCU_VECTOR_LOP3_STEP,
+                         "achieved": NCU_VECTOR_LOP3_STEP * 32 / kern_s / 1e12,
+                         "frac": NCU_VECTOR_LOP3_STEP * 32 / kern_s / peak_lop3,
+                         "basis": "every LOP3 the three launches issued on the vector ALU pipe (ncu count of the "
+                                  "same kernels and shapes, full adders included) / CUDA-event step time"}},
         "nominal_lop3_ratio": executed / nominal if nominal else None,
         "alu_probe": {"lop3_tops": lop3_probe, "of_nominal_peak": lop3_probe / (peak_lop3 / 1e12),
                       "basis": "fbg_probe_lop3_rate: 16 independent lop3.b32 chains per thread, CUDA events"},

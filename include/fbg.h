@@ -126,8 +126,9 @@ typedef struct {
                                across lanes (the vector ALU pipe's work) */
   double lop3_nominal;      /* lane operations without pruning: every word evaluated */
   int engine;               /* engine that ran */
-  double lop3_uniform;      /* warp operations of lop3 whose inputs are all warp-uniform (constants
-                               and loop counters; the compiler may run them on the uniform pipe) */
+  double lop3_uniform;      /* warp operations of lop3 whose inputs are all warp-uniform (constants,
+                               unit letters and loop counters; the compiler may run them on the
+                               uniform pipe) */
 } fbg_exec_stats;
 
 /*

@@ -32,8 +32,8 @@ struct Sym {
   uint32_t c = 0;
   std::string name;
   bool neg = false;
-  // provably the same in every lane: built only from constants and loop
-  // counters (the compiler may run such lop3 on the uniform datapath)
+  // provably the same in every lane: built only from constants, unit letters
+  // and loop counters (the compiler may run such lop3 on the uniform datapath)
   bool uni = true;
   bool operator==(const Sym& o) const {
     return is_const == o.is_const && (is_const ? c == o.c : (name == o.name && neg == o.neg));
@@ -202,7 +202,10 @@ class SrcGen {
       } else {
         x.is_const = false;
         x.name = "V" + std::to_string(v.id);
-        x.uni = L.level_of_pos(v.id) >= 2;   // loop counters are uniform; thread and unit bits are not
+        // unit and loop letters are the same in every lane of a warp (an
+        // item is one unit of one warp; the compiler can keep them in uniform
+        // registers); the lane, register and warp bits of a thread are not
+        x.uni = L.level_of_pos(v.id) >= 1;
       }
     } else {
       size_t r = (size_t)((uint32_t)s & p.luts[(size_t)v.id].rmask);
