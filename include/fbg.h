@@ -114,7 +114,8 @@ typedef struct {
   int64_t gates;            /* 2-input gates after level-aware lowering (count layout) */
   int64_t luts;             /* 3-input LUTs after mapping (count layout) */
   int nlevels;              /* 2 + loop levels */
-  int64_t lop3_per_level[16];  /* lop3.b32 per thread per execution of each level */
+  int64_t lop3_per_level[16];  /* lane-varying lop3.b32 per thread per execution of each level of
+                                  the count kernel the current options build */
   int regs_log2, lane_bits, warp_bits, unit_bits;
   int loop_bits[8];
   int interp_slots;         /* shared-memory slots of the interpreter program */

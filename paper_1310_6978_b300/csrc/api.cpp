@@ -420,6 +420,7 @@ fbg_status fbg_program_stats(fbg_program* p, fbg_stats* out) {
   try {
     Layout L = make_layout(p->n, jit_params(p), order_for(p, true));
     lp = lower_and_map(p->g, L);
+    if (!p->opt_prune) strip_prune(lp);   // as the count kernel is built
   } catch (CompileError& e) {
     return set_error(FBG_ETOOBIG, e.msg);
   }
