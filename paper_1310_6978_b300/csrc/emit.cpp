@@ -225,8 +225,9 @@ class SrcGen {
   std::string operand(const Val& v, int s, int copy = -1) const { return expr(operand_sym(v, s, copy)); }
 
   // fold one LUT register; *call receives the lop3 call when one is needed
-  Sym fold_one(const Lut& lu, int s, int copy, const std::string& name, std::map<std::string, std::string>& cse,
-               std::string* call) {
+  using CseMap = std::unordered_map<std::string, std::string>;
+
+  Sym fold_one(const Lut& lu, int s, int copy, const std::string& name, CseMap& cse, std::string* call) {
     call->clear();
     Sym in[3];
     for (int k = 0; k < 3; k++) in[k] = operand_sym(lu.in[k], s, copy);
@@ -242,19 +243,19 @@ class SrcGen {
         in[k].neg = false;
       }
     }
-    std::vector<Sym> fs;
+    Sym fs[3];
+    unsigned kf = 0;
     int map[3] = {-1, -1, -1};
     for (int k = 0; k < 3; k++) {
       if (fixed[k] >= 0) continue;
-      for (size_t t = 0; t < fs.size(); t++)
+      for (unsigned t = 0; t < kf; t++)
         if (fs[t] == in[k]) map[k] = (int)t;
       if (map[k] < 0) {
-        map[k] = (int)fs.size();
-        fs.push_back(in[k]);
+        map[k] = (int)kf;
+        fs[kf++] = in[k];
       }
     }
-    unsigned kf = (unsigned)fs.size();
-    std::vector<uint8_t> g(1u << kf);
+    uint8_t g[8];
     for (unsigned a = 0; a < (1u << kf); a++) {
       int bit[3];
       for (int k = 0; k < 3; k++) bit[k] = fixed[k] >= 0 ? fixed[k] : (int)((a >> map[k]) & 1u);
@@ -265,20 +266,20 @@ class SrcGen {
       for (unsigned a = 0; a < (1u << kf); a++)
         if (g[a] != g[a ^ (1u << t)]) dep = true;
       if (dep) continue;
-      std::vector<uint8_t> h(1u << (kf - 1));
-      for (unsigned a = 0; a < h.size(); a++) {
+      uint8_t h[8];
+      for (unsigned a = 0; a < (1u << (kf - 1)); a++) {
         unsigned lo = a & ((1u << t) - 1u), hi = a >> t;
         h[a] = g[lo | (hi << (t + 1))];
       }
-      fs.erase(fs.begin() + t);
-      g.swap(h);
+      for (unsigned q = (unsigned)t; q + 1 < kf; q++) fs[q] = std::move(fs[q + 1]);
+      std::memcpy(g, h, sizeof h);
       kf--;
     }
     Sym out;
     bool all_imm = true, uni = true;
-    for (auto& x : fs) {
-      all_imm &= x.is_const;
-      uni &= x.uni;
+    for (unsigned q = 0; q < kf; q++) {
+      all_imm &= fs[q].is_const;
+      uni &= fs[q].uni;
     }
     if (kf == 0) {
       out.c = g[0] ? 0xFFFFFFFFu : 0u;
@@ -313,8 +314,8 @@ class SrcGen {
         out.name = name;
         *call = c3;
         CallInfo ci;
-        for (auto& x : fs)
-          if (!x.is_const) ci.deps.push_back(x.name);
+        for (unsigned q = 0; q < kf; q++)
+          if (!fs[q].is_const) ci.deps.push_back(fs[q].name);
         ci.level = copy >= 0 ? unroll_lv : lu.level;
         ci.uni = uni;
         calls_[name] = std::move(ci);
@@ -327,7 +328,7 @@ class SrcGen {
     const size_t n = p.luts.size();
     sym.assign(n, {});
     code.assign(n, {});
-    std::map<std::string, std::string> cse;
+    CseMap cse;
     int cur = -100;
     for (size_t i = 0; i < n; i++) {
       const Lut& lu = p.luts[i];
@@ -353,7 +354,7 @@ class SrcGen {
     usym.assign((size_t)copies, {});
     ustmt.assign((size_t)copies, {});
     ustmt_name.assign((size_t)copies, {});
-    std::map<std::string, std::string> cse;   // shared: the copies are one straight-line block
+    CseMap cse;   // shared: the copies are one straight-line block
     for (int c = 0; c < copies; c++) {
       usym[(size_t)c].assign((size_t)(li.lut_end - li.lut_begin), std::vector<Sym>((size_t)nreg));
       for (int i = li.lut_begin; i < li.lut_end; i++) {
