@@ -73,6 +73,30 @@ def test_option_validation():
         with pytest.raises(L.FbgError) as ei:
             p.set_option(opt, bad)
         assert ei.value.status == L.FBG_EINVAL
+    # item pieces are a scheduling choice: accepted as on/off, no rebuild
+    for v in (1, 0, 5):
+        p.set_option(L.OPT_SPLIT_ITEMS, v)
+
+
+@pytest.mark.parametrize("opts", [
+    {}, {L.OPT_UNIT_BITS: 2}, {L.OPT_UNIT_BITS: 0, L.OPT_LOOP_LEVEL_BITS: 3},
+    {L.OPT_UNIT_BITS: 2, L.OPT_LOOP_LEVEL_BITS: 5}, {L.OPT_UNIT_BITS: 2, L.OPT_LOOP_LEVEL_BITS: 16},
+    {L.OPT_UNIT_BITS: 6}, {L.OPT_UNIT_BITS: 4, L.OPT_LOOP_LEVEL_BITS: 2, L.OPT_INNER_BITS: 1}])
+def test_piece_bits_follow_the_loop_levels(opts):
+    """An item can be split over the first loop level only when that level
+    is a runtime loop: there is one, and it is not the unrolled innermost
+    level (at most 5 bits, emitted as straight-line copies); pieces go up to
+    16 (4 bits)."""
+    from paper_1310_6978_b300 import workloads as W
+    p = F.compile(W.posets(5).text, 5)
+    for k, v in opts.items():
+        p.set_option(k, v)
+    lay = p.debug_dump(0)["layout"]
+    lb = lay["loop_bits"]
+    runtime_first = len(lb) >= 2 or (len(lb) == 1 and lb[0] > 5)
+    assert lay["split_bits"] == (min(lb[0], 4) if runtime_first else 0), lay
+    src = p.source(0)
+    assert ("for (fbg_u32 i2 = lo2; i2 < hi2; ++i2)" in src) == runtime_first
 
 
 def test_batch_specialised_kernels_compile_without_a_device():
