@@ -218,3 +218,50 @@ def test_n36_counts(name):
     r = F.compile(wl.text, wl.k).set_option(L.OPT_PRUNE, 0)
     assert r.count() == cnt
     _check_units(p, th, np.random.default_rng(5), samples=2)
+
+
+def test_n36_counts_in_the_timed_configuration():
+    """The three n = 36 counts exactly as the benchmark times them: the
+    committed tuned shapes, the longest-first item order, the three counts
+    on side streams captured once as a CUDA graph and replayed; each replay
+    equals the independent counters (backtracking over relations and graphs,
+    brute force over the 720 permutations), and sampled per-unit counts of
+    the tuned layouts equal the oracle's counts over the same subcubes."""
+    from paper_1310_6978_b300 import tuning
+    wls = [W.TRANSITIVE6, W.TRIFREE9, W.AUT6]
+    want = [C.count_transitive_backtrack(6), C.count_triangle_free_backtrack(9),
+            C.count_automorphisms(W.random_graph_bits(6, 3), 6)]
+    stream = torch.cuda.Stream()
+    cache = tuning.load()
+    progs = [F.compile(w.text, w.k) for w in wls]
+    for p in progs:
+        assert tuning.ensure(p, 0, cache, tune=False, stream=stream) is not None
+        p.schedule_units(stream=stream)
+    out = torch.zeros(len(progs), dtype=torch.int64, device="cuda")
+    side = [torch.cuda.Stream() for _ in progs]
+    fork = torch.cuda.Event()
+    joins = [torch.cuda.Event() for _ in progs]
+
+    def step(on):
+        fork.record(on)
+        for i, p in enumerate(progs):
+            side[i].wait_event(fork)
+            p.count_async(out[i:i + 1], stream=side[i])
+            joins[i].record(side[i])
+            on.wait_event(joins[i])
+
+    step(stream)
+    stream.synchronize()
+    assert out.cpu().tolist() == want
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        step(stream)
+    for _ in range(5):
+        out.zero_()
+        with torch.cuda.stream(stream):
+            graph.replay()
+        stream.synchronize()
+        assert out.cpu().tolist() == want
+    rng = np.random.default_rng(11)
+    for w, p in zip(wls, progs):
+        _check_units(p, oracle.Theory(w.text, w.k), rng, samples=2)
