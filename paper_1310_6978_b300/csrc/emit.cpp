@@ -94,7 +94,8 @@ class SrcGen {
   int unroll_bits = 0, unroll_base = 0;
   std::vector<std::vector<Sym>> sym;                  // [lut][s], levels other than unroll_lv
   std::vector<std::vector<std::string>> code;         // real lop3 calls of those
-  std::vector<std::vector<std::vector<Sym>>> usym;    // [copy][lut - first][s]
+  std::vector<Sym> usym;   // [(copy * luts of the level + lut - first) * nreg + s]
+  size_t ulevel_luts = 0;
   std::vector<std::vector<std::string>> ustmt;        // [copy] statements
   std::vector<std::vector<std::string>> ustmt_name;   // [copy] the value each statement defines
   // every lop3 call emitted by folding: its name, the values it reads, its
@@ -210,7 +211,7 @@ class SrcGen {
     } else {
       size_t r = (size_t)((uint32_t)s & p.luts[(size_t)v.id].rmask);
       if (copy >= 0 && in_unrolled(v.id))
-        x = usym[(size_t)copy][(size_t)(v.id - p.levels[(size_t)unroll_lv].lut_begin)][r];
+        x = usym[((size_t)copy * ulevel_luts + (size_t)(v.id - p.levels[(size_t)unroll_lv].lut_begin)) * (size_t)nreg + r];
       else
         x = sym[(size_t)v.id][r];
     }
@@ -351,19 +352,19 @@ class SrcGen {
   void fold_unrolled() {
     const LevelInfo& li = p.levels[(size_t)unroll_lv];
     const int copies = 1 << unroll_bits;
-    usym.assign((size_t)copies, {});
+    ulevel_luts = (size_t)(li.lut_end - li.lut_begin);
+    usym.assign((size_t)copies * ulevel_luts * (size_t)nreg, Sym{});
     ustmt.assign((size_t)copies, {});
     ustmt_name.assign((size_t)copies, {});
     CseMap cse;   // shared: the copies are one straight-line block
     for (int c = 0; c < copies; c++) {
-      usym[(size_t)c].assign((size_t)(li.lut_end - li.lut_begin), std::vector<Sym>((size_t)nreg));
       for (int i = li.lut_begin; i < li.lut_end; i++) {
         const Lut& lu = p.luts[(size_t)i];
         for (int s = 0; s < nreg; s++) {
           if (((uint32_t)s & lu.rmask) != (uint32_t)s) continue;
           std::string call, nm = "L" + std::to_string(i) + "_" + std::to_string(s) + "_u" + std::to_string(c);
           Sym v = fold_one(lu, s, c, nm, cse, &call);
-          usym[(size_t)c][(size_t)(i - li.lut_begin)][(size_t)s] = v;
+          usym[((size_t)c * ulevel_luts + (size_t)(i - li.lut_begin)) * (size_t)nreg + (size_t)s] = v;
           if (!call.empty()) {
             ustmt[(size_t)c].push_back("const fbg_u32 " + nm + " = " + call + ";");
             ustmt_name[(size_t)c].push_back(nm);

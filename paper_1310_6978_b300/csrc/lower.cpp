@@ -183,7 +183,20 @@ std::vector<uint8_t> alive_items(const Grounded& g, const Layout& L) {
     need[(size_t)x] = 1;
     for (int c : d.node(x).kids) stack.push_back(c);
   }
+  // values are released after their last needed parent, and each kept
+  // conjunct is folded into the AND as soon as it is known, so only the
+  // live frontier of the DAG is held
+  std::vector<int> users((size_t)d.size(), 0);
+  std::vector<char> kept((size_t)d.size(), 0);
+  for (int c : keep) kept[(size_t)c] = 1;
+  for (int x = 0; x < d.size(); x++)
+    if (need[(size_t)x])
+      for (int c : d.node(x).kids) users[(size_t)c]++;
+  std::vector<uint64_t> all(W, tail);
   std::vector<std::vector<uint64_t>> val((size_t)d.size());
+  auto release = [&](int x) {
+    if (users[(size_t)x] == 0) std::vector<uint64_t>().swap(val[(size_t)x]);
+  };
   for (int x = 0; x < d.size(); x++) {
     if (!need[(size_t)x]) continue;
     const FNode& f = d.node(x);
@@ -214,11 +227,17 @@ std::vector<uint8_t> alive_items(const Grounded& g, const Layout& L) {
         for (size_t w = 0; w < W; w++) out[w] = val[(size_t)f.kids[0]][w] ^ val[(size_t)f.kids[1]][w];
         break;
     }
+    for (int c : f.kids) {
+      users[(size_t)c]--;
+      if (!kept[(size_t)c]) release(c);
+    }
+    if (kept[(size_t)x]) {
+      // the AND of the kept conjuncts, word by word
+      for (size_t w = 0; w < W; w++) all[w] &= out[w];
+      kept[(size_t)x] = 0;
+      release(x);
+    }
   }
-  // the AND of the kept conjuncts, word by word, then one byte per item
-  std::vector<uint64_t> all(W, tail);
-  for (int c : keep)
-    for (size_t w = 0; w < W; w++) all[w] &= val[(size_t)c][w];
   std::vector<uint8_t> alive((size_t)U, 0);
   for (uint64_t u = 0; u < U; u++) alive[(size_t)u] = (uint8_t)((all[(size_t)(u >> 6)] >> (u & 63)) & 1);
   return alive;
