@@ -242,6 +242,13 @@ fbg_status fbg_autotune(fbg_program *prog, void *stream, int mode, int reps, fbg
 /* executed work of the last fbg_count with FBG_OPT_STATS = 1 */
 fbg_status fbg_last_exec_stats(fbg_program *prog, fbg_exec_stats *out);
 
+/* Diagnostics (no counterpart in the paper): host wall time, in seconds,
+ * that this program has spent so far building specialised kernels (layout,
+ * lowering, item pruning, source emission, the kernel cache, uploads; an
+ * NVRTC compile when the cache misses) and inside fbg_count outside those
+ * builds (launch, copy of the count, synchronisation).  FBG_EINVAL on null. */
+fbg_status fbg_debug_host_times(const fbg_program *prog, double *build_s, double *count_s);
+
 /* CUDA source of the specialised kernel (mode 0 count, 1 table); *len
    receives the size; buf may be NULL to query it */
 fbg_status fbg_program_source(fbg_program *prog, int mode, char *buf, size_t *len);

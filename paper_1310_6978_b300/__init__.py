@@ -110,6 +110,13 @@ class Program:
         self._L.check(self._L.lib.fbg_schedule_units(self._h, _stream_ptr(stream)))
         return self
 
+    def debug_host_times(self):
+        """fbg_debug_host_times: (seconds building kernels, seconds in
+        fbg_count outside builds) spent by this program so far."""
+        b, c = ctypes.c_double(), ctypes.c_double()
+        self._L.check(self._L.lib.fbg_debug_host_times(self._h, ctypes.byref(b), ctypes.byref(c)))
+        return b.value, c.value
+
     def debug_item_trace(self, dev_ns, stream=None) -> None:
         """fbg_debug_item_trace: nanoseconds per (unit, warp slice) item."""
         self._L.check(self._L.lib.fbg_debug_item_trace(self._h, _stream_ptr(stream), _ptr(dev_ns), dev_ns.numel()))

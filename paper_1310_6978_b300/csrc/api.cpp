@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -163,9 +164,18 @@ fbg_status upload_items(JitBuild& b, const std::vector<unsigned>& items) {
   return FBG_OK;
 }
 
+fbg_status build_jit_impl(fbg_program* p, int mode);
+
 fbg_status build_jit(fbg_program* p, int mode) {
+  if (p->jb[mode].valid) return FBG_OK;
+  const auto t0 = std::chrono::steady_clock::now();
+  fbg_status s = build_jit_impl(p, mode);
+  p->t_build += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return s;
+}
+
+fbg_status build_jit_impl(fbg_program* p, int mode) {
   JitBuild& b = p->jb[mode];
-  if (b.valid) return FBG_OK;
   try {
     Layout L = make_layout(p->n, jit_params(p), order_for(p, mode == 0));
     b.lp = lower_and_map(p->g, L);
@@ -443,11 +453,14 @@ fbg_status fbg_count(fbg_program* p, void* stream, uint64_t* out_count) {
   if (!p || !out_count) return set_error(FBG_EINVAL, "null argument");
   cudaStream_t st = (cudaStream_t)stream;
   bool jit = false;
+  const auto t0 = std::chrono::steady_clock::now();
+  const double build0 = p->t_build;
   fbg_status s = launch_count(p, st, nullptr, nullptr, &jit);
   if (s != FBG_OK) return s;
   unsigned long long host[kScratchHead];
   CK(cudaMemcpyAsync(host, p->d_scratch, sizeof host, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  p->t_count += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() - (p->t_build - build0);
   *out_count = host[1];
   // executed work
   fbg_exec_stats& es = p->last;
@@ -584,6 +597,13 @@ fbg_status fbg_schedule_units(fbg_program* p, void* stream) {
   std::vector<unsigned> perm(pieces.size());
   for (size_t i = 0; i < pieces.size(); i++) perm[i] = pieces[i].code;
   return upload_items(b, perm);
+}
+
+fbg_status fbg_debug_host_times(const fbg_program* p, double* build_s, double* count_s) {
+  if (!p || !build_s || !count_s) return set_error(FBG_EINVAL, "null argument");
+  *build_s = p->t_build;
+  *count_s = p->t_count;
+  return FBG_OK;
 }
 
 fbg_status fbg_debug_item_trace(fbg_program* p, void* stream, uint64_t* dev_ns, uint64_t nitems) {

@@ -93,6 +93,8 @@ struct fbg_program {
   bool scratch_clean = false;   // counters of self-resetting count launches are zero
   size_t scratch_words = 0;
   fbg_exec_stats last{};
+  // wall time (s) in kernel builds and in fbg_count outside builds (fbg_debug_host_times)
+  double t_build = 0, t_count = 0;
   std::string jit_log;
 
   void invalidate() {

@@ -57,3 +57,18 @@ def test_exec_stats_follow_the_layout(case, prune):
         assert abs(lhs - es.lop3_nominal) <= 1e-9 * es.lop3_nominal
     else:
         assert es.lop3_executed < es.lop3_nominal
+
+
+def test_host_times_split_builds_from_counts():
+    """fbg_debug_host_times: the first count builds the kernel (build time
+    grows), a second count of the same program does not rebuild (build time
+    unchanged, count time grows)."""
+    from paper_1310_6978_b300 import workloads as W
+    p = F.compile(W.posets(5).text, 5)
+    assert p.debug_host_times() == (0.0, 0.0)
+    assert p.count() == 4231
+    b1, c1 = p.debug_host_times()
+    assert b1 > 0 and c1 > 0
+    assert p.count() == 4231
+    b2, c2 = p.debug_host_times()
+    assert b2 == b1 and c2 > c1
