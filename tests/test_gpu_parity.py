@@ -163,16 +163,30 @@ def test_count_async_on_caller_stream():
 
 # ---------------------------------------------------------------- full size --
 
+def _golden(name):
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        rows = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+    return {k: v for k, v in rows}
+
+
 def test_cnf32_table_sampled_and_count():
     """3-CNF, n = 32, m = 136, seed 1: the 512 MiB table in the launch the
-    benchmark times; sampled words against the oracle, popcount = count, and
-    per-unit counts against the oracle on sampled subcubes."""
+    benchmark times; the whole table bit-exact (SHA-256 of its words) and the
+    count equal to the oracle's full 2^32 evaluation (tests/golden/
+    cnf32_seed1.txt, written by tests/golden/make_cnf32.py), sampled words
+    against the oracle, popcount = count, and per-unit counts against the
+    oracle on sampled subcubes."""
+    import hashlib
     wl = W.CNF32
     th = oracle.Theory(wl.text, wl.k)
     p = F.compile(wl.text, wl.k)
     table = torch.empty(p.table_words(), dtype=torch.int64, device="cuda")
     p.truth_table(table)
     torch.cuda.synchronize()
+    gold = _golden("cnf32_seed1.txt")
+    host = table.cpu().numpy().view(np.uint64)
+    assert hashlib.sha256(host.astype("<u8").tobytes()).hexdigest() == gold["sha256"]
+    assert p.count() == int(gold["count"])
     rng = np.random.default_rng(11)
     idx = np.unique(np.concatenate([rng.integers(0, table.numel(), 1500), [0, table.numel() - 1]]))
     words = table[torch.from_numpy(idx).cuda()].cpu().numpy().view(np.uint64)
@@ -184,6 +198,27 @@ def test_cnf32_table_sampled_and_count():
     pop = int(np.bitwise_count(table.cpu().numpy().view(np.uint64)).sum())
     assert pop == p.count()
     _check_units(p, th, rng, samples=3)
+
+
+def test_cnf32_satisfiable_table_bit_exact():
+    """3-CNF, n = 32, m = 136, seed 2 (satisfiable; the benchmark's seed 1 is
+    not, so its table is all zero): the whole 512 MiB table and the count
+    equal the oracle's evaluation of all 2^32 assignments
+    (tests/golden/cnf32_seed2.txt), with the default table and count kernels
+    and with the interpreter's count."""
+    import hashlib
+    wl = W.cnf3(32, 2)
+    gold = _golden("cnf32_seed2.txt")
+    p = F.compile(wl.text, wl.k)
+    table = torch.empty(p.table_words(), dtype=torch.int64, device="cuda")
+    p.truth_table(table)
+    torch.cuda.synchronize()
+    host = table.cpu().numpy().view(np.uint64)
+    assert int(np.bitwise_count(host).sum()) == int(gold["count"])
+    assert hashlib.sha256(host.astype("<u8").tobytes()).hexdigest() == gold["sha256"]
+    assert p.count() == int(gold["count"])
+    q = F.compile(wl.text, wl.k).set_option(L.OPT_ENGINE, L.ENGINE_INTERP)
+    assert q.count() == int(gold["count"])
 
 
 def _check_units(p, th, rng, samples):
