@@ -1,0 +1,48 @@
+"""Host logic of bench.py without a GPU: the clock record that rejects a
+timed run (samples inside the timed window, the median SM clock, throttle
+reasons) from synthetic nvidia-smi lines."""
+import datetime
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+def _line(t, mhz, reasons=("Not Active",) * 4, max_mhz=2032):
+    ts = datetime.datetime.fromtimestamp(t).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+    return ", ".join([ts, "0", str(mhz), str(max_mhz), "900.0", "0x0", *reasons])
+
+
+def _sampler(lines, t0, t1):
+    s = bench.ClockSampler(0)
+    s.lines = list(lines)
+    s.t0, s.t1 = t0, t1
+    return s
+
+
+def test_samples_inside_the_window_give_median_clock_and_reasons():
+    t0 = 1_700_000_000.0
+    lines = [_line(t0 - 5, 345)]                              # idle, before the window
+    lines += [_line(t0 + 0.1 * i, mhz) for i, mhz in enumerate([2032, 2010, 2032, 1995, 2032])]
+    lines += [_line(t0 + 0.25, 2032, ("Not Active", "Not Active", "Not Active", "Active"))]
+    lines += [_line(t0 + 9, 345, ("Active", "Not Active", "Not Active", "Not Active"))]   # after the window
+    lines += ["garbage", "2024/01/01, short"]
+    s = _sampler(lines, t0, t0 + 0.5).summary()
+    assert s["samples"] == 6 and s["sm_mhz"] == 2032.0 and s["sm_max_mhz"] == 2032.0
+    assert s["reasons"] == ["sw_power_cap"] and s["nearest_outside_window"] is False
+    assert abs(s["window_s"] - 0.5) < 1e-9
+
+
+def test_a_window_shorter_than_the_sampling_period_uses_the_nearest_samples():
+    t0 = 1_700_000_000.0
+    lines = [_line(t0 - 1.0, 2032), _line(t0 + 0.3, 1900, ("Not Active", "Active", "Not Active", "Not Active")),
+             _line(t0 + 2.0, 2032), _line(t0 + 5.0, 345)]
+    s = _sampler(lines, t0 + 0.05, t0 + 0.06).summary()
+    assert s["nearest_outside_window"] is True and s["samples"] == 3
+    assert "hw_thermal_slowdown" in s["reasons"]
+
+
+def test_no_samples_at_all():
+    s = _sampler([], 1.0, 2.0).summary()
+    assert s["sm_mhz"] is None and s["samples"] == 0 and s["reasons"] == []
