@@ -46,3 +46,36 @@ def test_a_window_shorter_than_the_sampling_period_uses_the_nearest_samples():
 def test_no_samples_at_all():
     s = _sampler([], 1.0, 2.0).summary()
     assert s["sm_mhz"] is None and s["samples"] == 0 and s["reasons"] == []
+
+
+def _run_bench(args, env_extra=None, timeout=300):
+    import json
+    import subprocess
+    env = dict(os.environ)
+    env.update(env_extra or {})
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), *args], cwd=root, env=env,
+                       capture_output=True, text=True, timeout=timeout)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    return [json.loads(ln) for ln in lines]
+
+
+def test_reference_arm_prints_one_contract_line():
+    """bench.py --impl reference times the oracle on the host (no GPU): one
+    JSON line with the metric, its own e2e and cpu_baseline, the sample
+    sized from the time budget."""
+    out = _run_bench(["--impl", "reference", "--steps", "3", "--warmup", "3", "--ref-total-seconds", "3"])
+    assert len(out) == 1
+    d = out[0]
+    assert d["impl"] == "reference" and d["metric"] == "model-count throughput at n=36 (Gassign/s)"
+    assert d["unit"] == "Gassign/s" and d["higher_is_better"] is True and d["steps"] == 3 and d["warmup"] == 3
+    assert d["value"] > 0 and d["e2e"]["value"] == d["value"] and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["cores"] >= 1
+    assert "2^" in d["cpu_baseline"]["sample"]
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    out = _run_bench(["--impl", "reference", "--steps", "3", "--warmup", "3", "--ref-total-seconds", "2"],
+                     {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert out == []
