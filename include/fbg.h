@@ -259,6 +259,11 @@ fbg_status fbg_program_source(fbg_program *prog, int mode, char *buf, size_t *le
  * LUTs with levels); 2 / 3: interpreter bytecode of the count / identity
  * layout.  Used to check the compiler on a machine without a GPU; it does
  * not evaluate anything.  *len receives the size; buf may be NULL.
+ * For which = 0 the layout also gives "split_bits" (the largest s of the
+ * item pieces the count kernel takes, 0 when none), and the object gives
+ * "alive_items" (the (unit, warp slice) items that can hold models, when
+ * the build-time pruning removes any) and, once the count kernel is built,
+ * "item_list_entries" (entries of the item list full-range counts hand out).
  */
 fbg_status fbg_debug_dump(fbg_program *prog, int which, char *buf, size_t *len);
 
