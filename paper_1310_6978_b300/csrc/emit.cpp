@@ -228,7 +228,16 @@ class SrcGen {
   // fold one LUT register; *call receives the lop3 call when one is needed
   using CseMap = std::unordered_map<std::string, std::string>;
 
-  Sym fold_one(const Lut& lu, int s, int copy, const std::string& name, CseMap& cse, std::string* call) {
+  // the register name of LUT i, register s (copy c of the unrolled level, or c < 0)
+  static std::string fold_name(int i, int s, int c) {
+    std::string nm = "L" + std::to_string(i) + "_" + std::to_string(s);
+    if (c >= 0) nm += "_u" + std::to_string(c);
+    return nm;
+  }
+
+  // fold register s of LUT i; the name is made only when a new lop3 is needed
+  Sym fold_one(int i, int s, int copy, CseMap& cse, std::string* call) {
+    const Lut& lu = p.luts[(size_t)i];
     call->clear();
     Sym in[3];
     for (int k = 0; k < 3; k++) in[k] = operand_sym(lu.in[k], s, copy);
@@ -303,14 +312,24 @@ class SrcGen {
         for (unsigned q = 0; q < kf; q++) a |= ab[q] << q;
         tt |= g[a] << m;
       }
-      std::string c3 = "fbg_lop3<" + std::to_string(tt) + ">(" + expr(fs[0]) + ", " + expr(fs[kf > 1 ? 1 : 0]) + ", " +
-                       expr(fs[kf > 2 ? 2 : 0]) + ")";
+      std::string c3;
+      c3.reserve(64);
+      c3 += "fbg_lop3<";
+      c3 += std::to_string(tt);
+      c3 += ">(";
+      c3 += expr(fs[0]);
+      c3 += ", ";
+      c3 += expr(fs[kf > 1 ? 1 : 0]);
+      c3 += ", ";
+      c3 += expr(fs[kf > 2 ? 2 : 0]);
+      c3 += ")";
       out.is_const = false;
       out.uni = uni;
       auto it = cse.find(c3);
       if (it != cse.end()) {
         out.name = it->second;
       } else {
+        const std::string name = fold_name(i, s, copy);
         cse.emplace(c3, name);
         out.name = name;
         *call = c3;
@@ -343,7 +362,7 @@ class SrcGen {
       for (int s = 0; s < nreg; s++) {
         if (((uint32_t)s & lu.rmask) != (uint32_t)s) continue;
         std::string call;
-        sym[i][(size_t)s] = fold_one(lu, s, -1, "L" + std::to_string(i) + "_" + std::to_string(s), cse, &call);
+        sym[i][(size_t)s] = fold_one((int)i, s, -1, cse, &call);
         if (!call.empty()) code[i][(size_t)s] = call;
       }
     }
@@ -362,12 +381,12 @@ class SrcGen {
         const Lut& lu = p.luts[(size_t)i];
         for (int s = 0; s < nreg; s++) {
           if (((uint32_t)s & lu.rmask) != (uint32_t)s) continue;
-          std::string call, nm = "L" + std::to_string(i) + "_" + std::to_string(s) + "_u" + std::to_string(c);
-          Sym v = fold_one(lu, s, c, nm, cse, &call);
+          std::string call;
+          Sym v = fold_one(i, s, c, cse, &call);
           usym[((size_t)c * ulevel_luts + (size_t)(i - li.lut_begin)) * (size_t)nreg + (size_t)s] = v;
           if (!call.empty()) {
-            ustmt[(size_t)c].push_back("const fbg_u32 " + nm + " = " + call + ";");
-            ustmt_name[(size_t)c].push_back(nm);
+            ustmt[(size_t)c].push_back("const fbg_u32 " + v.name + " = " + call + ";");
+            ustmt_name[(size_t)c].push_back(v.name);
           }
         }
       }
