@@ -26,19 +26,43 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-SM_COUNT = 148
-LOP3_LANES_PER_CLK_SM = 64      # measured issue rate of lop3.b32 per SM per clock (sm_103a)
+LOP3_LANES_PER_CLK_SM = 64      # lop3.b32 issue rate per SM per clock on sm_103a (fbg_probe_lop3_rate: 0.99 of it)
+NOMINAL_SM_MHZ = 2032.0         # maximum SM clock of the part, when nvidia-smi gives none
+
+# Figures from one ncu capture of the count and table kernels, valid only for
+# the kernel sources they were taken from: `sources_sha` is
+# kernel_fingerprint() of the captured build (the NVRTC sources of the three
+# count kernels in their tuned shapes, or of the table kernel).  When the
+# running build's fingerprint differs, the figures are reported as null with
+# the reason.
+#   count: DRAM bytes (read + write) of the three count launches of a step, and
+#          their vector-pipe LOP3 warp instructions (sass__inst_executed_per_opcode:
+#          the formulas' LUTs and the popcount's full adders, not the ULOP3 of
+#          the uniform datapath)
+#   table: DRAM bytes of one truth-table launch
+NCU_COUNT = {"sources_sha": None, "traffic_step": None, "vector_lop3_step": None}
+NCU_TABLE = {"sources_sha": None, "traffic_launch": None}
 
 
-# DRAM bytes (read + write) per launch from one ncu capture of the current
-# kernels (profiles/fbg_jit_count_n36.md, profiles/fbg_jit_table_cnf32.md):
-# the three count launches of a step, and one truth-table launch.
-TRAFFIC_COUNT_STEP = 48_384 + 103_936 + 67_328
-# Vector-pipe LOP3 warp instructions of the three count launches of a step in
-# the same capture (sass__inst_executed_per_opcode; the formulas' LUTs and the
-# full adders of the popcount, not the ULOP3 of the uniform datapath).
-NCU_VECTOR_LOP3_STEP = 9_460_222 + 21_021_412 + 32_735
-TRAFFIC_TABLE_LAUNCH = 478_839_808 + 70_400
+def kernel_fingerprint(progs, mode: int = 0) -> str:
+    """SHA-256 (16 hex digits) of the programs' generated kernel sources in
+    their current shapes: it changes whenever the emitter, a shape or the
+    device header changes."""
+    import hashlib
+    h = hashlib.sha256()
+    for p in progs:
+        h.update(p.source(mode).encode())
+        h.update(b"\0")
+    return h.hexdigest()[:16]
+
+
+def ncu_figures(table: dict, fingerprint: str, keys) -> dict:
+    """The captured figures when they belong to this build, else nulls and why."""
+    if table.get("sources_sha") and table["sources_sha"] == fingerprint:
+        return {k: table[k] for k in keys} | {"stale": False}
+    why = ("no capture recorded" if not table.get("sources_sha") else
+           f"captured on sources {table['sources_sha']}, running {fingerprint}")
+    return {k: None for k in keys} | {"stale": True, "reason": why}
 
 
 def load_peaks():
@@ -303,11 +327,14 @@ def run_table(args, torch, F, L, peaks):
     assert pop == cnt
     nbytes = table.numel() * 8
     peak = peaks.get("hbm_gbs")
+    ncu = ncu_figures(NCU_TABLE, kernel_fingerprint([p], 1), ["traffic_launch"])
     return {"workload": "3-CNF n=32 m=136 seed 1 (unsatisfiable: an all-zero table), full truth table", "shape": shape, "value": (1 << 32) / t / 1e9, "unit": "Gassign/s",
             "ms": t * 1e3, "bytes_written": nbytes, "count": cnt, "popcount_equals_count": True,
             "roofline": {"bound": "hbm", "achieved": nbytes / t / 1e9, "peak": peak, "unit": "GB/s",
-                         "frac": (nbytes / t / 1e9) / peak if peak else None, "traffic": TRAFFIC_TABLE_LAUNCH,
-                         "basis": "algorithmic bytes = 2^32/8 written per launch; peak = measured copy GB/s"}}
+                         "frac": (nbytes / t / 1e9) / peak if peak else None, "traffic": ncu["traffic_launch"],
+                         "traffic_capture": ncu,
+                         "basis": "algorithmic bytes = 2^32/8 written per launch; peak = measured copy GB/s "
+                                  "(MEASURED_PEAKS.json hbm_gbs)"}}
 
 
 def run_batched(args, torch, F, L):
@@ -551,7 +578,15 @@ def run_ours(args, rank, world):
     kern_s = sum(step_ms) / args.steps / 1e3   # the three concurrent count launches of a step
     lop3_probe = F.probe_lop3_rate(stream)      # independent lop3 chains: the measured roof
     clocks = clk.summary()
-    peak_lop3 = SM_COUNT * LOP3_LANES_PER_CLK_SM * 2032e6
+    # the integer-logic roof of this GPU: its SM count x the lop3.b32 lanes per
+    # SM and clock x the median SM clock sampled in the timed window (and, for
+    # comparison, x the maximum SM clock)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = clocks.get("sm_max_mhz") or load_peaks().get("sm_max_mhz") or NOMINAL_SM_MHZ
+    run_mhz = clocks.get("sm_mhz") or max_mhz
+    peak_lop3 = sms * LOP3_LANES_PER_CLK_SM * run_mhz * 1e6
+    peak_lop3_max = sms * LOP3_LANES_PER_CLK_SM * max_mhz * 1e6
+    ncu = ncu_figures(NCU_COUNT, kernel_fingerprint(progs, 0), ["traffic_step", "vector_lop3_step"])
 
     # the paper's brute-force evaluation (every word), same kernels without pruning
     brute = {}
@@ -601,16 +636,22 @@ def run_ours(args, rank, world):
                    "flush_l2": True, "parallelism": f"replicas x{world}", "counts": expected,
                    "shapes": shapes},
         "roofline": {"bound": "alu", "achieved": executed / kern_s / 1e12, "peak": peak_lop3 / 1e12,
-                     "unit": "Tlop3/s", "frac": executed / kern_s / peak_lop3, "traffic": TRAFFIC_COUNT_STEP,
+                     "unit": "Tlop3/s", "frac": executed / kern_s / peak_lop3, "traffic": ncu["traffic_step"],
+                     "frac_at_max_clock": executed / kern_s / peak_lop3_max,
+                     "peak_basis": {"sms": sms, "lop3_lanes_per_clk_sm": LOP3_LANES_PER_CLK_SM,
+                                    "sm_mhz": run_mhz, "sm_max_mhz": max_mhz,
+                                    "clock": "median SM clock sampled in the timed window" if clocks.get("sm_mhz")
+                                             else "no clock sample: maximum SM clock"},
                      "basis": "executed lane-varying lop3.b32 lane-ops of the step's three concurrent "
                               "fbg_jit_count launches (in-kernel level counters, untimed run) / CUDA-event step "
-                              "time on the launching stream; peak = 148 SM x 64 lanes/clk x 2032 MHz; lop3 whose "
-                              "inputs are all warp-uniform (constants, unit letters, loop counters: the uniform datapath) are not counted",
+                              "time on the launching stream; lop3 whose inputs are all warp-uniform (constants, "
+                              "unit letters, loop counters: the uniform datapath) are not counted",
                      "uniform_lop3_warp_ops_per_step": uniform,
-                     "ncu_cross_check": {
-                         "vector_lop3_warp_instructions_per_step": NCU_VECTOR_LOP3_STEP,
-                         "achieved": NCU_VECTOR_LOP3_STEP * 32 / kern_s / 1e12,
-                         "frac": NCU_VECTOR_LOP3_STEP * 32 / kern_s / peak_lop3,
+                     "ncu_capture": ncu,
+                     "ncu_cross_check": None if ncu["stale"] else {
+                         "vector_lop3_warp_instructions_per_step": ncu["vector_lop3_step"],
+                         "achieved": ncu["vector_lop3_step"] * 32 / kern_s / 1e12,
+                         "frac": ncu["vector_lop3_step"] * 32 / kern_s / peak_lop3,
                          "basis": "every LOP3 the three launches issued on the vector ALU pipe (ncu count of the "
                                   "same kernels and shapes, full adders included) / CUDA-event step time"}},
         "nominal_lop3_ratio": executed / nominal if nominal else None,

@@ -57,6 +57,8 @@ def _load():
             lib.oracle_count_cube.restype = u64
             lib.oracle_count_cube_par.argtypes = [vp, u64, u64, ctypes.c_int]
             lib.oracle_count_cube_par.restype = u64
+            lib.oracle_cube_size.argtypes = [ctypes.c_int]
+            lib.oracle_cube_size.restype = u64
             lib.oracle_count_par.argtypes = [vp, u64, u64, ctypes.c_int]
             lib.oracle_count_par.restype = u64
             lib.oracle_max_threads.restype = ctypes.c_int
@@ -125,15 +127,28 @@ class Theory:
                                buf.ctypes.data_as(ctypes.c_void_p), cap, ctypes.byref(tot))
         return buf[: min(cap, tot.value)].copy(), tot.value
 
+    def _cube_checked(self, mask: int, r: int) -> int:
+        if r == (1 << 64) - 1 and self.n - bin(mask & ((1 << self.n) - 1)).count("1") >= 64:
+            raise ValueError("a subcube with 64 free variables has a count beyond 64 bits")
+        return r
+
     def count_cube(self, mask: int, vals: int) -> int:
         """Models with the variables of ``mask`` fixed to the bits of ``vals``."""
-        return self._lib.oracle_count_cube(self._h, mask, vals)
+        return self._cube_checked(mask, self._lib.oracle_count_cube(self._h, mask, vals))
 
     def count_cube_par(self, mask: int, vals: int, threads: int = 0) -> int:
-        return self._lib.oracle_count_cube_par(self._h, mask, vals, threads)
+        """count_cube with the subcube's points split across threads."""
+        return self._cube_checked(mask, self._lib.oracle_count_cube_par(self._h, mask, vals, threads))
 
     def count_par(self, lo: int, hi: int, threads: int = 0) -> int:
         return self._lib.oracle_count_par(self._h, lo, hi, threads)
+
+
+def cube_size(nf: int):
+    """Points of a subcube with ``nf`` free variables (the loop bound both
+    cube counters use), or None where the count need not fit 64 bits."""
+    r = _load().oracle_cube_size(nf)
+    return None if r == (1 << 64) - 1 else r
 
 
 def max_threads() -> int:

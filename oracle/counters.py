@@ -47,8 +47,10 @@ def _transitive_mask(rel: np.ndarray) -> np.ndarray:
     return ok
 
 
-def count_relations(k: int, kind: str) -> int:
-    """Brute force over all relations on k points (k <= 4)."""
+def relation_models(k: int, kind: str) -> np.ndarray:
+    """Brute force over all relations on k points (k <= 4): a boolean array
+    over the 2^(k^2) relations, indexed as in _all_relations, that is true
+    for the relations of the given kind."""
     if k > 4:
         raise ValueError("brute force over relations only for k <= 4")
     rel = _all_relations(k)
@@ -62,14 +64,19 @@ def count_relations(k: int, kind: str) -> int:
                 sym &= rel[:, i, j] == rel[:, j, i]
                 anti &= ~(rel[:, i, j] & rel[:, j, i])
     if kind == "poset":
-        return int(np.count_nonzero(diag.all(axis=1) & anti & trans))
+        return diag.all(axis=1) & anti & trans
     if kind == "equiv":
-        return int(np.count_nonzero(diag.all(axis=1) & sym & trans))
+        return diag.all(axis=1) & sym & trans
     if kind == "transitive":
-        return int(np.count_nonzero(trans))
+        return trans
     if kind == "graph":
-        return int(np.count_nonzero((~diag).all(axis=1) & sym))
+        return (~diag).all(axis=1) & sym
     raise ValueError(kind)
+
+
+def count_relations(k: int, kind: str) -> int:
+    """Brute force over all relations on k points (k <= 4)."""
+    return int(np.count_nonzero(relation_models(k, kind)))
 
 
 def count_posets_backtrack(k: int) -> int:
@@ -113,8 +120,10 @@ def count_posets_backtrack(k: int) -> int:
     return rec(0)
 
 
-def count_triangle_free(k: int) -> int:
-    """Brute force over all 2^C(k,2) graphs (k <= 7), vectorised."""
+def triangle_free_models(k: int) -> np.ndarray:
+    """Brute force over all 2^C(k,2) graphs (k <= 7), vectorised: a boolean
+    array indexed by the graph whose bit t is the t-th pair a<b in
+    lexicographic order, true for the triangle-free graphs."""
     pairs = [(a, b) for a in range(k) for b in range(a + 1, k)]
     m = len(pairs)
     if m > 21:
@@ -125,7 +134,19 @@ def count_triangle_free(k: int) -> int:
     for a, b, c in itertools.combinations(range(k), 3):
         bits = np.uint64((1 << pos[(a, b)]) | (1 << pos[(b, c)]) | (1 << pos[(a, c)]))
         ok &= (idx & bits) != bits
-    return int(np.count_nonzero(ok))
+    return ok
+
+
+def count_triangle_free(k: int) -> int:
+    """Brute force over all 2^C(k,2) graphs (k <= 7)."""
+    return int(np.count_nonzero(triangle_free_models(k)))
+
+
+def count_in_cube(models: np.ndarray, mask: int, vals: int) -> int:
+    """Structures of a brute-force model array whose index has the bits of
+    ``mask`` equal to those of ``vals`` (a subcube of the index space)."""
+    idx = np.arange(models.shape[0], dtype=np.uint64)
+    return int(np.count_nonzero(models & ((idx & np.uint64(mask)) == np.uint64(vals & mask))))
 
 
 def count_automorphisms(adj_bits: str, k: int) -> int:

@@ -914,38 +914,57 @@ void oracle_range(const oracle_prog *p, uint64_t lo, uint64_t hi, uint64_t *coun
   if (nmodels) *nmodels = cnt;
 }
 
-/* models with the variables in `mask` fixed to the bits of `vals`
-   (a subcube of 2^n): loop over the free variables' values */
-uint64_t oracle_count_cube(const oracle_prog *p, uint64_t mask, uint64_t vals) {
-  int freev[64], nf = 0;
+/* Subcube of 2^n: the variables in `mask` fixed to the bits of `vals`, the
+   others free.  The free variables, lowest first, go to freev; the return
+   value is their number nf.  The subcube has 2^nf assignments; a count over
+   it fits a u64 only for nf <= 63, so the counters below refuse nf = 64. */
+static int cube_free_vars(const oracle_prog *p, uint64_t mask, int freev[64]) {
+  int nf = 0;
   for (int i = 0; i < p->nvars; i++)
     if (!((mask >> i) & 1)) freev[nf++] = i;
+  return nf;
+}
+
+/* the assignment integer of point t (bit b of t = the b-th free variable) */
+static uint64_t cube_point(uint64_t mask, uint64_t vals, const int *freev, int nf, uint64_t t) {
+  uint64_t j = vals & mask;
+  for (int b = 0; b < nf; b++) j |= ((t >> b) & 1ull) << freev[b];
+  return j;
+}
+
+/* Number of assignments of a subcube with nf free variables, or
+   ORACLE_CUBE_TOO_BIG (all ones) for nf = 64, whose count need not fit. */
+uint64_t oracle_cube_size(int nf) {
+  if (nf < 0 || nf > 63) return ~0ull;
+  return 1ull << nf;
+}
+
+/* models with the variables in `mask` fixed to the bits of `vals`: the
+   definition (Prop. 2.2) restricted to a subcube, by a loop over the free
+   variables' values.  Returns all ones when 64 variables are free. */
+uint64_t oracle_count_cube(const oracle_prog *p, uint64_t mask, uint64_t vals) {
+  int freev[64];
+  const int nf = cube_free_vars(p, mask, freev);
+  const uint64_t total = oracle_cube_size(nf);
+  if (total == ~0ull) return ~0ull;
   uint64_t cnt = 0;
-  uint64_t total = nf >= 64 ? 0 : (1ull << nf);
-  for (uint64_t t = 0; t < total; t++) {
-    uint64_t j = vals & mask;
-    for (int b = 0; b < nf; b++) j |= ((t >> b) & 1ull) << freev[b];
-    cnt += (uint64_t)oracle_eval(p, j);
-  }
+  for (uint64_t t = 0; t < total; t++) cnt += (uint64_t)oracle_eval(p, cube_point(mask, vals, freev, nf, t));
   return cnt;
 }
 
-/* count_cube with the free assignments split across threads (same arithmetic) */
+/* count_cube with the free assignments split statically across threads:
+   the same subcube, the same points, the same refusal at 64 free variables */
 uint64_t oracle_count_cube_par(const oracle_prog *p, uint64_t mask, uint64_t vals, int nthreads) {
-  int freev[64], nf = 0;
-  for (int i = 0; i < p->nvars; i++)
-    if (!((mask >> i) & 1)) freev[nf++] = i;
+  int freev[64];
+  const int nf = cube_free_vars(p, mask, freev);
+  const uint64_t total = oracle_cube_size(nf);
+  if (total == ~0ull) return ~0ull;
   uint64_t cnt = 0;
-  long long total = nf >= 63 ? 0 : (1ll << nf);
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for reduction(+ : cnt) schedule(static)
 #endif
-  for (long long t = 0; t < total; t++) {
-    uint64_t j = vals & mask;
-    for (int b = 0; b < nf; b++) j |= (((uint64_t)t >> b) & 1ull) << freev[b];
-    cnt += (uint64_t)oracle_eval(p, j);
-  }
+  for (uint64_t t = 0; t < total; t++) cnt += (uint64_t)oracle_eval(p, cube_point(mask, vals, freev, nf, t));
   (void)nthreads;
   return cnt;
 }

@@ -11,7 +11,16 @@ from __future__ import annotations
 import ctypes
 import json
 
-__all__ = ["compile", "Program", "Batch", "Server", "FbgError"]
+__all__ = ["compile", "Program", "Batch", "Server", "FbgError", "read_counts"]
+
+MASK64 = (1 << 64) - 1
+
+
+def read_counts(dev_words) -> "list[int]":
+    """The unsigned 64-bit counts that ``count_async`` (or ``count_units``)
+    wrote into a torch.int64 tensor, as Python ints: the tensor's elements are
+    read as bit patterns, so a count of 2^63 (n = 63) is not negative."""
+    return [int(v) & MASK64 for v in dev_words.detach().reshape(-1).cpu().tolist()]
 
 
 def _L():
@@ -81,6 +90,9 @@ class Program:
         return out.value
 
     def count_async(self, dev_out, stream=None) -> None:
+        """fbg_count_async: the count into ``dev_out`` (one 64-bit device
+        element, e.g. a torch.int64 tensor) without waiting; read it back
+        with ``read_counts`` (an unsigned 64-bit value)."""
         self._L.check(self._L.lib.fbg_count_async(self._h, _stream_ptr(stream), _ptr(dev_out)))
 
     def count_noalloc(self, dev_out, stream=None) -> None:

@@ -31,15 +31,22 @@ fbg_status cuda_error(cudaError_t e, const char* where) {
                    std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// SM count of the current device, cached per device (up to 64 devices)
 int device_sms() {
-  static int sms = 0;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  });
+  static std::mutex mu;
+  static int sms_of[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const bool cached = dev >= 0 && dev < 64;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (cached && sms_of[dev] > 0) return sms_of[dev];
+  }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0) sms = 1;
+  std::lock_guard<std::mutex> lock(mu);
+  if (cached) sms_of[dev] = sms;
   return sms;
 }
 
@@ -261,6 +268,22 @@ fbg_status launch_count(fbg_program* p, cudaStream_t st, unsigned long long* dev
   s = ensure_scratch(p, words);
   if (s != FBG_OK) return s;
   if (!dev_count) dev_count = p->d_scratch + 1;
+  if (p->g.root == 0 || p->g.root == 1) {
+    // the Reduction left a constant: every assignment of a unit is a model
+    // (true) or none is (false), so the counts are written without an
+    // evaluation (2^n models for a tautology, up to 2^63)
+    const Layout& L = jit ? p->jb[0].lp.layout : p->ib[0].lp.layout;
+    const uint64_t nunits = 1ull << L.unit_bits;
+    const uint64_t e = std::min<uint64_t>(uend, nunits);
+    if (ubegin > e) return set_error(FBG_EINVAL, "empty or inverted unit range");
+    const uint64_t per_unit = p->g.root == 1 ? (1ull << (p->n - L.unit_bits)) : 0ull;
+    CK(cudaMemsetAsync(p->d_scratch, 0, kScratchHead * 8, st));
+    p->scratch_clean = true;
+    CK(launch_fill_u64(dev_count, 1, (e - ubegin) * per_unit, st));
+    if (unit_counts) CK(launch_fill_u64(unit_counts, e - ubegin, per_unit, st));
+    *used_jit = jit;
+    return FBG_OK;
+  }
   // a plain count of a non-empty range with the NVRTC engine resets its own
   // counters and writes the total: no memset is needed once the head is clean
   bool self_reset = false;

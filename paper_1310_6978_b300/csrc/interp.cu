@@ -5,6 +5,8 @@
 // batch: blocks pull work items (program, unit range) from a device counter.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "interp_device.cuh"
 #include "kernels.hpp"
 
@@ -75,20 +77,33 @@ __global__ void scan_kernel(const fbg_u64* in, fbg_u64* out, fbg_u64 n, fbg_u64*
   }
 }
 
+// out[i] = value for i < n (grid-stride)
+__global__ void fill_u64_kernel(fbg_u64* out, fbg_u64 n, fbg_u64 value) {
+  for (fbg_u64 i = (fbg_u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (fbg_u64)gridDim.x * blockDim.x)
+    out[i] = value;
+}
+
 }  // namespace
 
 size_t interp_smem_bytes(unsigned nslots) { return (size_t)nslots * B * sizeof(fbg_u64); }
 
 // the dynamic shared memory limit is raised only when a larger size is needed,
-// so launches (also inside stream capture) do not call cudaFuncSetAttribute
+// so launches (also inside stream capture) do not call cudaFuncSetAttribute;
+// the attribute belongs to the current device, so the size set is kept per
+// device (up to 64 devices; others set the attribute on every call)
 static cudaError_t ensure_smem(int mode, size_t smem) {
-  static size_t set_to[3] = {0, 0, 0};
-  if (smem <= set_to[mode]) return cudaSuccess;
-  cudaError_t e;
+  static std::mutex mu;
+  static size_t set_to[64][3] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const bool cached = dev >= 0 && dev < 64;
+  std::lock_guard<std::mutex> lock(mu);
+  if (cached && smem <= set_to[dev][mode]) return cudaSuccess;
   if (mode == 0) e = cudaFuncSetAttribute(interp_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   else if (mode == 1) e = cudaFuncSetAttribute(interp_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   else e = cudaFuncSetAttribute(interp_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) set_to[mode] = smem;
+  if (e == cudaSuccess && cached) set_to[dev][mode] = smem;
   return e;
 }
 
@@ -111,6 +126,14 @@ cudaError_t launch_interp(int mode, const FbgInterpProg* progs, const FbgWorkIte
 cudaError_t launch_scan(const unsigned long long* in, unsigned long long* out, unsigned long long n,
                         unsigned long long* total, cudaStream_t stream) {
   scan_kernel<<<1, 1024, 0, stream>>>(in, out, n, total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_u64(unsigned long long* out, unsigned long long n, unsigned long long value,
+                            cudaStream_t stream) {
+  if (n == 0) return cudaSuccess;
+  const unsigned long long blocks = (n + 255) / 256;
+  fill_u64_kernel<<<(unsigned)(blocks < 1024 ? blocks : 1024), 256, 0, stream>>>(out, n, value);
   return cudaGetLastError();
 }
 

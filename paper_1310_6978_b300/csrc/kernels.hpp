@@ -16,5 +16,8 @@ cudaError_t launch_interp(int mode, const FbgInterpProg* progs, const FbgWorkIte
 cudaError_t launch_scan(const unsigned long long* in, unsigned long long* out, unsigned long long n,
                         unsigned long long* total, cudaStream_t stream);
 int interp_blocks_per_sm(int mode, unsigned nslots);
+// out[i] = value for i < n
+cudaError_t launch_fill_u64(unsigned long long* out, unsigned long long n, unsigned long long value,
+                            cudaStream_t stream);
 
 }  // namespace fbg

@@ -9,6 +9,16 @@ the count is provided here.
 """
 from __future__ import annotations
 
+MASK64 = (1 << 64) - 1
+
+
+def to_int64_bits(count: int) -> int:
+    """The signed 64-bit integer with the same bits as the unsigned count
+    (a torch.int64 element holds it; a count may reach 2^63 at n = 63)."""
+    if not 0 <= count <= MASK64:
+        raise ValueError("a count is an unsigned 64-bit integer")
+    return count - (1 << 64) if count >> 63 else count
+
 
 def unit_range(nunits: int, rank: int, world: int) -> tuple[int, int]:
     """Contiguous slice of [0, nunits) for ``rank``: sizes differ by at most
@@ -33,6 +43,8 @@ def count_sharded(prog, group=None, stream=None) -> int:
     begin, end = unit_range(nunits, rank, world)
     local = prog.count_range(begin, end, stream) if end > begin else 0
     dev = "cuda" if dist.get_backend(group) == "nccl" else "cpu"
-    t = torch.tensor([local], dtype=torch.int64, device=dev)
+    # the 64-bit words add modulo 2^64 whatever their sign, so the sum read
+    # back as unsigned is the exact count (at most 2^63)
+    t = torch.tensor([to_int64_bits(local)], dtype=torch.int64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
-    return int(t.item())
+    return int(t.item()) & MASK64

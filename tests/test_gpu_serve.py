@@ -1,12 +1,16 @@
 """GPU: the continuous-batching server (fbg_server_*).  Every result must be
-the same alone and in the mix, and equal to the single-program entry points
-and, at small n, to the oracle (exact integers: bit-exact)."""
+the same alone and in the mix, and equal to the oracle's (exact integers:
+bit-exact): whole counts and model lists where the oracle evaluates every
+assignment, per-unit subcube counts and sampled model checks above that
+(tests/oracle_checks.py)."""
 import time
 
 import numpy as np
 import pytest
 
 import oracle
+import oracle_checks as OC
+from oracle import counters as C
 import paper_1310_6978_b300 as F
 from paper_1310_6978_b300 import _lib as L
 from paper_1310_6978_b300 import workloads as W
@@ -21,15 +25,6 @@ def _cuda():
         pytest.skip("no CUDA device")
 
 
-def reference(wl, mode, cap):
-    p = F.compile(wl.text, wl.k)
-    if mode == L.MODE_COUNT:
-        return p.count(), []
-    buf = torch.zeros(max(1, cap), dtype=torch.int64, device="cuda")
-    total, written = p.enumerate_models(buf, cap)
-    return total, [int(x) for x in buf[:written].cpu().numpy().view(np.uint64)]
-
-
 def mixed_requests(count, seed, n_hi=30):
     reqs = W.request_stream(count, rate_per_s=1e6, seed=seed, n_lo=8, n_hi=n_hi, enum_frac=0.25, cap=1000)
     return [(r.workload, L.MODE_ENUMERATE if r.mode == "enumerate" else L.MODE_COUNT, r.cap) for r in reqs]
@@ -40,28 +35,53 @@ def wait_all(srv, ids, timeout=300):
     return {i: srv.poll(i) for i in ids}
 
 
+def check_with_oracle(wl, mode, cap, r, rng, cache):
+    assert r is not None and r["status"] == 0
+    OC.check_count(wl, r["count"], rng, cache=cache)
+    if mode == L.MODE_ENUMERATE:
+        OC.check_models(wl, r["models"], r["count"], cap, rng, cache=cache)
+
+
 @pytest.mark.parametrize("opts", [{}, {"max_inflight": 3, "tick_units": 16}, {"mem_budget_bytes": 4096}])
 def test_results_same_alone_and_in_mix(opts):
     reqs = mixed_requests(60, 21)
     srv = F.Server(**opts)
     ids = [srv.submit(wl.text, wl.k, mode, cap) for wl, mode, cap in reqs]
     res = wait_all(srv, ids)
+    rng = np.random.default_rng(21)
+    cache = {}
     for i, (wl, mode, cap) in zip(ids, reqs):
-        r = res[i]
-        assert r is not None and r["status"] == 0
-        want_count, want_models = reference(wl, mode, cap)
-        assert r["count"] == want_count
-        if mode == L.MODE_ENUMERATE:
-            assert r["models"] == want_models
-    # alone: a fresh server, one request at a time
+        check_with_oracle(wl, mode, cap, res[i], rng, cache)
+    # alone: a fresh server, one request at a time; the same result as in the mix
     alone = F.Server(**opts)
-    for wl, mode, cap in reqs[:12]:
+    for i, (wl, mode, cap) in list(zip(ids, reqs))[:12]:
         rid = alone.submit(wl.text, wl.k, mode, cap)
         r = wait_all(alone, [rid])[rid]
-        want_count, want_models = reference(wl, mode, cap)
-        assert r["count"] == want_count and (mode == L.MODE_COUNT or r["models"] == want_models)
+        assert r["status"] == 0 and r["count"] == res[i]["count"] and r["models"] == res[i]["models"]
     srv.close()
     alone.close()
+
+
+def test_serving_stream_shape_against_oracle():
+    """Requests drawn as the serving benchmark draws them (seed 5: n uniform
+    in 16..38, a family with exactly n letters else 3-CNF, 10% model lists
+    capped at 10^6), submitted back to back; every count and model list is
+    checked against the oracle."""
+    reqs = W.request_stream(160, rate_per_s=1e6, seed=5)
+    srv = F.Server()
+    ids = [srv.submit(r.workload.text, r.workload.k, L.MODE_ENUMERATE if r.mode == "enumerate" else L.MODE_COUNT,
+                      r.cap) for r in reqs]
+    res = wait_all(srv, ids, timeout=600)
+    srv.close()
+    rng = np.random.default_rng(5)
+    cache = {}
+    how = {}
+    for i, r in zip(ids, reqs):
+        mode = L.MODE_ENUMERATE if r.mode == "enumerate" else L.MODE_COUNT
+        check_with_oracle(r.workload, mode, r.cap, res[i], rng, cache)
+        how[r.workload.n > 22] = how.get(r.workload.n > 22, 0) + 1
+    assert how.get(True, 0) >= 50 and how.get(False, 0) >= 20
+    assert max(r.workload.n for r in reqs) == 38
 
 
 def test_small_requests_equal_oracle_and_latency_fields():
@@ -89,7 +109,7 @@ def test_requests_arriving_while_running_join_later_ticks():
     time.sleep(0.01)
     later = [srv.submit(W.posets(4).text, 4, L.MODE_COUNT, 0) for _ in range(5)]
     res = wait_all(srv, [first] + later)
-    assert res[first]["count"] == F.compile(big.text, big.k).count()
+    assert res[first]["count"] == C.count_transitive_backtrack(6)
     assert all(res[i]["count"] == 219 for i in later)
     srv.close()
 

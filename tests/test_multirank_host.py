@@ -37,6 +37,18 @@ class OracleUnits:
         return sum(self.th.count_cube(mask, unit << (n - self.u)) for unit in range(begin, end))
 
 
+class HugeCounts:
+    """A program stand-in whose units hold 2^63 / nunits models each: the
+    sharded sum must reach 2^63, which a signed 64-bit read would turn
+    negative."""
+
+    def unit_vars(self):
+        return list(range(32)), 1 << 32
+
+    def count_range(self, begin, end, stream=None):
+        return (end - begin) << 31
+
+
 def worker(rank, world, port, q):
     sys.path.insert(0, ROOT)
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
@@ -50,8 +62,9 @@ def worker(rank, world, port, q):
         rate = bench.whole_job_rate(world * 10 ** 9, t_max)
         wl = W.posets(4)
         total = shard.count_sharded(OracleUnits(wl.text, wl.k, 5))
+        huge = shard.count_sharded(HugeCounts())
         dist.barrier()
-        q.put((rank, t_max, rate, total))
+        q.put((rank, t_max, rate, total, huge))
     finally:
         dist.destroy_process_group()
 
@@ -68,7 +81,8 @@ def test_two_and_three_gloo_ranks(world):
         p.join(120)
         assert p.exitcode == 0
     res = sorted(q.get(timeout=5) for _ in range(world))
-    for rank, t_max, rate, total in res:
+    for rank, t_max, rate, total, huge in res:
+        assert huge == 1 << 63                        # a tautology at n = 63, summed unsigned
         assert t_max == float(world)                  # the slowest rank: 1 + (world - 1)
         assert rate == pytest.approx(world / t_max)   # world * 1e9 units over t_max, in G/s
         assert total == 219                           # posets on 4 points, summed over the slices
@@ -86,3 +100,12 @@ def test_unit_ranges_cover_once():
             assert seen == list(range(nunits))
     with pytest.raises(ValueError):
         unit_range(8, 2, 2)
+
+
+def test_int64_bit_patterns_of_counts():
+    from paper_1310_6978_b300.shard import MASK64, to_int64_bits
+    for c in (0, 1, (1 << 63) - 1, 1 << 63, MASK64):
+        assert to_int64_bits(c) & MASK64 == c
+        assert -(1 << 63) <= to_int64_bits(c) < (1 << 63)
+    with pytest.raises(ValueError):
+        to_int64_bits(-1)
