@@ -194,6 +194,13 @@ fbg_status fbg_truth_table(fbg_program *prog, void *stream, uint64_t *dev_words,
  * min(cap, total) are written to caller-owned device memory dev_models;
  * *total (host) receives the exact number of models, *written the number
  * stored.  Synchronises `stream`.  n <= 40.
+ * Engine: the specialised (NVRTC) kernel by default -- its layout makes every
+ * (unit, warp slice) work item an interval of j; one pass counts each item's
+ * models, a scan gives each item its first position, and a second pass has
+ * each warp write its items' models in order (warp prefix sums of the
+ * lanes' popcounts), skipping items that start at or past cap -- or the
+ * interpreter (FBG_OPT_ENGINE = FBG_ENGINE_INTERP, or when the specialised
+ * build fails under FBG_ENGINE_AUTO).  FBG_ETOOBIG above 2^26 items.
  */
 fbg_status fbg_enumerate_models(fbg_program *prog, void *stream, uint64_t *dev_models, size_t cap,
                                 uint64_t *total, uint64_t *written);
@@ -239,7 +246,9 @@ typedef struct {
 } fbg_tune_result;
 fbg_status fbg_autotune(fbg_program *prog, void *stream, int mode, int reps, fbg_tune_result *out);
 
-/* executed work of the last fbg_count with FBG_OPT_STATS = 1 */
+/* executed work of the last fbg_count with FBG_OPT_STATS = 1, or of the last
+   fbg_truth_table of the specialised kernel with FBG_OPT_STATS = 1 (which then
+   synchronises its stream to read the level counters) */
 fbg_status fbg_last_exec_stats(fbg_program *prog, fbg_exec_stats *out);
 
 /* Diagnostics (no counterpart in the paper): host wall time, in seconds,
@@ -249,15 +258,31 @@ fbg_status fbg_last_exec_stats(fbg_program *prog, fbg_exec_stats *out);
  * builds (launch, copy of the count, synchronisation).  FBG_EINVAL on null. */
 fbg_status fbg_debug_host_times(const fbg_program *prog, double *build_s, double *count_s);
 
-/* CUDA source of the specialised kernel (mode 0 count, 1 table); *len
-   receives the size; buf may be NULL to query it */
+/*
+ * Host compile caches (no counterpart in the paper; the host half of the
+ * Translate and Reduction submodules of Sec. 4.1 is repeated work when the
+ * same text comes back).  fbg_compile keeps the parsed and grounded theory of
+ * the last 512 (text, domain_k) pairs; kernel builds keep the layout, LUT
+ * program, emitted source or bytecode and the build-time item pruning of the
+ * last 256 specialised and 512 interpreter builds, keyed by text, domain_k,
+ * mode and every shape option.  Entries are immutable and shared; device
+ * buffers stay per program.  out[0..8] receives hits, misses and entries of
+ * the compile, specialised-build and interpreter-build caches.  With
+ * clear != 0 the caches are emptied first (the counters are kept).
+ * FBG_EINVAL on null.
+ */
+fbg_status fbg_debug_host_caches(int clear, uint64_t out[9]);
+
+/* CUDA source of the specialised kernel (mode 0 count, 1 table, 2 model
+   list), exactly as the kernel build compiles it with the current options;
+   *len receives the size; buf may be NULL to query it */
 fbg_status fbg_program_source(fbg_program *prog, int mode, char *buf, size_t *len);
 
 /*
- * Diagnostic: the compiled program as JSON text -- which = 0 / 1: LUT program
- * of the specialised count / table kernel (layout, constants per register,
- * LUTs with levels); 2 / 3: interpreter bytecode of the count / identity
- * layout.  Used to check the compiler on a machine without a GPU; it does
+ * Diagnostic: the compiled program as JSON text -- which = 0 / 1 / 4: LUT
+ * program of the specialised count / table / model-list kernel (layout,
+ * constants per register, LUTs with levels); 2 / 3: interpreter bytecode of
+ * the count / identity layout.  Used to check the compiler on a machine without a GPU; it does
  * not evaluate anything.  *len receives the size; buf may be NULL.
  * For which = 0 the layout also gives "split_bits" (the largest s of the
  * item pieces the count kernel takes, 0 when none), and the object gives

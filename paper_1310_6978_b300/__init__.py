@@ -240,6 +240,16 @@ class Batch:
         return {"items": items.value, "units": units.value, "grid": grid.value, "specialized": spec.value}
 
 
+def host_caches(clear: bool = False) -> dict:
+    """fbg_debug_host_caches: hits, misses and entries of the host compile
+    caches (optionally emptied first)."""
+    L = _L()
+    out = (ctypes.c_uint64 * 9)()
+    L.check(L.lib.fbg_debug_host_caches(1 if clear else 0, out))
+    names = ("compile", "jit_build", "interp_build")
+    return {nm: {"hits": out[3 * i], "misses": out[3 * i + 1], "entries": out[3 * i + 2]} for i, nm in enumerate(names)}
+
+
 def probe_lop3_rate(stream=None) -> float:
     """fbg_probe_lop3_rate: measured lop3.b32 issue rate of this GPU (T/s)."""
     L = _L()

@@ -88,6 +88,7 @@ _sig("fbg_enumerate_models", c_int, c_vp, c_vp, c_vp, c_sz, ctypes.POINTER(c_u64
 _sig("fbg_autotune", c_int, c_vp, c_vp, c_int, c_int, ctypes.POINTER(FbgTuneResult))
 _sig("fbg_last_exec_stats", c_int, c_vp, ctypes.POINTER(FbgExecStats))
 _sig("fbg_debug_host_times", c_int, c_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double))
+_sig("fbg_debug_host_caches", c_int, c_int, ctypes.POINTER(ctypes.c_uint64))
 _sig("fbg_program_source", c_int, c_vp, c_int, c_char_p, ctypes.POINTER(c_sz))
 _sig("fbg_debug_dump", c_int, c_vp, c_int, c_char_p, ctypes.POINTER(c_sz))
 _sig("fbg_program_jit_log", c_char_p, c_vp)

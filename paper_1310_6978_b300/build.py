@@ -20,6 +20,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-Wall", f"-I{os.path.join(ROOT, 'include')}", f"-I{CSRC}"]
 
 SOURCES = ["parse.cpp", "ground.cpp", "lower.cpp", "emit.cpp", "jit.cpp", "api.cpp", "batch.cpp", "serve.cpp", "autotune.cpp",
+           "cache.cpp",
            "interp.cu", "noalloc.cu", "peaks.cu"]
 
 

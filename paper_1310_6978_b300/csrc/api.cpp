@@ -8,6 +8,7 @@
 #include <mutex>
 #include <sstream>
 
+#include "build_cache.hpp"
 #include "emit.hpp"
 #include "fbg.h"
 #include "fbg_internal.hpp"
@@ -84,7 +85,7 @@ void strip_prune(LutProgram& lp) {
 }
 
 std::vector<int> order_for(const fbg_program* p, bool count_layout) {
-  if (count_layout && p->opt_search) return search_order(p->g);
+  if (count_layout && p->opt_search) return search_order(*p->g);
   return identity_order(p->n);
 }
 
@@ -103,36 +104,54 @@ fbg_status ensure_scratch(fbg_program* p, size_t words) {
 
 namespace fbg {
 
-fbg_status build_interp(fbg_program* p, int which) {
-  InterpBuild& b = p->ib[which];
-  if (b.valid) return FBG_OK;
-  try {
-    Layout L = make_layout(p->n, interp_params(p), order_for(p, which == 0));
-    b.lp = lower_and_map(p->g, L);
-    if (!p->opt_prune) strip_prune(b.lp);
-    b.code = emit_bytecode(b.lp);
-  } catch (CompileError& e) {
-    return set_error(FBG_ETOOBIG, e.msg);
-  }
-  b.nunits = b.code.prog.nunits;
+// the host half of an interpreter build: layout, LUTs, bytecode, item
+// grouping and the units that can hold models
+static std::shared_ptr<const InterpHost> interp_host(fbg_program* p, int which) {
+  const std::string key = build_key(p, "interp", which);
+  if (auto hit = interp_host_get(key)) return hit;
+  auto h = std::make_shared<InterpHost>();
+  Layout L = make_layout(p->n, interp_params(p), order_for(p, which == 0));
+  h->lp = lower_and_map(*p->g, L);
+  if (!p->opt_prune) strip_prune(h->lp);
+  h->code = emit_bytecode(h->lp);
+  const uint64_t nunits = h->code.prog.nunits;
   // work items: single units while that keeps the queue short, else ranges
   uint64_t per = 1;
-  while (b.nunits / per > 65536) per <<= 1;
-  b.live.clear();
+  while (nunits / per > 65536) per <<= 1;
+  h->units_per_item = per;
   if (p->opt_prune && per == 1) {
     // units on which a conjunct over unit and warp letters is false have no
     // models: counts, tables (zeroed before the launch) and model lists leave
     // them out when that removes a quarter of them
-    std::vector<uint8_t> alive = alive_items(p->g, b.lp.layout);
-    const int wb = b.lp.layout.warp_bits;
+    std::vector<uint8_t> alive = alive_items(*p->g, h->lp.layout);
+    const int wb = h->lp.layout.warp_bits;
     std::vector<uint32_t> live;
-    for (uint64_t u = 0; !alive.empty() && u < b.nunits; u++) {
+    for (uint64_t u = 0; !alive.empty() && u < nunits; u++) {
       bool any = false;
       for (int w = 0; w < (1 << wb); w++) any = any || alive[(size_t)((u << wb) | (uint64_t)w)];
       if (any) live.push_back((uint32_t)u);
     }
-    if (!alive.empty() && live.size() * 4 <= b.nunits * 3) b.live = std::move(live);
+    if (!alive.empty() && live.size() * 4 <= nunits * 3) h->live = std::move(live);
   }
+  std::shared_ptr<const InterpHost> hc = std::move(h);
+  interp_host_put(key, hc);
+  return hc;
+}
+
+fbg_status build_interp(fbg_program* p, int which) {
+  InterpBuild& b = p->ib[which];
+  if (b.valid) return FBG_OK;
+  std::shared_ptr<const InterpHost> h;
+  try {
+    h = interp_host(p, which);
+  } catch (CompileError& e) {
+    return set_error(FBG_ETOOBIG, e.msg);
+  }
+  b.lp = h->lp;
+  b.code = h->code;
+  b.nunits = b.code.prog.nunits;
+  b.live = h->live;
+  const uint64_t per = h->units_per_item;
   std::vector<FbgWorkItem> items;
   if (per == 1)
     b.append_items(items, 0u, 0, b.live_units(), 1);
@@ -181,21 +200,50 @@ fbg_status build_jit(fbg_program* p, int mode) {
   return s;
 }
 
+// the host half of a specialised-kernel build: layout, LUTs, source and the
+// (unit, warp slice) items that can hold models
+static std::shared_ptr<const JitHost> jit_host(fbg_program* p, int mode) {
+  const std::string key = build_key(p, "jit", mode);
+  if (auto hit = jit_host_get(key)) return hit;
+  auto h = std::make_shared<JitHost>();
+  const std::vector<int> ord = mode == 2 ? enum_order(p->n, jit_params(p)) : order_for(p, mode == 0);
+  Layout L = make_layout(p->n, jit_params(p), ord);
+  h->lp = lower_and_map(*p->g, L);
+  if (!p->opt_prune) strip_prune(h->lp);
+  h->block = h->lp.layout.lane_bits < 5 ? 32 : 32 << h->lp.layout.warp_bits;
+  h->src = emit_cuda_source(h->lp, mode, h->block, (int)p->opt_min_blocks, &h->ops, &h->unrolled_level,
+                            p->opt_stats != 0, &h->uops);
+  if (mode == 0 && p->opt_prune) {
+    // items on which a conjunct over unit and warp letters is false have no
+    // models: full-range counts skip them when that removes at least a
+    // quarter of the items
+    h->alive = alive_items(*p->g, h->lp.layout);
+    uint64_t live = 0;
+    for (uint8_t a : h->alive) live += a;
+    if (h->alive.empty() || live * 4 > h->alive.size() * 3) h->alive.clear();
+  }
+  std::shared_ptr<const JitHost> hc = std::move(h);
+  jit_host_put(key, hc);
+  return hc;
+}
+
 fbg_status build_jit_impl(fbg_program* p, int mode) {
   JitBuild& b = p->jb[mode];
+  std::shared_ptr<const JitHost> h;
   try {
-    Layout L = make_layout(p->n, jit_params(p), order_for(p, mode == 0));
-    b.lp = lower_and_map(p->g, L);
-    if (!p->opt_prune) strip_prune(b.lp);
-    b.block = b.lp.layout.lane_bits < 5 ? 32 : 32 << b.lp.layout.warp_bits;
-    b.src = emit_cuda_source(b.lp, mode, b.block, (int)p->opt_min_blocks, &b.ops, &b.unrolled_level,
-                             p->opt_stats != 0, &b.uops);
+    h = jit_host(p, mode);
   } catch (CompileError& e) {
     return set_error(FBG_ETOOBIG, e.msg);
   }
+  b.lp = h->lp;
+  b.src = h->src;
+  b.ops = h->ops;
+  b.uops = h->uops;
+  b.unrolled_level = h->unrolled_level;
+  b.block = h->block;
   int dev = 0;
   cudaGetDevice(&dev);
-  JitResult r = jit_compile(b.src, mode == 0 ? "fbg_jit_count" : "fbg_jit_table", dev);
+  JitResult r = jit_compile(b.src, mode == 0 ? "fbg_jit_count" : mode == 1 ? "fbg_jit_table" : "fbg_jit_enum", dev);
   b.log = r.log;
   p->jit_log = r.log;
   if (!r.ok) return set_error(FBG_EJIT, r.log);
@@ -205,23 +253,13 @@ fbg_status build_jit_impl(fbg_program* p, int mode) {
   if (per_sm <= 0) per_sm = 1;
   b.nunits = 1ull << b.lp.layout.unit_bits;
   b.grid = (int)std::min<uint64_t>(b.nunits, (uint64_t)device_sms() * (uint64_t)per_sm);
-  if (mode == 0 && p->opt_prune) {
-    // items on which a conjunct over unit and warp letters is false have no
-    // models: full-range counts skip them when that removes at least a
-    // quarter of the items
-    b.alive = alive_items(p->g, b.lp.layout);
-    uint64_t live = 0;
-    for (uint8_t a : b.alive) live += a;
-    if (!b.alive.empty() && live * 4 <= b.alive.size() * 3) {
-      std::vector<unsigned> items;
-      items.reserve((size_t)live);
-      for (size_t t = 0; t < b.alive.size(); t++)
-        if (b.alive[t]) items.push_back((unsigned)t);
-      fbg_status s = upload_items(b, items);
-      if (s != FBG_OK) return s;
-    } else {
-      b.alive.clear();
-    }
+  b.alive = h->alive;
+  if (!b.alive.empty()) {
+    std::vector<unsigned> items;
+    for (size_t t = 0; t < b.alive.size(); t++)
+      if (b.alive[t]) items.push_back((unsigned)t);
+    fbg_status s = upload_items(b, items);
+    if (s != FBG_OK) return s;
   }
   b.valid = true;
   return FBG_OK;
@@ -268,7 +306,7 @@ fbg_status launch_count(fbg_program* p, cudaStream_t st, unsigned long long* dev
   s = ensure_scratch(p, words);
   if (s != FBG_OK) return s;
   if (!dev_count) dev_count = p->d_scratch + 1;
-  if (p->g.root == 0 || p->g.root == 1) {
+  if (p->g->root == 0 || p->g->root == 1) {
     // the Reduction left a constant: every assignment of a unit is a model
     // (true) or none is (false), so the counts are written without an
     // evaluation (2^n models for a tautology, up to 2^63)
@@ -276,7 +314,7 @@ fbg_status launch_count(fbg_program* p, cudaStream_t st, unsigned long long* dev
     const uint64_t nunits = 1ull << L.unit_bits;
     const uint64_t e = std::min<uint64_t>(uend, nunits);
     if (ubegin > e) return set_error(FBG_EINVAL, "empty or inverted unit range");
-    const uint64_t per_unit = p->g.root == 1 ? (1ull << (p->n - L.unit_bits)) : 0ull;
+    const uint64_t per_unit = p->g->root == 1 ? (1ull << (p->n - L.unit_bits)) : 0ull;
     CK(cudaMemsetAsync(p->d_scratch, 0, kScratchHead * 8, st));
     p->scratch_clean = true;
     CK(launch_fill_u64(dev_count, 1, (e - ubegin) * per_unit, st));
@@ -363,6 +401,31 @@ fbg_status launch_count(fbg_program* p, cudaStream_t st, unsigned long long* dev
 
 }  // namespace fbg
 
+// executed work of the last launch from its level counters (scratch head
+// words 4..19, FBG_OPT_STATS = 1): per level, executions x the lop3.b32 the
+// kernel issues per execution (JIT: the folded source's lane-varying ops;
+// interpreter: two per instruction for its 64-bit tiles)
+static void fill_exec_stats(fbg_program* p, bool jit, int mode, const unsigned long long* host) {
+  fbg_exec_stats& es = p->last;
+  std::memset(&es, 0, sizeof es);
+  es.engine = jit ? FBG_ENGINE_JIT : FBG_ENGINE_INTERP;
+  if (!p->opt_stats) return;
+  const JitBuild& jb = p->jb[mode];
+  const LutProgram& lp = jit ? jb.lp : p->ib[mode].lp;
+  const Layout& L = lp.layout;
+  double execs = (double)(1ull << L.unit_bits) * (double)(1 << L.warp_bits);
+  for (int lv = 0; lv < L.nlevels() && lv < 16; lv++) {
+    es.level_iters[lv] = host[4 + lv];
+    double per = jit ? (double)jb.ops[(size_t)lv] * 32.0
+                     : (double)(lp.levels[(size_t)lv].lut_end - lp.levels[(size_t)lv].lut_begin) * 64.0;
+    es.lop3_executed += (double)host[4 + lv] * per;
+    if (jit) es.lop3_uniform += (double)host[4 + lv] * (double)jb.uops[(size_t)lv];
+    if (lv >= 2 && !(jit && lv == jb.unrolled_level)) execs *= (double)(1u << L.loop_bits[(size_t)(lv - 2)]);
+    double nominal_execs = lv == 0 ? 0.0 : execs;
+    es.lop3_nominal += nominal_execs * (jit ? (double)(jb.ops[(size_t)lv] + jb.uops[(size_t)lv]) * 32.0 : per);
+  }
+}
+
 // ------------------------------------------------------------------ ABI --
 
 extern "C" {
@@ -372,8 +435,9 @@ fbg_status fbg_compile(const char* formula, int domain_k, fbg_program** out) {
   *out = nullptr;
   auto* p = new fbg_program();
   try {
-    p->th = parse_theory(formula, domain_k);
-    p->g = ground(p->th);
+    p->compiled = compile_cached(formula, domain_k);
+    p->th = &p->compiled->th;
+    p->g = &p->compiled->g;
   } catch (CompileError& e) {
     delete p;
     bool big = e.msg.find("more than") != std::string::npos;
@@ -381,7 +445,7 @@ fbg_status fbg_compile(const char* formula, int domain_k, fbg_program** out) {
   }
   p->text = formula;
   p->k = domain_k;
-  p->n = p->g.nvars;
+  p->n = p->g->nvars;
   *out = p;
   return FBG_OK;
 }
@@ -390,7 +454,7 @@ int fbg_num_vars(const fbg_program* p) { return p ? p->n : -1; }
 
 fbg_status fbg_var_name(const fbg_program* p, int i, char* buf, size_t len) {
   if (!p || !buf || i < 0 || i >= p->n) return set_error(FBG_EINVAL, "bad variable index");
-  const std::string& s = p->th.var_names[(size_t)p->g.letter_of_var[(size_t)i]];
+  const std::string& s = p->th->var_names[(size_t)p->g->letter_of_var[(size_t)i]];
   if (len < s.size() + 1) return set_error(FBG_EINVAL, "buffer too small");
   std::memcpy(buf, s.c_str(), s.size() + 1);
   return FBG_OK;
@@ -448,11 +512,11 @@ fbg_status fbg_program_stats(fbg_program* p, fbg_stats* out) {
   std::memset(out, 0, sizeof *out);
   out->n = p->n;
   out->domain_k = p->k;
-  out->dag_nodes = p->g.dag.size();
+  out->dag_nodes = p->g->dag.size();
   LutProgram lp;
   try {
     Layout L = make_layout(p->n, jit_params(p), order_for(p, true));
-    lp = lower_and_map(p->g, L);
+    lp = lower_and_map(*p->g, L);
     if (!p->opt_prune) strip_prune(lp);   // as the count kernel is built
   } catch (CompileError& e) {
     return set_error(FBG_ETOOBIG, e.msg);
@@ -485,29 +549,7 @@ fbg_status fbg_count(fbg_program* p, void* stream, uint64_t* out_count) {
   CK(cudaStreamSynchronize(st));
   p->t_count += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() - (p->t_build - build0);
   *out_count = host[1];
-  // executed work
-  fbg_exec_stats& es = p->last;
-  std::memset(&es, 0, sizeof es);
-  es.engine = jit ? FBG_ENGINE_JIT : FBG_ENGINE_INTERP;
-  if (p->opt_stats) {
-    const LutProgram& lp = jit ? p->jb[0].lp : p->ib[0].lp;
-    (void)lp;
-    const Layout& L = lp.layout;
-    double warps_per_block = (double)(1 << L.warp_bits);
-    double execs = (double)(1ull << L.unit_bits) * warps_per_block;
-    for (int lv = 0; lv < L.nlevels() && lv < 16; lv++) {
-      es.level_iters[lv] = host[4 + lv];
-      // JIT: lop3.b32 each thread issues per level execution (folded source);
-      // interpreter: two lop3.b32 per instruction (64-bit tiles)
-      double per = jit ? (double)p->jb[0].ops[(size_t)lv] * 32.0
-                       : (double)(lp.levels[(size_t)lv].lut_end - lp.levels[(size_t)lv].lut_begin) * 64.0;
-      es.lop3_executed += (double)host[4 + lv] * per;
-      if (jit) es.lop3_uniform += (double)host[4 + lv] * (double)p->jb[0].uops[(size_t)lv];
-      if (lv >= 2 && !(jit && lv == p->jb[0].unrolled_level)) execs *= (double)(1u << L.loop_bits[(size_t)(lv - 2)]);
-      double nominal_execs = lv == 0 ? 0.0 : execs;
-      es.lop3_nominal += nominal_execs * (jit ? (double)(p->jb[0].ops[(size_t)lv] + p->jb[0].uops[(size_t)lv]) * 32.0 : per);
-    }
-  }
+  fill_exec_stats(p, jit, 0, host);
   return FBG_OK;
 }
 
@@ -622,6 +664,13 @@ fbg_status fbg_schedule_units(fbg_program* p, void* stream) {
   return upload_items(b, perm);
 }
 
+fbg_status fbg_debug_host_caches(int clear, uint64_t out[9]) {
+  if (!out) return set_error(FBG_EINVAL, "null argument");
+  if (clear) host_caches_clear();
+  host_cache_stats(out);
+  return FBG_OK;
+}
+
 fbg_status fbg_debug_host_times(const fbg_program* p, double* build_s, double* count_s) {
   if (!p || !build_s || !count_s) return set_error(FBG_EINVAL, "null argument");
   *build_s = p->t_build;
@@ -691,8 +740,15 @@ fbg_status fbg_truth_table(fbg_program* p, void* stream, uint64_t* dev_words, si
     if (p->n < 6) CK(cudaMemsetAsync(dev_words, 0, 8, st));
     P.unit_end = b.nunits;
     P.chunk = std::max<uint64_t>(1, b.nunits / ((uint64_t)b.grid * 16));
+    P.iters = p->opt_stats ? p->d_scratch + 4 : nullptr;
     void* args[] = {&P};
     CK(cudaLaunchKernel((const void*)b.kern, dim3((unsigned)b.grid), dim3((unsigned)b.block), args, 0, st));
+    if (p->opt_stats) {   // executed work of this table (fbg_last_exec_stats)
+      unsigned long long host[kScratchHead];
+      CK(cudaMemcpyAsync(host, p->d_scratch, sizeof host, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      fill_exec_stats(p, true, 1, host);
+    }
   } else {
     InterpBuild& b = p->ib[1];
     CK(cudaMemsetAsync(dev_words, 0, nwords * 8, st));
@@ -703,11 +759,59 @@ fbg_status fbg_truth_table(fbg_program* p, void* stream, uint64_t* dev_words, si
   return FBG_OK;
 }
 
+// Model list with the specialised kernel (layout of enum_order): pass 1 counts
+// the models of every (unit, warp slice) item, a scan turns the counts into
+// each item's first position, pass 2 writes the models of the items that
+// start below `cap`.
+static fbg_status enumerate_jit(fbg_program* p, cudaStream_t st, uint64_t* dev_models, size_t cap, uint64_t* total,
+                                uint64_t* written) {
+  JitBuild& b = p->jb[2];
+  const uint64_t nitems = b.nunits << b.lp.layout.warp_bits;
+  if (nitems > (1ull << 26)) return set_error(FBG_ETOOBIG, "too many work items for a model list");
+  fbg_status s = ensure_scratch(p, kScratchHead + 2 * nitems);
+  if (s != FBG_OK) return s;
+  unsigned long long* item_counts = p->d_scratch + kScratchHead;
+  unsigned long long* offsets = item_counts + nitems;
+  CK(cudaMemsetAsync(p->d_scratch, 0, kScratchHead * 8, st));
+  p->scratch_clean = false;
+  FbgLaunch P{};
+  P.unit_ctr = p->d_scratch + 0;
+  P.unit_begin = 0;
+  P.unit_end = b.nunits;
+  P.unit_counts = item_counts;
+  P.iters = p->opt_stats ? p->d_scratch + 4 : nullptr;
+  const uint64_t wpb = (uint64_t)(b.block / 32);
+  P.chunk = std::max<uint64_t>(1, nitems / ((uint64_t)b.grid * wpb * 16));
+  void* args[] = {&P};
+  CK(cudaLaunchKernel((const void*)b.kern, dim3((unsigned)b.grid), dim3((unsigned)b.block), args, 0, st));
+  CK(launch_scan(item_counts, offsets, nitems, p->d_scratch + 3, st));
+  if (cap) {
+    CK(cudaMemsetAsync(p->d_scratch + 0, 0, 8, st));
+    P.models = (unsigned long long*)dev_models;
+    P.cap = cap;
+    P.unit_offsets = offsets;
+    CK(cudaLaunchKernel((const void*)b.kern, dim3((unsigned)b.grid), dim3((unsigned)b.block), args, 0, st));
+  }
+  unsigned long long tot = 0;
+  CK(cudaMemcpyAsync(&tot, p->d_scratch + 3, 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  *total = tot;
+  *written = std::min<uint64_t>(tot, cap);
+  return FBG_OK;
+}
+
 fbg_status fbg_enumerate_models(fbg_program* p, void* stream, uint64_t* dev_models, size_t cap, uint64_t* total,
                                 uint64_t* written) {
   if (!p || !total || !written || (cap && !dev_models)) return set_error(FBG_EINVAL, "null argument");
   if (p->n > 40) return set_error(FBG_ETOOBIG, "model lists need n <= 40");
   cudaStream_t st = (cudaStream_t)stream;
+  // the specialised kernel unless the interpreter is asked for (or, with the
+  // automatic choice, the specialised build fails)
+  if (p->opt_engine != FBG_ENGINE_INTERP) {
+    fbg_status s = build_jit(p, 2);
+    if (s == FBG_OK) return enumerate_jit(p, st, dev_models, cap, total, written);
+    if (p->opt_engine == FBG_ENGINE_JIT) return s;
+  }
   fbg_status s = build_interp(p, 1);
   if (s != FBG_OK) return s;
   InterpBuild& b = p->ib[1];
@@ -748,13 +852,10 @@ fbg_status fbg_last_exec_stats(fbg_program* p, fbg_exec_stats* out) {
 }
 
 fbg_status fbg_program_source(fbg_program* p, int mode, char* buf, size_t* len) {
-  if (!p || !len || mode < 0 || mode > 1) return set_error(FBG_EINVAL, "bad argument");
+  if (!p || !len || mode < 0 || mode > 2) return set_error(FBG_EINVAL, "bad argument");
   std::string src;
   try {
-    Layout L = make_layout(p->n, jit_params(p), order_for(p, mode == 0));
-    LutProgram lp = lower_and_map(p->g, L);
-    if (!p->opt_prune) strip_prune(lp);
-    src = emit_cuda_source(lp, mode, 32 << (int)p->opt_warps_log2, (int)p->opt_min_blocks);
+    src = jit_host(p, mode)->src;   // exactly the source the kernel build compiles
   } catch (CompileError& e) {
     return set_error(FBG_ETOOBIG, e.msg);
   }
@@ -767,7 +868,7 @@ fbg_status fbg_program_source(fbg_program* p, int mode, char* buf, size_t* len) 
 }
 
 fbg_status fbg_debug_dump(fbg_program* p, int which, char* buf, size_t* len) {
-  if (!p || !len || which < 0 || which > 3) return set_error(FBG_EINVAL, "bad argument");
+  if (!p || !len || which < 0 || which > 4) return set_error(FBG_EINVAL, "bad argument");
   std::ostringstream o;
   auto layout_json = [&](const Layout& L) {
     o << "\"layout\": {\"n\": " << L.n << ", \"r\": " << L.r << ", \"lane_bits\": " << L.lane_bits
@@ -781,11 +882,12 @@ fbg_status fbg_debug_dump(fbg_program* p, int which, char* buf, size_t* len) {
     o << "]}";
   };
   auto val_json = [&](const Val& v) { o << "[" << (int)v.kind << ", " << v.id << "]"; };
-  if (which < 2) {
+  if (which < 2 || which == 4) {
     LutProgram lp;
     try {
-      Layout L = make_layout(p->n, jit_params(p), order_for(p, which == 0));
-      lp = lower_and_map(p->g, L);
+      Layout L = make_layout(p->n, jit_params(p),
+                             which == 4 ? enum_order(p->n, jit_params(p)) : order_for(p, which == 0));
+      lp = lower_and_map(*p->g, L);
       if (!p->opt_prune) strip_prune(lp);
     } catch (CompileError& e) {
       return set_error(FBG_ETOOBIG, e.msg);
@@ -822,7 +924,7 @@ fbg_status fbg_debug_dump(fbg_program* p, int which, char* buf, size_t* len) {
     for (size_t j = 0; j < lp.const_acc.w.size(); j++) o << (j ? ", " : "") << lp.const_acc.w[j];
     o << "]";
     if (which == 0 && p->opt_prune) {   // units the count kernel hands out (all when absent)
-      std::vector<uint8_t> alive = alive_items(p->g, lp.layout);
+      std::vector<uint8_t> alive = alive_items(*p->g, lp.layout);
       if (!alive.empty()) {
         o << ", \"alive_items\": [";
         bool first = true;
@@ -843,7 +945,7 @@ fbg_status fbg_debug_dump(fbg_program* p, int which, char* buf, size_t* len) {
     LutProgram lp;
     try {
       Layout L = make_layout(p->n, interp_params(p), order_for(p, which == 2));
-      lp = lower_and_map(p->g, L);
+      lp = lower_and_map(*p->g, L);
       if (!p->opt_prune) strip_prune(lp);
       code = emit_bytecode(lp);
     } catch (CompileError& e) {

@@ -179,7 +179,7 @@ BatchPlan plan_batch(fbg_program* const* progs, int nprogs, std::string* err) {
   std::map<std::pair<std::string, int>, std::vector<int>> groups;
   std::vector<double> cost((size_t)nprogs);
   for (int i = 0; i < nprogs; i++) {
-    size_t ins = progs[i]->ib[0].valid ? progs[i]->ib[0].code.ins.size() : (size_t)progs[i]->g.dag.size();
+    size_t ins = progs[i]->ib[0].valid ? progs[i]->ib[0].code.ins.size() : (size_t)progs[i]->g->dag.size();
     cost[(size_t)i] = std::ldexp((double)std::max<size_t>(1, ins), progs[i]->n);
     groups[{progs[i]->text, progs[i]->k}].push_back(i);
   }
@@ -199,14 +199,14 @@ BatchPlan plan_batch(fbg_program* const* progs, int nprogs, std::string* err) {
     lp.unit_bits_max = 13;
     lp.loop_level_bits = 2;
     try {
-      Layout L = make_layout(p0->n, lp, search_order(p0->g));
-      LutProgram prog = lower_and_map(p0->g, L);
+      Layout L = make_layout(p0->n, lp, search_order(*p0->g));
+      LutProgram prog = lower_and_map(*p0->g, L);
       int block = prog.layout.lane_bits < 5 ? 32 : 32 << prog.layout.warp_bits;
       plan.src.push_back(emit_cuda_source(prog, 0, block, 2, nullptr, nullptr, false));
       plan.block.push_back(block);
       // units whose unit-only conjuncts are false have no models: left out
       // when that removes at least a quarter of them
-      std::vector<uint8_t> alive = alive_items(p0->g, prog.layout);
+      std::vector<uint8_t> alive = alive_items(*p0->g, prog.layout);
       std::vector<unsigned> live;
       uint64_t nlive = 0;
       for (uint8_t a : alive) nlive += a;

@@ -1,0 +1,46 @@
+// build_cache.hpp -- shared host products of a kernel build (cache.cpp).
+#pragma once
+
+#include <cstdint>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "emit.hpp"
+#include "fbg_internal.hpp"
+
+struct fbg_program;
+
+namespace fbg {
+
+// the host half of a specialised-kernel build (JitBuild without device state)
+struct JitHost {
+  LutProgram lp;
+  std::string src;
+  std::vector<long long> ops, uops;
+  int unrolled_level = -1;
+  int block = 256;
+  std::vector<uint8_t> alive;   // empty: every item may hold models (or pruning off)
+};
+
+// the host half of an interpreter build
+struct InterpHost {
+  LutProgram lp;
+  InterpCode code;
+  uint64_t units_per_item = 1;
+  std::vector<uint32_t> live;
+};
+
+// key of a build: what ("jit"/"interp"), mode or layout, every option that
+// shapes the build, the domain size and the text
+std::string build_key(const fbg_program* p, const char* what, int mode);
+std::shared_ptr<const JitHost> jit_host_get(const std::string& key);
+void jit_host_put(const std::string& key, std::shared_ptr<const JitHost> v);
+std::shared_ptr<const InterpHost> interp_host_get(const std::string& key);
+void interp_host_put(const std::string& key, std::shared_ptr<const InterpHost> v);
+void host_caches_clear();
+// hits, misses and entries of the compile, specialised-build and
+// interpreter-build caches
+void host_cache_stats(uint64_t out[9]);
+
+}  // namespace fbg

@@ -85,6 +85,7 @@ class SrcGen {
   std::string generate(int mode, int block, int minb);
   std::string unit_fn_count(const std::string& fname);
   std::string unit_fn_table(const std::string& fname);
+  std::string unit_fn_enum(const std::string& fname);
 
  private:
   const LutProgram& p;
@@ -104,7 +105,14 @@ class SrcGen {
     std::vector<std::string> deps;
     int level = 0;
     bool uni = false;
+    int copy = -1;                 // copy of the unrolled level, or -1
+    int tt = 0;                    // lop3 immLut over args (arg 0 = bit 2 of the index)
+    std::string args[3];           // operand expressions: names or 32-bit immediates
   };
+  static std::string call_text(const CallInfo& ci) {
+    return "fbg_lop3<" + std::to_string(ci.tt) + ">(" + ci.args[0] + ", " + ci.args[1] + ", " + ci.args[2] + ")";
+  }
+  bool merged_ = false;
   std::unordered_map<std::string, CallInfo> calls_;
   std::unordered_set<std::string> live_;
   bool is_live(const std::string& name) const { return live_.count(name) != 0; }
@@ -338,6 +346,11 @@ class SrcGen {
           if (!fs[q].is_const) ci.deps.push_back(fs[q].name);
         ci.level = copy >= 0 ? unroll_lv : lu.level;
         ci.uni = uni;
+        ci.copy = copy;
+        ci.tt = tt;
+        ci.args[0] = expr(fs[0]);
+        ci.args[1] = expr(fs[kf > 1 ? 1 : 0]);
+        ci.args[2] = expr(fs[kf > 2 ? 2 : 0]);
         calls_[name] = std::move(ci);
       }
     }
@@ -419,22 +432,12 @@ class SrcGen {
   // pruning off, the level conjunctions feed no vote); they are neither
   // emitted nor counted in ops / uops.
   void mark_live(int mode) {
-    const int last = nl - 1;
-    std::vector<std::string> stack;
-    auto root = [&](const Val& v, int copy) {
-      for (int s = 0; s < nreg; s++) {
-        Sym x = operand_sym(v, s, copy);
-        if (!x.is_const) stack.push_back(x.name);
-      }
-    };
-    if (unroll_lv >= 0)
-      for (int c = 0; c < (1 << unroll_bits); c++) root(p.out, c);
-    else
-      root(p.out, -1);
-    if (p.levels[0].has_acc && (mode == 0 || last > 0)) root(p.levels[0].acc, -1);
-    if (nl > 1 && p.levels[1].has_acc && last > 1) root(p.levels[1].acc, -1);
-    for (int lv = 2; lv < last; lv++)
-      if (lv != unroll_lv && p.levels[(size_t)lv].has_acc) root(p.levels[(size_t)lv].acc, -1);
+    mark_live_from_roots(mode);
+    merge_chains(mode);
+  }
+
+  void mark_live_from_roots(int mode) {
+    std::vector<std::string> stack = root_names(mode);
     live_.clear();
     while (!stack.empty()) {
       std::string nm = stack.back();
@@ -457,8 +460,127 @@ class SrcGen {
     std::vector<std::vector<std::string>> out(ustmt.size());
     for (size_t c = 0; c < ustmt.size(); c++)
       for (size_t t = 0; t < ustmt[c].size(); t++)
-        if (is_live(ustmt_name[c][t])) out[c].push_back(ustmt[c][t]);
+        if (is_live(ustmt_name[c][t]))
+          out[c].push_back("const fbg_u32 " + ustmt_name[c][t] + " = " + call_text(calls_.at(ustmt_name[c][t])) + ";");
     return out;
+  }
+
+  // The value names the kernel reads outside lop3 calls: the result words of
+  // every copy and the partial conjunctions of the levels whose votes the
+  // kernel of `mode` emits (the roots of mark_live).
+  std::vector<std::string> root_names(int mode) const {
+    const int last = nl - 1;
+    std::vector<std::string> r;
+    auto root = [&](const Val& v, int copy) {
+      for (int s = 0; s < nreg; s++) {
+        Sym x = operand_sym(v, s, copy);
+        if (!x.is_const) r.push_back(x.name);
+      }
+    };
+    if (unroll_lv >= 0)
+      for (int c = 0; c < (1 << unroll_bits); c++) root(p.out, c);
+    else
+      root(p.out, -1);
+    if (p.levels[0].has_acc && (mode == 0 || last > 0)) root(p.levels[0].acc, -1);
+    if (nl > 1 && p.levels[1].has_acc && last > 1) root(p.levels[1].acc, -1);
+    for (int lv = 2; lv < last; lv++)
+      if (lv != unroll_lv && p.levels[(size_t)lv].has_acc) root(p.levels[(size_t)lv].acc, -1);
+    return r;
+  }
+
+  // Constant folding leaves many lop3 calls with one or two distinct
+  // operands (a loop letter of an unrolled copy, a register's constant, a
+  // repeated input), so a chain of such calls may fit fewer 3-input LUTs
+  // than the mapping before folding found.  A live call Y that is not read
+  // outside lop3 calls, whose every reader X is a live call of the same
+  // level (and copy), is merged into all its readers when, for each, the
+  // operands of X and Y together are at most three: X's truth table is
+  // recomputed over them and Y disappears (one lop3 fewer; a reader never
+  // grows).  Repeated until no merge applies.  Results are unchanged (each
+  // reader computes the same function of the operands).
+  static int merged_tt(const CallInfo& X, const CallInfo& Y, const std::string& yn, const std::vector<std::string>& ops) {
+    auto val = [&](const std::vector<int>& v, const std::string& a) {
+      return v[(size_t)(std::find(ops.begin(), ops.end(), a) - ops.begin())];
+    };
+    const size_t m = ops.size();
+    // slot q < m of the new call holds operand q; slots q >= m repeat
+    // operand 0, so only the first m slot bits select the value
+    int tt = 0;
+    for (int idx = 0; idx < 8; idx++) {
+      std::vector<int> v(m, 0);
+      for (size_t q = 0; q < m; q++) v[q] = (idx >> (2 - (int)q)) & 1;
+      const int ybit = (Y.tt >> ((val(v, Y.args[0]) << 2) | (val(v, Y.args[1]) << 1) | val(v, Y.args[2]))) & 1;
+      auto xin = [&](const std::string& a) { return a == yn ? ybit : val(v, a); };
+      const int xbit = (X.tt >> ((xin(X.args[0]) << 2) | (xin(X.args[1]) << 1) | xin(X.args[2]))) & 1;
+      tt |= xbit << idx;
+    }
+    return tt;
+  }
+
+  static std::vector<std::string> merged_ops(const CallInfo& X, const CallInfo& Y, const std::string& yn) {
+    std::vector<std::string> ops;
+    auto add = [&](const std::string& a) {
+      if (std::find(ops.begin(), ops.end(), a) == ops.end()) ops.push_back(a);
+    };
+    for (const std::string& a : X.args)
+      if (a != yn) add(a);
+    for (const std::string& a : Y.args) add(a);
+    return ops;
+  }
+
+  void merge_chains(int mode) {
+    if (merged_) return;
+    merged_ = true;
+    for (;;) {
+      std::unordered_set<std::string> roots;
+      for (const std::string& r : root_names(mode)) roots.insert(r);
+      // readers of every live call (each reader once)
+      std::unordered_map<std::string, std::vector<std::string>> readers;
+      std::vector<std::string> order(live_.begin(), live_.end());
+      std::sort(order.begin(), order.end());   // a fixed order: the same source on every build
+      for (const std::string& nm : order) {
+        const CallInfo& ci = calls_.at(nm);
+        for (int q = 0; q < 3; q++) {
+          const std::string& a = ci.args[q];
+          if (calls_.count(a) && (q == 0 || (a != ci.args[0] && (q == 1 || a != ci.args[1]))))
+            readers[a].push_back(nm);
+        }
+      }
+      std::unordered_set<std::string> touched, gone;
+      bool changed = false;
+      for (const std::string& yn : order) {
+        if (roots.count(yn) || touched.count(yn)) continue;
+        auto rit = readers.find(yn);
+        if (rit == readers.end() || rit->second.empty()) continue;
+        const CallInfo& Y = calls_.at(yn);
+        bool ok = true;
+        for (const std::string& xn : rit->second) {
+          const CallInfo& X = calls_.at(xn);
+          ok = ok && !touched.count(xn) && !gone.count(xn) && X.level == Y.level && X.copy == Y.copy &&
+               merged_ops(X, Y, yn).size() <= 3;
+        }
+        if (!ok) continue;
+        for (const std::string& xn : rit->second) {
+          CallInfo& X = calls_.at(xn);
+          const std::vector<std::string> ops = merged_ops(X, Y, yn);
+          CallInfo nx = X;
+          nx.tt = merged_tt(X, Y, yn, ops);
+          for (int q = 0; q < 3; q++) nx.args[q] = ops[(size_t)q < ops.size() ? (size_t)q : 0];
+          nx.deps.clear();
+          for (const std::string& a : ops)
+            if (a.compare(0, 2, "0x") != 0) nx.deps.push_back(a);
+          nx.uni = X.uni && Y.uni;
+          X = nx;
+          touched.insert(xn);
+        }
+        touched.insert(yn);
+        gone.insert(yn);
+        changed = true;
+      }
+      if (!changed) break;
+      // liveness again from the roots: merged-away calls are no longer read
+      mark_live_from_roots(mode);
+    }
   }
 
   void declare_level(int lv, const std::string& ind) {
@@ -474,7 +596,7 @@ class SrcGen {
     for (int i = li.lut_begin; i < li.lut_end; i++)
       for (int s = 0; s < nreg; s++)
         if (!code[(size_t)i][(size_t)s].empty() && is_live(lut_name(i, s)))
-          o << ind << lut_name(i, s) << " = " << code[(size_t)i][(size_t)s] << ";\n";
+          o << ind << lut_name(i, s) << " = " << call_text(calls_.at(lut_name(i, s))) << ";\n";
   }
 
   std::string any_nonzero(const Val& v) const {
@@ -593,6 +715,110 @@ std::string SrcGen::unit_fn_count(const std::string& fname) {
   return o.str();
 }
 
+// Per-item device function of enumerate mode (layout of enum_order: the item
+// (unit u, warp slice w) is the interval of assignment integers
+// [(u << wb | w) << (n - ub - wb), +2^(n - ub - wb)), its loop letters come
+// next below the warp slice in the order of the loop nest, then the lane,
+// register and in-word bits).  The warp writes the models of the item in
+// ascending order from models[base]: per innermost execution (per copy of an
+// unrolled level) the lanes' popcounts are scanned across the warp, and each
+// lane writes its models at its offset; nothing at or beyond `cap` is
+// written, and the item stops once the running offset reaches it.
+std::string SrcGen::unit_fn_enum(const std::string& fname) {
+  auto vars = used_vars();
+  const int tvalid = 1 << (L.lane_bits + L.warp_bits);
+  const int last = nl - 1;
+  const int wb = L.warp_bits;
+  const int lane_mask = (1 << L.lane_bits) - 1;
+  o << "__device__ __noinline__ void " << fname
+    << "(fbg_u64 u, fbg_u32 tb, fbg_u64 base, fbg_u64* models, fbg_u64 cap, fbg_u64* lvl) {\n";
+  o << "  const fbg_u32 tm = (tb < " << tvalid << "u) ? " << hex32(valid_mask()) << " : 0u;\n";
+  o << "  const fbg_u32 lane = threadIdx.x & 31u;\n";
+  // the assignment integer of this lane's tile at loop coordinates 0
+  std::string jt = "((fbg_u64)(tb & " + std::to_string(lane_mask) + "u) << " + std::to_string(5 + L.r) + ")";
+  if (wb > 0) jt += " | ((fbg_u64)(tb >> 5) << " + std::to_string(L.n - L.unit_bits - wb) + ")";
+  if (L.unit_bits > 0) jt += " | (u << " + std::to_string(L.first_unit_pos()) + ")";
+  o << "  const fbg_u64 J0 = " << jt << ";\n";
+  o << "  fbg_u64 off = base;\n";
+  if (counters_) o << "  lvl[0]++;\n";
+  var_words(vars[0], "tb", L.first_lane_pos(), "  ", false);
+  declare_level(0, "  ");
+  luts(0, "  ");
+  if (p.levels[0].has_acc)
+    o << "  if (!__any_sync(FBG_FULL, " << any_nonzero(p.levels[0].acc) << ")) return;\n";
+  if (counters_) o << "  lvl[1]++;\n";
+  var_words(vars[1], "u", L.first_unit_pos(), "  ", true);
+  declare_level(1, "  ");
+  luts(1, "  ");
+  if (p.levels[1].has_acc && last > 1)
+    o << "  if (!__any_sync(FBG_FULL, " << any_nonzero(p.levels[1].acc) << ")) return;\n";
+  std::string ind = "  ";
+  std::string jexpr = "J0";
+  for (int lv = 2; lv < nl; lv++) {
+    if (lv == unroll_lv) break;
+    std::string iv = "i" + std::to_string(lv);
+    o << ind << "for (fbg_u32 " << iv << " = 0; " << iv << " < " << (1u << L.loop_bits[(size_t)(lv - 2)]) << "u; ++" << iv << ") {\n";
+    ind += "  ";
+    if (counters_) o << ind << "lvl[" << lv << "]++;\n";
+    var_words(vars[(size_t)lv], iv, L.loop_pos(lv - 2), ind, false);
+    declare_level(lv, ind);
+    luts(lv, ind);
+    if (p.levels[(size_t)lv].has_acc && lv < last)
+      o << ind << "if (!__any_sync(FBG_FULL, " << any_nonzero(p.levels[(size_t)lv].acc) << ")) continue;\n";
+    jexpr += " | ((fbg_u64)" + iv + " << " + std::to_string(L.loop_pos(lv - 2) - wb) + ")";
+  }
+  // compaction of one innermost execution (one copy): words w[s] of this lane
+  auto compact = [&](const std::vector<std::string>& w, const std::string& jbase, const std::string& in) {
+    o << in << "{\n";
+    o << in << "  const fbg_u32 ew[" << nreg << "] = {";
+    for (int s2 = 0; s2 < nreg; s2++) o << (s2 ? ", " : "") << "(" << w[(size_t)s2] << ") & tm";
+    o << "};\n";
+    o << in << "  fbg_u32 c = 0;\n";
+    o << in << "  #pragma unroll\n";
+    o << in << "  for (int s = 0; s < " << nreg << "; s++) c += (fbg_u32)__popc(ew[s]);\n";
+    o << in << "  fbg_u32 incl = c;\n";
+    o << in << "  #pragma unroll\n";
+    o << in << "  for (int d = 1; d < 32; d <<= 1) {\n";
+    o << in << "    const fbg_u32 y = __shfl_up_sync(FBG_FULL, incl, d);\n";
+    o << in << "    if (lane >= (fbg_u32)d) incl += y;\n";
+    o << in << "  }\n";
+    o << in << "  const fbg_u32 wtot = __shfl_sync(FBG_FULL, incl, 31);\n";
+    o << in << "  fbg_u64 at = off + (incl - c);\n";
+    o << in << "  const fbg_u64 J = " << jbase << ";\n";
+    o << in << "  for (int s = 0; s < " << nreg << " && at < cap; s++) {\n";
+    o << in << "    fbg_u32 x = ew[s];\n";
+    o << in << "    while (x && at < cap) {\n";
+    o << in << "      const int b = __ffs((int)x) - 1;\n";
+    o << in << "      x &= x - 1u;\n";
+    o << in << "      models[at++] = J | ((fbg_u64)s << 5) | (fbg_u64)b;\n";
+    o << in << "    }\n";
+    o << in << "  }\n";
+    o << in << "  off += wtot;\n";
+    o << in << "}\n";
+    o << in << "if (off >= cap) return;\n";
+  };
+  if (unroll_lv >= 0) {
+    if (counters_) o << ind << "lvl[" << unroll_lv << "]++;\n";
+    const std::vector<std::vector<std::string>> lst = live_ustmt();
+    for (int c = 0; c < (1 << unroll_bits); c++) {
+      for (auto& st : lst[(size_t)c]) o << ind << st << "\n";
+      std::vector<std::string> w;
+      for (int s2 = 0; s2 < nreg; s2++) w.push_back(operand(p.out, s2, c));
+      compact(w, jexpr + " | ((fbg_u64)" + std::to_string(c) + "u << " + std::to_string(unroll_base - wb) + ")", ind);
+    }
+  } else {
+    std::vector<std::string> w;
+    for (int s2 = 0; s2 < nreg; s2++) w.push_back(operand(p.out, s2));
+    compact(w, jexpr, ind);
+  }
+  for (int lv = (unroll_lv >= 0 ? unroll_lv - 1 : last); lv >= 2; lv--) {
+    ind.resize(ind.size() - 2);
+    o << ind << "}\n";
+  }
+  o << "}\n";
+  return o.str();
+}
+
 // Per-unit device function of truth-table mode: stores every tile of unit u;
 // tiles under a level whose partial conjunction is zero store zeros.
 std::string SrcGen::unit_fn_table(const std::string& fname) {
@@ -686,9 +912,45 @@ std::string SrcGen::unit_fn_table(const std::string& fname) {
 // Table mode: a block pulls whole units (its stores are dense and the work
 // per unit is even).
 std::string SrcGen::generate(int mode, int block, int minb) {
-  const char* kname = mode == 0 ? "fbg_jit_count" : "fbg_jit_table";
-  if (mode == 0) unit_fn_count("fbg_unit_count");
+  const char* kname = mode == 0 ? "fbg_jit_count" : mode == 1 ? "fbg_jit_table" : "fbg_jit_enum";
+  if (mode == 0 || mode == 2) unit_fn_count("fbg_unit_count");
   else unit_fn_table("fbg_unit_table");
+  if (mode == 2) {
+    // Enumerate mode, two passes of one kernel over the items t = u << wb | w
+    // (ascending t = ascending assignment integers): with P.models null each
+    // item's number of models goes to P.unit_counts[t]; with P.models set
+    // (P.unit_offsets = the exclusive prefix of those counts) each item
+    // writes its models from its offset, skipping items at or past P.cap.
+    unit_fn_enum("fbg_unit_enum");
+    const int wb = L.warp_bits;
+    o << "extern \"C\" __global__ void __launch_bounds__(" << block << ", " << minb << ") " << kname << "(FbgLaunch P) {\n";
+    o << "  fbg_u64 lvl[" << nl << "] = {0};\n";
+    o << "  const fbg_u32 lane = threadIdx.x & 31u;\n";
+    o << "  const fbg_u64 chunk = P.chunk ? P.chunk : 1ull;\n";
+    o << "  const fbg_u64 items = (P.unit_end - P.unit_begin) << " << wb << ";\n";
+    o << "  const fbg_u32 full2 = " << (split_bits > 0 ? (1u << L.loop_bits[0]) : 0u) << "u;\n";
+    o << "  for (;;) {\n";
+    o << "    fbg_u64 t = fbg_next_items_warp(P, chunk);\n";
+    o << "    if (t >= items) break;\n";
+    o << "    const fbg_u64 e = t + chunk < items ? t + chunk : items;\n";
+    o << "    for (; t < e; ++t) {\n";
+    o << "      const fbg_u64 v = t >> " << wb << ";\n";
+    o << "      const fbg_u32 tb = lane | ((fbg_u32)(t & " << ((1u << wb) - 1u) << "u) << 5);\n";
+    o << "      if (!P.models) {\n";
+    o << "        const fbg_u64 c = fbg_warp_sum(fbg_unit_count(P.unit_begin + v, P.unit_begin + v + 1, tb, lvl, 0u, full2));\n";
+    o << "        if (lane == 0u) P.unit_counts[t] = c;\n";
+    o << "      } else {\n";
+    o << "        const fbg_u64 b = P.unit_offsets[t];\n";
+    o << "        if (b < P.cap) fbg_unit_enum(P.unit_begin + v, tb, b, P.models, P.cap, lvl);\n";
+    o << "      }\n";
+    o << "    }\n";
+    o << "  }\n";
+    o << "  if (P.iters && lane == 0u) {\n";
+    o << "    for (int l = 0; l < " << nl << "; l++) if (lvl[l]) atomicAdd(P.iters + l, lvl[l]);\n";
+    o << "  }\n";
+    o << "}\n";
+    return o.str();
+  }
   o << "extern \"C\" __global__ void __launch_bounds__(" << block << ", " << minb << ") " << kname << "(FbgLaunch P) {\n";
   if (mode == 0) {
     o << "  fbg_u64 lvl[" << nl << "] = {0};\n";

@@ -86,6 +86,30 @@ std::vector<int> identity_order(int n) {
   return o;
 }
 
+// Enumerate-mode order: the layout of make_layout(n, prm, .) with the
+// letters placed so that the work item (unit u, warp slice w) holds the
+// assignment integers with top bits u, w (a contiguous, ascending interval)
+// and its loop nest runs through them in ascending order: unit positions
+// take the top letters, warp positions the letters just below them, the
+// loop positions the next ones, and lanes, registers and in-word bits keep
+// their own letters.
+std::vector<int> enum_order(int n, const LayoutParams& prm) {
+  const Layout S = make_layout(n, prm, identity_order(n));
+  const int wb = S.warp_bits, ub = S.unit_bits;
+  const int w0 = S.first_warp_pos();           // first warp position
+  const int l0 = w0 + wb;                      // first loop position
+  std::vector<int> var_at((size_t)n);
+  for (int p = 0; p < n; p++) {
+    int v = p;
+    if (p >= w0 && p < l0) v = n - ub - wb + (p - w0);   // warp slice: just below the units
+    else if (p >= l0 && p < n - ub) v = p - wb;           // loops: below the warp slice
+    var_at[(size_t)p] = v;
+  }
+  std::vector<int> order((size_t)n);
+  for (int t = 0; t < n; t++) order[(size_t)t] = var_at[(size_t)(n - 1 - t)];
+  return order;
+}
+
 // support of every DAG node as a 64-bit variable set
 static std::vector<uint64_t> supports(const FormDag& d) {
   std::vector<uint64_t> s((size_t)d.size(), 0);

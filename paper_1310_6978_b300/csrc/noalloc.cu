@@ -71,8 +71,8 @@ extern "C" fbg_status fbg_count_noalloc(fbg_program* p, void* stream, uint64_t* 
     lp.warps_log2 = FBG_INTERP_WARPS_LOG2;
     lp.unit_bits_max = (int)p->opt_unit_bits;
     lp.loop_level_bits = (int)p->opt_loop_level_bits;
-    Layout L = make_layout(p->n, lp, p->opt_search ? search_order(p->g) : identity_order(p->n));
-    LutProgram prog = lower_and_map(p->g, L);
+    Layout L = make_layout(p->n, lp, p->opt_search ? search_order(*p->g) : identity_order(p->n));
+    LutProgram prog = lower_and_map(*p->g, L);
     if (!p->opt_prune)
       for (auto& li : prog.levels) li.has_acc = false;
     code = emit_bytecode(prog);

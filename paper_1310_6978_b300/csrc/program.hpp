@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -77,18 +78,30 @@ int device_sms();
 
 }  // namespace fbg
 
+namespace fbg {
+// The parsed and grounded theory of one (text, domain size): immutable once
+// built and shared by every program compiled from the same text
+// (compile_cached keeps recent ones).
+struct Compiled {
+  Theory th;
+  Grounded g;
+};
+std::shared_ptr<const Compiled> compile_cached(const std::string& text, int k);   // throws CompileError
+}  // namespace fbg
+
 struct fbg_program {
   std::string text;
   int k = 1;
   int n = 0;
-  fbg::Theory th;
-  fbg::Grounded g;
+  std::shared_ptr<const fbg::Compiled> compiled;
+  const fbg::Theory* th = nullptr;      // = &compiled->th
+  const fbg::Grounded* g = nullptr;     // = &compiled->g
   // options (fbg_set_option)
   int64_t opt_engine = FBG_ENGINE_AUTO, opt_prune = 1, opt_regs_log2 = 2, opt_warps_log2 = 3, opt_unit_bits = 13,
           opt_loop_level_bits = 4, opt_search = 1, opt_min_blocks = 2, opt_stats = 0, opt_inner_bits = 0,
           opt_split_items = 0;
   fbg::InterpBuild ib[2];   // [0] count layout, [1] identity layout (tables, model lists)
-  fbg::JitBuild jb[2];      // [0] count kernel, [1] truth-table kernel
+  fbg::JitBuild jb[3];      // [0] count kernel, [1] truth-table kernel, [2] enumerate kernel
   unsigned long long* d_scratch = nullptr;
   bool scratch_clean = false;   // counters of self-resetting count launches are zero
   size_t scratch_words = 0;

@@ -155,7 +155,7 @@ void fbg_server::tick() {
       bool needs_slot = r->mode == FBG_MODE_COUNT;
       if (needs_slot && free_slots.empty()) break;
       // estimate before building; a request larger than the whole budget still runs alone
-      uint64_t est = (uint64_t)r->prog->g.dag.size() * 64 + (r->mode == FBG_MODE_ENUMERATE ? r->cap * 8 : 0);
+      uint64_t est = (uint64_t)r->prog->g->dag.size() * 64 + (r->mode == FBG_MODE_ENUMERATE ? r->cap * 8 : 0);
       if (mem_used && mem_used + est > opt.mem_budget_bytes) break;
       pending.pop_front();
       fbg_status s = admit_locked(r);

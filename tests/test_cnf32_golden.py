@@ -86,3 +86,63 @@ def test_seed2_model_found_by_dpll_is_an_oracle_model():
     j = sum(1 << (v - 1) for v, val in a.items() if val)   # unassigned letters: 0
     assert oracle.Theory(wl.text, wl.k).eval(j) == 1
     assert int(_golden("cnf32_seed2.txt")["count"]) >= 1
+
+
+def _count_models(cl, nvars):
+    """Exact model count by DPLL branching with unit propagation: a branch
+    whose clauses are all satisfied counts 2^(unassigned letters).  Shares
+    nothing with the oracle (no formula text, no evaluation per point)."""
+    def rec(clauses, assigned):
+        changed = True
+        clauses = [list(c) for c in clauses]
+        assigned = dict(assigned)
+        while changed:
+            changed = False
+            nxt = []
+            for c in clauses:
+                free, sat = [], False
+                for lit in c:
+                    v = assigned.get(abs(lit))
+                    if v is None:
+                        free.append(lit)
+                    elif v == (lit > 0):
+                        sat = True
+                        break
+                if sat:
+                    continue
+                if not free:
+                    return 0
+                if len(free) == 1:
+                    assigned[abs(free[0])] = free[0] > 0
+                    changed = True
+                nxt.append(free)
+            clauses = nxt
+        if not clauses:
+            return 1 << (nvars - len(assigned))
+        # branch on the most frequent free letter
+        freq = {}
+        for c in clauses:
+            for lit in c:
+                freq[abs(lit)] = freq.get(abs(lit), 0) + 1
+        v = max(freq, key=lambda x: (freq[x], -x))
+        return rec(clauses, {**assigned, v: True}) + rec(clauses, {**assigned, v: False})
+    return rec(cl, {})
+
+
+def test_dpll_counter_on_small_formulas_matches_brute_force():
+    import itertools
+    for seed in (1, 2, 3):
+        wl = W.cnf3(12, seed, 2.0)
+        cl = _clauses(wl.text)
+        brute = sum(all(any((bits[abs(l) - 1] == 1) == (l > 0) for l in c) for c in cl)
+                    for bits in itertools.product((0, 1), repeat=12))
+        assert _count_models(cl, 12) == brute
+
+
+def test_dense_ratio2_seed3_count_equals_dpll_count():
+    # the dense table of the benchmark (ratio 2, m = 64, seed 3): the oracle's
+    # stored count equals an exact DPLL model count of the clause list
+    wl = W.cnf3(32, 3, 2.0)
+    cl = _clauses(wl.text)
+    assert len(cl) == 64
+    assert int(_golden("cnf32_r2_seed3.txt")["count"]) == _count_models(cl, 32) == 624090

@@ -73,11 +73,18 @@ def test_count_and_table_small(wl, engine, li):
     assert np.array_equal(gpu_table(p), th.table())
 
 
+ENUM_LAYOUTS = LAYOUTS[:3] + [{L.OPT_INNER_BITS: 3, L.OPT_UNIT_BITS: 3}]
+
+
 @pytest.mark.parametrize("wl", SMALL, ids=lambda w: f"{w.family}{w.param}n{w.n}")
 @pytest.mark.parametrize("cap", [0, 5, 1 << 20])
-def test_enumerate_small(wl, cap):
+@pytest.mark.parametrize("engine", ["jit", "interp"])
+@pytest.mark.parametrize("li", range(len(ENUM_LAYOUTS)))
+def test_enumerate_small(wl, cap, engine, li):
+    if engine == "interp" and li:
+        pytest.skip("the interpreter's model lists use its own fixed layout")
     th = oracle.Theory(wl.text, wl.k)
-    p = F.compile(wl.text, wl.k)
+    p = program(wl, engine, ENUM_LAYOUTS[li])
     buf = torch.full((max(1, cap),), -1, dtype=torch.int64, device="cuda")
     total, written = p.enumerate_models(buf, cap)
     om, ot = th.models(cap)
@@ -86,6 +93,41 @@ def test_enumerate_small(wl, cap):
     assert np.array_equal(got, om)
     if cap > written:   # nothing written past the models
         assert bool((buf[written:] == -1).all())
+
+
+@pytest.mark.parametrize("cap", [1, 1000, 1 << 20])
+def test_enumerate_cap_cuts_inside_items(cap):
+    """Caps that end inside a work item, inside one warp's write and at the
+    exact total: posets on 5 points (4231 models, n = 25) and 3-CNF n = 22."""
+    for wl in (W.posets(5), W.cnf3(22, 7, 2.0)):
+        th = oracle.Theory(wl.text, wl.k)
+        om, ot = th.models(cap)
+        for opts in ({}, {L.OPT_REGS_LOG2: 1, L.OPT_WARPS_LOG2: 1, L.OPT_UNIT_BITS: 4}):
+            p = program(wl, "jit", opts)
+            buf = torch.full((cap + 7,), -1, dtype=torch.int64, device="cuda")
+            total, written = p.enumerate_models(buf, cap)
+            assert total == ot and written == len(om) == min(cap, ot)
+            assert np.array_equal(buf[:written].cpu().numpy().view(np.uint64), om)
+            assert bool((buf[written:] == -1).all())
+
+
+def test_enumerate_n36_first_million_against_oracle():
+    """Transitive relations on 6 points (n = 36): the first 10^6 models of
+    9,415,189 in ascending j from the specialised kernel equal the
+    interpreter's list; the oracle checks sampled models, the range before
+    the first and sampled gaps between consecutive models (no model missed)."""
+    import oracle_checks as OC
+    wl = W.TRANSITIVE6
+    cap = 1_000_000
+    lists = []
+    for engine in ("jit", "interp"):
+        p = program(wl, engine)
+        buf = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
+        total, written = p.enumerate_models(buf, cap)
+        assert total == C.count_transitive_backtrack(6) and written == cap
+        lists.append(buf.cpu().numpy().view(np.uint64).copy())
+    assert np.array_equal(lists[0], lists[1])
+    OC.check_models(wl, [int(x) for x in lists[0]], total, cap, np.random.default_rng(36), samples=3000, gaps=40)
 
 
 def test_poset3_config():
@@ -210,6 +252,28 @@ def test_cnf32_satisfiable_table_bit_exact():
     wl = W.cnf3(32, 2)
     gold = _golden("cnf32_seed2.txt")
     p = F.compile(wl.text, wl.k)
+    table = torch.empty(p.table_words(), dtype=torch.int64, device="cuda")
+    p.truth_table(table)
+    torch.cuda.synchronize()
+    host = table.cpu().numpy().view(np.uint64)
+    assert int(np.bitwise_count(host).sum()) == int(gold["count"])
+    assert hashlib.sha256(host.astype("<u8").tobytes()).hexdigest() == gold["sha256"]
+    assert p.count() == int(gold["count"])
+    q = F.compile(wl.text, wl.k).set_option(L.OPT_ENGINE, L.ENGINE_INTERP)
+    assert q.count() == int(gold["count"])
+
+
+@pytest.mark.parametrize("prune", [1, 0])
+def test_cnf32_dense_table_bit_exact(prune):
+    """3-CNF, n = 32, ratio 2 (m = 64), seed 3: a table with 624,090 models
+    whose level conjunctions prune far less.  The whole 512 MiB table, with
+    pruning and without (every block evaluated), equals the oracle's
+    evaluation of all 2^32 assignments (tests/golden/cnf32_r2_seed3.txt), and
+    so do the counts of both engines."""
+    import hashlib
+    wl = W.cnf3(32, 3, 2.0)
+    gold = _golden("cnf32_r2_seed3.txt")
+    p = F.compile(wl.text, wl.k).set_option(L.OPT_PRUNE, prune)
     table = torch.empty(p.table_words(), dtype=torch.int64, device="cuda")
     p.truth_table(table)
     torch.cuda.synchronize()
