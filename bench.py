@@ -465,7 +465,9 @@ def run_batched(args, torch, F, L):
     mix = W.batch_mix(4096, 2)[:args.batch_formulas]
     progs = [F.compile(w.text, w.k) for w in mix]
     stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
     b = F.Batch(progs, use_graph=True)
+    t_create = time.perf_counter() - t0         # plans, NVRTC compiles (worker pool), graph capture
     for _ in range(3):
         b.run(stream)
     counts = b.results(stream)
@@ -492,6 +494,21 @@ def run_batched(args, torch, F, L):
     single_counts = [p.count(stream) for p in singles]
     t_single = time.perf_counter() - t0
     assert single_counts == [int(x) for x in counts]
+    # plain launches without Python or synchronisation per formula: one count
+    # launch per formula issued back to back from C (fbg_count_each)
+    dev = torch.zeros(len(singles), dtype=torch.int64, device="cuda")
+    F.count_each(singles, dev, stream)
+    stream.synchronize()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        e2.record(stream)
+        F.count_each(singles, dev, stream)
+        e3.record(stream)
+    stream.synchronize()
+    t_plain_wall = time.perf_counter() - t0
+    t_plain = e2.elapsed_time(e3) / 1e3
+    assert F.read_counts(dev) == [int(x) for x in counts]
     small = [i for i, w in enumerate(mix) if w.n <= 20]
     sb = F.Batch([progs[i] for i in small], use_graph=True)
     for _ in range(3):
@@ -514,6 +531,11 @@ def run_batched(args, torch, F, L):
     return {"formulas": len(mix), "specialized_programs": info["specialized"],
             "specialized_formulas": int(sum(kinds)), "assignments": assign, "value": assign / t_batch / 1e9, "unit": "Gassign/s",
             "ms": t_batch * 1e3, "per_formula_ms": t_single * 1e3, "speedup_vs_per_formula": t_single / t_batch,
+            "create_s": t_create,
+            "plain_launches": {"ms": t_plain * 1e3, "wall_ms": t_plain_wall * 1e3, "speedup": t_plain / t_batch,
+                               "basis": "one count launch per formula issued back to back from C (fbg_count_each), "
+                                        "no per-formula synchronisation; CUDA events around all of them"},
+            "per_formula_basis": "Python loop of fbg_count (launch, copy of the count, synchronisation) per formula",
             "small_n_le_20": {"formulas": len(small), "batched_ms": t_small_b * 1e3, "per_formula_ms": t_small_s * 1e3,
                               "speedup": t_small_s / t_small_b,
                               "batched_gassign_s": assign_small / t_small_b / 1e9},
@@ -571,10 +593,43 @@ def run_serving(args, torch, F, L):
         r = reqs[i]
         assert F.compile(r.workload.text, r.workload.k).count() == counts[i]
     lat.sort()
+    small = sorted(l for l, r in zip(lat, reqs) if r.workload.n <= 27)
     return {"requests": len(reqs), "rate_per_s": rate, "wall_s": wall, "p50_ms": lat[len(lat) // 2] * 1e3,
             "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))] * 1e3, "value": assign / wall / 1e9,
             "unit": "Gassign/s", "ticks": st["ticks"], "launches": st["launches"],
-            "checked_against_single_counts": len(sample), "calibration": {"requests": len(calib), "s": t_cal}}
+            "p50_ms_n_le_27": small[len(small) // 2] * 1e3 if small else None,
+            "model_lists": sum(1 for r in reqs if r.mode == "enumerate"),
+            "checked_against_single_counts": len(sample), "calibration": {"requests": len(calib), "s": t_cal},
+            "_oracle_sample": [(reqs[i].workload, counts[i]) for i in sample[:24]]}
+
+
+def oracle_check_serving(F, L, torch, sample, seed=5):
+    """CPU-baseline leg: the oracle checks a sample of the served counts --
+    all 2^n assignments up to n = 22; above, the interpreter's per-unit counts
+    (units of 2^(n-16) or more assignments) must add up to the served count
+    and three sampled units must equal the oracle's subcube counts."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(seed)
+    checked = 0
+    for wl, count in sample:
+        th = oracle.Theory(wl.text, wl.k)
+        if wl.n <= 22:
+            assert th.count_par(0, 1 << wl.n) == count, wl
+        else:
+            p = F.compile(wl.text, wl.k).set_option(L.OPT_ENGINE, L.ENGINE_INTERP)
+            p.set_option(L.OPT_UNIT_BITS, min(16, wl.n - 18))
+            vars_, nunits = p.unit_vars()
+            dev = torch.zeros(nunits, dtype=torch.int64, device="cuda")
+            p.count_units(dev)
+            uc = F.read_counts(dev)
+            assert sum(uc) == count, wl
+            mask = sum(1 << v for v in vars_)
+            for u in {0, nunits - 1, int(rng.integers(0, nunits))}:
+                vals = sum(((u >> b) & 1) << v for b, v in enumerate(vars_))
+                assert uc[u] == th.count_cube_par(mask, vals), (wl, u)
+        checked += 1
+    return checked
 
 
 # -------------------------------------------------------------------- ours --
@@ -753,7 +808,10 @@ def run_ours(args, rank, world):
     if rank != 0:
         return
     cpu = {}
+    oracle_sample = serving.pop("_oracle_sample", None) if serving else None
     if world == 1 and not args.no_cpu:
+        if oracle_sample:
+            serving["checked_against_oracle"] = oracle_check_serving(F, L, torch, oracle_sample)
         rate, cores, sample = cpu_oracle_rate(wls, args.cpu_seconds)
         one = cpu_single_thread_rate(wls)
         cpu = {"value": rate / 1e9, "unit": "Gassign/s", "cores": cores, "kind": "oracle", "sample": sample,
@@ -856,6 +914,9 @@ def main():
             leg = run_batched(args, torch, F, L)
         else:
             leg = run_serving(args, torch, F, L)
+            sample = leg.pop("_oracle_sample", None)
+            if sample and not args.no_cpu:
+                leg["checked_against_oracle"] = oracle_check_serving(F, L, torch, sample)
         print(json.dumps(leg), flush=True)
         return
     if args.impl == "reference":

@@ -105,6 +105,12 @@ enum {
                                   Pieces shorten a lone launch whose longest items end it
                                   late; launches that share the GPU already fill that tail.
                                   Read by the next fbg_schedule_units; no rebuild */
+  FBG_OPT_POPC_COST = 12,      /* JIT count kernels: the cost of one POPC in lop3 issue slots that
+                                  decides how many full adders (two lop3 each, one POPC saved)
+                                  compress an innermost execution's result words before POPC:
+                                  about (c*W - A) / (c + 2) for W words and A lop3; 0 = none,
+                                  default 4 (POPC on the XU pipe at a quarter of the lop3 rate);
+                                  0..16 */
 };
 
 typedef struct {
@@ -164,6 +170,16 @@ fbg_status fbg_count(fbg_program *prog, void *stream, uint64_t *out_count);
    overlap: issue them on one stream (or order them with events); different
    programs may run concurrently on different streams. */
 fbg_status fbg_count_async(fbg_program *prog, void *stream, uint64_t *dev_out);
+
+/*
+ * One count launch per program, back to back on `stream` (no counterpart in
+ * the paper: the plain one-launch-per-formula evaluation that the batch of
+ * fbg_batch_* is measured against): progs[i]'s count goes to dev_out[i]
+ * (caller-owned device memory, nprogs 64-bit words), as fbg_count_async
+ * would write it.  Kernels are built on first use (NVRTC or interpreter per
+ * each program's engine option).  Asynchronous; stops at the first error.
+ */
+fbg_status fbg_count_each(fbg_program **progs, size_t nprogs, void *stream, uint64_t *dev_out);
 
 /*
  * Per-unit partial counts of the count layout: unit u fixes the letters
@@ -243,6 +259,7 @@ typedef struct {
   int trials;
   int regs_log2, warps_log2, min_blocks, loop_level_bits, unit_bits;
   int inner_bits;
+  int popc_cost;
 } fbg_tune_result;
 fbg_status fbg_autotune(fbg_program *prog, void *stream, int mode, int reps, fbg_tune_result *out);
 
@@ -381,16 +398,27 @@ void fbg_batch_free(fbg_batch *batch);
 
 /*
  * Serving loop: requests (formula text, domain, count or enumerate) are
- * compiled on submission, admitted while their device memory fits the budget,
- * and evaluated in ticks; each tick runs one persistent launch over the work
- * of every admitted request (chunks of units), so requests that arrive while
- * others run join the next tick.  Partial counts stay on the device across
- * ticks.  A host thread drives the ticks on its own stream.
+ * compiled on submission, admitted while their device memory fits the budget
+ * and a slot is free, and evaluated in ticks with the interpreter kernel (no
+ * kernel compile on the serving path); each tick runs one launch over a
+ * share of the work of every admitted request (chunks of units), so requests
+ * that arrive while others run join the next tick.  Partial counts stay on
+ * the device across ticks.  A model list is tick work as well: its units are
+ * counted in the same launch, each into its own counter; in the tick that
+ * counts its last unit, a scan gives every unit its first position and one
+ * more launch (shared by all model lists finishing in that tick) writes the
+ * models in ascending j into a device buffer of `cap` words, from which the
+ * first min(cap, total) reach the result.  A host thread drives the ticks on
+ * its own stream; per-request device buffers come from the stream-ordered
+ * allocator of that stream.
  */
 typedef struct {
   uint64_t mem_budget_bytes;   /* device memory for admitted requests (0 = 1 GiB) */
-  uint64_t tick_units;         /* max units evaluated per tick (0 = automatic) */
+  uint64_t tick_units;         /* max units evaluated per tick (0 = 65536) */
   int max_inflight;            /* max admitted requests (0 = 4096) */
+  uint64_t tick_assignments;   /* assignments evaluated per tick, at least one unit per admitted
+                                  request (0 = 2^36); requests with the least remaining work go
+                                  first and finish in one tick when they fit a fair share */
 } fbg_server_options;
 
 enum { FBG_MODE_COUNT = 0, FBG_MODE_ENUMERATE = 1 };
@@ -414,8 +442,8 @@ fbg_status fbg_server_drain(fbg_server *srv, double timeout_s);
 fbg_status fbg_server_release(fbg_server *srv, uint64_t request_id);
 fbg_status fbg_server_stats(fbg_server *srv, uint64_t *ticks, uint64_t *launches, double *busy_s);
 /* diagnostics: seconds the server thread spent admitting requests (building
-   their interpreter programs), in count ticks (launch to completion) and on
-   model lists */
+   their interpreter programs), in ticks (launches to completion) and copying
+   finished model lists to the host */
 fbg_status fbg_server_profile(fbg_server *srv, double *admit_s, double *count_s, double *enum_s);
 void fbg_server_free(fbg_server *srv);
 

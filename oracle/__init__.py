@@ -66,6 +66,8 @@ def _load():
             lib.counter_transitive.restype = u64
             lib.counter_posets.argtypes = [ctypes.c_int]
             lib.counter_posets.restype = u64
+            lib.counter_posets_special.argtypes = [ctypes.c_int]
+            lib.counter_posets_special.restype = u64
             lib.counter_triangle_free.argtypes = [ctypes.c_int]
             lib.counter_triangle_free.restype = u64
             _lib = lib

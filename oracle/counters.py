@@ -176,3 +176,23 @@ def count_posets_c(k: int) -> int:
     """Partial orders on k labelled points (k <= 9), backtracking in C."""
     from . import _load
     return int(_load().counter_posets(k))
+
+
+def count_posets_special_c(k: int) -> int:
+    """Partial orders on k labelled points with an element comparable with
+    every element (k <= 9), backtracking in C."""
+    from . import _load
+    return int(_load().counter_posets_special(k))
+
+
+def count_posets_special_brute(k: int) -> int:
+    """The same by brute force over all relations on k points (k <= 4)."""
+    rel = _all_relations(k)
+    posets = relation_models(k, "poset")
+    special = np.zeros(rel.shape[0], dtype=bool)
+    for a in range(k):
+        ok = np.ones(rel.shape[0], dtype=bool)
+        for b in range(k):
+            ok &= rel[:, a, b] | rel[:, b, a]
+        special |= ok
+    return int(np.count_nonzero(posets & special))

@@ -160,14 +160,14 @@ class Program:
         self._L.check(self._L.lib.fbg_autotune(self._h, _stream_ptr(stream), mode, reps, ctypes.byref(r)))
         return {"best_ms": r.best_ms, "trials": r.trials, "regs_log2": r.regs_log2, "warps_log2": r.warps_log2,
                 "min_blocks": r.min_blocks, "loop_level_bits": r.loop_level_bits, "unit_bits": r.unit_bits,
-                "inner_bits": r.inner_bits}
+                "inner_bits": r.inner_bits, "popc_cost": r.popc_cost}
 
     def apply_shape(self, shape: dict) -> "Program":
         """Set the kernel-shape options recorded by ``autotune``."""
         L = self._L
         for key, opt in (("regs_log2", L.OPT_REGS_LOG2), ("warps_log2", L.OPT_WARPS_LOG2),
                          ("min_blocks", L.OPT_MIN_BLOCKS), ("loop_level_bits", L.OPT_LOOP_LEVEL_BITS),
-                         ("inner_bits", L.OPT_INNER_BITS),
+                         ("inner_bits", L.OPT_INNER_BITS), ("popc_cost", L.OPT_POPC_COST),
                          ("unit_bits", L.OPT_UNIT_BITS)):
             if key in shape:
                 self.set_option(opt, shape[key])
@@ -240,6 +240,14 @@ class Batch:
         return {"items": items.value, "units": units.value, "grid": grid.value, "specialized": spec.value}
 
 
+def count_each(programs, dev_out, stream=None) -> None:
+    """fbg_count_each: one count launch per program, back to back on the
+    stream, into dev_out[i] (a device int64 tensor of len(programs))."""
+    L = _L()
+    arr = (ctypes.c_void_p * len(programs))(*[p.handle.value for p in programs])
+    L.check(L.lib.fbg_count_each(arr, len(programs), _stream_ptr(stream), _ptr(dev_out)))
+
+
 def host_caches(clear: bool = False) -> dict:
     """fbg_debug_host_caches: hits, misses and entries of the host compile
     caches (optionally emptied first)."""
@@ -292,10 +300,11 @@ def nvrtc_check(body: str):
 class Server:
     """Continuous-batching request loop (fbg_server_*)."""
 
-    def __init__(self, mem_budget_bytes: int = 0, tick_units: int = 0, max_inflight: int = 0):
+    def __init__(self, mem_budget_bytes: int = 0, tick_units: int = 0, max_inflight: int = 0,
+                 tick_assignments: int = 0):
         L = _L()
         self._L = L
-        o = L.FbgServerOptions(mem_budget_bytes, tick_units, max_inflight)
+        o = L.FbgServerOptions(mem_budget_bytes, tick_units, max_inflight, tick_assignments)
         h = ctypes.c_void_p()
         L.check(L.lib.fbg_server_create(ctypes.byref(o), ctypes.byref(h)))
         self._h = h

@@ -29,7 +29,7 @@ STATUS_NAMES = ["FBG_OK", "FBG_EINVAL", "FBG_EPARSE", "FBG_ETOOBIG", "FBG_ENOMEM
 
 ENGINE_AUTO, ENGINE_JIT, ENGINE_INTERP = 0, 1, 2
 OPT_ENGINE, OPT_PRUNE, OPT_REGS_LOG2, OPT_WARPS_LOG2, OPT_UNIT_BITS, OPT_LOOP_LEVEL_BITS, OPT_SEARCH_ORDER, \
-    OPT_MIN_BLOCKS, OPT_STATS, OPT_INNER_BITS, OPT_SPLIT_ITEMS = range(1, 12)
+    OPT_MIN_BLOCKS, OPT_STATS, OPT_INNER_BITS, OPT_SPLIT_ITEMS, OPT_POPC_COST = range(1, 13)
 MODE_COUNT, MODE_ENUMERATE = 0, 1
 BATCH_GRAPH, BATCH_SPECIALIZE = 1, 2
 
@@ -47,11 +47,13 @@ class FbgExecStats(ctypes.Structure):
 
 class FbgTuneResult(ctypes.Structure):
     _fields_ = [("best_ms", ctypes.c_double), ("trials", c_int), ("regs_log2", c_int), ("warps_log2", c_int),
-                ("min_blocks", c_int), ("loop_level_bits", c_int), ("unit_bits", c_int), ("inner_bits", c_int)]
+                ("min_blocks", c_int), ("loop_level_bits", c_int), ("unit_bits", c_int), ("inner_bits", c_int),
+                ("popc_cost", c_int)]
 
 
 class FbgServerOptions(ctypes.Structure):
-    _fields_ = [("mem_budget_bytes", c_u64), ("tick_units", c_u64), ("max_inflight", c_int)]
+    _fields_ = [("mem_budget_bytes", c_u64), ("tick_units", c_u64), ("max_inflight", c_int),
+                ("tick_assignments", c_u64)]
 
 
 class FbgResult(ctypes.Structure):
@@ -75,6 +77,7 @@ _sig("fbg_set_option", c_int, c_vp, c_int, c_i64)
 _sig("fbg_program_stats", c_int, c_vp, ctypes.POINTER(FbgStats))
 _sig("fbg_count", c_int, c_vp, c_vp, ctypes.POINTER(c_u64))
 _sig("fbg_count_async", c_int, c_vp, c_vp, c_vp)
+_sig("fbg_count_each", c_int, ctypes.POINTER(c_vp), c_sz, c_vp, c_vp)
 _sig("fbg_count_noalloc", c_int, c_vp, c_vp, c_vp)
 _sig("fbg_count_range", c_int, c_vp, c_vp, c_u64, c_u64, ctypes.POINTER(c_u64))
 _sig("fbg_count_units", c_int, c_vp, c_vp, c_vp, c_u64)

@@ -59,8 +59,10 @@ int device_sms() {
     if (e_ != cudaSuccess) return cuda_error(e_, #call);  \
   } while (0)
 
-namespace {
+namespace fbg {
 
+// the interpreter's layout parameters, the variable order of a layout and the
+// removal of prune points: one recipe for every count path
 LayoutParams interp_params(const fbg_program* p) {
   LayoutParams lp;
   lp.r_max = 1;
@@ -88,6 +90,10 @@ std::vector<int> order_for(const fbg_program* p, bool count_layout) {
   if (count_layout && p->opt_search) return search_order(*p->g);
   return identity_order(p->n);
 }
+
+}  // namespace fbg
+
+namespace {
 
 fbg_status ensure_scratch(fbg_program* p, size_t words) {
   if (p->d_scratch && p->scratch_words >= words) return FBG_OK;
@@ -212,7 +218,7 @@ static std::shared_ptr<const JitHost> jit_host(fbg_program* p, int mode) {
   if (!p->opt_prune) strip_prune(h->lp);
   h->block = h->lp.layout.lane_bits < 5 ? 32 : 32 << h->lp.layout.warp_bits;
   h->src = emit_cuda_source(h->lp, mode, h->block, (int)p->opt_min_blocks, &h->ops, &h->unrolled_level,
-                            p->opt_stats != 0, &h->uops);
+                            p->opt_stats != 0, &h->uops, (int)p->opt_popc_cost);
   if (mode == 0 && p->opt_prune) {
     // items on which a conjunct over unit and warp letters is false have no
     // models: full-range counts skip them when that removes at least a
@@ -494,6 +500,10 @@ fbg_status fbg_set_option(fbg_program* p, int option, int64_t v) {
       if (v < 0 || v > 5) return bad();
       p->opt_inner_bits = v;
       break;
+    case FBG_OPT_POPC_COST:
+      if (v < 0 || v > 16) return bad();
+      p->opt_popc_cost = v;
+      break;
     case FBG_OPT_SPLIT_ITEMS:   // read by the next fbg_schedule_units; kernels stay valid
       p->opt_split_items = v ? 1 : 0;
       return FBG_OK;
@@ -570,6 +580,17 @@ fbg_status fbg_count_async(fbg_program* p, void* stream, uint64_t* dev_out) {
   if (!p || !dev_out) return set_error(FBG_EINVAL, "null argument");
   bool jit = false;
   return launch_count(p, (cudaStream_t)stream, (unsigned long long*)dev_out, nullptr, &jit);
+}
+
+fbg_status fbg_count_each(fbg_program** progs, size_t nprogs, void* stream, uint64_t* dev_out) {
+  if ((!progs || !dev_out) && nprogs) return set_error(FBG_EINVAL, "null argument");
+  for (size_t i = 0; i < nprogs; i++) {
+    if (!progs[i]) return set_error(FBG_EINVAL, "null program");
+    bool jit = false;
+    fbg_status s = launch_count(progs[i], (cudaStream_t)stream, (unsigned long long*)(dev_out + i), nullptr, &jit);
+    if (s != FBG_OK) return s;
+  }
+  return FBG_OK;
 }
 
 fbg_status fbg_unit_vars(fbg_program* p, int* vars, int max_vars, int* nvars, uint64_t* nunits) {

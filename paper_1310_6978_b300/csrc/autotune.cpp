@@ -87,6 +87,7 @@ extern "C" fbg_status fbg_autotune(fbg_program* p, void* stream, int mode, int r
       {FBG_OPT_WARPS_LOG2, {2, 3, 4}},
       {FBG_OPT_UNIT_BITS, {10, 12, 13, 14}},
       {FBG_OPT_INNER_BITS, {0, 1, 3, 4}},
+      {FBG_OPT_POPC_COST, {0, 2, 4, 8}},
   };
   auto get = [&](int opt) -> int64_t {
     switch (opt) {
@@ -95,6 +96,7 @@ extern "C" fbg_status fbg_autotune(fbg_program* p, void* stream, int mode, int r
       case FBG_OPT_MIN_BLOCKS: return p->opt_min_blocks;
       case FBG_OPT_WARPS_LOG2: return p->opt_warps_log2;
       case FBG_OPT_INNER_BITS: return p->opt_inner_bits;
+      case FBG_OPT_POPC_COST: return p->opt_popc_cost;
       default: return p->opt_unit_bits;
     }
   };
@@ -133,5 +135,6 @@ extern "C" fbg_status fbg_autotune(fbg_program* p, void* stream, int mode, int r
   out->loop_level_bits = (int)p->opt_loop_level_bits;
   out->unit_bits = (int)p->opt_unit_bits;
   out->inner_bits = (int)p->opt_inner_bits;
+  out->popc_cost = (int)p->opt_popc_cost;
   return err;
 }

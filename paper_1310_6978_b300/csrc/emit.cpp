@@ -63,9 +63,10 @@ class SrcGen {
  public:
   // counters: count level executions (lvl[]) for fbg_exec_stats; a kernel
   // built without them spends no instructions or registers on them
-  explicit SrcGen(const LutProgram& prog, bool counters = true)
-      : p(prog), L(prog.layout), nreg(1 << prog.layout.r), nl(prog.layout.nlevels()), counters_(counters),
-        split_bits(top_loop_split_bits(prog.layout)) {
+  explicit SrcGen(const LutProgram& prog, bool counters = true, int popc_cost = 4)
+      : split_bits(top_loop_split_bits(prog.layout)), p(prog), L(prog.layout), nreg(1 << prog.layout.r),
+        nl(prog.layout.nlevels()), counters_(counters) {
+    popc_cost_ = popc_cost;
     if (innermost_unrolled(L)) {
       unroll_lv = nl - 1;
       unroll_bits = L.loop_bits.back();
@@ -138,10 +139,14 @@ class SrcGen {
 
   static std::string acc_name(int k) { return k == 0 ? "ucnt" : "ucnt" + std::to_string(1 << k); }
 
-  // full adders per innermost execution: balance ALU cycles (2 per warp lop3
-  // or add) against XU cycles (8 per warp POPC) for W words and A ALU ops
-  static int full_adder_budget(int W, long long A) {
-    long long f = (4LL * W - A + 3) / 6;
+  // full adders per innermost execution: balance the ALU work (A lop3 and
+  // adds, plus two lop3 per full adder) against the POPC work of the W
+  // words, a POPC costing `cost` lop3 slots (4: the XU pipe at a quarter of
+  // the lop3 rate); each full adder saves one POPC
+  int popc_cost_ = 4;
+  int full_adder_budget(int W, long long A) const {
+    const long long c = popc_cost_;
+    long long f = (c * W - A + (c + 2) / 2) / (c + 2);
     if (f < 0) f = 0;
     if (f > W / 2) f = W / 2;
     return (int)f;
@@ -1038,8 +1043,8 @@ std::string SrcGen::generate(int mode, int block, int minb) {
 
 std::string emit_cuda_source(const LutProgram& p, int mode, int block, int minblocks,
                              std::vector<long long>* ops_per_level, int* unrolled_level, bool counters,
-                             std::vector<long long>* uniform_ops_per_level) {
-  SrcGen g(p, counters);
+                             std::vector<long long>* uniform_ops_per_level, int popc_cost) {
+  SrcGen g(p, counters, popc_cost);
   std::string src = g.generate(mode, block, minblocks);
   if (ops_per_level) *ops_per_level = g.ops;
   if (uniform_ops_per_level) *uniform_ops_per_level = g.uops;

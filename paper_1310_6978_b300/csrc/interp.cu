@@ -20,7 +20,7 @@ template <int MODE>
 __global__ void __launch_bounds__(NT) interp_kernel(const FbgInterpProg* __restrict__ progs,
                                                    const FbgWorkItem* __restrict__ items, fbg_u64 nitems,
                                                    fbg_u64* item_ctr, fbg_u64* prog_counts, fbg_u64* unit_counts,
-                                                   FbgLaunch P) {
+                                                   FbgLaunch P, const FbgSlotOut* __restrict__ slot_out) {
   extern __shared__ fbg_u64 dyn_slots[];
   __shared__ Shared S;
   Thread T;
@@ -36,13 +36,25 @@ __global__ void __launch_bounds__(NT) interp_kernel(const FbgInterpProg* __restr
     if (item >= nitems) break;
     FbgWorkItem W = items[item];
     fbg_u64 cnt = 0;
-    process_item<MODE>(S, T, progs, W, cur, alive0, P, cnt, iters);
+    if (MODE == 2 && slot_out) {
+      // the program's own offsets, model buffer and capacity
+      FbgLaunch Q = P;
+      const FbgSlotOut so = slot_out[W.prog];
+      Q.unit_begin = 0;
+      Q.unit_offsets = so.unit_offsets;
+      Q.models = so.models;
+      Q.cap = so.cap;
+      process_item<MODE>(S, T, progs, W, cur, alive0, Q, cnt, iters);
+    } else {
+      process_item<MODE>(S, T, progs, W, cur, alive0, P, cnt, iters);
+    }
     if (MODE == 0) {
       cnt = fbg_warp_sum(cnt);
       if ((threadIdx.x & 31) == 0 && cnt) {
         if (prog_counts) atomicAdd(prog_counts + W.prog, cnt);
         // per-unit counts: items of one unit each (the caller ensures it)
         if (unit_counts) atomicAdd(unit_counts + (W.unit_begin - P.unit_begin), cnt);
+        if (slot_out && (W.flags & FBG_ITEM_UNIT_COUNTS)) atomicAdd(slot_out[W.prog].unit_counts + W.unit_begin, cnt);
       }
     }
   }
@@ -110,16 +122,16 @@ static cudaError_t ensure_smem(int mode, size_t smem) {
 cudaError_t launch_interp(int mode, const FbgInterpProg* progs, const FbgWorkItem* items, unsigned long long nitems,
                           unsigned long long* item_ctr, unsigned long long* prog_counts,
                           unsigned long long* unit_counts, const FbgLaunch& P, unsigned nslots, int grid,
-                          cudaStream_t stream) {
+                          cudaStream_t stream, const FbgSlotOut* slot_out) {
   size_t smem = interp_smem_bytes(nslots);
   cudaError_t e = ensure_smem(mode, smem);
   if (e != cudaSuccess) return e;
   if (mode == 0)
-    interp_kernel<0><<<grid, NT, smem, stream>>>(progs, items, nitems, item_ctr, prog_counts, unit_counts, P);
+    interp_kernel<0><<<grid, NT, smem, stream>>>(progs, items, nitems, item_ctr, prog_counts, unit_counts, P, slot_out);
   else if (mode == 1)
-    interp_kernel<1><<<grid, NT, smem, stream>>>(progs, items, nitems, item_ctr, prog_counts, unit_counts, P);
+    interp_kernel<1><<<grid, NT, smem, stream>>>(progs, items, nitems, item_ctr, prog_counts, unit_counts, P, slot_out);
   else
-    interp_kernel<2><<<grid, NT, smem, stream>>>(progs, items, nitems, item_ctr, prog_counts, unit_counts, P);
+    interp_kernel<2><<<grid, NT, smem, stream>>>(progs, items, nitems, item_ctr, prog_counts, unit_counts, P, slot_out);
   return cudaGetLastError();
 }
 

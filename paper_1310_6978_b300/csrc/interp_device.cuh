@@ -168,7 +168,10 @@ __device__ void run_unit(Shared& S, Thread& T, fbg_u64 u, const FbgLaunch& P, fb
   for (int k = 0; k < NTILE; k++) tvalid[k] = threadIdx.x + k * NT < G.tvalid;
   set_thread_coords(T, G.unit_bits ? (u << G.first_unit_pos) : 0ull);
   fbg_u64 base = 0;
-  if (MODE == 2) base = P.unit_offsets[u - P.unit_begin];
+  if (MODE == 2) {
+    base = P.unit_offsets[u - P.unit_begin];
+    if (base >= P.cap) return;   // every model of this unit lies past the cap
+  }
   exec_level(S, T, G.lev[1]);
   if (!level_alive<MODE>(S, T, G.lev[1])) return;
   unsigned it[FBG_INTERP_MAX_LEVELS];

@@ -49,3 +49,17 @@ struct FbgWorkItem {
   unsigned int flags;
   unsigned long long unit_begin, unit_end;
 };
+
+// FbgWorkItem.flags: count pass of an item of one unit whose count also goes
+// to its program's per-unit counts (FbgSlotOut.unit_counts[unit])
+#define FBG_ITEM_UNIT_COUNTS 1u
+
+// Per-program outputs of a launch over several programs (the server's model
+// lists): per-unit counts of the count pass, and for the write pass the
+// exclusive prefix of those counts, the model buffer and its capacity.
+struct FbgSlotOut {
+  unsigned long long* unit_counts;
+  const unsigned long long* unit_offsets;
+  unsigned long long* models;
+  unsigned long long cap;
+};

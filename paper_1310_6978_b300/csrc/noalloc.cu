@@ -66,15 +66,10 @@ extern "C" fbg_status fbg_count_noalloc(fbg_program* p, void* stream, uint64_t* 
   // host-side compilation into bytecode (host memory only)
   InterpCode code;
   try {
-    LayoutParams lp;
-    lp.r_max = 1;
-    lp.warps_log2 = FBG_INTERP_WARPS_LOG2;
-    lp.unit_bits_max = (int)p->opt_unit_bits;
-    lp.loop_level_bits = (int)p->opt_loop_level_bits;
-    Layout L = make_layout(p->n, lp, p->opt_search ? search_order(*p->g) : identity_order(p->n));
+    // the layout, order and prune points of the interpreter's count build
+    Layout L = make_layout(p->n, interp_params(p), order_for(p, true));
     LutProgram prog = lower_and_map(*p->g, L);
-    if (!p->opt_prune)
-      for (auto& li : prog.levels) li.has_acc = false;
+    if (!p->opt_prune) strip_prune(prog);
     code = emit_bytecode(prog);
   } catch (CompileError& ce) {
     return set_error(FBG_ETOOBIG, ce.msg);

@@ -3,13 +3,17 @@
 // Requests (formula text, domain, count or enumerate) are compiled on the
 // submitting thread and queued.  A server thread runs ticks on its own
 // stream: it admits queued requests while their device memory fits the
-// budget and a slot is free, gives every admitted count request a share of
-// the tick's units, and evaluates all of them in ONE interpreter launch over
-// a work queue of (slot, unit range) items.  Partial counts stay in device
-// memory across ticks (one u64 per slot); a request finishes when its last
-// unit has run.  Requests arriving while a tick runs join the next tick.
-// Model lists (enumerate) run as ordered two-pass evaluations between ticks.
-// Every tick is a bounded launch: nothing runs forever on the GPU.
+// budget and a slot is free, gives every admitted request a share of the
+// tick's units, and evaluates all of them in ONE interpreter launch over a
+// work queue of (slot, unit range) items.  Partial counts stay in device
+// memory across ticks (one u64 per slot); a count request finishes when its
+// last unit has run.  A model list (enumerate) is tick work too: its units
+// are counted in the same launch, each into its own per-unit counter; in the
+// tick where its last unit is counted, a scan turns those counts into unit
+// offsets and one more launch, over every such request of the tick, writes
+// the models in ascending order into the request's device buffer.  Requests
+// arriving while a tick runs join the next tick.  Every tick is a bounded
+// launch: nothing runs forever on the GPU.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -48,6 +52,11 @@ struct Request {
   fbg_status status = FBG_EBUSY;
   uint64_t count = 0;
   std::vector<uint64_t> models;
+  // model lists: per-unit counts, their exclusive prefix, the model buffer
+  // (stream-ordered allocations of the server's stream)
+  unsigned long long* d_unit_counts = nullptr;
+  unsigned long long* d_offsets = nullptr;
+  unsigned long long* d_models = nullptr;
   double submit_s = 0, admit_s = 0, done_s = 0;
   bool done = false;
   ~Request() { fbg_program_free(prog); }
@@ -78,8 +87,14 @@ struct fbg_server {
   FbgWorkItem* h_items = nullptr;                 // pinned
   uint64_t item_cap = 0;
   std::vector<int> free_slots;
-  unsigned long long* d_models = nullptr;         // enumerate output buffer
-  size_t models_cap = 0;
+  FbgSlotOut* d_slot_out = nullptr;               // per-slot outputs of model lists
+  FbgSlotOut* h_slot_out = nullptr;               // pinned staging
+  FbgWorkItem* d_witems = nullptr;                // items of the write launch
+  std::vector<FbgWorkItem> h_wvec;
+  unsigned long long* d_scan_total = nullptr;     // scan totals (unused: the slot count has it)
+  unsigned long long* h_models = nullptr;         // pinned staging of model lists
+  size_t h_models_cap = 0;
+  uint64_t witem_cap = 0;
   // statistics
   std::atomic<uint64_t> ticks{0}, launches{0};
   double busy_s = 0;
@@ -90,6 +105,7 @@ struct fbg_server {
   void tick();
   fbg_status admit_locked(Request* r);
   void finish(Request* r, fbg_status s);
+  void release_device(Request* r);
 };
 
 namespace {
@@ -105,7 +121,15 @@ uint64_t request_mem(const fbg_program* p, int mode, uint64_t cap) {
 
 }  // namespace
 
+void fbg_server::release_device(Request* r) {
+  for (unsigned long long** q : {&r->d_unit_counts, &r->d_offsets, &r->d_models}) {
+    if (*q) cudaFreeAsync(*q, stream);
+    *q = nullptr;
+  }
+}
+
 void fbg_server::finish(Request* r, fbg_status s) {
+  release_device(r);
   r->status = s;
   r->done_s = now_s();
   r->done = true;
@@ -124,19 +148,37 @@ fbg_status fbg_server::admit_locked(Request* r) {
   if (s != FBG_OK) return s;
   r->mem = request_mem(r->prog, r->mode, r->cap);
   r->admit_s = now_s();
-  if (r->mode == FBG_MODE_COUNT) {
-    const InterpBuild& b = r->prog->ib[0];
-    r->slot = free_slots.back();
-    free_slots.pop_back();
-    r->nunits = b.live_units();   // positions in the program's list of live units
-    r->next_unit = 0;
-    FbgInterpProg G = b.code.prog;
-    G.ins = b.d_ins;
-    G.consts = b.d_consts;
-    h_progs[r->slot] = G;
-    cudaError_t e = cudaMemcpyAsync(d_progs + r->slot, h_progs + r->slot, sizeof G, cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_counts + r->slot, 0, 8, stream);
-    if (e != cudaSuccess) return cuda_error(e, "server admit");
+  const bool count = r->mode == FBG_MODE_COUNT;
+  const InterpBuild& b = r->prog->ib[count ? 0 : 1];
+  if (!count && b.units_per_item != 1) return set_error(FBG_ETOOBIG, "too many units for a model list");
+  r->slot = free_slots.back();
+  free_slots.pop_back();
+  r->nunits = b.live_units();   // positions in the program's list of live units
+  r->next_unit = 0;
+  FbgInterpProg G = b.code.prog;
+  G.ins = b.d_ins;
+  G.consts = b.d_consts;
+  h_progs[r->slot] = G;
+  cudaError_t e = cudaMemcpyAsync(d_progs + r->slot, h_progs + r->slot, sizeof G, cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_counts + r->slot, 0, 8, stream);
+  if (e == cudaSuccess && !count) {
+    // per-unit counts (zeroed), offsets and the model buffer of this request
+    const size_t nu = (size_t)b.nunits;
+    e = cudaMallocAsync((void**)&r->d_unit_counts, nu * 8, stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&r->d_offsets, nu * 8, stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&r->d_models, std::max<size_t>(1, (size_t)r->cap) * 8, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->d_unit_counts, 0, nu * 8, stream);
+    if (e == cudaSuccess) {
+      h_slot_out[r->slot] = FbgSlotOut{r->d_unit_counts, r->d_offsets, r->d_models, r->cap};
+      e = cudaMemcpyAsync(d_slot_out + r->slot, h_slot_out + r->slot, sizeof(FbgSlotOut), cudaMemcpyHostToDevice,
+                          stream);
+    }
+  }
+  if (e != cudaSuccess) {
+    free_slots.push_back(r->slot);
+    r->slot = -1;
+    release_device(r);
+    return cuda_error(e, "server admit");
   }
   mem_used += r->mem;
   active.push_back(r);
@@ -152,8 +194,7 @@ void fbg_server::tick() {
     // admission by device memory and free slots, in arrival order
     while (!pending.empty()) {
       Request* r = pending.front();
-      bool needs_slot = r->mode == FBG_MODE_COUNT;
-      if (needs_slot && free_slots.empty()) break;
+      if (free_slots.empty()) break;
       // estimate before building; a request larger than the whole budget still runs alone
       uint64_t est = (uint64_t)r->prog->g->dag.size() * 64 + (r->mode == FBG_MODE_ENUMERATE ? r->cap * 8 : 0);
       if (mem_used && mem_used + est > opt.mem_budget_bytes) break;
@@ -165,32 +206,56 @@ void fbg_server::tick() {
     for (Request* r : active) (r->mode == FBG_MODE_COUNT ? count_reqs : enum_reqs).push_back(r);
   }
   const double tc = now_s();
-  // one launch over a share of every admitted count request
-  if (!count_reqs.empty()) {
-    uint64_t budget = opt.tick_units;
-    uint64_t share = std::max<uint64_t>(1, budget / count_reqs.size());
-    uint64_t n = 0, units = 0;
+  std::vector<Request*> work = count_reqs;
+  work.insert(work.end(), enum_reqs.begin(), enum_reqs.end());
+  // model lists whose last unit is counted in this tick (write pass follows)
+  std::vector<Request*> writes;
+  if (!work.empty()) {
+    // one launch over a share of every admitted request: count requests in
+    // runs of up to 8 consecutive live units, model lists one unit per item
+    // (each item's count also goes to that unit's counter).  The tick's work
+    // is bounded by tick_units units and tick_assignments assignments; the
+    // requests with the least remaining work go first and take all of it when
+    // it fits their fair share of what is left, the others take a fair share
+    // (at least one unit), so short requests finish in the tick they join
+    // while long ones keep advancing.
+    auto unit_size = [](const Request* r) {
+      const InterpBuild& ib = r->prog->ib[r->mode == FBG_MODE_COUNT ? 0 : 1];
+      return (1ull << r->prog->n) / std::max<uint64_t>(1, ib.nunits);
+    };
+    auto remaining = [&](const Request* r) { return (double)(r->nunits - r->next_unit) * (double)unit_size(r); };
+    std::stable_sort(work.begin(), work.end(),
+                     [&](const Request* a, const Request* b) { return remaining(a) < remaining(b); });
+    double assign_left = (double)opt.tick_assignments;
+    uint64_t units_left = opt.tick_units;
+    uint64_t n = 0;
     unsigned nslots = 1;
-    for (Request* r : count_reqs) {
-      if (n >= item_cap) break;   // the rest waits for the next tick
-      uint64_t take = std::min<uint64_t>(r->nunits - r->next_unit, share);
-      // runs of consecutive live units, at most 8 units per item so that
-      // blocks share large requests, while the tick's item buffer has room
-      const InterpBuild& ib = r->prog->ib[0];
+    for (size_t wi = 0; wi < work.size(); wi++) {
+      Request* r = work[wi];
+      if (n >= item_cap || units_left == 0) break;   // the rest waits for the next tick
+      const bool cnt = r->mode == FBG_MODE_COUNT;
+      const double fair = assign_left / (double)(work.size() - wi);
+      const uint64_t usz = std::max<uint64_t>(1, unit_size(r));
+      uint64_t take = r->nunits - r->next_unit;
+      if ((double)take * (double)usz > fair) take = std::max<uint64_t>(1, (uint64_t)(fair / (double)usz));
+      take = std::min<uint64_t>(take, std::max<uint64_t>(1, units_left / (work.size() - wi)));
+      take = std::min<uint64_t>(take, r->nunits - r->next_unit);
+      assign_left = std::max(0.0, assign_left - (double)take * (double)usz);
+      units_left -= std::min(units_left, take);
+      const InterpBuild& ib = r->prog->ib[cnt ? 0 : 1];
       uint64_t i = r->next_unit;
       const uint64_t end = r->next_unit + take;
       while (i < end && n < item_cap) {
         const uint64_t u0 = ib.unit_at(i);
         uint64_t len = 1;
-        while (i + len < end && len < 8 && ib.unit_at(i + len) == u0 + len) len++;
-        h_items[n++] = FbgWorkItem{(unsigned)r->slot, 0u, u0, u0 + len};
+        while (cnt && i + len < end && len < 8 && ib.unit_at(i + len) == u0 + len) len++;
+        h_items[n++] = FbgWorkItem{(unsigned)r->slot, cnt ? 0u : FBG_ITEM_UNIT_COUNTS, u0, u0 + len};
         i += len;
       }
-      units += i - r->next_unit;
       r->next_unit = i;
       nslots = std::max(nslots, ib.code.nslots);
+      if (!cnt && r->next_unit >= r->nunits) writes.push_back(r);
     }
-    (void)units;
     cudaError_t e = cudaMemcpyAsync(d_items, h_items, n * sizeof(FbgWorkItem), cudaMemcpyHostToDevice, stream);
     uint64_t slots = (uint64_t)opt.max_inflight;
     if (e == cudaSuccess) e = cudaMemsetAsync(d_counts + slots, 0, 8, stream);
@@ -200,17 +265,65 @@ void fbg_server::tick() {
     P.unit_begin = 0;
     P.unit_end = ~0ull;
     if (e == cudaSuccess)
-      e = launch_interp(0, d_progs, d_items, n, d_counts + slots, d_counts, nullptr, P, nslots, std::max(1, grid), stream);
+      e = launch_interp(0, d_progs, d_items, n, d_counts + slots, d_counts, nullptr, P, nslots, std::max(1, grid), stream,
+                        d_slot_out);
+    launches++;
+    // model lists complete in this launch: offsets by a scan of the unit
+    // counts, then one ordered write launch over all of them
+    if (e == cudaSuccess && !writes.empty()) {
+      h_wvec.clear();
+      unsigned wslots = 1;
+      for (Request* r : writes) {
+        const InterpBuild& ib = r->prog->ib[1];
+        if (e == cudaSuccess) e = launch_scan(r->d_unit_counts, r->d_offsets, ib.nunits, d_scan_total, stream);
+        ib.append_items(h_wvec, (unsigned)r->slot, 0, ib.live_units(), 1);
+        wslots = std::max(wslots, ib.code.nslots);
+      }
+      if (e == cudaSuccess && h_wvec.size() > witem_cap) {
+        if (d_witems) cudaFreeAsync(d_witems, stream);
+        d_witems = nullptr;
+        witem_cap = 0;
+        e = cudaMallocAsync((void**)&d_witems, h_wvec.size() * sizeof(FbgWorkItem), stream);
+        if (e == cudaSuccess) witem_cap = h_wvec.size();
+      }
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_witems, h_wvec.data(), h_wvec.size() * sizeof(FbgWorkItem), cudaMemcpyHostToDevice,
+                            stream);
+      if (e == cudaSuccess) e = cudaMemsetAsync(d_counts + slots, 0, 8, stream);
+      int wper = interp_blocks_per_sm(2, wslots);
+      int wgrid = (int)std::min<uint64_t>(h_wvec.size(), (uint64_t)device_sms() * (uint64_t)std::max(1, wper));
+      if (e == cudaSuccess)
+        e = launch_interp(2, d_progs, d_witems, h_wvec.size(), d_counts + slots, nullptr, nullptr, P, wslots,
+                          std::max(1, wgrid), stream, d_slot_out);
+      launches += 1 + writes.size();
+    }
     if (e == cudaSuccess) e = cudaMemcpyAsync(h_counts, d_counts, slots * 8, cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-    launches++;
+    // the model lists of the finished requests (their totals are now known)
+    const double tw = now_s();
+    for (Request* r : writes) {
+      if (e != cudaSuccess) break;
+      const uint64_t written = std::min<uint64_t>(h_counts[r->slot], r->cap);
+      if (written > h_models_cap) {
+        if (h_models) cudaFreeHost(h_models);
+        h_models = nullptr;
+        h_models_cap = 0;
+        e = cudaMallocHost((void**)&h_models, written * 8);
+        if (e != cudaSuccess) break;
+        h_models_cap = written;
+      }
+      if (written) e = cudaMemcpyAsync(h_models, r->d_models, written * 8, cudaMemcpyDeviceToHost, stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+      if (e == cudaSuccess) r->models.assign(h_models, h_models + written);
+    }
+    enum_s += now_s() - tw;
     std::unique_lock<std::mutex> lk(mu);
     if (e != cudaSuccess) {
       cuda_error(e, "server tick");
       fatal = FBG_ECUDA;
-      for (Request* r : count_reqs) finish(r, FBG_ECUDA);
+      for (Request* r : work) finish(r, FBG_ECUDA);
     } else {
-      for (Request* r : count_reqs)
+      for (Request* r : work)
         if (r->next_unit >= r->nunits) {
           r->count = h_counts[r->slot];
           finish(r, FBG_OK);
@@ -219,31 +332,6 @@ void fbg_server::tick() {
     active.erase(std::remove_if(active.begin(), active.end(), [](Request* r) { return r->done; }), active.end());
   }
   count_s += now_s() - tc;
-  const double te = now_s();
-  // model lists: ordered two-pass evaluation, one request after another
-  for (Request* r : enum_reqs) {
-    size_t cap = (size_t)r->cap;
-    if (cap > models_cap) {
-      if (d_models) cudaFree(d_models);
-      d_models = nullptr;
-      models_cap = 0;
-      if (cudaMalloc(&d_models, std::max<size_t>(cap, 1) * 8) == cudaSuccess) models_cap = std::max<size_t>(cap, 1);
-    }
-    uint64_t total = 0, written = 0;
-    fbg_status s = models_cap >= cap ? fbg_enumerate_models(r->prog, stream, (uint64_t*)d_models, cap, &total, &written)
-                                     : FBG_ENOMEM;
-    if (s == FBG_OK) {
-      r->models.resize(written);
-      if (written && cudaMemcpy(r->models.data(), d_models, written * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
-        s = FBG_ECUDA;
-      r->count = total;
-    }
-    launches += 3;
-    std::unique_lock<std::mutex> lk(mu);
-    finish(r, s);
-    active.erase(std::remove(active.begin(), active.end(), r), active.end());
-  }
-  enum_s += now_s() - te;
   ticks++;
   busy_s += now_s() - t0;
 }
@@ -270,6 +358,7 @@ fbg_status fbg_server_create(const fbg_server_options* opt, fbg_server** out) {
   if (!s->opt.mem_budget_bytes) s->opt.mem_budget_bytes = kDefaultBudget;
   if (s->opt.max_inflight <= 0) s->opt.max_inflight = 4096;
   if (!s->opt.tick_units) s->opt.tick_units = 65536;
+  if (!s->opt.tick_assignments) s->opt.tick_assignments = 1ull << 36;
   s->item_cap = s->opt.tick_units / 8 + 2 * (uint64_t)s->opt.max_inflight + 16;
   cudaGetDevice(&s->device);
   const size_t slots = (size_t)s->opt.max_inflight;
@@ -280,7 +369,10 @@ fbg_status fbg_server_create(const fbg_server_options* opt, fbg_server** out) {
       (e = cudaMalloc(&s->d_counts, (slots + 1) * 8)) != cudaSuccess ||
       (e = cudaMallocHost(&s->h_counts, slots * 8)) != cudaSuccess ||
       (e = cudaMalloc(&s->d_items, s->item_cap * sizeof(FbgWorkItem))) != cudaSuccess ||
-      (e = cudaMallocHost(&s->h_items, s->item_cap * sizeof(FbgWorkItem))) != cudaSuccess) {
+      (e = cudaMallocHost(&s->h_items, s->item_cap * sizeof(FbgWorkItem))) != cudaSuccess ||
+      (e = cudaMalloc(&s->d_slot_out, slots * sizeof(FbgSlotOut))) != cudaSuccess ||
+      (e = cudaMallocHost(&s->h_slot_out, slots * sizeof(FbgSlotOut))) != cudaSuccess ||
+      (e = cudaMalloc(&s->d_scan_total, 8)) != cudaSuccess) {
     fbg_server_free(s);
     return cuda_error(e, "server setup");
   }
@@ -297,6 +389,8 @@ fbg_status fbg_server_submit(fbg_server* s, const char* formula, int domain_k, i
   fbg_program* p = nullptr;
   fbg_status st = fbg_compile(formula, domain_k, &p);
   if (st != FBG_OK) return st;
+  // ticks run the interpreter: no kernel compile on the server thread
+  p->opt_engine = FBG_ENGINE_INTERP;
   if (p->n > (mode == FBG_MODE_COUNT ? 63 : 40)) {
     fbg_program_free(p);
     return set_error(FBG_ETOOBIG, "request too large");
@@ -382,7 +476,12 @@ void fbg_server_free(fbg_server* s) {
   }
   s->cv.notify_all();
   if (s->worker.joinable()) s->worker.join();
-  if (s->stream) cudaStreamSynchronize(s->stream);
+  if (s->stream) {
+    for (auto& kv : s->all) s->release_device(kv.second.get());
+    if (s->d_witems) cudaFreeAsync(s->d_witems, s->stream);
+    s->d_witems = nullptr;
+    cudaStreamSynchronize(s->stream);
+  }
   s->all.clear();
   if (s->d_progs) cudaFree(s->d_progs);
   if (s->h_progs) cudaFreeHost(s->h_progs);
@@ -390,7 +489,10 @@ void fbg_server_free(fbg_server* s) {
   if (s->h_counts) cudaFreeHost(s->h_counts);
   if (s->d_items) cudaFree(s->d_items);
   if (s->h_items) cudaFreeHost(s->h_items);
-  if (s->d_models) cudaFree(s->d_models);
+  if (s->d_slot_out) cudaFree(s->d_slot_out);
+  if (s->h_slot_out) cudaFreeHost(s->h_slot_out);
+  if (s->d_scan_total) cudaFree(s->d_scan_total);
+  if (s->h_models) cudaFreeHost(s->h_models);
   if (s->stream) cudaStreamDestroy(s->stream);
   delete s;
 }

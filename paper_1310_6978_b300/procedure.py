@@ -8,11 +8,14 @@ the reduced theory T_X is counted, and eq. (ltn) combines the counts:
     l_{T,n} = sum over X of  C(beta_1, alpha_1) ... C(beta_k, alpha_k) |K_X|.
 
 Here the reduced theories are written as formula text (with ``assume``
-lines) and all of them are counted in one batch (``fbg_batch_*``).  The
-worked instance is Sec. 5.2: partial orders with a least element 0 and a
-greatest element n-1 (two definable constants: a factor n(n-1), Sec. 3.3) whose
-middle elements are split into layers of k-minimal elements; there are
-2^(n-3) layer partitions (Prop. posn).
+lines) and all of them are counted in one batch (``fbg_batch_*``).
+``count_by_partition`` runs the procedure for any theory given its good
+definable partition (the formulas theta_k and the literals S_kl); two
+instances are provided: the layers of Sec. 5.2 (partial orders with a least
+element 0 and a greatest element n-1, two definable constants: a factor
+n(n-1), Sec. 3.3, middle elements split into layers of k-minimal elements,
+2^(n-3) layer partitions, Prop. posn) and the minimal / non-minimal split of
+partial orders with a special element (the SO.txt script of Sec. 4.2).
 """
 from __future__ import annotations
 
@@ -111,6 +114,100 @@ def count_bounded_posets_by_layers(n: int, counter: Callable[[List[Workload]], L
     counts = counter(wls)
     detail = [(a, multinomial_weight(a), c) for a, c in zip(parts, counts)]
     return n * (n - 1) * sum(w * c for _, w, c in detail), detail
+
+
+# -- the procedure for any theory with a good definable partition ------------
+
+# S_kl(x, y) of a good definable partition (Sec. 3.4): for x in X_k, y in X_l,
+# k <= l, the theory proves one of these literals; each kills one letter.
+S_FORMS = ("R(x,y)", "R(y,x)", "~R(x,y)", "~R(y,x)")
+
+
+def partition_kills(comps: Sequence[Sequence[int]], S: dict, rel: str = "r", distinct: bool = True) -> List[str]:
+    """Step 3 (killing variables): for every pair of components k <= l with a
+    form S[(k, l)] and every x in X_k, y in X_l (x != y when ``distinct``,
+    the reading for reflexive relations), the literal that S_kl fixes, as
+    formula text ("r(2,5)" or "~r(5,2)").  Components are numbered from 1."""
+    lits = {}
+    for k in range(1, len(comps) + 1):
+        for l in range(k, len(comps) + 1):
+            form = S.get((k, l))
+            if form is None:
+                continue
+            if form not in S_FORMS:
+                raise ValueError(f"S[{k},{l}] must be one of {S_FORMS}")
+            neg = form.startswith("~")
+            swap = "R(y,x)" in form
+            for x in comps[k - 1]:
+                for y in comps[l - 1]:
+                    if distinct and x == y:
+                        continue
+                    a, b = (y, x) if swap else (x, y)
+                    lit = f"{rel}({a},{b})"
+                    want = f"~{lit}" if neg else lit
+                    if lits.get(lit, want) != want:
+                        raise ValueError(f"S fixes {lit} both ways: not a good partition")
+                    lits[lit] = want
+    return list(lits.values())
+
+
+def canonical_components(alphas: Sequence[int]) -> List[List[int]]:
+    """The canonical arrangement of eq. (c2): X_1 = {0..alpha_1-1}, X_2 the
+    next alpha_2 elements, and so on."""
+    comps, start = [], 0
+    for a in alphas:
+        comps.append(list(range(start, start + a)))
+        start += a
+    return comps
+
+
+def partition_theory(base_text: str, alphas: Sequence[int], theta: Callable[[int, int], str], S: dict,
+                     rel: str = "r", distinct: bool = True) -> str:
+    """T_X (step 4): the theory text, the letters killed by S for the
+    c-partition X of sizes ``alphas`` (as ``assume`` lines), and theta_k(x)
+    for every x in X_k (so that Delta defines exactly X in every model of
+    T_X).  ``theta(k, x)`` returns the formula text of theta_k at the
+    element x."""
+    comps = canonical_components(alphas)
+    lines = [base_text.rstrip("\n")]
+    kills = partition_kills(comps, S, rel, distinct)
+    for c in range(0, len(kills), 64):
+        lines.append("assume " + " & ".join(kills[c:c + 64]))
+    for k, comp in enumerate(comps, start=1):
+        for x in comp:
+            lines.append(theta(k, x))
+    return "\n".join(lines) + "\n"
+
+
+def count_by_partition(base_text: str, n: int, m: int, theta: Callable[[int, int], str], S: dict,
+                       counter: Callable[[List[Workload]], List[int]], rel: str = "r", distinct: bool = True,
+                       factor: int = 1):
+    """l_{T,n} by the counting procedure of Sec. 3.4 (steps 1-8): every
+    c-partition X = (X_1..X_m) of I_n in the arrangement (c2) (component sizes
+    alpha_i >= 0, c_{nm} of them), its reduced theory T_X counted by
+    ``counter`` (all of them in one call, e.g. one GPU batch), and eq. (ltn):
+    l = factor * sum_X C(beta_1, alpha_1)...C(beta_m, alpha_m) |K_X|.
+    ``factor`` carries the n(n-1)..(n-k+1) of k definable constants killed
+    in ``base_text`` (Sec. 3.3).  Returns (l, [(alphas, weight, |K_X|)])."""
+    parts = list(c_partitions(n, m))
+    wls = [Workload("partition", n, partition_theory(base_text, a, theta, S, rel, distinct), n, -1) for a in parts]
+    counts = counter(wls)
+    detail = [(a, multinomial_weight(a), c) for a, c in zip(parts, counts)]
+    return factor * sum(w * c for _, w, c in detail), detail
+
+
+# Posets with a special element (the SO.txt script of Sec. 4.2) and the
+# partition into minimal and non-minimal elements: theta_1(x) says nothing
+# lies strictly below x, theta_2(x) that something does; S_11 = ~R(x,y) (two
+# minimal elements are incomparable), S_12 = ~R(y,x) (nothing lies strictly
+# below a minimal element); no literal holds between two non-minimal ones.
+def minimal_theta(k: int, x: int, rel: str = "r") -> str:
+    if k == 1:
+        return f"A[y:S | y != {x}] ~{rel}(y,{x})"
+    return f"E[y:S | y != {x}] {rel}(y,{x})"
+
+
+MINIMAL_S = {(1, 1): "~R(x,y)", (1, 2): "~R(y,x)"}
 
 
 def gpu_batch_counter(workloads: List[Workload], stream=None) -> List[int]:

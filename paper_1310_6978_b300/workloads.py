@@ -237,6 +237,18 @@ def posets_reflexivity_killed(k: int) -> Workload:
     return Workload("poset_killed", k, text, k, k * k - k)
 
 
+def posets_special(k: int) -> Workload:
+    """Partial orders with a special element, the SO.txt script of Sec. 4.2:
+    p(i,j) reads i <= j; reflexivity is assumed (the letters p(i,i) killed to
+    1, k^2 - k free letters); antisymmetry and transitivity over distinct
+    pairs and triples; some element is comparable with every element."""
+    text = "\n".join(["var p(S,S)", "assume A[i:S] p(i,i)",
+                      "A[i,j:S2] (~p(i,j) | ~p(j,i))",
+                      "A[i,j,l:S3] (~(p(i,j) & p(j,l)) | p(i,l))",
+                      "E[i:S].A[j:S] (p(i,j) | p(j,i))"]) + "\n"
+    return Workload("poset_special", k, text, k, k * k - k)
+
+
 def bounded_posets(k: int) -> Workload:
     """Partial orders with a least and a greatest element (Sec. 5.2), k >= 2."""
     text = "\n".join(["var r(S,S)", *POSET_AXIOMS, "E[x:S].A[y:S] r(x,y)", "E[x:S].A[y:S] r(y,x)"]) + "\n"

@@ -93,3 +93,19 @@ def test_batch_single_program_and_errors():
     assert int(b.results()[0]) == 219
     with pytest.raises(L.FbgError):
         F.Batch([])
+
+
+def test_count_each_equals_oracle_on_both_engines():
+    """fbg_count_each (one launch per program from C, the plain baseline of
+    the batch) writes every program's count, on both engines."""
+    mix = small_mix(40, 17)
+    want = [oracle.Theory(w.text, w.k).count() for w in mix]
+    for engine in (L.ENGINE_JIT, L.ENGINE_INTERP):
+        progs = [F.compile(w.text, w.k).set_option(L.OPT_ENGINE, engine) for w in mix]
+        dev = torch.full((len(progs),), -1, dtype=torch.int64, device="cuda")
+        F.count_each(progs, dev)
+        torch.cuda.synchronize()
+        assert F.read_counts(dev) == want
+        F.count_each(progs, dev)            # again: the self-resetting counters start from zero
+        torch.cuda.synchronize()
+        assert F.read_counts(dev) == want

@@ -11,6 +11,7 @@ from paper_1310_6978_b300 import procedure as P
 from paper_1310_6978_b300 import workloads as W
 
 import kernel_model as KM
+from oracle import counters as C
 
 
 def oracle_counter(wls):
@@ -60,3 +61,39 @@ def test_procedure_on_compiled_programs_equals_killed_family(n):
     l_proc, _ = P.count_bounded_posets_by_layers(n, model_counter)
     K = oracle_counter([W.bounded_posets_killed(n)])[0]
     assert l_proc == n * (n - 1) * K
+
+
+def test_special_element_posets_pinned():
+    # the SO.txt theory of Sec. 4.2: brute force over relations (k <= 4), the
+    # backtracking counter, and the oracle agree
+    for k in range(1, 5):
+        w = W.posets_special(k)
+        th = oracle.Theory(w.text, k)
+        assert th.n == k * k - k
+        assert th.count() == C.count_posets_special_brute(k) == C.count_posets_special_c(k)
+    assert [C.count_posets_special_c(k) for k in (3, 4)] == [12, 116]
+
+
+def test_partition_kills_follow_S():
+    comps = P.canonical_components((2, 1))
+    assert comps == [[0, 1], [2]]
+    kills = P.partition_kills(comps, P.MINIMAL_S, "p")
+    # S_11 = ~R(x,y) on the two minimal elements; S_12 = ~R(y,x): p(2,0), p(2,1) = 0
+    assert sorted(kills) == sorted(["~p(0,1)", "~p(1,0)", "~p(2,0)", "~p(2,1)"])
+    with pytest.raises(ValueError):
+        P.partition_kills([[0, 1]], {(1, 1): "R(x,z)"}, "p")
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_general_procedure_on_two_theories_equals_direct_counts(k):
+    """The counting procedure of Sec. 3.4 with the minimal / non-minimal
+    partition reproduces the direct counts of partial orders (reflexivity
+    killed) and of partial orders with a special element (SO.txt)."""
+    for w, rel in ((W.posets_special(k), "p"), (W.posets_reflexivity_killed(k), "r")):
+        direct = oracle_counter([w])[0]
+        l, detail = P.count_by_partition(w.text, k, 2, lambda c, x: P.minimal_theta(c, x, rel), P.MINIMAL_S,
+                                         oracle_counter, rel=rel)
+        assert l == direct
+        assert len(detail) == P.c_partition_count(k, 2)
+        # no model has zero minimal elements
+        assert [c for a, _, c in detail if a[0] == 0] == [0]

@@ -74,3 +74,32 @@ def test_noalloc_refuses_programs_larger_than_its_array():
     q = F.compile(W.posets(4).text, 4)
     q.count_noalloc(out)
     assert int(out.item()) == 219
+
+
+def test_noalloc_first_on_fresh_programs_against_known_counts():
+    # programs counted only through fbg_count_noalloc (no fbg_count before):
+    # posets on 5 points (4231) and equivalence relations on 5 points
+    # (the Bell number 52)
+    out = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    for text, k, want in ((W.posets(5).text, 5, 4231), (W.equivalences(5).text, 5, 52)):
+        p = F.compile(text, k)
+        for _ in range(2):
+            out.fill_(-1)
+            p.count_noalloc(out)
+            assert int(out.item()) == want
+
+
+def test_noalloc_allocates_no_device_memory():
+    # after one warm-up call (the per-device set-up), further calls leave
+    # the device's free memory exactly as it was
+    out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    progs = [F.compile(W.posets(4).text, 4), F.compile(W.cnf3(22, 5).text, 22), F.compile(W.triangle_free(7).text, 7)]
+    progs[0].count_noalloc(out)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        for p in progs:
+            p.count_noalloc(out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
