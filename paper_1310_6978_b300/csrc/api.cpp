@@ -227,6 +227,8 @@ static std::shared_ptr<const JitHost> jit_host(fbg_program* p, int mode) {
     uint64_t live = 0;
     for (uint8_t a : h->alive) live += a;
     if (h->alive.empty() || live * 4 > h->alive.size() * 3) h->alive.clear();
+    for (size_t t = 0; t < h->alive.size(); t++)
+      if (h->alive[t]) h->items.push_back((unsigned)t);
   }
   std::shared_ptr<const JitHost> hc = std::move(h);
   jit_host_put(key, hc);
@@ -249,23 +251,48 @@ fbg_status build_jit_impl(fbg_program* p, int mode) {
   b.block = h->block;
   int dev = 0;
   cudaGetDevice(&dev);
-  JitResult r = jit_compile(b.src, mode == 0 ? "fbg_jit_count" : mode == 1 ? "fbg_jit_table" : "fbg_jit_enum", dev);
-  b.log = r.log;
-  p->jit_log = r.log;
-  if (!r.ok) return set_error(FBG_EJIT, r.log);
-  b.kern = r.kernel;
-  int per_sm = 0;
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)b.kern, b.block, 0));
-  if (per_sm <= 0) per_sm = 1;
+  // the kernel and the live-item list of this build on this device, shared
+  // with earlier programs built from the same text and options
+  const std::string key = build_key(p, "jit", mode);
+  std::shared_ptr<JitDevice> jd = jit_device_get(key, dev);
+  if (jd) {
+    b.kern = (cudaKernel_t)jd->kernel;
+  } else {
+    JitResult r = jit_compile(b.src, mode == 0 ? "fbg_jit_count" : mode == 1 ? "fbg_jit_table" : "fbg_jit_enum", dev);
+    b.log = r.log;
+    p->jit_log = r.log;
+    if (!r.ok) return set_error(FBG_EJIT, r.log);
+    b.kern = r.kernel;
+  }
+  int per_sm = jd ? jd->blocks_per_sm : 0;
+  if (per_sm <= 0) {
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)b.kern, b.block, 0));
+    if (per_sm <= 0) per_sm = 1;
+  }
   b.nunits = 1ull << b.lp.layout.unit_bits;
   b.grid = (int)std::min<uint64_t>(b.nunits, (uint64_t)device_sms() * (uint64_t)per_sm);
   b.alive = h->alive;
-  if (!b.alive.empty()) {
-    std::vector<unsigned> items;
-    for (size_t t = 0; t < b.alive.size(); t++)
-      if (b.alive[t]) items.push_back((unsigned)t);
-    fbg_status s = upload_items(b, items);
-    if (s != FBG_OK) return s;
+  if (!h->items.empty()) {
+    if (!jd || !jd->items) {
+      auto nd = std::make_shared<JitDevice>();
+      nd->kernel = (void*)b.kern;
+      nd->blocks_per_sm = per_sm;
+      unsigned* d = nullptr;
+      CK(cudaMalloc(&d, h->items.size() * sizeof(unsigned)));
+      nd->items = std::shared_ptr<void>(d, [](void* q) { cudaFree(q); });
+      CK(cudaMemcpy(d, h->items.data(), h->items.size() * sizeof(unsigned), cudaMemcpyHostToDevice));
+      jit_device_put(key, dev, nd);
+      jd = nd;
+    }
+    b.free_device();
+    b.perm_owner = jd->items;
+    b.d_perm = static_cast<unsigned*>(jd->items.get());
+    b.nperm = h->items.size();
+  } else if (!jd) {
+    auto nd = std::make_shared<JitDevice>();
+    nd->kernel = (void*)b.kern;
+    nd->blocks_per_sm = per_sm;
+    jit_device_put(key, dev, nd);
   }
   b.valid = true;
   return FBG_OK;
@@ -983,7 +1010,7 @@ fbg_status fbg_debug_dump(fbg_program* p, int which, char* buf, size_t* len) {
     for (unsigned i = 0; i < G.nlevels; i++)
       o << (i ? ", " : "") << "[" << G.lev[i].ins_begin << ", " << G.lev[i].ins_end << ", " << G.lev[i].bits << ", "
         << G.lev[i].pos << ", " << G.lev[i].has_acc << ", " << G.lev[i].acc_op << "]";
-    o << "], \"out_op\": " << G.out_op << ", \"nslots\": " << G.nslots << ", \"tvalid\": " << G.tvalid
+    o << "], \"out_op\": " << G.out_op << ", \"nslots\": " << G.nslots << ", \"nshared\": " << G.nshared << ", \"tvalid\": " << G.tvalid
       << ", \"vmask\": " << G.vmask << ", \"first_unit_pos\": " << G.first_unit_pos << ", \"unit_bits\": "
       << G.unit_bits << ", \"nunits\": " << G.nunits << "}";
   }

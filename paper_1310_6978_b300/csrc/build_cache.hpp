@@ -21,7 +21,19 @@ struct JitHost {
   int unrolled_level = -1;
   int block = 256;
   std::vector<uint8_t> alive;   // empty: every item may hold models (or pruning off)
+  std::vector<unsigned> items;  // the live items in natural order (empty with alive)
 };
+
+// The live-item list of a cached build on one device, shared by every
+// program built from it (freed when the last holder lets go), and the
+// kernel of that build on that device (owned by the process-wide JIT cache).
+struct JitDevice {
+  std::shared_ptr<void> items;   // device array of JitHost::items
+  void* kernel = nullptr;        // cudaKernel_t
+  int blocks_per_sm = 0;         // occupancy of the kernel at its block size
+};
+std::shared_ptr<JitDevice> jit_device_get(const std::string& key, int device);
+void jit_device_put(const std::string& key, int device, std::shared_ptr<JitDevice> v);
 
 // the host half of an interpreter build
 struct InterpHost {

@@ -72,6 +72,10 @@ SharedCache<JitHost>& jit_cache() {
   static SharedCache<JitHost> c(256);
   return c;
 }
+SharedCache<JitDevice>& jit_device_cache() {
+  static SharedCache<JitDevice> c(512);
+  return c;
+}
 SharedCache<InterpHost>& interp_cache() {
   static SharedCache<InterpHost> c(512);
   return c;
@@ -107,9 +111,18 @@ void interp_host_put(const std::string& key, std::shared_ptr<const InterpHost> v
   interp_cache().put(key, std::move(v));
 }
 
+std::shared_ptr<JitDevice> jit_device_get(const std::string& key, int device) {
+  auto v = jit_device_cache().get(std::to_string(device) + "#" + key);
+  return std::const_pointer_cast<JitDevice>(v);
+}
+void jit_device_put(const std::string& key, int device, std::shared_ptr<JitDevice> v) {
+  jit_device_cache().put(std::to_string(device) + "#" + key, std::move(v));
+}
+
 void host_caches_clear() {
   compiled_cache().clear();
   jit_cache().clear();
+  jit_device_cache().clear();
   interp_cache().clear();
 }
 

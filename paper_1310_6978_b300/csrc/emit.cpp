@@ -1100,16 +1100,34 @@ InterpCode emit_bytecode(const LutProgram& p) {
     to_end[(size_t)p.out.id] = true;
     pinned[(size_t)p.out.id] = true;
   }
-  // slots: accumulator for a value read only by the next instruction of its level
+  // Which values are equal in every tile of a block: those whose letters
+  // avoid the lane and warp positions (a tile is the 64 assignments of the
+  // in-word and register positions, and the tiles of a block differ only in
+  // their lane and warp bits).  Such a value needs one word per block (a
+  // block slot) instead of one per tile: the slot file, which sets how many
+  // one-warp blocks fit an SM, holds only the values that differ per tile.
+  const uint64_t tile_bits = (((1ull << (L.lane_bits + L.warp_bits)) - 1ull) << L.first_lane_pos());
+  std::vector<uint64_t> support((size_t)nluts, 0);
+  for (int i = 0; i < nluts; i++)
+    for (const Val& v : p.luts[(size_t)i].in) {
+      if (v.kind == V_VAR) support[(size_t)i] |= 1ull << v.id;
+      if (v.kind == V_LUT) support[(size_t)i] |= support[(size_t)v.id];
+    }
+  auto per_tile = [&](int i) { return (support[(size_t)i] & tile_bits) != 0; };
+  // slots: accumulator for a value read only by the next instruction of its
+  // level; otherwise a block slot when the value is equal in every tile and
+  // one is free, else a tile slot
   std::vector<int> slot((size_t)nluts, -1);
-  std::vector<int> free_slots;
-  std::vector<std::pair<int, int>> busy;   // (last use, slot)
-  int nslots = 0;
+  std::vector<bool> shared_slot((size_t)nluts, false);
+  std::vector<int> free_tile, free_shared;
+  std::vector<std::pair<int, int>> busy;   // (last use, value)
+  int nslots = 0, nshared = 0;
   for (int i = 0; i < nluts; i++) {
     // release values whose last use is this instruction or earlier
     for (size_t q = 0; q < busy.size();) {
       if (busy[q].first <= i) {
-        free_slots.push_back(busy[q].second);
+        const int v = busy[q].second;
+        (shared_slot[(size_t)v] ? free_shared : free_tile).push_back(slot[(size_t)v]);
         busy[q] = busy.back();
         busy.pop_back();
       } else {
@@ -1119,26 +1137,32 @@ InterpCode emit_bytecode(const LutProgram& p) {
     bool acc = !to_end[(size_t)i] && !pinned[(size_t)i] && users[(size_t)i] == 1 && only_user[(size_t)i] == i + 1 &&
                p.luts[(size_t)(i + 1)].level == p.luts[(size_t)i].level;
     if (acc) continue;
-    int s;
-    if (!free_slots.empty()) {
-      auto it = std::min_element(free_slots.begin(), free_slots.end());
-      s = *it;
-      free_slots.erase(it);
-    } else {
-      s = nslots++;
-    }
-    slot[(size_t)i] = s;
-    if (!to_end[(size_t)i]) busy.push_back({std::max(last_use[(size_t)i], i), s});
+    auto take = [](std::vector<int>& fl, int& count) {
+      if (!fl.empty()) {
+        auto it = std::min_element(fl.begin(), fl.end());
+        const int s = *it;
+        fl.erase(it);
+        return s;
+      }
+      return count++;
+    };
+    const bool sh = !per_tile(i) && (!free_shared.empty() || nshared < FBG_INTERP_MAX_SHARED);
+    shared_slot[(size_t)i] = sh;
+    slot[(size_t)i] = sh ? take(free_shared, nshared) : take(free_tile, nslots);
+    if (!to_end[(size_t)i]) busy.push_back({std::max(last_use[(size_t)i], i), i});
   }
   if (nslots > FBG_INTERP_MAX_SLOTS) throw CompileError{"program needs " + std::to_string(nslots) + " live values (max " + std::to_string(FBG_INTERP_MAX_SLOTS) + ")"};
   auto code = [&](const Val& v) -> uint32_t {
     if (v.kind == V_CONST) return FBG_OP_CONST | (uint32_t)v.id;
     if (v.kind == V_VAR) return FBG_OP_VAR | (uint32_t)v.id;
-    return slot[(size_t)v.id] < 0 ? FBG_OP_ACC : (uint32_t)slot[(size_t)v.id];
+    if (slot[(size_t)v.id] < 0) return FBG_OP_ACC;
+    return shared_slot[(size_t)v.id] ? (FBG_OP_SHARED | (uint32_t)slot[(size_t)v.id]) : (uint32_t)slot[(size_t)v.id];
   };
   for (int i = 0; i < nluts; i++) {
     const Lut& lu = p.luts[(size_t)i];
-    uint64_t dst = slot[(size_t)i] < 0 ? FBG_DST_ACC : (uint64_t)slot[(size_t)i];
+    uint64_t dst = slot[(size_t)i] < 0 ? FBG_DST_ACC
+                   : shared_slot[(size_t)i] ? (uint64_t)(FBG_DST_SHARED + (unsigned)slot[(size_t)i])
+                                            : (uint64_t)slot[(size_t)i];
     uint64_t w = (uint64_t)lu.tt | (dst << 8) | ((uint64_t)code(lu.in[0]) << 16) | ((uint64_t)code(lu.in[1]) << 32) |
                  ((uint64_t)code(lu.in[2]) << 48);
     c.ins.push_back(w);
@@ -1148,6 +1172,7 @@ InterpCode emit_bytecode(const LutProgram& p) {
   G.nlevels = (unsigned)L.nlevels();
   if (G.nlevels > FBG_INTERP_MAX_LEVELS) throw CompileError{"too many loop levels"};
   G.nslots = (unsigned)std::max(1, nslots);
+  G.nshared = (unsigned)nshared;
   G.nconst = (unsigned)c.consts.size();
   G.tvalid = 1u << (L.lane_bits + L.warp_bits);
   G.first_unit_pos = (unsigned)L.first_unit_pos();

@@ -28,7 +28,6 @@ constexpr int B = FBG_INTERP_BLOCK;          // tiles per block (the layout's th
 constexpr int NT = FBG_INTERP_THREADS;       // threads per block
 constexpr int NTILE = B / NT;                // tiles per thread
 static_assert(NT == 32 && NTILE * NT == B, "one warp per block, B / 32 tiles per thread");
-constexpr int MAX_CONST_SMEM = FBG_INTERP_MAX_CONSTS;
 
 // the tiles of a thread: tile k is the layout's thread lane + 32 k
 struct Pair {
@@ -60,7 +59,7 @@ __device__ __forceinline__ Pair lop3_dyn(unsigned lut, const Pair& a, const Pair
 
 struct Shared {
   FbgInterpProg prog;
-  fbg_u64 consts[MAX_CONST_SMEM];
+  fbg_u64 svals[FBG_INTERP_MAX_SHARED];   // block slots: one word each, equal in every tile
   fbg_u64 unit;
   fbg_u64 item;
 };
@@ -94,7 +93,15 @@ __device__ __forceinline__ Pair fetch(const Shared& S, const Thread& T, unsigned
     return r;
   }
   if (op & FBG_OP_CONST) {
-    const fbg_u64 c = S.consts[op & 0x3FFFu];
+    // the constant table stays in global memory (a few words, cached in L1):
+    // no shared-memory copy per block, which leaves room for more blocks
+    const fbg_u64 c = __ldg(S.prog.consts + (op & 0x3FFFu));
+#pragma unroll
+    for (int k = 0; k < NTILE; k++) r.v[k] = c;
+    return r;
+  }
+  if (op & FBG_OP_SHARED) {
+    const fbg_u64 c = S.svals[op & 0xFFFu];
 #pragma unroll
     for (int k = 0; k < NTILE; k++) r.v[k] = c;
     return r;
@@ -106,7 +113,7 @@ __device__ __forceinline__ Pair fetch(const Shared& S, const Thread& T, unsigned
 
 // instructions of one level; the next instruction word is loaded while the
 // current one executes
-__device__ __forceinline__ void exec_level(const Shared& S, Thread& T, const FbgInterpLevel& L) {
+__device__ __forceinline__ void exec_level(Shared& S, Thread& T, const FbgInterpLevel& L) {
   const fbg_u64* ins = S.prog.ins;
   unsigned i = L.ins_begin;
   if (i >= L.ins_end) return;
@@ -120,6 +127,14 @@ __device__ __forceinline__ void exec_level(const Shared& S, Thread& T, const Fbg
     const Pair d = lop3_dyn(lut, a, b, c);
     if (dst == FBG_DST_ACC) {
       T.acc = d;
+    } else if (dst >= FBG_DST_SHARED) {
+      // every lane computed the same word (the value is equal in all tiles);
+      // the warp (the whole block) synchronises so that no lane overwrites a
+      // block slot before every lane has read its previous value, and no lane
+      // reads it before every lane has stored the new one
+      __syncwarp();
+      S.svals[dst - FBG_DST_SHARED] = d.v[0];
+      __syncwarp();
     } else {
 #pragma unroll
       for (int k = 0; k < NTILE; k++) T.slots[(unsigned long long)dst * B + k * NT] = d.v[k];
@@ -144,8 +159,6 @@ __device__ __forceinline__ bool level_alive(const Shared& S, const Thread& T, co
 __device__ __forceinline__ void load_prog(Shared& S, const FbgInterpProg* progs, unsigned p) {
   __syncthreads();
   if (threadIdx.x == 0) S.prog = progs[p];
-  __syncthreads();
-  for (unsigned i = threadIdx.x; i < S.prog.nconst && i < MAX_CONST_SMEM; i += NT) S.consts[i] = S.prog.consts[i];
   __syncthreads();
 }
 

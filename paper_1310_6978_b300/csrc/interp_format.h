@@ -3,9 +3,13 @@
 // A program is a list of 64-bit instructions, each one 3-input LUT on 64-bit
 // words (two lop3.b32: the thread's tile is 2 registers, r = 1), grouped by
 // loop level.  Instruction word: lut[0:8) dst[8:16) a[16:32) b[32:48) c[48:64).
-// Operand codes (16 bit): a shared-memory slot 0..255, FBG_OP_CONST|i (entry
-// i of the constant table), FBG_OP_VAR|p (generator word of bit position p,
-// p >= 6), FBG_OP_ACC (the accumulator register).  dst: slot or FBG_DST_ACC.
+// Operand codes (16 bit): a tile slot 0..FBG_INTERP_MAX_SLOTS-1 (one 64-bit
+// word per tile: a column of the block's slot file), FBG_OP_SHARED|i (block
+// slot i: one word for the whole block, for values that do not depend on the
+// lane and warp letters and so are equal in every tile), FBG_OP_CONST|i
+// (entry i of the constant table), FBG_OP_VAR|p (generator word of bit
+// position p, p >= 6), FBG_OP_ACC (the accumulator register).  dst: a tile
+// slot, FBG_DST_SHARED + i for block slot i, or FBG_DST_ACC.
 #pragma once
 
 #define FBG_INTERP_MAX_LEVELS 10
@@ -15,12 +19,15 @@
 #define FBG_INTERP_BLOCK 64
 #define FBG_INTERP_THREADS 32        // threads per block; each evaluates BLOCK / THREADS tiles
 #define FBG_INTERP_WARPS_LOG2 1
-#define FBG_INTERP_MAX_SLOTS 160
-#define FBG_INTERP_MAX_CONSTS 512   // constant table entries staged in shared memory
+#define FBG_INTERP_MAX_SLOTS 160      // tile slots
+#define FBG_INTERP_MAX_SHARED 95      // block slots (dst codes 160..254)
+#define FBG_INTERP_MAX_CONSTS 512   // constant table entries (global memory)
 
+#define FBG_OP_SHARED 0x1000u
 #define FBG_OP_CONST 0x4000u
 #define FBG_OP_VAR 0x8000u
 #define FBG_OP_ACC 0xFFFFu
+#define FBG_DST_SHARED 160u
 #define FBG_DST_ACC 255u
 
 struct FbgInterpLevel {
@@ -32,7 +39,8 @@ struct FbgInterpLevel {
 struct FbgInterpProg {
   unsigned int n;                    // number of variables
   unsigned int nlevels;              // 2 + loop levels (level 0 thread, 1 unit)
-  unsigned int nslots, nconst;
+  unsigned int nslots, nconst;       // tile slots, constants
+  unsigned int nshared;              // block slots
   unsigned int tvalid;               // threads of a block that hold real tiles
   unsigned int first_unit_pos, unit_bits;
   unsigned int out_op;               // operand holding the formula value

@@ -64,9 +64,11 @@ struct JitBuild {
   uint64_t nunits = 1;
   unsigned* d_perm = nullptr;    // items of full-range counts, in order, or null (all, natural order)
   uint64_t nperm = 0;
+  std::shared_ptr<void> perm_owner;   // set when d_perm is the shared list of a cached build
   std::vector<uint8_t> alive;    // per (unit, warp slice) item: 0 = no models, empty = all live
   void free_device() {
-    if (d_perm) cudaFree(d_perm);
+    if (d_perm && !perm_owner) cudaFree(d_perm);
+    perm_owner.reset();
     d_perm = nullptr;
     nperm = 0;
   }

@@ -245,10 +245,12 @@ void fbg_server::tick() {
       const InterpBuild& ib = r->prog->ib[cnt ? 0 : 1];
       uint64_t i = r->next_unit;
       const uint64_t end = r->next_unit + take;
+      // runs of consecutive units of at most 2^22 assignments (and 8 units)
+      const uint64_t run_max = cnt ? std::max<uint64_t>(1, std::min<uint64_t>(8, (1ull << 22) / usz)) : 1;
       while (i < end && n < item_cap) {
         const uint64_t u0 = ib.unit_at(i);
         uint64_t len = 1;
-        while (cnt && i + len < end && len < 8 && ib.unit_at(i + len) == u0 + len) len++;
+        while (i + len < end && len < run_max && ib.unit_at(i + len) == u0 + len) len++;
         h_items[n++] = FbgWorkItem{(unsigned)r->slot, cnt ? 0u : FBG_ITEM_UNIT_COUNTS, u0, u0 + len};
         i += len;
       }
@@ -359,7 +361,7 @@ fbg_status fbg_server_create(const fbg_server_options* opt, fbg_server** out) {
   if (s->opt.max_inflight <= 0) s->opt.max_inflight = 4096;
   if (!s->opt.tick_units) s->opt.tick_units = 65536;
   if (!s->opt.tick_assignments) s->opt.tick_assignments = 1ull << 36;
-  s->item_cap = s->opt.tick_units / 8 + 2 * (uint64_t)s->opt.max_inflight + 16;
+  s->item_cap = s->opt.tick_units + 2 * (uint64_t)s->opt.max_inflight + 16;
   cudaGetDevice(&s->device);
   const size_t slots = (size_t)s->opt.max_inflight;
   cudaError_t e;
@@ -389,8 +391,11 @@ fbg_status fbg_server_submit(fbg_server* s, const char* formula, int domain_k, i
   fbg_program* p = nullptr;
   fbg_status st = fbg_compile(formula, domain_k, &p);
   if (st != FBG_OK) return st;
-  // ticks run the interpreter: no kernel compile on the server thread
+  // ticks run the interpreter: no kernel compile on the server thread; up to
+  // 2^16 units per program, so that a large request is cut into many small
+  // work items that spread over every SM instead of a few long ones
   p->opt_engine = FBG_ENGINE_INTERP;
+  p->opt_unit_bits = 16;
   if (p->n > (mode == FBG_MODE_COUNT ? 63 : 40)) {
     fbg_program_free(p);
     return set_error(FBG_ETOOBIG, "request too large");

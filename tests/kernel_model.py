@@ -108,7 +108,7 @@ def lut_program_prune_sound(d: dict) -> bool:
 
 # ------------------------------------------------------------- interpreter --
 
-OP_CONST, OP_VAR, OP_ACC, DST_ACC = 0x4000, 0x8000, 0xFFFF, 255
+OP_SHARED, OP_CONST, OP_VAR, OP_ACC, DST_SHARED, DST_ACC = 0x1000, 0x4000, 0x8000, 0xFFFF, 160, 255
 BLOCK = 64   # tiles of a block: one warp of 32 threads, two tiles each
 
 
@@ -136,6 +136,9 @@ class InterpModel:
             return np.where(bit == 1, M64, np.uint64(0))
         if op & OP_CONST:
             return np.full(BLOCK, self.consts[op & 0x3FFF], dtype=np.uint64)
+        if op & OP_SHARED:
+            # a block slot holds one word; the value must be equal in every tile
+            return np.full(BLOCK, self.svals[op & 0xFFF], dtype=np.uint64)
         return self.slots[op]
 
     def exec_level(self, lv):
@@ -149,6 +152,11 @@ class InterpModel:
             v = lut_apply(lut, a, bb, c)
             if dst == DST_ACC:
                 self.acc = v
+            elif dst >= DST_SHARED:
+                # only values equal in every (valid) tile may live in a block slot
+                vv = v[self.tvalid]
+                assert len(vv) == 0 or bool(np.all(vv == vv[0])), "block slot value differs between tiles"
+                self.svals[dst - DST_SHARED] = v[0]
             else:
                 self.slots[dst] = v
 
@@ -160,6 +168,7 @@ class InterpModel:
     def run(self, mode, cap=0, unit_offsets=None):
         d = self.d
         self.slots = np.zeros((max(1, self.nslots), BLOCK), dtype=np.uint64)
+        self.svals = np.zeros(96, dtype=np.uint64)
         self.acc = np.zeros(BLOCK, dtype=np.uint64)
         self.coords = self.tb << np.uint64(6)
         nl = len(self.levels)
