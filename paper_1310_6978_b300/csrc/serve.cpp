@@ -130,6 +130,10 @@ void fbg_server::release_device(Request* r) {
 
 void fbg_server::finish(Request* r, fbg_status s) {
   release_device(r);
+  // the result (count, model list) is all a poll needs: the program and its
+  // device buffers go now, not when the caller releases the request
+  fbg_program_free(r->prog);
+  r->prog = nullptr;
   r->status = s;
   r->done_s = now_s();
   r->done = true;
