@@ -111,6 +111,10 @@ enum {
                                   about (c*W - A) / (c + 2) for W words and A lop3; 0 = none,
                                   default 4 (POPC on the XU pipe at a quarter of the lop3 rate);
                                   0..16 */
+  FBG_OPT_ORDER_SEED = 13,     /* counts: variant of the heuristic variable order (0 = default: ties
+                                  go to the lowest letter; 1..255: ties broken by a seeded hash).
+                                  The order decides how much of the space the level conjunctions
+                                  prune; counts are the same under every order */
 };
 
 typedef struct {
@@ -222,6 +226,38 @@ fbg_status fbg_enumerate_models(fbg_program *prog, void *stream, uint64_t *dev_m
                                 uint64_t *total, uint64_t *written);
 
 /*
+ * Unit ranges of truth tables and model lists (no counterpart in the paper;
+ * the assignment space split by its top letters, one range per GPU).  The
+ * specialised kernel's table layout (mode 1) and model-list layout (mode 2)
+ * each have *nunits units; unit u holds the assignments j with j >> (n - log2 nunits) == u, a
+ * contiguous range of *words_per_unit 64-bit table words.  Ranges need the
+ * specialised engine (FBG_EINVAL when the program asks for the
+ * interpreter); n <= 40.
+ */
+fbg_status fbg_table_units(fbg_program *prog, int mode, uint64_t *nunits, uint64_t *words_per_unit);
+
+/*
+ * The table words of units [unit_begin, unit_end): nwords must be
+ * (unit_end - unit_begin) * words_per_unit; dev_words[i] is word
+ * unit_begin * words_per_unit + i of the whole table (bit j at word j>>6,
+ * bit j&63).  Asynchronous.  FBG_EINVAL for an empty or out-of-range range
+ * or when a unit is smaller than one 64-bit word (then only the whole range
+ * is allowed).
+ */
+fbg_status fbg_truth_table_range(fbg_program *prog, void *stream, uint64_t unit_begin, uint64_t unit_end,
+                                 uint64_t *dev_words, size_t nwords);
+
+/*
+ * The models among units [unit_begin, unit_end) of the model-list layout, in
+ * ascending j: the first min(cap, *total) are written to dev_models, *total
+ * is the exact number of models in the range.  Concatenating the lists of
+ * consecutive ranges in order gives the list of fbg_enumerate_models.
+ * Synchronises `stream`.
+ */
+fbg_status fbg_enumerate_models_range(fbg_program *prog, void *stream, uint64_t unit_begin, uint64_t unit_end,
+                                      uint64_t *dev_models, size_t cap, uint64_t *total, uint64_t *written);
+
+/*
  * Count without any device allocation by the library.  The paper has no
  * counterpart of this entry point; it exists for callers that cannot let a
  * library call cudaMalloc -- a process whose caching allocator already owns
@@ -260,6 +296,7 @@ typedef struct {
   int regs_log2, warps_log2, min_blocks, loop_level_bits, unit_bits;
   int inner_bits;
   int popc_cost;
+  int order_seed;
 } fbg_tune_result;
 fbg_status fbg_autotune(fbg_program *prog, void *stream, int mode, int reps, fbg_tune_result *out);
 

@@ -154,13 +154,36 @@ class Program:
                                                        ctypes.byref(total), ctypes.byref(written)))
         return total.value, written.value
 
+    def table_units(self, mode: int = 1):
+        """fbg_table_units: (units, 64-bit words per unit) of the table
+        (mode 1) or model-list (mode 2) layout of the specialised kernel."""
+        nu, wpu = ctypes.c_uint64(), ctypes.c_uint64()
+        self._L.check(self._L.lib.fbg_table_units(self._h, mode, ctypes.byref(nu), ctypes.byref(wpu)))
+        return nu.value, wpu.value
+
+    def truth_table_range(self, unit_begin: int, unit_end: int, dev_words, stream=None) -> None:
+        """fbg_truth_table_range: the table words of units [unit_begin, unit_end)."""
+        self._L.check(self._L.lib.fbg_truth_table_range(self._h, _stream_ptr(stream), unit_begin, unit_end,
+                                                        _ptr(dev_words), dev_words.numel()))
+
+    def enumerate_models_range(self, unit_begin: int, unit_end: int, dev_models, cap: int | None = None,
+                               stream=None):
+        """fbg_enumerate_models_range: (total, written) for the models among
+        units [unit_begin, unit_end), ascending, the first `cap` stored."""
+        cap = dev_models.numel() if cap is None else cap
+        total, written = ctypes.c_uint64(), ctypes.c_uint64()
+        self._L.check(self._L.lib.fbg_enumerate_models_range(self._h, _stream_ptr(stream), unit_begin, unit_end,
+                                                             _ptr(dev_models), cap, ctypes.byref(total),
+                                                             ctypes.byref(written)))
+        return total.value, written.value
+
     def autotune(self, mode: int = 0, reps: int = 3, stream=None) -> dict:
         """fbg_autotune: search the kernel shape; the program keeps the best."""
         r = self._L.FbgTuneResult()
         self._L.check(self._L.lib.fbg_autotune(self._h, _stream_ptr(stream), mode, reps, ctypes.byref(r)))
         return {"best_ms": r.best_ms, "trials": r.trials, "regs_log2": r.regs_log2, "warps_log2": r.warps_log2,
                 "min_blocks": r.min_blocks, "loop_level_bits": r.loop_level_bits, "unit_bits": r.unit_bits,
-                "inner_bits": r.inner_bits, "popc_cost": r.popc_cost}
+                "inner_bits": r.inner_bits, "popc_cost": r.popc_cost, "order_seed": r.order_seed}
 
     def apply_shape(self, shape: dict) -> "Program":
         """Set the kernel-shape options recorded by ``autotune``."""
@@ -168,6 +191,7 @@ class Program:
         for key, opt in (("regs_log2", L.OPT_REGS_LOG2), ("warps_log2", L.OPT_WARPS_LOG2),
                          ("min_blocks", L.OPT_MIN_BLOCKS), ("loop_level_bits", L.OPT_LOOP_LEVEL_BITS),
                          ("inner_bits", L.OPT_INNER_BITS), ("popc_cost", L.OPT_POPC_COST),
+                         ("order_seed", L.OPT_ORDER_SEED),
                          ("unit_bits", L.OPT_UNIT_BITS)):
             if key in shape:
                 self.set_option(opt, shape[key])

@@ -29,7 +29,7 @@ STATUS_NAMES = ["FBG_OK", "FBG_EINVAL", "FBG_EPARSE", "FBG_ETOOBIG", "FBG_ENOMEM
 
 ENGINE_AUTO, ENGINE_JIT, ENGINE_INTERP = 0, 1, 2
 OPT_ENGINE, OPT_PRUNE, OPT_REGS_LOG2, OPT_WARPS_LOG2, OPT_UNIT_BITS, OPT_LOOP_LEVEL_BITS, OPT_SEARCH_ORDER, \
-    OPT_MIN_BLOCKS, OPT_STATS, OPT_INNER_BITS, OPT_SPLIT_ITEMS, OPT_POPC_COST = range(1, 13)
+    OPT_MIN_BLOCKS, OPT_STATS, OPT_INNER_BITS, OPT_SPLIT_ITEMS, OPT_POPC_COST, OPT_ORDER_SEED = range(1, 14)
 MODE_COUNT, MODE_ENUMERATE = 0, 1
 BATCH_GRAPH, BATCH_SPECIALIZE = 1, 2
 
@@ -48,7 +48,7 @@ class FbgExecStats(ctypes.Structure):
 class FbgTuneResult(ctypes.Structure):
     _fields_ = [("best_ms", ctypes.c_double), ("trials", c_int), ("regs_log2", c_int), ("warps_log2", c_int),
                 ("min_blocks", c_int), ("loop_level_bits", c_int), ("unit_bits", c_int), ("inner_bits", c_int),
-                ("popc_cost", c_int)]
+                ("popc_cost", c_int), ("order_seed", c_int)]
 
 
 class FbgServerOptions(ctypes.Structure):
@@ -88,6 +88,9 @@ _sig("fbg_debug_item_trace", c_int, c_vp, c_vp, c_vp, c_u64)
 _sig("fbg_unit_vars", c_int, c_vp, ctypes.POINTER(c_int), c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_u64))
 _sig("fbg_truth_table", c_int, c_vp, c_vp, c_vp, c_sz)
 _sig("fbg_enumerate_models", c_int, c_vp, c_vp, c_vp, c_sz, ctypes.POINTER(c_u64), ctypes.POINTER(c_u64))
+_sig("fbg_table_units", c_int, c_vp, c_int, ctypes.POINTER(c_u64), ctypes.POINTER(c_u64))
+_sig("fbg_truth_table_range", c_int, c_vp, c_vp, c_u64, c_u64, c_vp, c_sz)
+_sig("fbg_enumerate_models_range", c_int, c_vp, c_vp, c_u64, c_u64, c_vp, c_sz, ctypes.POINTER(c_u64), ctypes.POINTER(c_u64))
 _sig("fbg_autotune", c_int, c_vp, c_vp, c_int, c_int, ctypes.POINTER(FbgTuneResult))
 _sig("fbg_last_exec_stats", c_int, c_vp, ctypes.POINTER(FbgExecStats))
 _sig("fbg_debug_host_times", c_int, c_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double))

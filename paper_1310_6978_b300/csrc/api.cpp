@@ -87,7 +87,7 @@ void strip_prune(LutProgram& lp) {
 }
 
 std::vector<int> order_for(const fbg_program* p, bool count_layout) {
-  if (count_layout && p->opt_search) return search_order(*p->g);
+  if (count_layout && p->opt_search) return search_order(*p->g, (uint64_t)p->opt_order_seed);
   return identity_order(p->n);
 }
 
@@ -531,6 +531,10 @@ fbg_status fbg_set_option(fbg_program* p, int option, int64_t v) {
       if (v < 0 || v > 16) return bad();
       p->opt_popc_cost = v;
       break;
+    case FBG_OPT_ORDER_SEED:
+      if (v < 0 || v > 255) return bad();
+      p->opt_order_seed = v;
+      break;
     case FBG_OPT_SPLIT_ITEMS:   // read by the next fbg_schedule_units; kernels stay valid
       p->opt_split_items = v ? 1 : 0;
       return FBG_OK;
@@ -812,9 +816,10 @@ fbg_status fbg_truth_table(fbg_program* p, void* stream, uint64_t* dev_words, si
 // each item's first position, pass 2 writes the models of the items that
 // start below `cap`.
 static fbg_status enumerate_jit(fbg_program* p, cudaStream_t st, uint64_t* dev_models, size_t cap, uint64_t* total,
-                                uint64_t* written) {
+                                uint64_t* written, uint64_t ubegin = 0, uint64_t uend = ~0ull) {
   JitBuild& b = p->jb[2];
-  const uint64_t nitems = b.nunits << b.lp.layout.warp_bits;
+  uend = std::min<uint64_t>(uend, b.nunits);
+  const uint64_t nitems = (uend - ubegin) << b.lp.layout.warp_bits;
   if (nitems > (1ull << 26)) return set_error(FBG_ETOOBIG, "too many work items for a model list");
   fbg_status s = ensure_scratch(p, kScratchHead + 2 * nitems);
   if (s != FBG_OK) return s;
@@ -824,8 +829,8 @@ static fbg_status enumerate_jit(fbg_program* p, cudaStream_t st, uint64_t* dev_m
   p->scratch_clean = false;
   FbgLaunch P{};
   P.unit_ctr = p->d_scratch + 0;
-  P.unit_begin = 0;
-  P.unit_end = b.nunits;
+  P.unit_begin = ubegin;
+  P.unit_end = uend;
   P.unit_counts = item_counts;
   P.iters = p->opt_stats ? p->d_scratch + 4 : nullptr;
   const uint64_t wpb = (uint64_t)(b.block / 32);
@@ -846,6 +851,60 @@ static fbg_status enumerate_jit(fbg_program* p, cudaStream_t st, uint64_t* dev_m
   *total = tot;
   *written = std::min<uint64_t>(tot, cap);
   return FBG_OK;
+}
+
+fbg_status fbg_table_units(fbg_program* p, int mode, uint64_t* nunits, uint64_t* words_per_unit) {
+  if (!p || !nunits || !words_per_unit || (mode != 1 && mode != 2)) return set_error(FBG_EINVAL, "bad argument");
+  if (p->n > 40) return set_error(FBG_ETOOBIG, "truth tables and model lists need n <= 40");
+  if (p->opt_engine == FBG_ENGINE_INTERP) return set_error(FBG_EINVAL, "unit ranges need the specialised kernel");
+  fbg_status s = build_jit(p, mode);
+  if (s != FBG_OK) return s;
+  const Layout& L = p->jb[mode].lp.layout;
+  *nunits = 1ull << L.unit_bits;
+  const int below = p->n - L.unit_bits;   // letters inside one unit
+  *words_per_unit = below <= 6 ? 1ull : 1ull << (below - 6);
+  return FBG_OK;
+}
+
+fbg_status fbg_truth_table_range(fbg_program* p, void* stream, uint64_t unit_begin, uint64_t unit_end,
+                                 uint64_t* dev_words, size_t nwords) {
+  if (!p || !dev_words) return set_error(FBG_EINVAL, "null argument");
+  uint64_t nunits = 0, wpu = 0;
+  fbg_status s = fbg_table_units(p, 1, &nunits, &wpu);
+  if (s != FBG_OK) return s;
+  if (unit_begin >= unit_end || unit_end > nunits) return set_error(FBG_EINVAL, "empty or out-of-range unit range");
+  if (nunits > 1 && (p->n - p->jb[1].lp.layout.unit_bits) < 6)
+    return set_error(FBG_EINVAL, "units smaller than one 64-bit word: take the whole table");
+  const uint64_t need = (unit_end - unit_begin) * wpu;
+  if (nwords != need) return set_error(FBG_EINVAL, "nwords must be " + std::to_string(need));
+  cudaStream_t st = (cudaStream_t)stream;
+  s = ensure_scratch(p, kScratchHead);
+  if (s != FBG_OK) return s;
+  CK(cudaMemsetAsync(p->d_scratch, 0, kScratchHead * 8, st));
+  p->scratch_clean = false;
+  JitBuild& b = p->jb[1];
+  if (p->n < 6) CK(cudaMemsetAsync(dev_words, 0, 8, st));
+  FbgLaunch P{};
+  P.table = (fbg_u32*)dev_words;
+  P.table_word0 = unit_begin * wpu;
+  P.unit_ctr = p->d_scratch + 0;
+  P.unit_begin = unit_begin;
+  P.unit_end = unit_end;
+  const uint64_t grid = std::min<uint64_t>((uint64_t)b.grid, unit_end - unit_begin);
+  P.chunk = std::max<uint64_t>(1, (unit_end - unit_begin) / (grid * 16));
+  void* args[] = {&P};
+  CK(cudaLaunchKernel((const void*)b.kern, dim3((unsigned)grid), dim3((unsigned)b.block), args, 0, st));
+  return FBG_OK;
+}
+
+fbg_status fbg_enumerate_models_range(fbg_program* p, void* stream, uint64_t unit_begin, uint64_t unit_end,
+                                      uint64_t* dev_models, size_t cap, uint64_t* total, uint64_t* written) {
+  if (!p || !total || !written || (cap && !dev_models)) return set_error(FBG_EINVAL, "null argument");
+  uint64_t nunits = 0, wpu = 0;
+  fbg_status s = fbg_table_units(p, 2, &nunits, &wpu);
+  if (s != FBG_OK) return s;
+  if (unit_begin >= unit_end || unit_end > nunits) return set_error(FBG_EINVAL, "empty or out-of-range unit range");
+  return enumerate_jit(p, (cudaStream_t)stream, dev_models, cap, total, written, unit_begin, unit_end);
 }
 
 fbg_status fbg_enumerate_models(fbg_program* p, void* stream, uint64_t* dev_models, size_t cap, uint64_t* total,

@@ -88,6 +88,7 @@ extern "C" fbg_status fbg_autotune(fbg_program* p, void* stream, int mode, int r
       {FBG_OPT_UNIT_BITS, {10, 12, 13, 14}},
       {FBG_OPT_INNER_BITS, {0, 1, 3, 4}},
       {FBG_OPT_POPC_COST, {0, 2, 4, 8}},
+      {FBG_OPT_ORDER_SEED, {0, 1, 2, 3, 4, 5, 6, 7}},
   };
   auto get = [&](int opt) -> int64_t {
     switch (opt) {
@@ -97,6 +98,7 @@ extern "C" fbg_status fbg_autotune(fbg_program* p, void* stream, int mode, int r
       case FBG_OPT_WARPS_LOG2: return p->opt_warps_log2;
       case FBG_OPT_INNER_BITS: return p->opt_inner_bits;
       case FBG_OPT_POPC_COST: return p->opt_popc_cost;
+      case FBG_OPT_ORDER_SEED: return p->opt_order_seed;
       default: return p->opt_unit_bits;
     }
   };
@@ -109,6 +111,7 @@ extern "C" fbg_status fbg_autotune(fbg_program* p, void* stream, int mode, int r
     return err;
   }
   for (const Knob& k : knobs) {
+    if (mode != 0 && (k.option == FBG_OPT_ORDER_SEED || k.option == FBG_OPT_POPC_COST)) continue;   // count-only knobs
     int64_t keep = get(k.option);
     for (int64_t v : k.values) {
       if (v == keep) continue;
@@ -136,5 +139,6 @@ extern "C" fbg_status fbg_autotune(fbg_program* p, void* stream, int mode, int r
   out->unit_bits = (int)p->opt_unit_bits;
   out->inner_bits = (int)p->opt_inner_bits;
   out->popc_cost = (int)p->opt_popc_cost;
+  out->order_seed = (int)p->opt_order_seed;
   return err;
 }

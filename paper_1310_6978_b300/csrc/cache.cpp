@@ -98,7 +98,8 @@ std::string build_key(const fbg_program* p, const char* what, int mode) {
   std::string key = what;
   key += ":" + std::to_string(mode);
   for (int64_t v : {p->opt_prune, p->opt_regs_log2, p->opt_warps_log2, p->opt_unit_bits, p->opt_loop_level_bits,
-                    p->opt_search, p->opt_min_blocks, p->opt_stats, p->opt_inner_bits, p->opt_popc_cost})
+                    p->opt_search, p->opt_min_blocks, p->opt_stats, p->opt_inner_bits, p->opt_popc_cost,
+                    p->opt_order_seed})
     key += ":" + std::to_string(v);
   key += ":" + std::to_string(p->k) + "\n" + p->text;
   return key;

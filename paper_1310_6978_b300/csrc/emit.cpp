@@ -632,13 +632,13 @@ class SrcGen {
     if (L.r == 0) {
       o << ind << "reinterpret_cast<fbg_u64*>(table)[0] = (fbg_u64)" << w[0] << ";\n";
     } else if (L.r == 1) {
-      o << ind << "reinterpret_cast<uint2*>(table)[" << T << "] = make_uint2(" << w[0] << ", " << w[1] << ");\n";
+      o << ind << "reinterpret_cast<uint2*>(table)[(" << T << ") - tile0] = make_uint2(" << w[0] << ", " << w[1] << ");\n";
     } else if (L.r == 2) {
-      o << ind << "reinterpret_cast<uint4*>(table)[" << T << "] = make_uint4(" << w[0] << ", " << w[1] << ", " << w[2]
-        << ", " << w[3] << ");\n";
+      o << ind << "reinterpret_cast<uint4*>(table)[(" << T << ") - tile0] = make_uint4(" << w[0] << ", " << w[1] << ", "
+        << w[2] << ", " << w[3] << ");\n";
     } else {
       for (int q = 0; q < nreg / 4; q++)
-        o << ind << "reinterpret_cast<uint4*>(table)[(" << T << ") * " << nreg / 4 << " + " << q << "] = make_uint4("
+        o << ind << "reinterpret_cast<uint4*>(table)[((" << T << ") - tile0) * " << nreg / 4 << " + " << q << "] = make_uint4("
           << w[4 * q] << ", " << w[4 * q + 1] << ", " << w[4 * q + 2] << ", " << w[4 * q + 3] << ");\n";
     }
   }
@@ -831,7 +831,7 @@ std::string SrcGen::unit_fn_table(const std::string& fname) {
   auto vars = used_vars();
   const int tvalid = 1 << (L.lane_bits + L.warp_bits);
   const int last = nl - 1;
-  o << "__device__ __noinline__ void " << fname << "(fbg_u64 u, fbg_u32* table, fbg_u64* lvl) {\n";
+  o << "__device__ __noinline__ void " << fname << "(fbg_u64 u, fbg_u32* table, fbg_u64 tile0, fbg_u64* lvl) {\n";
   o << "  const fbg_u32 tb = threadIdx.x;\n";
   o << "  const fbg_u32 tm = (tb < " << tvalid << "u) ? " << hex32(valid_mask()) << " : 0u;\n";
   var_words(vars[0], "tb", L.first_lane_pos(), "  ", false);
@@ -1030,7 +1030,9 @@ std::string SrcGen::generate(int mode, int block, int minb) {
   o << "    const fbg_u64 u = fbg_next_units(P, &s_unit, chunk);\n";
   o << "    if (u >= P.unit_end) break;\n";
   o << "    const fbg_u64 e = u + chunk < P.unit_end ? u + chunk : P.unit_end;\n";
-  o << "    for (fbg_u64 v = u; v < e; ++v) fbg_unit_table(v, P.table, lvl);\n";
+  // a slice of the table starts at 64-bit word P.table_word0: tiles of 2^r
+  // 32-bit words before it are not stored
+  o << "    for (fbg_u64 v = u; v < e; ++v) fbg_unit_table(v, P.table, (P.table_word0 * 2ull) >> " << L.r << ", lvl);\n";
   o << "  }\n";
   o << "  if (P.iters && (threadIdx.x & 31u) == 0u) {\n";
   o << "    for (int l = 0; l < " << nl << "; l++) if (lvl[l]) atomicAdd(P.iters + l, lvl[l]);\n";

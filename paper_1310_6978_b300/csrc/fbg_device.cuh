@@ -32,6 +32,8 @@ struct FbgLaunch {
   fbg_u64* done;           //   warps finished, the destination of the total, warps in the grid;
   fbg_u64* out;            //   acc, done and unit_ctr are zero before the launch and after it
   fbg_u32 nwarps;
+  fbg_u64 table_word0;     // table mode: 64-bit word index of the first word of `table` (a slice
+                           // of the units [unit_begin, unit_end); 0 for a whole table)
 };
 
 #define FBG_FULL 0xffffffffu

@@ -157,7 +157,9 @@ struct LayoutParams {
 
 Layout make_layout(int n, const LayoutParams& prm, const std::vector<int>& order_top_first);
 std::vector<int> identity_order(int n);                          // top position first
-std::vector<int> search_order(const Grounded& g);                // count-mode heuristic
+// count-mode heuristic; seed != 0 breaks ties between equally good letters
+// by a seeded hash instead of the lowest index (a variant the autotuner tries)
+std::vector<int> search_order(const Grounded& g, uint64_t seed = 0);
 std::vector<int> enum_order(int n, const LayoutParams& prm);     // enumerate mode: items are intervals
 // Per work item (unit u, warp slice w) of layout L, index u << warp_bits | w
 // (1 byte each): 0 when a top-level conjunct whose letters all sit in unit

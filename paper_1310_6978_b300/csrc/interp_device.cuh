@@ -86,6 +86,13 @@ __device__ __forceinline__ void set_thread_coords(Thread& T, fbg_u64 upper) {
 
 __device__ __forceinline__ Pair fetch(const Shared& S, const Thread& T, unsigned op) {
   Pair r;
+  // tile slots (codes below FBG_OP_SHARED) are the most frequent operands:
+  // one test, and 32-bit shared-memory offsets
+  if (op < FBG_OP_SHARED) {
+#pragma unroll
+    for (int k = 0; k < NTILE; k++) r.v[k] = T.slots[op * (unsigned)B + (unsigned)(k * NT)];
+    return r;
+  }
   if (op == FBG_OP_ACC) return T.acc;
   if (op & FBG_OP_VAR) {
 #pragma unroll
@@ -100,14 +107,9 @@ __device__ __forceinline__ Pair fetch(const Shared& S, const Thread& T, unsigned
     for (int k = 0; k < NTILE; k++) r.v[k] = c;
     return r;
   }
-  if (op & FBG_OP_SHARED) {
-    const fbg_u64 c = S.svals[op & 0xFFFu];
+  const fbg_u64 c = S.svals[op & 0xFFFu];   // a block slot
 #pragma unroll
-    for (int k = 0; k < NTILE; k++) r.v[k] = c;
-    return r;
-  }
-#pragma unroll
-  for (int k = 0; k < NTILE; k++) r.v[k] = T.slots[(unsigned long long)op * B + k * NT];
+  for (int k = 0; k < NTILE; k++) r.v[k] = c;
   return r;
 }
 
@@ -137,7 +139,7 @@ __device__ __forceinline__ void exec_level(Shared& S, Thread& T, const FbgInterp
       __syncwarp();
     } else {
 #pragma unroll
-      for (int k = 0; k < NTILE; k++) T.slots[(unsigned long long)dst * B + k * NT] = d.v[k];
+      for (int k = 0; k < NTILE; k++) T.slots[dst * (unsigned)B + (unsigned)(k * NT)] = d.v[k];
     }
     w = next;
   }
@@ -220,7 +222,7 @@ __device__ void run_unit(Shared& S, Thread& T, fbg_u64 u, const FbgLaunch& P, fb
       } else if (MODE == 1) {
 #pragma unroll
         for (int k = 0; k < NTILE; k++)
-          if (tvalid[k]) reinterpret_cast<fbg_u64*>(P.table)[T.coords[k] >> 6] = word[k];
+          if (tvalid[k]) reinterpret_cast<fbg_u64*>(P.table)[(T.coords[k] >> 6) - P.table_word0] = word[k];
       } else {
         // ordered compaction: tiles ascend with lane + 32 k, so all tiles 0
         // of the warp precede all tiles 1

@@ -126,7 +126,15 @@ static std::vector<uint64_t> supports(const FormDag& d) {
 // variables already placed, then the one most connected to them, then the
 // most frequent.  Conjuncts decided high up let whole warps skip inner
 // levels; the order does not change any count.
-std::vector<int> search_order(const Grounded& g) {
+// tie-break of search_order variant `seed` (splitmix64 of seed, step, letter)
+static uint64_t order_tie(uint64_t seed, int step, int v) {
+  uint64_t z = seed * 0x9E3779B97F4A7C15ull + (uint64_t)step * 0xBF58476D1CE4E5B9ull + (uint64_t)v * 0x94D049BB133111EBull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+std::vector<int> search_order(const Grounded& g, uint64_t seed) {
   const FormDag& d = g.dag;
   std::vector<uint64_t> sup = supports(d);
   std::vector<uint64_t> conj;
@@ -155,7 +163,10 @@ std::vector<int> search_order(const Grounded& g) {
         conn += __builtin_popcountll(s & chosen);
       }
       long long key[3] = {done, conn, occ[(size_t)v]};
-      if (best < 0 || std::lexicographical_compare(bk, bk + 3, key, key + 3)) {
+      const bool tie = best >= 0 && !std::lexicographical_compare(bk, bk + 3, key, key + 3) &&
+                       !std::lexicographical_compare(key, key + 3, bk, bk + 3);
+      if (best < 0 || std::lexicographical_compare(bk, bk + 3, key, key + 3) ||
+          (tie && seed && order_tie(seed, step, v) < order_tie(seed, step, best))) {
         best = v;
         std::memcpy(bk, key, sizeof bk);
       }

@@ -4,8 +4,12 @@ The assignment space is cut by the unit bits (the top of the layout): rank g
 of G counts a contiguous range of units with ``fbg_count_range`` and the
 partial counts are added with one 8-byte all-reduce, the only exchange the
 method has (counts over disjoint sets of assignments add, Sec. 3.2).  Truth
-tables and model lists would concatenate per-rank slices in rank order; only
-the count is provided here.
+tables and model lists split the same way: rank g evaluates the table words
+or the models of its contiguous unit range (fbg_truth_table_range,
+fbg_enumerate_models_range), and the whole table or list is the
+concatenation of the ranks' parts in rank order.  A capped model list needs
+one more 8-byte exchange: every rank's number of models, which fixes where
+its part starts and how much of it falls under the cap.
 """
 from __future__ import annotations
 
@@ -48,3 +52,56 @@ def count_sharded(prog, group=None, stream=None) -> int:
     t = torch.tensor([to_int64_bits(local)], dtype=torch.int64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
     return int(t.item()) & MASK64
+
+
+def keep_counts(totals, written, cap: int):
+    """For a model list split over ranks in rank order: rank g found
+    totals[g] models in its range and stored the first written[g]; the global
+    list keeps the first ``cap`` models overall.  Returns (offsets, keep):
+    rank g's models start at position offsets[g] of the global list, and its
+    first keep[g] stored models belong to the list."""
+    offsets, keep, at = [], [], 0
+    for t, w in zip(totals, written):
+        offsets.append(at)
+        keep.append(max(0, min(w, cap - at)))
+        at += t
+    return offsets, keep
+
+
+def table_sharded(prog, group=None, stream=None):
+    """This rank's part of the truth table: (index of its first 64-bit word
+    in the whole table, a tensor of its words).  ``prog`` needs
+    ``table_units(1)`` and ``truth_table_range(begin, end, words, stream)``."""
+    import torch
+    import torch.distributed as dist
+    rank, world = dist.get_rank(group), dist.get_world_size(group)
+    nunits, wpu = prog.table_units(1)
+    begin, end = unit_range(nunits, rank, world)
+    dev = "cuda" if dist.get_backend(group) == "nccl" else "cpu"
+    words = torch.empty(max(0, end - begin) * wpu, dtype=torch.int64, device=dev)
+    if end > begin:
+        prog.truth_table_range(begin, end, words, stream)
+    return begin * wpu, words
+
+
+def models_sharded(prog, cap: int, group=None, stream=None):
+    """This rank's part of the list of the first ``cap`` models in ascending
+    order: (exact number of models over all ranks, position of this rank's
+    part in the global list, a tensor of its models that belong to the
+    list).  One 8-byte exchange (every rank's model count) sizes the parts.
+    ``prog`` needs ``table_units(2)`` and ``enumerate_models_range``."""
+    import torch
+    import torch.distributed as dist
+    rank, world = dist.get_rank(group), dist.get_world_size(group)
+    nunits, _ = prog.table_units(2)
+    begin, end = unit_range(nunits, rank, world)
+    dev = "cuda" if dist.get_backend(group) == "nccl" else "cpu"
+    buf = torch.empty(max(1, cap), dtype=torch.int64, device=dev)
+    total, written = prog.enumerate_models_range(begin, end, buf, cap, stream) if end > begin else (0, 0)
+    mine = torch.tensor([to_int64_bits(total), to_int64_bits(written)], dtype=torch.int64, device=dev)
+    every = [torch.zeros_like(mine) for _ in range(world)]
+    dist.all_gather(every, mine, group=group)
+    totals = [int(t[0].item()) & MASK64 for t in every]
+    writtens = [int(t[1].item()) & MASK64 for t in every]
+    offsets, keep = keep_counts(totals, writtens, cap)
+    return sum(totals), offsets[rank], buf[:keep[rank]]

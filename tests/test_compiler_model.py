@@ -121,3 +121,16 @@ def test_dag_sharing_and_constant_removal():
     a = F.compile("var a, b\n(a | 0) & (b | 0) & 1\n").stats()
     b = F.compile("var a, b\na & b\na & b\n").stats()
     assert a.luts == b.luts
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 5])
+def test_order_variants_keep_counts(seed):
+    # the seeded tie-break variants of the count order (FBG_OPT_ORDER_SEED)
+    # place the letters differently and leave every count unchanged
+    import oracle
+    from paper_1310_6978_b300 import _lib as L
+    for wl in (W.triangle_free(6), W.posets(4), W.transitive(4), W.cnf3(14, 3)):
+        p = F.compile(wl.text, wl.k).set_option(L.OPT_ORDER_SEED, seed)
+        d = p.debug_dump(0)
+        assert sorted(d["layout"]["pos_of_var"]) == list(range(wl.n))
+        assert KM.lut_program_count(d) == oracle.Theory(wl.text, wl.k).count()
