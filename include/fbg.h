@@ -473,6 +473,10 @@ fbg_status fbg_server_submit(fbg_server *srv, const char *formula, int domain_k,
                              uint64_t *request_id);
 /* FBG_OK with *out filled when done, FBG_EBUSY while pending */
 fbg_status fbg_server_poll(fbg_server *srv, uint64_t request_id, fbg_result *out);
+/* ids of requests finished since the last call, oldest first: up to max_ids
+   go to ids[], *n receives how many (each finished request is handed out
+   once; poll it for the result, then release it) */
+fbg_status fbg_server_completed(fbg_server *srv, uint64_t *ids, size_t max_ids, size_t *n);
 /* block until every submitted request is done (timeout_s <= 0: no limit) */
 fbg_status fbg_server_drain(fbg_server *srv, double timeout_s);
 /* release a finished request's result memory */
@@ -482,6 +486,9 @@ fbg_status fbg_server_stats(fbg_server *srv, uint64_t *ticks, uint64_t *launches
    their interpreter programs), in ticks (launches to completion) and copying
    finished model lists to the host */
 fbg_status fbg_server_profile(fbg_server *srv, double *admit_s, double *count_s, double *enum_s);
+/* diagnostics: seconds of device time of the ticks' launches (CUDA events
+   around each tick's launches), summed */
+fbg_status fbg_server_gpu_time(fbg_server *srv, double *gpu_s);
 void fbg_server_free(fbg_server *srv);
 
 #ifdef __cplusplus

@@ -357,6 +357,13 @@ class Server:
         return {"status": r.status, "count": r.count, "written": r.written, "models": models,
                 "submit_s": r.submit_s, "admit_s": r.admit_s, "done_s": r.done_s}
 
+    def completed(self, max_ids: int = 4096):
+        """fbg_server_completed: ids of requests finished since the last call."""
+        buf = (ctypes.c_uint64 * max_ids)()
+        n = ctypes.c_size_t()
+        self._L.check(self._L.lib.fbg_server_completed(self._h, buf, max_ids, ctypes.byref(n)))
+        return [buf[i] for i in range(n.value)]
+
     def drain(self, timeout_s: float = 0.0) -> None:
         self._L.check(self._L.lib.fbg_server_drain(self._h, timeout_s))
 
@@ -368,5 +375,7 @@ class Server:
         self._L.check(self._L.lib.fbg_server_stats(self._h, ctypes.byref(t), ctypes.byref(l), ctypes.byref(b)))
         a, c, e = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         self._L.check(self._L.lib.fbg_server_profile(self._h, ctypes.byref(a), ctypes.byref(c), ctypes.byref(e)))
+        g = ctypes.c_double()
+        self._L.check(self._L.lib.fbg_server_gpu_time(self._h, ctypes.byref(g)))
         return {"ticks": t.value, "launches": l.value, "busy_s": b.value, "admit_s": a.value, "count_s": c.value,
-                "enum_s": e.value}
+                "enum_s": e.value, "gpu_s": g.value}

@@ -113,11 +113,13 @@ _sig("fbg_batch_free", None, c_vp)
 _sig("fbg_server_create", c_int, ctypes.POINTER(FbgServerOptions), ctypes.POINTER(c_vp))
 _sig("fbg_server_submit", c_int, c_vp, c_char_p, c_int, c_int, c_u64, ctypes.POINTER(c_u64))
 _sig("fbg_server_poll", c_int, c_vp, c_u64, ctypes.POINTER(FbgResult))
+_sig("fbg_server_completed", c_int, c_vp, ctypes.POINTER(c_u64), c_sz, ctypes.POINTER(c_sz))
 _sig("fbg_server_drain", c_int, c_vp, ctypes.c_double)
 _sig("fbg_server_release", c_int, c_vp, c_u64)
 _sig("fbg_server_stats", c_int, c_vp, ctypes.POINTER(c_u64), ctypes.POINTER(c_u64), ctypes.POINTER(ctypes.c_double))
 _sig("fbg_server_profile", c_int, c_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
      ctypes.POINTER(ctypes.c_double))
+_sig("fbg_server_gpu_time", c_int, c_vp, ctypes.POINTER(ctypes.c_double))
 _sig("fbg_server_free", None, c_vp)
 
 

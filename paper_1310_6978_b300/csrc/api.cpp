@@ -144,6 +144,15 @@ static std::shared_ptr<const InterpHost> interp_host(fbg_program* p, int which) 
   return hc;
 }
 
+fbg_status prebuild_interp_host(fbg_program* p, int which) {
+  try {
+    interp_host(p, which);
+  } catch (CompileError& e) {
+    return set_error(FBG_ETOOBIG, e.msg);
+  }
+  return FBG_OK;
+}
+
 fbg_status build_interp(fbg_program* p, int which) {
   InterpBuild& b = p->ib[which];
   if (b.valid) return FBG_OK;
@@ -166,19 +175,29 @@ fbg_status build_interp(fbg_program* p, int which) {
   b.units_per_item = per;
   b.nitems = items.size();
   b.free_device();
-  CK(cudaMalloc(&b.d_ins, std::max<size_t>(1, b.code.ins.size()) * 8));
-  CK(cudaMalloc(&b.d_consts, std::max<size_t>(1, b.code.consts.size()) * 8));
-  CK(cudaMalloc(&b.d_prog, sizeof(FbgInterpProg)));
-  CK(cudaMalloc(&b.d_items, std::max<size_t>(1, items.size()) * sizeof(FbgWorkItem)));
-  if (!b.code.ins.empty()) CK(cudaMemcpy(b.d_ins, b.code.ins.data(), b.code.ins.size() * 8, cudaMemcpyHostToDevice));
-  if (!b.code.consts.empty())
-    CK(cudaMemcpy(b.d_consts, b.code.consts.data(), b.code.consts.size() * 8, cudaMemcpyHostToDevice));
+  // one allocation and one copy: [descriptor][bytecode][constants][items],
+  // each part 16-byte aligned
+  auto al = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  const size_t off_ins = al(sizeof(FbgInterpProg));
+  const size_t off_consts = al(off_ins + std::max<size_t>(1, b.code.ins.size()) * 8);
+  const size_t off_items = al(off_consts + std::max<size_t>(1, b.code.consts.size()) * 8);
+  const size_t total = off_items + std::max<size_t>(1, items.size()) * sizeof(FbgWorkItem);
+  char* base = nullptr;
+  CK(cudaMalloc(&base, total));
+  b.d_prog = reinterpret_cast<FbgInterpProg*>(base);
+  b.d_ins = reinterpret_cast<unsigned long long*>(base + off_ins);
+  b.d_consts = reinterpret_cast<unsigned long long*>(base + off_consts);
+  b.d_items = reinterpret_cast<FbgWorkItem*>(base + off_items);
+  std::vector<char> staging(total, 0);
   FbgInterpProg G = b.code.prog;
   G.ins = b.d_ins;
   G.consts = b.d_consts;
-  CK(cudaMemcpy(b.d_prog, &G, sizeof G, cudaMemcpyHostToDevice));
-  if (!items.empty())
-    CK(cudaMemcpy(b.d_items, items.data(), items.size() * sizeof(FbgWorkItem), cudaMemcpyHostToDevice));
+  std::memcpy(staging.data(), &G, sizeof G);
+  if (!b.code.ins.empty()) std::memcpy(staging.data() + off_ins, b.code.ins.data(), b.code.ins.size() * 8);
+  if (!b.code.consts.empty())
+    std::memcpy(staging.data() + off_consts, b.code.consts.data(), b.code.consts.size() * 8);
+  if (!items.empty()) std::memcpy(staging.data() + off_items, items.data(), items.size() * sizeof(FbgWorkItem));
+  CK(cudaMemcpy(base, staging.data(), total, cudaMemcpyHostToDevice));
   int per_sm = interp_blocks_per_sm(which == 0 ? 0 : 2, b.code.nslots);
   if (per_sm <= 0) return set_error(FBG_ETOOBIG, "interpreter program does not fit in shared memory");
   b.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(b.nitems, (uint64_t)device_sms() * (uint64_t)per_sm));

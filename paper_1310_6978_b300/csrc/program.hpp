@@ -41,11 +41,10 @@ struct InterpBuild {
       i += len;
     }
   }
+  // descriptor, bytecode, constants and items share one device allocation
+  // (d_prog is its start)
   void free_device() {
     if (d_prog) cudaFree(d_prog);
-    if (d_ins) cudaFree(d_ins);
-    if (d_consts) cudaFree(d_consts);
-    if (d_items) cudaFree(d_items);
     d_prog = nullptr;
     d_ins = d_consts = nullptr;
     d_items = nullptr;
@@ -135,6 +134,9 @@ LayoutParams jit_params(const fbg_program* p);
 void strip_prune(LutProgram& lp);
 std::vector<int> order_for(const fbg_program* p, bool count_layout);
 fbg_status build_interp(fbg_program* p, int which);
+// the host half of an interpreter build (layout, LUTs, bytecode, live units)
+// into the build cache, so that a later build_interp only uploads
+fbg_status prebuild_interp_host(fbg_program* p, int which);
 fbg_status build_jit(fbg_program* p, int mode);
 fbg_status pick_engine(fbg_program* p, int mode, bool* use_jit);
 }  // namespace fbg

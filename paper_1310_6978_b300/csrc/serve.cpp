@@ -73,6 +73,7 @@ struct fbg_server {
   bool stop = false;
   uint64_t next_id = 1;
   std::deque<Request*> pending;
+  std::deque<uint64_t> completed;                 // finished requests not yet handed out by fbg_server_completed
   std::vector<Request*> active;                   // admitted, not finished
   std::unordered_map<uint64_t, std::unique_ptr<Request>> all;
   uint64_t outstanding = 0;
@@ -99,6 +100,8 @@ struct fbg_server {
   std::atomic<uint64_t> ticks{0}, launches{0};
   double busy_s = 0;
   double admit_s = 0, count_s = 0, enum_s = 0;   // server-thread time by activity
+  double gpu_s = 0;                               // device time of the ticks' launches (CUDA events)
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   fbg_status fatal = FBG_OK;
 
   void run();
@@ -137,6 +140,7 @@ void fbg_server::finish(Request* r, fbg_status s) {
   r->status = s;
   r->done_s = now_s();
   r->done = true;
+  completed.push_back(r->id);
   if (r->slot >= 0) {
     free_slots.push_back(r->slot);
     r->slot = -1;
@@ -263,6 +267,7 @@ void fbg_server::tick() {
       if (!cnt && r->next_unit >= r->nunits) writes.push_back(r);
     }
     cudaError_t e = cudaMemcpyAsync(d_items, h_items, n * sizeof(FbgWorkItem), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev0, stream);
     uint64_t slots = (uint64_t)opt.max_inflight;
     if (e == cudaSuccess) e = cudaMemsetAsync(d_counts + slots, 0, 8, stream);
     int per_sm = interp_blocks_per_sm(0, nslots);
@@ -303,8 +308,13 @@ void fbg_server::tick() {
                           std::max(1, wgrid), stream, d_slot_out);
       launches += 1 + writes.size();
     }
+    if (e == cudaSuccess) e = cudaEventRecord(ev1, stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h_counts, d_counts, slots * 8, cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e == cudaSuccess) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess) gpu_s += ms * 1e-3;
+    }
     // the model lists of the finished requests (their totals are now known)
     const double tw = now_s();
     for (Request* r : writes) {
@@ -370,6 +380,7 @@ fbg_status fbg_server_create(const fbg_server_options* opt, fbg_server** out) {
   const size_t slots = (size_t)s->opt.max_inflight;
   cudaError_t e;
   if ((e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreate(&s->ev0)) != cudaSuccess || (e = cudaEventCreate(&s->ev1)) != cudaSuccess ||
       (e = cudaMalloc(&s->d_progs, slots * sizeof(FbgInterpProg))) != cudaSuccess ||
       (e = cudaMallocHost(&s->h_progs, slots * sizeof(FbgInterpProg))) != cudaSuccess ||
       (e = cudaMalloc(&s->d_counts, (slots + 1) * 8)) != cudaSuccess ||
@@ -400,6 +411,13 @@ fbg_status fbg_server_submit(fbg_server* s, const char* formula, int domain_k, i
   // work items that spread over every SM instead of a few long ones
   p->opt_engine = FBG_ENGINE_INTERP;
   p->opt_unit_bits = 16;
+  // the host half of the interpreter build runs here, on the submitting
+  // thread; admission on the server thread then only uploads it
+  st = prebuild_interp_host(p, mode == FBG_MODE_COUNT ? 0 : 1);
+  if (st != FBG_OK) {
+    fbg_program_free(p);
+    return st;
+  }
   if (p->n > (mode == FBG_MODE_COUNT ? 63 : 40)) {
     fbg_program_free(p);
     return set_error(FBG_ETOOBIG, "request too large");
@@ -438,6 +456,18 @@ fbg_status fbg_server_poll(fbg_server* s, uint64_t id, fbg_result* out) {
   return FBG_OK;
 }
 
+fbg_status fbg_server_completed(fbg_server* s, uint64_t* ids, size_t max_ids, size_t* n) {
+  if (!s || !n || (max_ids && !ids)) return set_error(FBG_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  size_t k = 0;
+  while (k < max_ids && !s->completed.empty()) {
+    ids[k++] = s->completed.front();
+    s->completed.pop_front();
+  }
+  *n = k;
+  return FBG_OK;
+}
+
 fbg_status fbg_server_drain(fbg_server* s, double timeout_s) {
   if (!s) return set_error(FBG_EINVAL, "null server");
   std::unique_lock<std::mutex> lk(s->mu);
@@ -465,6 +495,13 @@ fbg_status fbg_server_stats(fbg_server* s, uint64_t* ticks, uint64_t* launches, 
   if (ticks) *ticks = s->ticks.load();
   if (launches) *launches = s->launches.load();
   if (busy_s) *busy_s = s->busy_s;
+  return FBG_OK;
+}
+
+fbg_status fbg_server_gpu_time(fbg_server* s, double* gpu_s) {
+  if (!s || !gpu_s) return set_error(FBG_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  *gpu_s = s->gpu_s;
   return FBG_OK;
 }
 
@@ -502,6 +539,8 @@ void fbg_server_free(fbg_server* s) {
   if (s->h_slot_out) cudaFreeHost(s->h_slot_out);
   if (s->d_scan_total) cudaFree(s->d_scan_total);
   if (s->h_models) cudaFreeHost(s->h_models);
+  if (s->ev0) cudaEventDestroy(s->ev0);
+  if (s->ev1) cudaEventDestroy(s->ev1);
   if (s->stream) cudaStreamDestroy(s->stream);
   delete s;
 }

@@ -126,3 +126,15 @@ def test_submit_errors_and_release():
     with pytest.raises(L.FbgError):
         srv.poll(rid)
     srv.close()
+
+
+def test_completed_queue_hands_out_each_finished_request_once():
+    srv = F.Server()
+    ids = [srv.submit(W.posets(k).text, k, L.MODE_COUNT, 0) for k in (2, 3, 4, 3)]
+    srv.drain(60)
+    seen = srv.completed(2) + srv.completed()
+    assert sorted(seen) == sorted(ids) and srv.completed() == []
+    for rid, want in zip(ids, (3, 19, 219, 19)):
+        assert srv.poll(rid)["count"] == want
+        srv.release(rid)
+    srv.close()
