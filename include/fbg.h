@@ -446,8 +446,9 @@ void fbg_batch_free(fbg_batch *batch);
  * more launch (shared by all model lists finishing in that tick) writes the
  * models in ascending j into a device buffer of `cap` words, from which the
  * first min(cap, total) reach the result.  A host thread drives the ticks on
- * its own stream; per-request device buffers come from the stream-ordered
- * allocator of that stream.
+ * its own stream, two ticks in flight (it prepares and enqueues the next tick
+ * while the GPU runs the current one); per-request device buffers come from
+ * the stream-ordered allocator.
  */
 typedef struct {
   uint64_t mem_budget_bytes;   /* device memory for admitted requests (0 = 1 GiB) */

@@ -183,7 +183,13 @@ fbg_status build_interp(fbg_program* p, int which) {
   const size_t off_items = al(off_consts + std::max<size_t>(1, b.code.consts.size()) * 8);
   const size_t total = off_items + std::max<size_t>(1, items.size()) * sizeof(FbgWorkItem);
   char* base = nullptr;
-  CK(cudaMalloc(&base, total));
+  if (p->alloc_stream) {
+    CK(cudaMallocAsync((void**)&base, total, p->alloc_stream));
+    b.pooled = true;
+    b.free_stream = p->free_stream ? p->free_stream : p->alloc_stream;
+  } else {
+    CK(cudaMalloc(&base, total));
+  }
   b.d_prog = reinterpret_cast<FbgInterpProg*>(base);
   b.d_ins = reinterpret_cast<unsigned long long*>(base + off_ins);
   b.d_consts = reinterpret_cast<unsigned long long*>(base + off_consts);
@@ -197,7 +203,10 @@ fbg_status build_interp(fbg_program* p, int which) {
   if (!b.code.consts.empty())
     std::memcpy(staging.data() + off_consts, b.code.consts.data(), b.code.consts.size() * 8);
   if (!items.empty()) std::memcpy(staging.data() + off_items, items.data(), items.size() * sizeof(FbgWorkItem));
-  CK(cudaMemcpy(base, staging.data(), total, cudaMemcpyHostToDevice));
+  if (p->alloc_stream)   // returns once the pageable source is staged
+    CK(cudaMemcpyAsync(base, staging.data(), total, cudaMemcpyHostToDevice, p->alloc_stream));
+  else
+    CK(cudaMemcpy(base, staging.data(), total, cudaMemcpyHostToDevice));
   int per_sm = interp_blocks_per_sm(which == 0 ? 0 : 2, b.code.nslots);
   if (per_sm <= 0) return set_error(FBG_ETOOBIG, "interpreter program does not fit in shared memory");
   b.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(b.nitems, (uint64_t)device_sms() * (uint64_t)per_sm));

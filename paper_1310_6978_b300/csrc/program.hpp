@@ -42,9 +42,16 @@ struct InterpBuild {
     }
   }
   // descriptor, bytecode, constants and items share one device allocation
-  // (d_prog is its start)
+  // (d_prog is its start); a build from the stream-ordered pool is freed in
+  // the order of free_stream, without waiting for the device
+  bool pooled = false;
+  cudaStream_t free_stream = nullptr;
   void free_device() {
-    if (d_prog) cudaFree(d_prog);
+    if (d_prog) {
+      if (pooled) cudaFreeAsync(d_prog, free_stream);
+      else cudaFree(d_prog);
+    }
+    pooled = false;
     d_prog = nullptr;
     d_ins = d_consts = nullptr;
     d_items = nullptr;
@@ -105,6 +112,9 @@ struct fbg_program {
   fbg::JitBuild jb[3];      // [0] count kernel, [1] truth-table kernel, [2] enumerate kernel
   unsigned long long* d_scratch = nullptr;
   bool scratch_clean = false;   // counters of self-resetting count launches are zero
+  // when set (by the server), interpreter builds come from the stream-ordered
+  // pool: allocated and uploaded on alloc_stream, freed on free_stream
+  cudaStream_t alloc_stream = nullptr, free_stream = nullptr;
   size_t scratch_words = 0;
   fbg_exec_stats last{};
   // wall time (s) in kernel builds and in fbg_count outside builds (fbg_debug_host_times)

@@ -12,8 +12,13 @@
 // tick where its last unit is counted, a scan turns those counts into unit
 // offsets and one more launch, over every such request of the tick, writes
 // the models in ascending order into the request's device buffer.  Requests
-// arriving while a tick runs join the next tick.  Every tick is a bounded
-// launch: nothing runs forever on the GPU.
+// arriving while a tick runs join the next tick.  Two ticks are in flight:
+// the server thread enqueues tick k+1 (admission, items, launches) while the
+// GPU runs tick k, then completes tick k (its counts and model lists come
+// back through double-buffered pinned memory); programs are uploaded on a
+// stream of their own from the stream-ordered pool, so no host step waits
+// for the GPU except the completion of the older tick.  Every tick is a
+// bounded launch: nothing runs forever on the GPU.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -83,29 +88,45 @@ struct fbg_server {
   FbgInterpProg* d_progs = nullptr;               // one descriptor per slot
   FbgInterpProg* h_progs = nullptr;               // pinned staging
   unsigned long long* d_counts = nullptr;         // per-slot partial counts, then the item counter
-  unsigned long long* h_counts = nullptr;         // pinned
-  FbgWorkItem* d_items = nullptr;
-  FbgWorkItem* h_items = nullptr;                 // pinned
+  // two ticks can be in flight: items and the copy of the counts are double
+  // buffered (index = tick number & 1)
+  unsigned long long* h_counts_buf[2] = {nullptr, nullptr};   // pinned
+  FbgWorkItem* d_items_buf[2] = {nullptr, nullptr};
+  FbgWorkItem* h_items_buf[2] = {nullptr, nullptr};           // pinned
+  cudaStream_t upload = nullptr;                  // uploads of admitted programs (pageable sources)
+  cudaStream_t copies = nullptr;                  // copies of finished model lists to the host
+  cudaEvent_t uploaded = nullptr;
   uint64_t item_cap = 0;
   std::vector<int> free_slots;
   FbgSlotOut* d_slot_out = nullptr;               // per-slot outputs of model lists
   FbgSlotOut* h_slot_out = nullptr;               // pinned staging
-  FbgWorkItem* d_witems = nullptr;                // items of the write launch
+  FbgWorkItem* d_witems_buf[2] = {nullptr, nullptr};   // items of the write launch (per tick parity)
+  FbgWorkItem* h_witems_buf[2] = {nullptr, nullptr};   // pinned
+  size_t witem_cap_buf[2] = {0, 0};
   std::vector<FbgWorkItem> h_wvec;
   unsigned long long* d_scan_total = nullptr;     // scan totals (unused: the slot count has it)
   unsigned long long* h_models = nullptr;         // pinned staging of model lists
   size_t h_models_cap = 0;
-  uint64_t witem_cap = 0;
   // statistics
   std::atomic<uint64_t> ticks{0}, launches{0};
   double busy_s = 0;
   double admit_s = 0, count_s = 0, enum_s = 0;   // server-thread time by activity
   double gpu_s = 0;                               // device time of the ticks' launches (CUDA events)
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // a tick whose launches are enqueued and not yet completed
+  struct InFlight {
+    std::vector<Request*> finishing;   // requests whose last units run in this tick
+    std::vector<Request*> writes;      // model lists whose ordered write runs in this tick
+    int buf = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;   // launches begin / end, counts copied
+  };
+  cudaEvent_t evs[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  uint64_t tick_no = 0;
+  std::deque<InFlight> inflight;
   fbg_status fatal = FBG_OK;
 
   void run();
-  void tick();
+  bool enqueue_tick();
+  void complete_tick();
   fbg_status admit_locked(Request* r);
   void finish(Request* r, fbg_status s);
   void release_device(Request* r);
@@ -151,7 +172,11 @@ void fbg_server::finish(Request* r, fbg_status s) {
 }
 
 fbg_status fbg_server::admit_locked(Request* r) {
-  // build the interpreter program on this (server) thread
+  // upload the interpreter program (its host half was built at submission)
+  // on the upload stream, from the stream-ordered pool, freed on the tick
+  // stream: nothing here waits for the ticks in flight
+  r->prog->alloc_stream = upload;
+  r->prog->free_stream = stream;
   fbg_status s = build_interp(r->prog, r->mode == FBG_MODE_COUNT ? 0 : 1);
   if (s != FBG_OK) return s;
   r->mem = request_mem(r->prog, r->mode, r->cap);
@@ -193,9 +218,15 @@ fbg_status fbg_server::admit_locked(Request* r) {
   return FBG_OK;
 }
 
-void fbg_server::tick() {
+// Enqueue one tick: admission, the shared count launch over a share of every
+// admitted request with units left, and the scans and ordered write launch
+// of the model lists whose last units it counts, then the copy of the slot
+// counts into this tick's host buffer.  Nothing waits for the GPU here.
+// Returns false when there was nothing to launch.
+bool fbg_server::enqueue_tick() {
   double t0 = now_s();
-  std::vector<Request*> count_reqs, enum_reqs;
+  std::vector<Request*> work;
+  bool admitted = false;
   {
     std::unique_lock<std::mutex> lk(mu);
     const double ta = now_s();
@@ -209,158 +240,207 @@ void fbg_server::tick() {
       pending.pop_front();
       fbg_status s = admit_locked(r);
       if (s != FBG_OK) finish(r, s);
+      else admitted = true;
     }
     admit_s += now_s() - ta;
-    for (Request* r : active) (r->mode == FBG_MODE_COUNT ? count_reqs : enum_reqs).push_back(r);
+    for (Request* r : active)
+      if (r->next_unit < r->nunits) work.push_back(r);   // requests with units not yet launched
   }
+  if (work.empty()) return false;
   const double tc = now_s();
-  std::vector<Request*> work = count_reqs;
-  work.insert(work.end(), enum_reqs.begin(), enum_reqs.end());
-  // model lists whose last unit is counted in this tick (write pass follows)
-  std::vector<Request*> writes;
-  if (!work.empty()) {
-    // one launch over a share of every admitted request: count requests in
-    // runs of up to 8 consecutive live units, model lists one unit per item
-    // (each item's count also goes to that unit's counter).  The tick's work
-    // is bounded by tick_units units and tick_assignments assignments; the
-    // requests with the least remaining work go first and take all of it when
-    // it fits their fair share of what is left, the others take a fair share
-    // (at least one unit), so short requests finish in the tick they join
-    // while long ones keep advancing.
-    auto unit_size = [](const Request* r) {
-      const InterpBuild& ib = r->prog->ib[r->mode == FBG_MODE_COUNT ? 0 : 1];
-      return (1ull << r->prog->n) / std::max<uint64_t>(1, ib.nunits);
-    };
-    auto remaining = [&](const Request* r) { return (double)(r->nunits - r->next_unit) * (double)unit_size(r); };
-    std::stable_sort(work.begin(), work.end(),
-                     [&](const Request* a, const Request* b) { return remaining(a) < remaining(b); });
-    double assign_left = (double)opt.tick_assignments;
-    uint64_t units_left = opt.tick_units;
-    uint64_t n = 0;
-    unsigned nslots = 1;
-    for (size_t wi = 0; wi < work.size(); wi++) {
-      Request* r = work[wi];
-      if (n >= item_cap || units_left == 0) break;   // the rest waits for the next tick
-      const bool cnt = r->mode == FBG_MODE_COUNT;
-      const double fair = assign_left / (double)(work.size() - wi);
-      const uint64_t usz = std::max<uint64_t>(1, unit_size(r));
-      uint64_t take = r->nunits - r->next_unit;
-      if ((double)take * (double)usz > fair) take = std::max<uint64_t>(1, (uint64_t)(fair / (double)usz));
-      take = std::min<uint64_t>(take, std::max<uint64_t>(1, units_left / (work.size() - wi)));
-      take = std::min<uint64_t>(take, r->nunits - r->next_unit);
-      assign_left = std::max(0.0, assign_left - (double)take * (double)usz);
-      units_left -= std::min(units_left, take);
-      const InterpBuild& ib = r->prog->ib[cnt ? 0 : 1];
-      uint64_t i = r->next_unit;
-      const uint64_t end = r->next_unit + take;
-      // runs of consecutive units of at most 2^22 assignments (and 8 units)
-      const uint64_t run_max = cnt ? std::max<uint64_t>(1, std::min<uint64_t>(8, (1ull << 22) / usz)) : 1;
-      while (i < end && n < item_cap) {
-        const uint64_t u0 = ib.unit_at(i);
-        uint64_t len = 1;
-        while (i + len < end && len < run_max && ib.unit_at(i + len) == u0 + len) len++;
-        h_items[n++] = FbgWorkItem{(unsigned)r->slot, cnt ? 0u : FBG_ITEM_UNIT_COUNTS, u0, u0 + len};
-        i += len;
-      }
-      r->next_unit = i;
-      nslots = std::max(nslots, ib.code.nslots);
-      if (!cnt && r->next_unit >= r->nunits) writes.push_back(r);
-    }
-    cudaError_t e = cudaMemcpyAsync(d_items, h_items, n * sizeof(FbgWorkItem), cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess) e = cudaEventRecord(ev0, stream);
-    uint64_t slots = (uint64_t)opt.max_inflight;
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_counts + slots, 0, 8, stream);
-    int per_sm = interp_blocks_per_sm(0, nslots);
-    int grid = (int)std::min<uint64_t>(n, (uint64_t)device_sms() * (uint64_t)std::max(1, per_sm));
-    FbgLaunch P{};
-    P.unit_begin = 0;
-    P.unit_end = ~0ull;
-    if (e == cudaSuccess)
-      e = launch_interp(0, d_progs, d_items, n, d_counts + slots, d_counts, nullptr, P, nslots, std::max(1, grid), stream,
-                        d_slot_out);
-    launches++;
-    // model lists complete in this launch: offsets by a scan of the unit
-    // counts, then one ordered write launch over all of them
-    if (e == cudaSuccess && !writes.empty()) {
-      h_wvec.clear();
-      unsigned wslots = 1;
-      for (Request* r : writes) {
-        const InterpBuild& ib = r->prog->ib[1];
-        if (e == cudaSuccess) e = launch_scan(r->d_unit_counts, r->d_offsets, ib.nunits, d_scan_total, stream);
-        ib.append_items(h_wvec, (unsigned)r->slot, 0, ib.live_units(), 1);
-        wslots = std::max(wslots, ib.code.nslots);
-      }
-      if (e == cudaSuccess && h_wvec.size() > witem_cap) {
-        if (d_witems) cudaFreeAsync(d_witems, stream);
-        d_witems = nullptr;
-        witem_cap = 0;
-        e = cudaMallocAsync((void**)&d_witems, h_wvec.size() * sizeof(FbgWorkItem), stream);
-        if (e == cudaSuccess) witem_cap = h_wvec.size();
-      }
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(d_witems, h_wvec.data(), h_wvec.size() * sizeof(FbgWorkItem), cudaMemcpyHostToDevice,
-                            stream);
-      if (e == cudaSuccess) e = cudaMemsetAsync(d_counts + slots, 0, 8, stream);
-      int wper = interp_blocks_per_sm(2, wslots);
-      int wgrid = (int)std::min<uint64_t>(h_wvec.size(), (uint64_t)device_sms() * (uint64_t)std::max(1, wper));
-      if (e == cudaSuccess)
-        e = launch_interp(2, d_progs, d_witems, h_wvec.size(), d_counts + slots, nullptr, nullptr, P, wslots,
-                          std::max(1, wgrid), stream, d_slot_out);
-      launches += 1 + writes.size();
-    }
-    if (e == cudaSuccess) e = cudaEventRecord(ev1, stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(h_counts, d_counts, slots * 8, cudaMemcpyDeviceToHost, stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-    if (e == cudaSuccess) {
-      float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess) gpu_s += ms * 1e-3;
-    }
-    // the model lists of the finished requests (their totals are now known)
-    const double tw = now_s();
-    for (Request* r : writes) {
-      if (e != cudaSuccess) break;
-      const uint64_t written = std::min<uint64_t>(h_counts[r->slot], r->cap);
-      if (written > h_models_cap) {
-        if (h_models) cudaFreeHost(h_models);
-        h_models = nullptr;
-        h_models_cap = 0;
-        e = cudaMallocHost((void**)&h_models, written * 8);
-        if (e != cudaSuccess) break;
-        h_models_cap = written;
-      }
-      if (written) e = cudaMemcpyAsync(h_models, r->d_models, written * 8, cudaMemcpyDeviceToHost, stream);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-      if (e == cudaSuccess) r->models.assign(h_models, h_models + written);
-    }
-    enum_s += now_s() - tw;
-    std::unique_lock<std::mutex> lk(mu);
-    if (e != cudaSuccess) {
-      cuda_error(e, "server tick");
-      fatal = FBG_ECUDA;
-      for (Request* r : work) finish(r, FBG_ECUDA);
-    } else {
-      for (Request* r : work)
-        if (r->next_unit >= r->nunits) {
-          r->count = h_counts[r->slot];
-          finish(r, FBG_OK);
-        }
-    }
-    active.erase(std::remove_if(active.begin(), active.end(), [](Request* r) { return r->done; }), active.end());
+  InFlight f;
+  f.buf = (int)(tick_no & 1);
+  f.ev0 = evs[f.buf][0];
+  f.ev1 = evs[f.buf][1];
+  f.ev2 = evs[f.buf][2];
+  FbgWorkItem* h_items = h_items_buf[f.buf];
+  FbgWorkItem* d_items = d_items_buf[f.buf];
+  cudaError_t e = cudaSuccess;
+  // the programs admitted above are uploaded on the upload stream
+  if (admitted) {
+    e = cudaEventRecord(uploaded, upload);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, uploaded, 0);
   }
+  // one launch over a share of every admitted request: count requests in
+  // runs of up to 8 consecutive live units, model lists one unit per item
+  // (each item's count also goes to that unit's counter).  The tick's work
+  // is bounded by tick_units units and tick_assignments assignments; the
+  // requests with the least remaining work go first and take all of it when
+  // it fits their fair share of what is left, the others take a fair share
+  // (at least one unit), so short requests finish in the tick they join
+  // while long ones keep advancing.
+  auto unit_size = [](const Request* r) {
+    const InterpBuild& ib = r->prog->ib[r->mode == FBG_MODE_COUNT ? 0 : 1];
+    return (1ull << r->prog->n) / std::max<uint64_t>(1, ib.nunits);
+  };
+  auto remaining = [&](const Request* r) { return (double)(r->nunits - r->next_unit) * (double)unit_size(r); };
+  std::stable_sort(work.begin(), work.end(),
+                   [&](const Request* x, const Request* y) { return remaining(x) < remaining(y); });
+  double assign_left = (double)opt.tick_assignments;
+  uint64_t units_left = opt.tick_units;
+  uint64_t n = 0;
+  unsigned nslots = 1;
+  for (size_t wi = 0; wi < work.size(); wi++) {
+    Request* r = work[wi];
+    if (n >= item_cap || units_left == 0) break;   // the rest waits for the next tick
+    const bool cnt = r->mode == FBG_MODE_COUNT;
+    const double fair = assign_left / (double)(work.size() - wi);
+    const uint64_t usz = std::max<uint64_t>(1, unit_size(r));
+    uint64_t take = r->nunits - r->next_unit;
+    if ((double)take * (double)usz > fair) take = std::max<uint64_t>(1, (uint64_t)(fair / (double)usz));
+    take = std::min<uint64_t>(take, std::max<uint64_t>(1, units_left / (work.size() - wi)));
+    take = std::min<uint64_t>(take, r->nunits - r->next_unit);
+    assign_left = std::max(0.0, assign_left - (double)take * (double)usz);
+    units_left -= std::min(units_left, take);
+    const InterpBuild& ib = r->prog->ib[cnt ? 0 : 1];
+    uint64_t i = r->next_unit;
+    const uint64_t end = r->next_unit + take;
+    // runs of consecutive units of at most 2^22 assignments (and 8 units)
+    const uint64_t run_max = cnt ? std::max<uint64_t>(1, std::min<uint64_t>(8, (1ull << 22) / usz)) : 1;
+    while (i < end && n < item_cap) {
+      const uint64_t u0 = ib.unit_at(i);
+      uint64_t len = 1;
+      while (i + len < end && len < run_max && ib.unit_at(i + len) == u0 + len) len++;
+      h_items[n++] = FbgWorkItem{(unsigned)r->slot, cnt ? 0u : FBG_ITEM_UNIT_COUNTS, u0, u0 + len};
+      i += len;
+    }
+    r->next_unit = i;
+    nslots = std::max(nslots, ib.code.nslots);
+    if (r->next_unit >= r->nunits) {
+      f.finishing.push_back(r);
+      if (!cnt) f.writes.push_back(r);
+    }
+  }
+  uint64_t slots = (uint64_t)opt.max_inflight;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_items, h_items, n * sizeof(FbgWorkItem), cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaEventRecord(f.ev0, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_counts + slots, 0, 8, stream);
+  int per_sm = interp_blocks_per_sm(0, nslots);
+  int grid = (int)std::min<uint64_t>(n, (uint64_t)device_sms() * (uint64_t)std::max(1, per_sm));
+  FbgLaunch P{};
+  P.unit_begin = 0;
+  P.unit_end = ~0ull;
+  if (e == cudaSuccess)
+    e = launch_interp(0, d_progs, d_items, n, d_counts + slots, d_counts, nullptr, P, nslots, std::max(1, grid), stream,
+                      d_slot_out);
+  launches++;
+  // model lists complete in this launch: offsets by a scan of the unit
+  // counts, then one ordered write launch over all of them
+  if (e == cudaSuccess && !f.writes.empty()) {
+    h_wvec.clear();
+    unsigned wslots = 1;
+    for (Request* r : f.writes) {
+      const InterpBuild& ib = r->prog->ib[1];
+      if (e == cudaSuccess) e = launch_scan(r->d_unit_counts, r->d_offsets, ib.nunits, d_scan_total, stream);
+      ib.append_items(h_wvec, (unsigned)r->slot, 0, ib.live_units(), 1);
+      wslots = std::max(wslots, ib.code.nslots);
+    }
+    // the write launch's items, double buffered like the count items: the
+    // buffers of this index were last used by the tick before the previous
+    // one, which has completed
+    const size_t nw = h_wvec.size();
+    if (e == cudaSuccess && nw > witem_cap_buf[f.buf]) {
+      if (h_witems_buf[f.buf]) cudaFreeHost(h_witems_buf[f.buf]);
+      if (d_witems_buf[f.buf]) cudaFreeAsync(d_witems_buf[f.buf], stream);
+      h_witems_buf[f.buf] = nullptr;
+      d_witems_buf[f.buf] = nullptr;
+      witem_cap_buf[f.buf] = 0;
+      e = cudaMallocHost((void**)&h_witems_buf[f.buf], nw * sizeof(FbgWorkItem));
+      if (e == cudaSuccess) e = cudaMallocAsync((void**)&d_witems_buf[f.buf], nw * sizeof(FbgWorkItem), stream);
+      if (e == cudaSuccess) witem_cap_buf[f.buf] = nw;
+    }
+    FbgWorkItem* d_witems = d_witems_buf[f.buf];
+    if (e == cudaSuccess) {
+      std::memcpy(h_witems_buf[f.buf], h_wvec.data(), nw * sizeof(FbgWorkItem));
+      e = cudaMemcpyAsync(d_witems, h_witems_buf[f.buf], nw * sizeof(FbgWorkItem), cudaMemcpyHostToDevice, stream);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_counts + slots, 0, 8, stream);
+    int wper = interp_blocks_per_sm(2, wslots);
+    int wgrid = (int)std::min<uint64_t>(h_wvec.size(), (uint64_t)device_sms() * (uint64_t)std::max(1, wper));
+    if (e == cudaSuccess)
+      e = launch_interp(2, d_progs, d_witems, h_wvec.size(), d_counts + slots, nullptr, nullptr, P, wslots,
+                        std::max(1, wgrid), stream, d_slot_out);
+    launches += 1 + f.writes.size();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(f.ev1, stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_counts_buf[f.buf], d_counts, slots * 8, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaEventRecord(f.ev2, stream);
+  if (e != cudaSuccess) {
+    cuda_error(e, "server tick");
+    std::unique_lock<std::mutex> lk(mu);
+    fatal = FBG_ECUDA;
+    for (Request* r : work) finish(r, FBG_ECUDA);
+    active.erase(std::remove_if(active.begin(), active.end(), [](Request* r) { return r->done; }), active.end());
+    count_s += now_s() - tc;
+    return false;
+  }
+  inflight.push_back(std::move(f));
+  tick_no++;
   count_s += now_s() - tc;
+  busy_s += now_s() - t0;
+  return true;
+}
+
+// Complete the oldest tick in flight: wait for it, copy the model lists it
+// wrote to the host, finish the requests whose last units it ran.
+void fbg_server::complete_tick() {
+  const double t0 = now_s();
+  InFlight f = std::move(inflight.front());
+  inflight.pop_front();
+  // the tick's launches and the copy of its counts are done (the next tick,
+  // if enqueued, may still run; it writes the other count buffer)
+  cudaError_t e = cudaEventSynchronize(f.ev2);
+  if (e == cudaSuccess) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, f.ev0, f.ev1) == cudaSuccess) gpu_s += ms * 1e-3;
+  }
+  const unsigned long long* hc = h_counts_buf[f.buf];
+  const double tw = now_s();
+  for (Request* r : f.writes) {
+    if (e != cudaSuccess) break;
+    const uint64_t written = std::min<uint64_t>(hc[r->slot], r->cap);
+    if (written > h_models_cap) {
+      if (h_models) cudaFreeHost(h_models);
+      h_models = nullptr;
+      h_models_cap = 0;
+      e = cudaMallocHost((void**)&h_models, written * 8);
+      if (e != cudaSuccess) break;
+      h_models_cap = written;
+    }
+    if (written) e = cudaMemcpyAsync(h_models, r->d_models, written * 8, cudaMemcpyDeviceToHost, copies);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(copies);
+    if (e == cudaSuccess) r->models.assign(h_models, h_models + written);
+  }
+  enum_s += now_s() - tw;
+  std::unique_lock<std::mutex> lk(mu);
+  if (e != cudaSuccess) {
+    cuda_error(e, "server tick");
+    fatal = FBG_ECUDA;
+    for (Request* r : f.finishing) finish(r, FBG_ECUDA);
+  } else {
+    for (Request* r : f.finishing) {
+      r->count = hc[r->slot];
+      finish(r, FBG_OK);
+    }
+  }
+  active.erase(std::remove_if(active.begin(), active.end(), [](Request* r) { return r->done; }), active.end());
   ticks++;
   busy_s += now_s() - t0;
 }
 
+// Two ticks in flight: while the GPU runs one, the server thread admits
+// requests and enqueues the next, then completes the older one.
 void fbg_server::run() {
   cudaSetDevice(device);
   for (;;) {
     {
       std::unique_lock<std::mutex> lk(mu);
-      cv.wait(lk, [&] { return stop || !pending.empty() || !active.empty(); });
-      if (stop) return;
+      cv.wait(lk, [&] { return stop || !pending.empty() || !active.empty() || !inflight.empty(); });
+      if (stop && inflight.empty()) return;
     }
-    tick();
+    bool queued = false;
+    if (inflight.size() < 2 && !stop) queued = enqueue_tick();
+    if (!inflight.empty() && (inflight.size() >= 2 || !queued)) complete_tick();
   }
 }
 
@@ -379,14 +459,26 @@ fbg_status fbg_server_create(const fbg_server_options* opt, fbg_server** out) {
   cudaGetDevice(&s->device);
   const size_t slots = (size_t)s->opt.max_inflight;
   cudaError_t e;
+  bool ev_ok = true;
+  for (auto& pair : s->evs)
+    for (auto& ev : pair) ev_ok = ev_ok && cudaEventCreate(&ev) == cudaSuccess;
+  if (!ev_ok) {
+    fbg_server_free(s);
+    return set_error(FBG_ECUDA, "server setup: cudaEventCreate");
+  }
   if ((e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)) != cudaSuccess ||
-      (e = cudaEventCreate(&s->ev0)) != cudaSuccess || (e = cudaEventCreate(&s->ev1)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&s->upload, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&s->copies, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&s->uploaded, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaMalloc(&s->d_progs, slots * sizeof(FbgInterpProg))) != cudaSuccess ||
       (e = cudaMallocHost(&s->h_progs, slots * sizeof(FbgInterpProg))) != cudaSuccess ||
       (e = cudaMalloc(&s->d_counts, (slots + 1) * 8)) != cudaSuccess ||
-      (e = cudaMallocHost(&s->h_counts, slots * 8)) != cudaSuccess ||
-      (e = cudaMalloc(&s->d_items, s->item_cap * sizeof(FbgWorkItem))) != cudaSuccess ||
-      (e = cudaMallocHost(&s->h_items, s->item_cap * sizeof(FbgWorkItem))) != cudaSuccess ||
+      (e = cudaMallocHost(&s->h_counts_buf[0], slots * 8)) != cudaSuccess ||
+      (e = cudaMallocHost(&s->h_counts_buf[1], slots * 8)) != cudaSuccess ||
+      (e = cudaMalloc(&s->d_items_buf[0], s->item_cap * sizeof(FbgWorkItem))) != cudaSuccess ||
+      (e = cudaMalloc(&s->d_items_buf[1], s->item_cap * sizeof(FbgWorkItem))) != cudaSuccess ||
+      (e = cudaMallocHost(&s->h_items_buf[0], s->item_cap * sizeof(FbgWorkItem))) != cudaSuccess ||
+      (e = cudaMallocHost(&s->h_items_buf[1], s->item_cap * sizeof(FbgWorkItem))) != cudaSuccess ||
       (e = cudaMalloc(&s->d_slot_out, slots * sizeof(FbgSlotOut))) != cudaSuccess ||
       (e = cudaMallocHost(&s->h_slot_out, slots * sizeof(FbgSlotOut))) != cudaSuccess ||
       (e = cudaMalloc(&s->d_scan_total, 8)) != cudaSuccess) {
@@ -524,23 +616,32 @@ void fbg_server_free(fbg_server* s) {
   if (s->worker.joinable()) s->worker.join();
   if (s->stream) {
     for (auto& kv : s->all) s->release_device(kv.second.get());
-    if (s->d_witems) cudaFreeAsync(s->d_witems, s->stream);
-    s->d_witems = nullptr;
+    for (int b = 0; b < 2; b++) {
+      if (s->d_witems_buf[b]) cudaFreeAsync(s->d_witems_buf[b], s->stream);
+      s->d_witems_buf[b] = nullptr;
+    }
     cudaStreamSynchronize(s->stream);
   }
   s->all.clear();
   if (s->d_progs) cudaFree(s->d_progs);
   if (s->h_progs) cudaFreeHost(s->h_progs);
   if (s->d_counts) cudaFree(s->d_counts);
-  if (s->h_counts) cudaFreeHost(s->h_counts);
-  if (s->d_items) cudaFree(s->d_items);
-  if (s->h_items) cudaFreeHost(s->h_items);
+  for (int b = 0; b < 2; b++) {
+    if (s->h_witems_buf[b]) cudaFreeHost(s->h_witems_buf[b]);
+    if (s->h_counts_buf[b]) cudaFreeHost(s->h_counts_buf[b]);
+    if (s->d_items_buf[b]) cudaFree(s->d_items_buf[b]);
+    if (s->h_items_buf[b]) cudaFreeHost(s->h_items_buf[b]);
+  }
   if (s->d_slot_out) cudaFree(s->d_slot_out);
   if (s->h_slot_out) cudaFreeHost(s->h_slot_out);
   if (s->d_scan_total) cudaFree(s->d_scan_total);
   if (s->h_models) cudaFreeHost(s->h_models);
-  if (s->ev0) cudaEventDestroy(s->ev0);
-  if (s->ev1) cudaEventDestroy(s->ev1);
+  for (auto& pair : s->evs)
+    for (auto& ev : pair)
+      if (ev) cudaEventDestroy(ev);
+  if (s->uploaded) cudaEventDestroy(s->uploaded);
+  if (s->upload) cudaStreamDestroy(s->upload);
+  if (s->copies) cudaStreamDestroy(s->copies);
   if (s->stream) cudaStreamDestroy(s->stream);
   delete s;
 }
