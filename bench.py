@@ -40,9 +40,9 @@ NOMINAL_SM_MHZ = 2032.0         # maximum SM clock of the part, when nvidia-smi 
 #          the formulas' LUTs and the popcount's full adders, not the ULOP3 of
 #          the uniform datapath)
 #   table: DRAM bytes of one truth-table launch
-NCU_COUNT = {"sources_sha": "511da558a9d1ae8e", "traffic_step": 47_616 + 101_888 + 54_016,
+NCU_COUNT = {"sources_sha": "eb8600039356cfa3", "traffic_step": 47_104 + 101_632 + 54_016,
              "vector_lop3_step": 8_895_229 + 22_819_402 + 34_166}
-NCU_TABLE = {"sources_sha": "570b43a21fabb2c0", "traffic_launch": 478_851_840 + 70_912}
+NCU_TABLE = {"sources_sha": "898d05ddf8c3e3ff", "traffic_launch": 478_359_040 + 68_096}
 
 
 def kernel_fingerprint(progs, mode: int = 0) -> str:
