@@ -547,7 +547,9 @@ def run_batched(args, torch, F, L):
 def run_serving(args, torch, F, L):
     """Poisson stream of requests (seed 5): n uniform in 16..38, a family with
     exactly n letters else 3-CNF; 90% count, 10% enumerate (cap 1e6).  The
-    rate is 0.7x the throughput of a calibration burst."""
+    rate is 0.7x the throughput of a calibration burst.  Count requests of
+    recurring texts with at least jit_min_n letters move to specialised
+    kernels that the server compiles in the background."""
     import threading
     from paper_1310_6978_b300 import workloads as W
     nreq = args.serve_requests
@@ -555,13 +557,13 @@ def run_serving(args, torch, F, L):
     # untimed burst of other requests; the calibration burst has texts of its
     # own, as the stream has
     warm = W.request_stream(200, rate_per_s=1.0, seed=54)
-    srv = F.Server()
+    srv = F.Server(jit_min_n=args.serve_jit_min_n)
     for r in warm:
         srv.submit(r.workload.text, r.workload.k, L.MODE_ENUMERATE if r.mode == "enumerate" else L.MODE_COUNT, r.cap)
     srv.drain(600)
     srv.close()
     calib = W.request_stream(min(400, nreq), rate_per_s=1.0, seed=55)
-    srv = F.Server()
+    srv = F.Server(jit_min_n=args.serve_jit_min_n)
     t0 = time.perf_counter()
     ids = [srv.submit(r.workload.text, r.workload.k,
                       L.MODE_ENUMERATE if r.mode == "enumerate" else L.MODE_COUNT, r.cap) for r in calib]
@@ -570,7 +572,7 @@ def run_serving(args, torch, F, L):
     srv.close()
     rate = args.serve_rate if args.serve_rate > 0 else 0.7 * len(calib) / t_cal
     reqs = W.request_stream(nreq, rate_per_s=rate, seed=5)
-    srv = F.Server()
+    srv = F.Server(jit_min_n=args.serve_jit_min_n)
     index = {}                           # request id -> position in the stream
     done = [None] * len(reqs)            # (latency s, count) once collected
     start = time.perf_counter()
@@ -647,6 +649,9 @@ def run_serving(args, torch, F, L):
             "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))] * 1e3, "value": assign / wall / 1e9,
             "unit": "Gassign/s", "ticks": st["ticks"], "launches": st["launches"],
             "server_s": {k: st[k] for k in ("busy_s", "admit_s", "count_s", "enum_s", "gpu_s")}, "clients": nclients,
+            "recurring_texts": {"specialised_programs": st["jit_programs"], "requests_on_them": st["jit_requests"],
+                                "background_compile_s": st["jit_compile_s"],
+                                "jit_min_n": args.serve_jit_min_n or 30},
             "submit_lag_s": lag, "arrival_window_s": reqs[-1].arrival_s,
             "p50_ms_n_le_27": small[len(small) // 2] * 1e3 if small else None,
             "model_lists": sum(1 for r in reqs if r.mode == "enumerate"),
@@ -943,6 +948,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=100000)
     ap.add_argument("--serve-rate", type=float, default=0.0, help="offered requests/s (0: 0.7 x calibrated)")
+    ap.add_argument("--serve-jit-min-n", type=int, default=0,
+                    help="server option jit_min_n (0: the library default, 30; -1: interpreter only)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-total-seconds", type=float, default=90.0,
                     help="reference arm: seconds for all its warm-up and timed steps together")

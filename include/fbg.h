@@ -445,7 +445,9 @@ void fbg_batch_free(fbg_batch *batch);
  * counts its last unit, a scan gives every unit its first position and one
  * more launch (shared by all model lists finishing in that tick) writes the
  * models in ascending j into a device buffer of `cap` words, from which the
- * first min(cap, total) reach the result.  A host thread drives the ticks on
+ * first min(cap, total) reach the result.  Count requests whose text recurs
+ * move to a specialised kernel once a background thread has compiled it
+ * (jit_min_n, jit_after).  A host thread drives the ticks on
  * its own stream, two ticks in flight (it prepares and enqueues the next tick
  * while the GPU runs the current one); per-request device buffers come from
  * the stream-ordered allocator.
@@ -457,6 +459,16 @@ typedef struct {
   uint64_t tick_assignments;   /* assignments evaluated per tick, at least one unit per admitted
                                   request (0 = 2^36); requests with the least remaining work go
                                   first and finish in one tick when they fit a fair share */
+  int jit_min_n;               /* recurring texts: a count request with at least this many letters
+                                  (0 = 30; negative = never) whose (text, domain) has been submitted
+                                  jit_after times gets a specialised count kernel, compiled by a
+                                  background thread of the server (NVRTC), never by the tick loop;
+                                  count requests of that text admitted once it is ready are counted
+                                  by it (one launch over all their units, on a side stream that runs
+                                  beside the tick's interpreter launch) */
+  int jit_after;               /* submissions of one (text, domain) before its compile starts (0 = 2) */
+  int jit_max_programs;        /* specialised programs a server keeps (0 = 64); texts beyond stay
+                                  on the interpreter */
 } fbg_server_options;
 
 enum { FBG_MODE_COUNT = 0, FBG_MODE_ENUMERATE = 1 };
@@ -490,6 +502,10 @@ fbg_status fbg_server_profile(fbg_server *srv, double *admit_s, double *count_s,
 /* diagnostics: seconds of device time of the ticks' launches (CUDA events
    around each tick's launches), summed */
 fbg_status fbg_server_gpu_time(fbg_server *srv, double *gpu_s);
+/* recurring texts: specialised programs ready, count requests they have
+   counted, and the background thread's seconds of compiling (NVRTC, module
+   load, the ordering of the kernel's items, its first count) */
+fbg_status fbg_server_jit_stats(fbg_server *srv, uint64_t *programs, uint64_t *requests, double *compile_s);
 void fbg_server_free(fbg_server *srv);
 
 #ifdef __cplusplus

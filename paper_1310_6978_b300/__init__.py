@@ -325,10 +325,16 @@ class Server:
     """Continuous-batching request loop (fbg_server_*)."""
 
     def __init__(self, mem_budget_bytes: int = 0, tick_units: int = 0, max_inflight: int = 0,
-                 tick_assignments: int = 0):
+                 tick_assignments: int = 0, jit_min_n: int = 0, jit_after: int = 0, jit_max_programs: int = 0):
+        """Options as fbg_server_options (0 = the library's default).  jit_min_n
+        < 0 keeps every request on the interpreter; otherwise count requests
+        of a recurring text with at least jit_min_n letters (default 30) move
+        to a specialised kernel compiled in the background after jit_after
+        submissions (default 2)."""
         L = _L()
         self._L = L
-        o = L.FbgServerOptions(mem_budget_bytes, tick_units, max_inflight, tick_assignments)
+        o = L.FbgServerOptions(mem_budget_bytes, tick_units, max_inflight, tick_assignments, jit_min_n, jit_after,
+                               jit_max_programs)
         h = ctypes.c_void_p()
         L.check(L.lib.fbg_server_create(ctypes.byref(o), ctypes.byref(h)))
         self._h = h
@@ -377,5 +383,8 @@ class Server:
         self._L.check(self._L.lib.fbg_server_profile(self._h, ctypes.byref(a), ctypes.byref(c), ctypes.byref(e)))
         g = ctypes.c_double()
         self._L.check(self._L.lib.fbg_server_gpu_time(self._h, ctypes.byref(g)))
+        jp, jr, jc = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_double()
+        self._L.check(self._L.lib.fbg_server_jit_stats(self._h, ctypes.byref(jp), ctypes.byref(jr), ctypes.byref(jc)))
         return {"ticks": t.value, "launches": l.value, "busy_s": b.value, "admit_s": a.value, "count_s": c.value,
-                "enum_s": e.value, "gpu_s": g.value}
+                "enum_s": e.value, "gpu_s": g.value, "jit_programs": jp.value, "jit_requests": jr.value,
+                "jit_compile_s": jc.value}

@@ -53,7 +53,7 @@ class FbgTuneResult(ctypes.Structure):
 
 class FbgServerOptions(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", c_u64), ("tick_units", c_u64), ("max_inflight", c_int),
-                ("tick_assignments", c_u64)]
+                ("tick_assignments", c_u64), ("jit_min_n", c_int), ("jit_after", c_int), ("jit_max_programs", c_int)]
 
 
 class FbgResult(ctypes.Structure):
@@ -120,6 +120,7 @@ _sig("fbg_server_stats", c_int, c_vp, ctypes.POINTER(c_u64), ctypes.POINTER(c_u6
 _sig("fbg_server_profile", c_int, c_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
      ctypes.POINTER(ctypes.c_double))
 _sig("fbg_server_gpu_time", c_int, c_vp, ctypes.POINTER(ctypes.c_double))
+_sig("fbg_server_jit_stats", c_int, c_vp, ctypes.POINTER(c_u64), ctypes.POINTER(c_u64), ctypes.POINTER(ctypes.c_double))
 _sig("fbg_server_free", None, c_vp)
 
 

@@ -351,8 +351,8 @@ constexpr size_t kScratchHead = 32;
 constexpr size_t kScratchAcc = 24, kScratchDone = 25;
 
 fbg_status launch_count(fbg_program* p, cudaStream_t st, unsigned long long* dev_count, unsigned long long* unit_counts,
-                        bool* used_jit, uint64_t ubegin = 0, uint64_t uend = ~0ull,
-                        unsigned long long* unit_trace = nullptr, unsigned long long* item_trace = nullptr) {
+                        bool* used_jit, uint64_t ubegin, uint64_t uend, unsigned long long* unit_trace,
+                        unsigned long long* item_trace) {
   bool jit = false;
   fbg_status s = pick_engine(p, 0, &jit);
   if (s != FBG_OK) return s;

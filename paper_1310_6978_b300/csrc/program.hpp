@@ -149,4 +149,9 @@ fbg_status build_interp(fbg_program* p, int which);
 fbg_status prebuild_interp_host(fbg_program* p, int which);
 fbg_status build_jit(fbg_program* p, int mode);
 fbg_status pick_engine(fbg_program* p, int mode, bool* use_jit);
+// one count of units [ubegin, uend) on stream st into dev_count (null: the
+// program's scratch word); the engine is picked (and built) first
+fbg_status launch_count(fbg_program* p, cudaStream_t st, unsigned long long* dev_count, unsigned long long* unit_counts,
+                        bool* used_jit, uint64_t ubegin = 0, uint64_t uend = ~0ull,
+                        unsigned long long* unit_trace = nullptr, unsigned long long* item_trace = nullptr);
 }  // namespace fbg

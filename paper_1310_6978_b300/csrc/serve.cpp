@@ -19,6 +19,16 @@
 // stream of their own from the stream-ordered pool, so no host step waits
 // for the GPU except the completion of the older tick.  Every tick is a
 // bounded launch: nothing runs forever on the GPU.
+//
+// Recurring texts.  A count request whose (text, domain) has been submitted
+// jit_after times and has at least jit_min_n letters is a family: a
+// background thread compiles its specialised count kernel (NVRTC), orders
+// the kernel's items longest first and counts once, off the tick loop.  A
+// count request of a ready family is admitted without an interpreter
+// upload, and its tick counts all its units with one launch of that kernel
+// on a side stream, which runs beside the tick's interpreter launch and
+// joins the tick before its counts are copied.  Requests admitted before
+// the kernel was ready finish on the interpreter.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,6 +39,7 @@
 #include <deque>
 #include <memory>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -46,8 +57,21 @@ double now_s() {
   return duration<double>(steady_clock::now().time_since_epoch()).count();
 }
 
+// a (text, domain) of count requests that may get a specialised kernel
+struct TextFamily {
+  std::string text;
+  int k = 1;
+  uint64_t submissions = 0;
+  bool queued = false;
+  bool ready = false;              // prog holds the built kernel (set under the server's lock)
+  fbg_program* prog = nullptr;     // specialised count program, owned by the server
+  ~TextFamily() { fbg_program_free(prog); }
+};
+
 struct Request {
   uint64_t id = 0;
+  TextFamily* fam = nullptr;           // the request's family, if its text may be specialised
+  bool jit = false;                // counted by the family's specialised kernel
   int mode = FBG_MODE_COUNT;
   uint64_t cap = 0;
   fbg_program* prog = nullptr;
@@ -123,8 +147,19 @@ struct fbg_server {
   uint64_t tick_no = 0;
   std::deque<InFlight> inflight;
   fbg_status fatal = FBG_OK;
+  // recurring texts: families by text and domain, the background compile
+  // thread and its queue, the side stream of the specialised launches
+  std::unordered_map<std::string, std::unique_ptr<TextFamily>> families;
+  std::deque<TextFamily*> jit_queue;
+  std::condition_variable jit_cv;
+  std::thread jit_worker;
+  uint64_t jit_started = 0, jit_ready = 0, jit_requests = 0;
+  double jit_compile_s = 0;
+  cudaStream_t jit_stream = nullptr;
+  cudaEvent_t jit_fork = nullptr, jit_join = nullptr;
 
   void run();
+  void jit_run();
   bool enqueue_tick();
   void complete_tick();
   fbg_status admit_locked(Request* r);
@@ -172,6 +207,20 @@ void fbg_server::finish(Request* r, fbg_status s) {
 }
 
 fbg_status fbg_server::admit_locked(Request* r) {
+  if (r->fam && r->fam->ready && r->mode == FBG_MODE_COUNT) {
+    // the family's specialised kernel counts all of it in one launch: a slot
+    // for its count, no interpreter upload
+    r->jit = true;
+    r->mem = 64;
+    r->admit_s = now_s();
+    r->slot = free_slots.back();
+    free_slots.pop_back();
+    r->nunits = 1;
+    r->next_unit = 0;
+    mem_used += r->mem;
+    active.push_back(r);
+    return FBG_OK;
+  }
   // upload the interpreter program (its host half was built at submission)
   // on the upload stream, from the stream-ordered pool, freed on the tick
   // stream: nothing here waits for the ticks in flight
@@ -225,7 +274,8 @@ fbg_status fbg_server::admit_locked(Request* r) {
 // Returns false when there was nothing to launch.
 bool fbg_server::enqueue_tick() {
   double t0 = now_s();
-  std::vector<Request*> work;
+  std::vector<Request*> work;    // interpreter work
+  std::vector<Request*> jwork;   // requests counted by their family's specialised kernel
   bool admitted = false;
   {
     std::unique_lock<std::mutex> lk(mu);
@@ -244,9 +294,9 @@ bool fbg_server::enqueue_tick() {
     }
     admit_s += now_s() - ta;
     for (Request* r : active)
-      if (r->next_unit < r->nunits) work.push_back(r);   // requests with units not yet launched
+      if (r->next_unit < r->nunits) (r->jit ? jwork : work).push_back(r);   // units not yet launched
   }
-  if (work.empty()) return false;
+  if (work.empty() && jwork.empty()) return false;
   const double tc = now_s();
   InFlight f;
   f.buf = (int)(tick_no & 1);
@@ -312,18 +362,38 @@ bool fbg_server::enqueue_tick() {
     }
   }
   uint64_t slots = (uint64_t)opt.max_inflight;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_items, h_items, n * sizeof(FbgWorkItem), cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess && n)
+    e = cudaMemcpyAsync(d_items, h_items, n * sizeof(FbgWorkItem), cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess) e = cudaEventRecord(f.ev0, stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d_counts + slots, 0, 8, stream);
-  int per_sm = interp_blocks_per_sm(0, nslots);
-  int grid = (int)std::min<uint64_t>(n, (uint64_t)device_sms() * (uint64_t)std::max(1, per_sm));
+  // the specialised counts first, on the side stream (after the slots'
+  // zeroing above), so that they run beside the interpreter launch
+  fbg_status js = FBG_OK;
+  if (e == cudaSuccess && !jwork.empty()) {
+    e = cudaEventRecord(jit_fork, stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(jit_stream, jit_fork, 0);
+    for (Request* r : jwork) {
+      if (e != cudaSuccess || js != FBG_OK) break;
+      bool used_jit = false;
+      js = launch_count(r->fam->prog, jit_stream, d_counts + r->slot, nullptr, &used_jit);
+      r->next_unit = r->nunits;
+      f.finishing.push_back(r);
+      launches++;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(jit_join, jit_stream);
+    jit_requests += jwork.size();
+  }
   FbgLaunch P{};
   P.unit_begin = 0;
   P.unit_end = ~0ull;
-  if (e == cudaSuccess)
-    e = launch_interp(0, d_progs, d_items, n, d_counts + slots, d_counts, nullptr, P, nslots, std::max(1, grid), stream,
-                      d_slot_out);
-  launches++;
+  if (e == cudaSuccess && n) {
+    e = cudaMemsetAsync(d_counts + slots, 0, 8, stream);
+    int per_sm = interp_blocks_per_sm(0, nslots);
+    int grid = (int)std::min<uint64_t>(n, (uint64_t)device_sms() * (uint64_t)std::max(1, per_sm));
+    if (e == cudaSuccess)
+      e = launch_interp(0, d_progs, d_items, n, d_counts + slots, d_counts, nullptr, P, nslots, std::max(1, grid),
+                        stream, d_slot_out);
+    launches++;
+  }
   // model lists complete in this launch: offsets by a scan of the unit
   // counts, then one ordered write launch over all of them
   if (e == cudaSuccess && !f.writes.empty()) {
@@ -362,14 +432,16 @@ bool fbg_server::enqueue_tick() {
                         std::max(1, wgrid), stream, d_slot_out);
     launches += 1 + f.writes.size();
   }
+  if (e == cudaSuccess && !jwork.empty()) e = cudaStreamWaitEvent(stream, jit_join, 0);
   if (e == cudaSuccess) e = cudaEventRecord(f.ev1, stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h_counts_buf[f.buf], d_counts, slots * 8, cudaMemcpyDeviceToHost, stream);
   if (e == cudaSuccess) e = cudaEventRecord(f.ev2, stream);
-  if (e != cudaSuccess) {
-    cuda_error(e, "server tick");
+  if (e != cudaSuccess || js != FBG_OK) {
+    if (e != cudaSuccess) cuda_error(e, "server tick");
     std::unique_lock<std::mutex> lk(mu);
-    fatal = FBG_ECUDA;
-    for (Request* r : work) finish(r, FBG_ECUDA);
+    fatal = e != cudaSuccess ? FBG_ECUDA : js;
+    for (Request* r : work) finish(r, fatal);
+    for (Request* r : jwork) finish(r, fatal);
     active.erase(std::remove_if(active.begin(), active.end(), [](Request* r) { return r->done; }), active.end());
     count_s += now_s() - tc;
     return false;
@@ -428,6 +500,45 @@ void fbg_server::complete_tick() {
   busy_s += now_s() - t0;
 }
 
+// The background compiles of recurring texts: build the specialised count
+// kernel, order its items longest first (one timed launch) and count once on
+// a stream of this thread, then publish the program to the tick loop.  A
+// failed build leaves the family on the interpreter.
+void fbg_server::jit_run() {
+  cudaSetDevice(device);
+  cudaStream_t st = nullptr;
+  const bool have_stream = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
+  for (;;) {
+    TextFamily* fam = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      jit_cv.wait(lk, [&] { return stop || !jit_queue.empty(); });
+      if (stop) break;
+      fam = jit_queue.front();
+      jit_queue.pop_front();
+    }
+    const double t0 = now_s();
+    fbg_program* p = nullptr;
+    fbg_status s = have_stream ? fbg_compile(fam->text.c_str(), fam->k, &p) : FBG_ECUDA;
+    if (s == FBG_OK) {
+      p->opt_engine = FBG_ENGINE_JIT;
+      s = fbg_schedule_units(p, st);
+    }
+    uint64_t c = 0;
+    if (s == FBG_OK) s = fbg_count(p, st, &c);   // leaves the self-resetting counters clean
+    std::lock_guard<std::mutex> lk(mu);
+    jit_compile_s += now_s() - t0;
+    if (s == FBG_OK) {
+      fam->prog = p;
+      fam->ready = true;
+      jit_ready++;
+    } else {
+      fbg_program_free(p);
+    }
+  }
+  if (st) cudaStreamDestroy(st);
+}
+
 // Two ticks in flight: while the GPU runs one, the server thread admits
 // requests and enqueues the next, then completes the older one.
 void fbg_server::run() {
@@ -455,6 +566,9 @@ fbg_status fbg_server_create(const fbg_server_options* opt, fbg_server** out) {
   if (s->opt.max_inflight <= 0) s->opt.max_inflight = 4096;
   if (!s->opt.tick_units) s->opt.tick_units = 65536;
   if (!s->opt.tick_assignments) s->opt.tick_assignments = 1ull << 36;
+  if (!s->opt.jit_min_n) s->opt.jit_min_n = 30;
+  if (s->opt.jit_after <= 0) s->opt.jit_after = 2;
+  if (s->opt.jit_max_programs <= 0) s->opt.jit_max_programs = 64;
   s->item_cap = s->opt.tick_units + 2 * (uint64_t)s->opt.max_inflight + 16;
   cudaGetDevice(&s->device);
   const size_t slots = (size_t)s->opt.max_inflight;
@@ -469,6 +583,9 @@ fbg_status fbg_server_create(const fbg_server_options* opt, fbg_server** out) {
   if ((e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)) != cudaSuccess ||
       (e = cudaStreamCreateWithFlags(&s->upload, cudaStreamNonBlocking)) != cudaSuccess ||
       (e = cudaStreamCreateWithFlags(&s->copies, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&s->jit_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&s->jit_fork, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&s->jit_join, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&s->uploaded, cudaEventDisableTiming)) != cudaSuccess ||
       (e = cudaMalloc(&s->d_progs, slots * sizeof(FbgInterpProg))) != cudaSuccess ||
       (e = cudaMallocHost(&s->h_progs, slots * sizeof(FbgInterpProg))) != cudaSuccess ||
@@ -487,6 +604,7 @@ fbg_status fbg_server_create(const fbg_server_options* opt, fbg_server** out) {
   }
   for (int i = (int)slots - 1; i >= 0; i--) s->free_slots.push_back(i);
   s->worker = std::thread([s] { s->run(); });
+  if (s->opt.jit_min_n > 0) s->jit_worker = std::thread([s] { s->jit_run(); });
   *out = s;
   return FBG_OK;
 }
@@ -519,8 +637,35 @@ fbg_status fbg_server_submit(fbg_server* s, const char* formula, int domain_k, i
   r->mode = mode;
   r->cap = cap;
   r->submit_s = now_s();
+  const bool may_jit = mode == FBG_MODE_COUNT && s->opt.jit_min_n > 0 && p->n >= s->opt.jit_min_n &&
+                       p->g->root != 0 && p->g->root != 1;
   {
     std::lock_guard<std::mutex> lk(s->mu);
+    if (may_jit) {
+      // the family of this (text, domain): count its submissions, queue its
+      // compile at the jit_after-th while the server keeps fewer than
+      // jit_max_programs
+      std::string key(formula);
+      key += '\0';
+      key += std::to_string(domain_k);
+      auto it = s->families.find(key);
+      if (it == s->families.end()) {
+        auto fam = std::make_unique<TextFamily>();
+        fam->text = formula;
+        fam->k = domain_k;
+        it = s->families.emplace(std::move(key), std::move(fam)).first;
+      }
+      TextFamily* fam = it->second.get();
+      fam->submissions++;
+      if (!fam->queued && fam->submissions >= (uint64_t)s->opt.jit_after &&
+          s->jit_started < (uint64_t)s->opt.jit_max_programs) {
+        fam->queued = true;
+        s->jit_started++;
+        s->jit_queue.push_back(fam);
+        s->jit_cv.notify_one();
+      }
+      r->fam = fam;
+    }
     r->id = s->next_id++;
     *request_id = r->id;
     s->pending.push_back(r.get());
@@ -597,6 +742,15 @@ fbg_status fbg_server_gpu_time(fbg_server* s, double* gpu_s) {
   return FBG_OK;
 }
 
+fbg_status fbg_server_jit_stats(fbg_server* s, uint64_t* programs, uint64_t* requests, double* compile_s) {
+  if (!s) return set_error(FBG_EINVAL, "null server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (programs) *programs = s->jit_ready;
+  if (requests) *requests = s->jit_requests;
+  if (compile_s) *compile_s = s->jit_compile_s;
+  return FBG_OK;
+}
+
 fbg_status fbg_server_profile(fbg_server* s, double* admit_s, double* count_s, double* enum_s) {
   if (!s) return set_error(FBG_EINVAL, "null server");
   std::lock_guard<std::mutex> lk(s->mu);
@@ -613,7 +767,10 @@ void fbg_server_free(fbg_server* s) {
     s->stop = true;
   }
   s->cv.notify_all();
+  s->jit_cv.notify_all();
   if (s->worker.joinable()) s->worker.join();
+  if (s->jit_worker.joinable()) s->jit_worker.join();
+  if (s->jit_stream) cudaStreamSynchronize(s->jit_stream);
   if (s->stream) {
     for (auto& kv : s->all) s->release_device(kv.second.get());
     for (int b = 0; b < 2; b++) {
@@ -623,6 +780,10 @@ void fbg_server_free(fbg_server* s) {
     cudaStreamSynchronize(s->stream);
   }
   s->all.clear();
+  s->families.clear();
+  if (s->jit_fork) cudaEventDestroy(s->jit_fork);
+  if (s->jit_join) cudaEventDestroy(s->jit_join);
+  if (s->jit_stream) cudaStreamDestroy(s->jit_stream);
   if (s->d_progs) cudaFree(s->d_progs);
   if (s->h_progs) cudaFreeHost(s->h_progs);
   if (s->d_counts) cudaFree(s->d_counts);

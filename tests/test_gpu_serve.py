@@ -138,3 +138,66 @@ def test_completed_queue_hands_out_each_finished_request_once():
         assert srv.poll(rid)["count"] == want
         srv.release(rid)
     srv.close()
+
+
+def _wait_programs(srv, want, timeout=180):
+    t0 = time.time()
+    while srv.stats()["jit_programs"] < want and time.time() - t0 < timeout:
+        time.sleep(0.05)
+    return srv.stats()["jit_programs"]
+
+
+def test_recurring_texts_move_to_a_specialised_kernel():
+    """Count requests of a text submitted jit_after times (with at least
+    jit_min_n letters) are counted by a specialised kernel that a background
+    thread compiles; once it is ready, new requests of that text run on it,
+    in the same ticks as interpreted requests.  Every count equals the
+    oracle's (all points up to n = 22, per-unit subcubes above) and the count
+    the interpreter gave the same text before the kernel was ready."""
+    fams = [W.triangle_free(7), W.transitive(5), W.posets(5), W.transitive(6)]   # n = 21, 25, 25, 36
+    srv = F.Server(jit_min_n=20, jit_after=2)
+    first = [srv.submit(wl.text, wl.k) for wl in fams for _ in range(2)]
+    srv.drain(300)
+    assert _wait_programs(srv, len(fams)) == len(fams)
+    before = srv.stats()["jit_requests"]
+    others = mixed_requests(24, 33, n_hi=24)
+    batch = [(wl, L.MODE_COUNT, 0) for wl in fams for _ in range(3)] + others
+    order = np.random.default_rng(3).permutation(len(batch))
+    batch = [batch[i] for i in order]
+    ids = [srv.submit(wl.text, wl.k, mode, cap) for wl, mode, cap in batch]
+    res = wait_all(srv, ids + first)
+    assert srv.stats()["jit_requests"] - before >= 3 * len(fams)
+    rng, cache = np.random.default_rng(5), {}
+    for i, (wl, mode, cap) in zip(ids, batch):
+        check_with_oracle(wl, mode, cap, res[i], rng, cache)
+    by_text = {}
+    for i, (wl, mode, cap) in zip(ids, batch):
+        if mode == L.MODE_COUNT:
+            by_text.setdefault((wl.text, wl.k), set()).add(res[i]["count"])
+    for j, i in enumerate(first):
+        assert res[i]["status"] == 0
+        assert by_text[(fams[j // 2].text, fams[j // 2].k)] == {res[i]["count"]}
+    srv.close()
+
+
+def test_default_server_specialises_n36_and_jit_off_keeps_the_interpreter():
+    wl = W.transitive(6)
+    on = F.Server()
+    ids = [on.submit(wl.text, wl.k) for _ in range(2)]
+    on.drain(300)
+    assert _wait_programs(on, 1) == 1
+    ids += [on.submit(wl.text, wl.k) for _ in range(2)]
+    res = wait_all(on, ids)
+    assert on.stats()["jit_requests"] == 2
+    assert len({res[i]["count"] for i in ids}) == 1 and res[ids[0]]["status"] == 0
+    want = res[ids[-1]]["count"]
+    OC.check_count(wl, want, np.random.default_rng(6))
+    on.close()
+    off = F.Server(jit_min_n=-1)
+    ids = [off.submit(wl.text, wl.k) for _ in range(3)]
+    res = wait_all(off, ids)
+    time.sleep(0.5)
+    st = off.stats()
+    assert st["jit_programs"] == 0 and st["jit_requests"] == 0
+    assert {res[i]["count"] for i in ids} == {want}
+    off.close()
