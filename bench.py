@@ -39,9 +39,15 @@ NOMINAL_SM_MHZ = 2032.0         # maximum SM clock of the part, when nvidia-smi 
 #          their vector-pipe LOP3 warp instructions (sass__inst_executed_per_opcode:
 #          the formulas' LUTs and the popcount's full adders, not the ULOP3 of
 #          the uniform datapath)
+#          and, per launch (transitive, triangle-free, Aut), the issue slots used
+#          and the ALU pipe's busy share, in % of the SMs' active cycles
+#          (smsp__issue_active, sm__inst_executed_pipe_alu), with the SMs'
+#          active and elapsed cycles (ncu serialises the three launches)
 #   table: DRAM bytes of one truth-table launch
 NCU_COUNT = {"sources_sha": "eb8600039356cfa3", "traffic_step": 47_104 + 101_632 + 54_016,
-             "vector_lop3_step": 8_895_229 + 22_819_402 + 34_166}
+             "vector_lop3_step": 8_895_229 + 22_819_402 + 34_166,
+             "per_launch": {"issue_slots_used_pct": [43.7, 64.9, 25.1], "alu_pipe_pct": [70.7, 79.4, 35.1],
+                            "sm_active_cycles": [46_995, 109_828, 374], "sm_elapsed_cycles": [58_887, 118_257, 13_903]}}
 NCU_TABLE = {"sources_sha": "898d05ddf8c3e3ff", "traffic_launch": 478_359_040 + 68_096}
 
 
@@ -64,6 +70,19 @@ def ncu_figures(table: dict, fingerprint: str, keys) -> dict:
     why = ("no capture recorded" if not table.get("sources_sha") else
            f"captured on sources {table['sources_sha']}, running {fingerprint}")
     return {k: None for k in keys} | {"stale": True, "reason": why}
+
+
+def ncu_utilisation(per: dict) -> dict:
+    """Issue slots used and ALU-pipe busy share of the count launches (ncu,
+    % of active cycles), per launch and weighted by each launch's SM active
+    cycles."""
+    w = per["sm_active_cycles"]
+    tot = sum(w)
+    return {"issue_slots_used_pct": per["issue_slots_used_pct"], "alu_pipe_pct": per["alu_pipe_pct"],
+            "issue_slots_used_pct_weighted": sum(a * b for a, b in zip(per["issue_slots_used_pct"], w)) / tot,
+            "alu_pipe_pct_weighted": sum(a * b for a, b in zip(per["alu_pipe_pct"], w)) / tot,
+            "sm_active_share": [a / e for a, e in zip(w, per["sm_elapsed_cycles"])],
+            "launches": ["transitive k=6", "triangle-free k=9", "Aut(G(6,1/2))"]}
 
 
 def load_peaks():
@@ -562,11 +581,23 @@ def run_serving(args, torch, F, L):
         srv.submit(r.workload.text, r.workload.k, L.MODE_ENUMERATE if r.mode == "enumerate" else L.MODE_COUNT, r.cap)
     srv.drain(600)
     srv.close()
-    calib = W.request_stream(min(400, nreq), rate_per_s=1.0, seed=55)
+    # the calibration burst: all at once from the same number of clients
+    # as the timed stream (submission compiles on the client's thread)
+    nclients = 8
+    calib = W.request_stream(min(800, nreq), rate_per_s=1.0, seed=55)
     srv = F.Server(jit_min_n=args.serve_jit_min_n)
+
+    def burst(c):
+        for r in calib[c::nclients]:
+            srv.submit(r.workload.text, r.workload.k, L.MODE_ENUMERATE if r.mode == "enumerate" else L.MODE_COUNT,
+                       r.cap)
+
     t0 = time.perf_counter()
-    ids = [srv.submit(r.workload.text, r.workload.k,
-                      L.MODE_ENUMERATE if r.mode == "enumerate" else L.MODE_COUNT, r.cap) for r in calib]
+    cal_threads = [threading.Thread(target=burst, args=(c,)) for c in range(nclients)]
+    for th in cal_threads:
+        th.start()
+    for th in cal_threads:
+        th.join()
     srv.drain(600)
     t_cal = time.perf_counter() - t0
     srv.close()
@@ -581,7 +612,6 @@ def run_serving(args, torch, F, L):
     # text on the calling thread, and one thread alone could not keep up with
     # the offered rate; client c submits requests c, c + nclients, ... at
     # their arrival times
-    nclients = 8
     late = [0.0] * nclients              # largest delay of a submission past its arrival time
 
     def producer(c):
@@ -828,7 +858,7 @@ def run_ours(args, rank, world):
     run_mhz = clocks.get("sm_mhz") or max_mhz
     peak_lop3 = sms * LOP3_LANES_PER_CLK_SM * run_mhz * 1e6
     peak_lop3_max = sms * LOP3_LANES_PER_CLK_SM * max_mhz * 1e6
-    ncu = ncu_figures(NCU_COUNT, kernel_fingerprint(progs, 0), ["traffic_step", "vector_lop3_step"])
+    ncu = ncu_figures(NCU_COUNT, kernel_fingerprint(progs, 0), ["traffic_step", "vector_lop3_step", "per_launch"])
 
     # the paper's brute-force evaluation (every word), same kernels without pruning
     brute = {}
@@ -900,7 +930,8 @@ def run_ours(args, rank, world):
                          "achieved": ncu["vector_lop3_step"] * 32 / kern_s / 1e12,
                          "frac": ncu["vector_lop3_step"] * 32 / kern_s / peak_lop3,
                          "basis": "every LOP3 the three launches issued on the vector ALU pipe (ncu count of the "
-                                  "same kernels and shapes, full adders included) / CUDA-event step time"}},
+                                  "same kernels and shapes, full adders included) / CUDA-event step time"},
+                     "ncu_utilisation": None if ncu["stale"] else ncu_utilisation(ncu["per_launch"])},
         "nominal_lop3_ratio": executed / nominal if nominal else None,
         "alu_probe": {"lop3_tops": lop3_probe, "of_nominal_peak": lop3_probe / (peak_lop3 / 1e12),
                       "basis": "fbg_probe_lop3_rate: 16 independent lop3.b32 chains per thread, CUDA events"},

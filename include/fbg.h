@@ -91,7 +91,9 @@ enum {
   FBG_OPT_REGS_LOG2 = 3,       /* JIT: 32-bit registers per thread tile, log2 (1..3, default 2) */
   FBG_OPT_WARPS_LOG2 = 4,      /* JIT: warps per block, log2 (0..5, default 3) */
   FBG_OPT_UNIT_BITS = 5,       /* max block-uniform unit bits (default 13) */
-  FBG_OPT_LOOP_LEVEL_BITS = 6, /* bits per loop level (default 4) */
+  FBG_OPT_LOOP_LEVEL_BITS = 6, /* bits per loop level (0, the default: 4 for the NVRTC kernels, 1 for
+                                  the interpreter, which prunes after every letter; the interpreter
+                                  widens levels to hold at most 8) */
   FBG_OPT_SEARCH_ORDER = 7,    /* counts: 1 (default) heuristic variable order, 0 identity */
   FBG_OPT_MIN_BLOCKS = 8,      /* JIT: __launch_bounds__ min blocks per SM (default 2) */
   FBG_OPT_STATS = 9,           /* 1: kernels carry level counters and record executed level

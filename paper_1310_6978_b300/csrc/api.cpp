@@ -68,7 +68,11 @@ LayoutParams interp_params(const fbg_program* p) {
   lp.r_max = 1;
   lp.warps_log2 = FBG_INTERP_WARPS_LOG2;
   lp.unit_bits_max = (int)p->opt_unit_bits;
-  lp.loop_level_bits = (int)p->opt_loop_level_bits;
+  // one letter per loop level by default: a level whose partial conjunction
+  // is zero for the whole warp skips the rest, so the interpreter, whose cost
+  // is per executed instruction, prunes at every letter
+  lp.loop_level_bits = p->opt_loop_level_bits ? (int)p->opt_loop_level_bits : 1;
+  lp.max_loop_levels = FBG_INTERP_MAX_LEVELS - 2;
   return lp;
 }
 
@@ -77,7 +81,7 @@ LayoutParams jit_params(const fbg_program* p) {
   lp.r_max = (int)p->opt_regs_log2;
   lp.warps_log2 = (int)p->opt_warps_log2;
   lp.unit_bits_max = (int)p->opt_unit_bits;
-  lp.loop_level_bits = (int)p->opt_loop_level_bits;
+  lp.loop_level_bits = p->opt_loop_level_bits ? (int)p->opt_loop_level_bits : 4;
   lp.inner_bits = (int)p->opt_inner_bits;
   return lp;
 }
@@ -124,11 +128,11 @@ static std::shared_ptr<const InterpHost> interp_host(fbg_program* p, int which) 
   // work items: single units while that keeps the queue short, else ranges
   uint64_t per = 1;
   while (nunits / per > 65536) per <<= 1;
-  h->units_per_item = per;
-  if (p->opt_prune && per == 1) {
+  if (p->opt_prune && nunits <= (1ull << 21)) {
     // units on which a conjunct over unit and warp letters is false have no
     // models: counts, tables (zeroed before the launch) and model lists leave
-    // them out when that removes a quarter of them
+    // them out when that removes a quarter of them; the live units are then
+    // single-unit items when at most 2^18 remain
     std::vector<uint8_t> alive = alive_items(*p->g, h->lp.layout);
     const int wb = h->lp.layout.warp_bits;
     std::vector<uint32_t> live;
@@ -137,8 +141,12 @@ static std::shared_ptr<const InterpHost> interp_host(fbg_program* p, int which) 
       for (int w = 0; w < (1 << wb); w++) any = any || alive[(size_t)((u << wb) | (uint64_t)w)];
       if (any) live.push_back((uint32_t)u);
     }
-    if (!alive.empty() && live.size() * 4 <= nunits * 3) h->live = std::move(live);
+    if (!alive.empty() && live.size() * 4 <= nunits * 3 && (per == 1 || live.size() <= (1u << 18))) {
+      h->live = std::move(live);
+      per = 1;
+    }
   }
+  h->units_per_item = per;
   std::shared_ptr<const InterpHost> hc = std::move(h);
   interp_host_put(key, hc);
   return hc;
@@ -543,7 +551,7 @@ fbg_status fbg_set_option(fbg_program* p, int option, int64_t v) {
       p->opt_unit_bits = v;
       break;
     case FBG_OPT_LOOP_LEVEL_BITS:
-      if (v < 1 || v > 16) return bad();
+      if (v < 0 || v > 16) return bad();
       p->opt_loop_level_bits = v;
       break;
     case FBG_OPT_SEARCH_ORDER: p->opt_search = v ? 1 : 0; break;

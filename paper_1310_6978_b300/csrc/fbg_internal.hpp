@@ -153,6 +153,7 @@ struct LayoutParams {
   int loop_level_bits = 4;
   int loop_bits_max = 16;
   int inner_bits = 0;        // innermost loop level's bits (0 = loop_level_bits)
+  int max_loop_levels = 64;  // wider levels when the loop bits would need more
 };
 
 Layout make_layout(int n, const LayoutParams& prm, const std::vector<int>& order_top_first);

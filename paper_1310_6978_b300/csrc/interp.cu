@@ -27,7 +27,8 @@ __global__ void __launch_bounds__(NT) interp_kernel(const FbgInterpProg* __restr
   init_thread(T, dyn_slots);
   unsigned cur = 0xFFFFFFFFu;
   bool alive0 = true;
-  fbg_u64 iters = 0;
+  if (P.iters && threadIdx.x == 0)
+    for (int lv = 0; lv < FBG_INTERP_MAX_LEVELS; lv++) S.lev_iters[lv] = 0;
   for (;;) {
     if (threadIdx.x == 0) S.item = atomicAdd(item_ctr, 1ull);
     __syncthreads();
@@ -44,9 +45,9 @@ __global__ void __launch_bounds__(NT) interp_kernel(const FbgInterpProg* __restr
       Q.unit_offsets = so.unit_offsets;
       Q.models = so.models;
       Q.cap = so.cap;
-      process_item<MODE>(S, T, progs, W, cur, alive0, Q, cnt, iters);
+      process_item<MODE>(S, T, progs, W, cur, alive0, Q, cnt);
     } else {
-      process_item<MODE>(S, T, progs, W, cur, alive0, P, cnt, iters);
+      process_item<MODE>(S, T, progs, W, cur, alive0, P, cnt);
     }
     if (MODE == 0) {
       cnt = fbg_warp_sum(cnt);
@@ -58,7 +59,9 @@ __global__ void __launch_bounds__(NT) interp_kernel(const FbgInterpProg* __restr
       }
     }
   }
-  if (P.iters && (threadIdx.x & 31) == 0 && iters) atomicAdd(P.iters, iters);
+  if (P.iters && threadIdx.x == 0)
+    for (int lv = 0; lv < FBG_INTERP_MAX_LEVELS; lv++)
+      if (S.lev_iters[lv]) atomicAdd(P.iters + lv, S.lev_iters[lv]);
 }
 
 // exclusive prefix sum of n u64 values, one block; total -> *total

@@ -62,7 +62,14 @@ struct Shared {
   fbg_u64 svals[FBG_INTERP_MAX_SHARED];   // block slots: one word each, equal in every tile
   fbg_u64 unit;
   fbg_u64 item;
+  // statistics launches (P.iters set): executions of each level by this
+  // block, in units of 32 tiles (the block is one warp: lane 0 counts)
+  fbg_u64 lev_iters[FBG_INTERP_MAX_LEVELS];
 };
+
+__device__ __forceinline__ void count_level(Shared& S, const FbgLaunch& P, int lv) {
+  if (P.iters && (threadIdx.x & 31) == 0) S.lev_iters[lv] += NTILE;
+}
 
 struct Thread {
   fbg_u64* slots;       // this thread's column: tile k of slot s at slots[s * B + k * NT]
@@ -176,7 +183,7 @@ __device__ __forceinline__ unsigned warp_incl(unsigned c) {
 }
 
 template <int MODE>
-__device__ void run_unit(Shared& S, Thread& T, fbg_u64 u, const FbgLaunch& P, fbg_u64& cnt, fbg_u64& iters) {
+__device__ void run_unit(Shared& S, Thread& T, fbg_u64 u, const FbgLaunch& P, fbg_u64& cnt) {
   const FbgInterpProg& G = S.prog;
   bool tvalid[NTILE];
 #pragma unroll
@@ -188,6 +195,7 @@ __device__ void run_unit(Shared& S, Thread& T, fbg_u64 u, const FbgLaunch& P, fb
     if (base >= P.cap) return;   // every model of this unit lies past the cap
   }
   exec_level(S, T, G.lev[1]);
+  count_level(S, P, 1);
   if (!level_alive<MODE>(S, T, G.lev[1])) return;
   unsigned it[FBG_INTERP_MAX_LEVELS];
   int lv = 2;
@@ -201,6 +209,7 @@ __device__ void run_unit(Shared& S, Thread& T, fbg_u64 u, const FbgLaunch& P, fb
 #pragma unroll
       for (int k = 0; k < NTILE; k++) T.coords[k] = (T.coords[k] & ~m) | ((fbg_u64)it[lv] << L.pos);
       exec_level(S, T, L);
+      count_level(S, P, lv);
       bool alive = level_alive<MODE>(S, T, L);
       if (alive && lv + 1 < nl) {
         lv++;
@@ -244,7 +253,6 @@ __device__ void run_unit(Shared& S, Thread& T, fbg_u64 u, const FbgLaunch& P, fb
         }
         base = off;
       }
-      if ((threadIdx.x & 31) == 0) iters += NTILE;
     }
     if (lv < 2 || nl <= 2) break;
     // odometer advance
@@ -256,17 +264,17 @@ __device__ void run_unit(Shared& S, Thread& T, fbg_u64 u, const FbgLaunch& P, fb
 // one work item (program, unit range) of a count / table / enumerate pass
 template <int MODE>
 __device__ __forceinline__ void process_item(Shared& S, Thread& T, const FbgInterpProg* progs, const FbgWorkItem& W,
-                                             unsigned& cur, bool& alive0, const FbgLaunch& P, fbg_u64& cnt,
-                                             fbg_u64& iters) {
+                                             unsigned& cur, bool& alive0, const FbgLaunch& P, fbg_u64& cnt) {
   if (W.prog != cur) {
     load_prog(S, progs, W.prog);
     cur = W.prog;
     set_thread_coords(T, 0ull);
     exec_level(S, T, S.prog.lev[0]);
+    count_level(S, P, 0);
     alive0 = level_alive<MODE>(S, T, S.prog.lev[0]);
   }
   if (alive0)
-    for (fbg_u64 u = W.unit_begin; u < W.unit_end; u++) run_unit<MODE>(S, T, u, P, cnt, iters);
+    for (fbg_u64 u = W.unit_begin; u < W.unit_end; u++) run_unit<MODE>(S, T, u, P, cnt);
 }
 
 }  // namespace fbg_interp

@@ -60,9 +60,11 @@ Layout make_layout(int n, const LayoutParams& prm, const std::vector<int>& order
     L.unit_bits = units;
     int lb = std::max(1, prm.loop_level_bits);
     // the innermost level may have its own width; the others split the rest
-    // from the top
+    // from the top, with no more levels than the engine holds
     int inner = prm.inner_bits > 0 ? std::min(prm.inner_bits, loops) : 0;
     loops -= inner;
+    const int room = std::max(1, prm.max_loop_levels - (inner > 0 ? 1 : 0));
+    lb = std::max(lb, (loops + room - 1) / room);
     while (loops > 0) {
       int b = std::min(lb, loops);
       L.loop_bits.push_back(b);
@@ -183,7 +185,7 @@ std::vector<int> search_order(const Grounded& g, uint64_t seed) {
 // so each DAG node costs one pass over 2^(unit + warp bits) / 64 words.
 std::vector<uint8_t> alive_items(const Grounded& g, const Layout& L) {
   const int wb = L.warp_bits, ub = L.unit_bits + wb;
-  if (L.unit_bits <= 0 || ub > 20) return {};
+  if (L.unit_bits <= 0 || ub > 22) return {};
   const FormDag& d = g.dag;
   std::vector<uint64_t> sup = supports(d);
   uint64_t umask = 0;

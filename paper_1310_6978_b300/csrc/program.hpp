@@ -106,7 +106,7 @@ struct fbg_program {
   const fbg::Grounded* g = nullptr;     // = &compiled->g
   // options (fbg_set_option)
   int64_t opt_engine = FBG_ENGINE_AUTO, opt_prune = 1, opt_regs_log2 = 2, opt_warps_log2 = 3, opt_unit_bits = 13,
-          opt_loop_level_bits = 4, opt_search = 1, opt_min_blocks = 2, opt_stats = 0, opt_inner_bits = 0,
+          opt_loop_level_bits = 0, opt_search = 1, opt_min_blocks = 2, opt_stats = 0, opt_inner_bits = 0,
           opt_split_items = 0, opt_popc_cost = 4, opt_order_seed = 0;
   fbg::InterpBuild ib[2];   // [0] count layout, [1] identity layout (tables, model lists)
   fbg::JitBuild jb[3];      // [0] count kernel, [1] truth-table kernel, [2] enumerate kernel

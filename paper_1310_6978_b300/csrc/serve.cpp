@@ -616,11 +616,14 @@ fbg_status fbg_server_submit(fbg_server* s, const char* formula, int domain_k, i
   fbg_program* p = nullptr;
   fbg_status st = fbg_compile(formula, domain_k, &p);
   if (st != FBG_OK) return st;
-  // ticks run the interpreter: no kernel compile on the server thread; up to
-  // 2^16 units per program, so that a large request is cut into many small
-  // work items that spread over every SM instead of a few long ones
+  // ticks run the interpreter: no kernel compile on the server thread.  A
+  // count is cut into up to 2^20 units (model lists: 2^16, which keeps their
+  // per-unit counters small), so that a large request becomes many short
+  // work items that spread over every SM; the units on which a conjunct over
+  // unit letters is false are left out at build time, and each of the
+  // remaining ones prunes letter by letter (one letter per loop level)
   p->opt_engine = FBG_ENGINE_INTERP;
-  p->opt_unit_bits = 16;
+  p->opt_unit_bits = mode == FBG_MODE_COUNT ? 20 : 16;
   // the host half of the interpreter build runs here, on the submitting
   // thread; admission on the server thread then only uploads it
   st = prebuild_interp_host(p, mode == FBG_MODE_COUNT ? 0 : 1);

@@ -69,7 +69,7 @@ def test_evaluation_fails_loudly_without_a_device(engine):
 def test_option_validation():
     p = F.compile("var a\na\n")
     for opt, bad in [(L.OPT_ENGINE, 7), (L.OPT_REGS_LOG2, 0), (L.OPT_REGS_LOG2, 4), (L.OPT_WARPS_LOG2, 6),
-                     (L.OPT_LOOP_LEVEL_BITS, 0), (999, 1)]:
+                     (L.OPT_LOOP_LEVEL_BITS, -1), (L.OPT_LOOP_LEVEL_BITS, 17), (999, 1)]:
         with pytest.raises(L.FbgError) as ei:
             p.set_option(opt, bad)
         assert ei.value.status == L.FBG_EINVAL

@@ -72,3 +72,37 @@ def test_host_times_split_builds_from_counts():
     assert p.count() == 4231
     b2, c2 = p.debug_host_times()
     assert b2 == b1 and c2 > c1
+
+
+@pytest.mark.parametrize("prune", [0, 1])
+def test_interpreter_exec_stats_follow_the_layout(prune):
+    """The interpreter's level counters (units of 32 tiles): level 1 runs once
+    per unit for each of the block's two 32-tile halves, a loop level
+    multiplies by its width; without pruning every level runs that often and
+    the executed lane operations (64 lop3.b32 per LUT and 32 tiles) of levels
+    1.. are the nominal work."""
+    from paper_1310_6978_b300 import _lib as L
+    from paper_1310_6978_b300 import workloads as W
+    wl = W.TRIFREE9
+    p = F.compile(wl.text, wl.k).set_option(L.OPT_ENGINE, L.ENGINE_INTERP).set_option(L.OPT_UNIT_BITS, 14)
+    p.set_option(L.OPT_PRUNE, prune)
+    p.set_option(L.OPT_STATS, 1)
+    assert p.count() == 246348115
+    es = p.exec_stats()
+    d = p.debug_dump(2)
+    lev = d["levels"]
+    nl = len(lev)
+    it = list(es.level_iters)[:nl]
+    luts = [l[1] - l[0] for l in lev]
+    assert es.lop3_executed == 64 * sum(i * n for i, n in zip(it, luts))
+    closed = [None, (1 << d["unit_bits"]) * 2]
+    for lv in range(2, nl):
+        closed.append(closed[-1] << lev[lv][2])
+    for lv in range(1, nl):
+        assert it[lv] <= closed[lv]
+        if not prune:
+            assert it[lv] == closed[lv], (lv, it, closed)
+    if not prune:
+        assert es.lop3_executed - 64 * it[0] * luts[0] == es.lop3_nominal
+    else:
+        assert es.lop3_executed < es.lop3_nominal
