@@ -353,13 +353,19 @@ class Server:
         self._L.check(self._L.lib.fbg_server_submit(self._h, text.encode(), int(domain_k), mode, cap, ctypes.byref(rid)))
         return rid.value
 
-    def poll(self, rid: int):
+    def poll(self, rid: int, models: bool = True):
+        """The result of a finished request (None while it runs); with
+        models=False the model list is left out (its length is "written")."""
         r = self._L.FbgResult()
         st = self._L.lib.fbg_server_poll(self._h, rid, ctypes.byref(r))
         if st == self._L.FBG_EBUSY:
             return None
         self._L.check(st)
-        models = [r.models[i] for i in range(r.written)] if r.written else []
+        if models and r.written:
+            import numpy as np
+            models = np.ctypeslib.as_array(r.models, shape=(r.written,)).tolist()
+        else:
+            models = []
         return {"status": r.status, "count": r.count, "written": r.written, "models": models,
                 "submit_s": r.submit_s, "admit_s": r.admit_s, "done_s": r.done_s}
 

@@ -133,16 +133,25 @@ static std::shared_ptr<const InterpHost> interp_host(fbg_program* p, int which) 
     // models: counts, tables (zeroed before the launch) and model lists leave
     // them out when that removes a quarter of them; the live units are then
     // single-unit items when at most 2^18 remain
-    std::vector<uint8_t> alive = alive_items(*p->g, h->lp.layout);
+    const std::vector<uint64_t> alive = alive_words(*p->g, h->lp.layout);
     const int wb = h->lp.layout.warp_bits;
     std::vector<uint32_t> live;
-    for (uint64_t u = 0; !alive.empty() && u < nunits; u++) {
-      bool any = false;
-      for (int w = 0; w < (1 << wb); w++) any = any || alive[(size_t)((u << wb) | (uint64_t)w)];
-      if (any) live.push_back((uint32_t)u);
+    if (!alive.empty()) {
+      // item t = (unit << wb) | warp slice: a unit lives when any slice does
+      const uint64_t nbits = nunits << wb;
+      for (uint64_t t0 = 0; t0 < nbits; t0 += 64) {
+        uint64_t word = alive[(size_t)(t0 >> 6)];
+        if (nbits - t0 < 64) word &= (1ull << (nbits - t0)) - 1ull;
+        while (word) {
+          const uint64_t t = t0 + (uint64_t)__builtin_ctzll(word);
+          const uint64_t u = t >> wb;
+          if (live.empty() || live.back() != (uint32_t)u) live.push_back((uint32_t)u);
+          word &= word - 1;
+        }
+      }
     }
     if (!alive.empty() && live.size() * 4 <= nunits * 3 && (per == 1 || live.size() <= (1u << 18))) {
-      h->live = std::move(live);
+      h->live = std::make_shared<const std::vector<uint32_t>>(std::move(live));
       per = 1;
     }
   }
@@ -175,11 +184,15 @@ fbg_status build_interp(fbg_program* p, int which) {
   b.nunits = b.code.prog.nunits;
   b.live = h->live;
   const uint64_t per = h->units_per_item;
+  // the program's own item list (full-range launches); a build for the
+  // server (pooled) has none: the server makes the items of every tick
   std::vector<FbgWorkItem> items;
-  if (per == 1)
-    b.append_items(items, 0u, 0, b.live_units(), 1);
-  else
-    for (uint64_t u = 0; u < b.nunits; u += per) items.push_back(FbgWorkItem{0u, 0u, u, std::min(b.nunits, u + per)});
+  if (!p->alloc_stream) {
+    if (per == 1)
+      b.append_items(items, 0u, 0, b.live_units(), 1);
+    else
+      for (uint64_t u = 0; u < b.nunits; u += per) items.push_back(FbgWorkItem{0u, 0u, u, std::min(b.nunits, u + per)});
+  }
   b.units_per_item = per;
   b.nitems = items.size();
   b.free_device();
@@ -1107,7 +1120,25 @@ fbg_status fbg_debug_dump(fbg_program* p, int which, char* buf, size_t* len) {
         << G.lev[i].pos << ", " << G.lev[i].has_acc << ", " << G.lev[i].acc_op << "]";
     o << "], \"out_op\": " << G.out_op << ", \"nslots\": " << G.nslots << ", \"nshared\": " << G.nshared << ", \"tvalid\": " << G.tvalid
       << ", \"vmask\": " << G.vmask << ", \"first_unit_pos\": " << G.first_unit_pos << ", \"unit_bits\": "
-      << G.unit_bits << ", \"nunits\": " << G.nunits << "}";
+      << G.unit_bits << ", \"nunits\": " << G.nunits;
+    if (p->opt_prune) {   // units that a conjunct over unit and warp letters leaves alive (-1: not evaluated)
+      const std::vector<uint64_t> alive = alive_words(*p->g, lp.layout);
+      long long nlive = -1;
+      if (!alive.empty()) {
+        nlive = 0;
+        const int wb = lp.layout.warp_bits;
+        for (uint64_t u = 0; u < G.nunits; u++) {
+          bool any = false;
+          for (int w = 0; w < (1 << wb); w++) {
+            const uint64_t t = (u << wb) | (uint64_t)w;
+            any = any || ((alive[(size_t)(t >> 6)] >> (t & 63)) & 1);
+          }
+          nlive += any;
+        }
+      }
+      o << ", \"live_units\": " << nlive;
+    }
+    o << "}";
   }
   std::string s = o.str();
   if (buf) {

@@ -40,7 +40,7 @@ struct InterpHost {
   LutProgram lp;
   InterpCode code;
   uint64_t units_per_item = 1;
-  std::vector<uint32_t> live;
+  std::shared_ptr<const std::vector<uint32_t>> live;   // null: every unit
 };
 
 // key of a build: what ("jit"/"interp"), mode or layout, every option that

@@ -167,6 +167,9 @@ std::vector<int> enum_order(int n, const LayoutParams& prm);     // enumerate mo
 // and warp positions is false on that item, so the item has no models;
 // empty when there is no such conjunct or more than 20 unit + warp bits.
 std::vector<uint8_t> alive_items(const Grounded& g, const Layout& L);
+// the same as a bit vector: bit t of word t / 64 set when item t may hold
+// models (empty: no conjunct over unit and warp letters, or too many items)
+std::vector<uint64_t> alive_words(const Grounded& g, const Layout& L);
 
 // ------------------------------------------------------------ LUT program --
 

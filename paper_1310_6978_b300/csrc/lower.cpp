@@ -180,10 +180,21 @@ std::vector<int> search_order(const Grounded& g, uint64_t seed) {
 }
 
 // The conjuncts over unit and warp letters are evaluated bitwise over all
-// 2^(unit bits + warp bits) items at once: item bit b is a free generator
-// over the item index (bit t of its word vector is bit b of t, Sec. 2.2-2.3),
-// so each DAG node costs one pass over 2^(unit + warp bits) / 64 words.
-std::vector<uint8_t> alive_items(const Grounded& g, const Layout& L) {
+// 2^(unit bits + warp bits) items: item bit b is a free generator over the
+// item index (bit t of its word vector is bit b of t, Sec. 2.2-2.3).  Each
+// kept conjunct is compiled into a short program over a small register file
+// and the programs run word by word (64 items at a time), one conjunct after
+// the other, until the word's AND is zero: nothing of the size of the item
+// vector is held but the result.
+namespace {
+struct CIns {
+  uint8_t op;        // 0 const 0, 1 const 1, 2 var, 3 not, 4 and, 5 or, 6 xor, 7 copy
+  uint8_t bit;       // var: item bit
+  uint32_t dst, a, b;
+};
+}  // namespace
+
+std::vector<uint64_t> alive_words(const Grounded& g, const Layout& L) {
   const int wb = L.warp_bits, ub = L.unit_bits + wb;
   if (L.unit_bits <= 0 || ub > 22) return {};
   const FormDag& d = g.dag;
@@ -205,76 +216,125 @@ std::vector<uint8_t> alive_items(const Grounded& g, const Layout& L) {
     keep.push_back(g.root);
   }
   if (keep.empty()) return {};
+  // one program per kept conjunct: the nodes under it, children first (a
+  // child's id is smaller), each in its own register
+  std::vector<std::vector<CIns>> progs;
+  std::vector<uint32_t> out_reg;
+  size_t nregs = 1;
+  std::vector<int> slot((size_t)d.size(), -1);
+  for (int c : keep) {
+    std::vector<int> nodes, stack{c};
+    while (!stack.empty()) {
+      int x = stack.back();
+      stack.pop_back();
+      if (slot[(size_t)x] != -1) continue;
+      slot[(size_t)x] = 0;
+      nodes.push_back(x);
+      for (int k : d.node(x).kids) stack.push_back(k);
+    }
+    std::sort(nodes.begin(), nodes.end());
+    for (size_t i = 0; i < nodes.size(); i++) slot[(size_t)nodes[i]] = (int)i;
+    std::vector<CIns> pr;
+    for (int x : nodes) {
+      const FNode& f = d.node(x);
+      const uint32_t r = (uint32_t)slot[(size_t)x];
+      switch (f.op) {
+        case F0: pr.push_back({0, 0, r, 0, 0}); break;
+        case F1: pr.push_back({1, 0, r, 0, 0}); break;
+        case FVAR: pr.push_back({2, (uint8_t)ubit[(size_t)f.var], r, 0, 0}); break;
+        case FNOT: pr.push_back({3, 0, r, (uint32_t)slot[(size_t)f.kids[0]], 0}); break;
+        case FXOR:
+          pr.push_back({6, 0, r, (uint32_t)slot[(size_t)f.kids[0]], (uint32_t)slot[(size_t)f.kids[1]]});
+          break;
+        case FAND:
+        case FOR: {
+          const uint8_t op = f.op == FAND ? 4 : 5;
+          if (f.kids.empty()) {
+            pr.push_back({(uint8_t)(f.op == FAND ? 1 : 0), 0, r, 0, 0});
+            break;
+          }
+          pr.push_back({7, 0, r, (uint32_t)slot[(size_t)f.kids[0]], 0});
+          for (size_t i = 1; i < f.kids.size(); i++) pr.push_back({op, 0, r, r, (uint32_t)slot[(size_t)f.kids[i]]});
+          break;
+        }
+      }
+    }
+    nregs = std::max(nregs, nodes.size());
+    out_reg.push_back((uint32_t)slot[(size_t)c]);
+    progs.push_back(std::move(pr));
+    for (int x : nodes) slot[(size_t)x] = -1;
+  }
   const uint64_t U = 1ull << ub;
   const size_t W = U >= 64 ? (size_t)(U / 64) : 1;
   const uint64_t tail = U >= 64 ? ~0ull : ((1ull << U) - 1ull);
   static const uint64_t pat[6] = {0xAAAAAAAAAAAAAAAAull, 0xCCCCCCCCCCCCCCCCull, 0xF0F0F0F0F0F0F0F0ull,
                                   0xFF00FF00FF00FF00ull, 0xFFFF0000FFFF0000ull, 0xFFFFFFFF00000000ull};
-  // nodes under the kept conjuncts, children first (a child's id is smaller)
-  std::vector<char> need((size_t)d.size(), 0);
-  std::vector<int> stack(keep.begin(), keep.end());
-  while (!stack.empty()) {
-    int x = stack.back();
-    stack.pop_back();
-    if (need[(size_t)x]) continue;
-    need[(size_t)x] = 1;
-    for (int c : d.node(x).kids) stack.push_back(c);
-  }
-  // values are released after their last needed parent, and each kept
-  // conjunct is folded into the AND as soon as it is known, so only the
-  // live frontier of the DAG is held
-  std::vector<int> users((size_t)d.size(), 0);
-  std::vector<char> kept((size_t)d.size(), 0);
-  for (int c : keep) kept[(size_t)c] = 1;
-  for (int x = 0; x < d.size(); x++)
-    if (need[(size_t)x])
-      for (int c : d.node(x).kids) users[(size_t)c]++;
-  std::vector<uint64_t> all(W, tail);
-  std::vector<std::vector<uint64_t>> val((size_t)d.size());
-  auto release = [&](int x) {
-    if (users[(size_t)x] == 0) std::vector<uint64_t>().swap(val[(size_t)x]);
-  };
-  for (int x = 0; x < d.size(); x++) {
-    if (!need[(size_t)x]) continue;
-    const FNode& f = d.node(x);
-    std::vector<uint64_t>& out = val[(size_t)x];
-    out.assign(W, 0);
-    switch (f.op) {
-      case F0: break;
-      case F1: std::fill(out.begin(), out.end(), ~0ull); break;
-      case FVAR: {
-        const int b = ubit[(size_t)f.var];
-        for (size_t w = 0; w < W; w++)
-          out[w] = b < 6 ? pat[b] : (((w >> (b - 6)) & 1) ? ~0ull : 0ull);
-        break;
+  std::vector<uint64_t> reg(nregs, 0);
+  auto run = [&](size_t c, uint64_t w) {
+    for (const CIns& in : progs[c]) {
+      uint64_t v = 0;
+      switch (in.op) {
+        case 0: v = 0; break;
+        case 1: v = ~0ull; break;
+        case 2: v = in.bit < 6 ? pat[in.bit] : (((w >> (in.bit - 6)) & 1) ? ~0ull : 0ull); break;
+        case 3: v = ~reg[in.a]; break;
+        case 4: v = reg[in.a] & reg[in.b]; break;
+        case 5: v = reg[in.a] | reg[in.b]; break;
+        case 6: v = reg[in.a] ^ reg[in.b]; break;
+        default: v = reg[in.a]; break;
       }
-      case FNOT:
-        for (size_t w = 0; w < W; w++) out[w] = ~val[(size_t)f.kids[0]][w];
-        break;
-      case FAND:
-        std::fill(out.begin(), out.end(), ~0ull);
-        for (int c : f.kids)
-          for (size_t w = 0; w < W; w++) out[w] &= val[(size_t)c][w];
-        break;
-      case FOR:
-        for (int c : f.kids)
-          for (size_t w = 0; w < W; w++) out[w] |= val[(size_t)c][w];
-        break;
-      case FXOR:
-        for (size_t w = 0; w < W; w++) out[w] = val[(size_t)f.kids[0]][w] ^ val[(size_t)f.kids[1]][w];
-        break;
+      reg[in.dst] = v;
     }
-    for (int c : f.kids) {
-      users[(size_t)c]--;
-      if (!kept[(size_t)c]) release(c);
+    return reg[out_reg[c]];
+  };
+  // a conjunct over few word-index letters (item bits >= 6) becomes a table:
+  // its 64-bit value for each setting of those letters (the in-word letters
+  // are the patterns), so a word costs a gather of those bits and a lookup
+  struct Table {
+    std::vector<int> hbits;        // item bits >= 6 in the support, as word-index bits
+    std::vector<uint64_t> words;   // value per setting of hbits
+  };
+  std::vector<Table> tables(progs.size());
+  std::vector<char> tabled(progs.size(), 0);
+  for (size_t c = 0; c < progs.size(); c++) {
+    std::vector<int> hb;
+    for (const CIns& in : progs[c])
+      if (in.op == 2 && in.bit >= 6 && std::find(hb.begin(), hb.end(), in.bit - 6) == hb.end()) hb.push_back(in.bit - 6);
+    if (hb.size() > 10) continue;
+    Table t;
+    t.hbits = hb;
+    t.words.resize(1ull << hb.size());
+    for (uint64_t m = 0; m < t.words.size(); m++) {
+      uint64_t w = 0;
+      for (size_t i = 0; i < hb.size(); i++)
+        if ((m >> i) & 1) w |= 1ull << hb[i];
+      t.words[m] = run(c, w);
     }
-    if (kept[(size_t)x]) {
-      // the AND of the kept conjuncts, word by word
-      for (size_t w = 0; w < W; w++) all[w] &= out[w];
-      kept[(size_t)x] = 0;
-      release(x);
-    }
+    tables[c] = std::move(t);
+    tabled[c] = 1;
   }
+  std::vector<uint64_t> all(W, 0);
+  for (size_t w = 0; w < W; w++) {
+    uint64_t acc = tail;
+    for (size_t c = 0; c < progs.size() && acc; c++) {
+      if (tabled[c]) {
+        const Table& t = tables[c];
+        uint64_t m = 0;
+        for (size_t i = 0; i < t.hbits.size(); i++) m |= ((w >> t.hbits[i]) & 1ull) << i;
+        acc &= t.words[m];
+      } else {
+        acc &= run(c, w);
+      }
+    }
+    all[w] = acc;
+  }
+  return all;
+}
+
+std::vector<uint8_t> alive_items(const Grounded& g, const Layout& L) {
+  std::vector<uint64_t> all = alive_words(g, L);
+  if (all.empty()) return {};
+  const uint64_t U = 1ull << (L.unit_bits + L.warp_bits);
   std::vector<uint8_t> alive((size_t)U, 0);
   for (uint64_t u = 0; u < U; u++) alive[(size_t)u] = (uint8_t)((all[(size_t)(u >> 6)] >> (u & 63)) & 1);
   return alive;

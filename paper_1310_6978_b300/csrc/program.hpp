@@ -23,11 +23,12 @@ struct InterpBuild {
   FbgWorkItem* d_items = nullptr;
   uint64_t nitems = 0, nunits = 0, units_per_item = 1;
   int grid = 1;
-  // the units that can have models, ascending (empty = all); units on which a
-  // conjunct over unit and warp letters is false are left out
-  std::vector<uint32_t> live;
-  uint64_t live_units() const { return live.empty() ? nunits : (uint64_t)live.size(); }
-  uint64_t unit_at(uint64_t i) const { return live.empty() ? i : (uint64_t)live[(size_t)i]; }
+  // the units that can have models, ascending (null = all); units on which a
+  // conjunct over unit and warp letters is false are left out.  Shared with
+  // the host build cache, not copied per program
+  std::shared_ptr<const std::vector<uint32_t>> live;
+  uint64_t live_units() const { return live ? (uint64_t)live->size() : nunits; }
+  uint64_t unit_at(uint64_t i) const { return live ? (uint64_t)(*live)[(size_t)i] : i; }
   // work items over the live units with positions [lo, hi): runs of
   // consecutive units, at most max_units each
   void append_items(std::vector<FbgWorkItem>& out, unsigned prog, uint64_t lo, uint64_t hi,

@@ -289,9 +289,21 @@ bool fbg_server::enqueue_tick() {
       if (mem_used && mem_used + est > opt.mem_budget_bytes) break;
       pending.pop_front();
       fbg_status s = admit_locked(r);
-      if (s != FBG_OK) finish(r, s);
-      else admitted = true;
+      if (s != FBG_OK) {
+        finish(r, s);
+      } else if (r->nunits == 0) {
+        // the build left no unit that can hold a model (a conjunct over unit
+        // letters is false on every one): no models, nothing to launch.  The
+        // program's memory is freed on the tick stream, after its upload
+        cudaError_t e = cudaEventRecord(uploaded, upload);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, uploaded, 0);
+        r->count = 0;
+        finish(r, e == cudaSuccess ? FBG_OK : cuda_error(e, "server admit"));
+      } else {
+        admitted = true;
+      }
     }
+    active.erase(std::remove_if(active.begin(), active.end(), [](Request* q) { return q->done; }), active.end());
     admit_s += now_s() - ta;
     for (Request* r : active)
       if (r->next_unit < r->nunits) (r->jit ? jwork : work).push_back(r);   // units not yet launched

@@ -201,3 +201,27 @@ def test_default_server_specialises_n36_and_jit_off_keeps_the_interpreter():
     assert st["jit_programs"] == 0 and st["jit_requests"] == 0
     assert {res[i]["count"] for i in ids} == {want}
     off.close()
+
+
+def test_requests_without_live_units_finish_with_zero():
+    """A request whose build leaves no unit (every unit killed by a conjunct
+    over unit letters) has no models: the server finishes it at admission,
+    alone and among other requests, and the standalone engines agree."""
+    wl = W.cnf3(30, 1, 8.0)            # no unit of the server's count layout survives its build
+    text, n = wl.text, wl.k
+    p = F.compile(text, n)
+    assert p.count() == 0
+    assert F.compile(text, n).set_option(L.OPT_ENGINE, L.ENGINE_INTERP).count() == 0
+    OC.check_count(wl, 0, np.random.default_rng(40))
+    srv = F.Server()
+    others = mixed_requests(20, 41, n_hi=24)
+    ids = [srv.submit(text, n, L.MODE_COUNT), srv.submit(text, n, L.MODE_ENUMERATE, 100)]
+    ids += [srv.submit(wl.text, wl.k, mode, cap) for wl, mode, cap in others]
+    ids += [srv.submit(text, n, L.MODE_COUNT)]
+    res = wait_all(srv, ids, timeout=120)
+    for i in (ids[0], ids[1], ids[-1]):
+        assert res[i]["status"] == 0 and res[i]["count"] == 0 and res[i]["models"] == []
+    rng, cache = np.random.default_rng(41), {}
+    for i, (wl, mode, cap) in zip(ids[2:-1], others):
+        check_with_oracle(wl, mode, cap, res[i], rng, cache)
+    srv.close()

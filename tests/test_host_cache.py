@@ -22,3 +22,18 @@ def test_compile_cache_hits_and_keys():
         F.compile("var x\nx &\n", 1)
     with pytest.raises(L.FbgError):
         F.compile("var x\nx &\n", 1)          # errors are not cached as programs
+
+
+def test_build_can_leave_no_live_unit():
+    """Random 3-CNF n = 30 at ratio 8 (seed 1): at the server's count layout
+    (2^20 units requested) the conjuncts over unit letters kill every unit at
+    build time, which the server finishes without a launch; at ratio 6 some
+    units survive."""
+    from paper_1310_6978_b300 import _lib as L
+    from paper_1310_6978_b300 import workloads as W
+    for ratio, dead in ((8.0, True), (6.0, False)):
+        wl = W.cnf3(30, 1, ratio)
+        p = F.compile(wl.text, wl.k).set_option(L.OPT_ENGINE, L.ENGINE_INTERP).set_option(L.OPT_UNIT_BITS, 20)
+        d = p.debug_dump(2)
+        assert p.stats().luts > 0
+        assert (d["live_units"] == 0) == dead and d["live_units"] >= 0
