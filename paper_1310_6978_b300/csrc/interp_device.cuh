@@ -197,23 +197,24 @@ __device__ void run_unit(Shared& S, Thread& T, fbg_u64 u, const FbgLaunch& P, fb
   exec_level(S, T, G.lev[1]);
   count_level(S, P, 1);
   if (!level_alive<MODE>(S, T, G.lev[1])) return;
-  unsigned it[FBG_INTERP_MAX_LEVELS];
+  // the loop nest as an odometer over the loop letters' bits, kept at their
+  // own positions in lc (no per-level counter array, which would live in
+  // local memory): a level's field is zero whenever the nest enters it
+  fbg_u64 lc = 0;
   int lv = 2;
   const int nl = (int)G.nlevels;
-  if (nl > 2) it[2] = 0;
   for (;;) {
     bool leaf = false;
     if (lv < nl) {
       const FbgInterpLevel& L = G.lev[lv];
       const fbg_u64 m = ((1ull << L.bits) - 1ull) << L.pos;
 #pragma unroll
-      for (int k = 0; k < NTILE; k++) T.coords[k] = (T.coords[k] & ~m) | ((fbg_u64)it[lv] << L.pos);
+      for (int k = 0; k < NTILE; k++) T.coords[k] = (T.coords[k] & ~m) | (lc & m);
       exec_level(S, T, L);
       count_level(S, P, lv);
       bool alive = level_alive<MODE>(S, T, L);
       if (alive && lv + 1 < nl) {
         lv++;
-        it[lv] = 0;
         continue;
       }
       leaf = alive;
@@ -255,8 +256,15 @@ __device__ void run_unit(Shared& S, Thread& T, fbg_u64 u, const FbgLaunch& P, fb
       }
     }
     if (lv < 2 || nl <= 2) break;
-    // odometer advance
-    while (lv >= 2 && ++it[lv] == (1u << G.lev[lv].bits)) lv--;
+    // odometer advance: add one at the current level; a level that wraps
+    // to zero carries into the level above
+    for (;;) {
+      const FbgInterpLevel& L = G.lev[lv];
+      const fbg_u64 m = ((1ull << L.bits) - 1ull) << L.pos;
+      const fbg_u64 f = ((lc & m) + (1ull << L.pos)) & m;
+      lc = (lc & ~m) | f;
+      if (f != 0ull || --lv < 2) break;
+    }
     if (lv < 2) break;
   }
 }
