@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(NT) interp_kernel(const FbgInterpProg* __restr
                                                    const FbgWorkItem* __restrict__ items, fbg_u64 nitems,
                                                    fbg_u64* item_ctr, fbg_u64* prog_counts, fbg_u64* unit_counts,
                                                    FbgLaunch P, const FbgSlotOut* __restrict__ slot_out) {
-  extern __shared__ fbg_u64 dyn_slots[];
+  extern __shared__ __align__(16) fbg_u64 dyn_slots[];
   __shared__ Shared S;
   Thread T;
   init_thread(T, dyn_slots);

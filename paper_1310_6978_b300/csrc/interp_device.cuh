@@ -28,6 +28,7 @@ constexpr int B = FBG_INTERP_BLOCK;          // tiles per block (the layout's th
 constexpr int NT = FBG_INTERP_THREADS;       // threads per block
 constexpr int NTILE = B / NT;                // tiles per thread
 static_assert(NT == 32 && NTILE * NT == B, "one warp per block, B / 32 tiles per thread");
+static_assert(NTILE == 2, "a thread's tiles of a slot are one 16-byte word");
 
 // the tiles of a thread: tile k is the layout's thread lane + 32 k
 struct Pair {
@@ -72,13 +73,13 @@ __device__ __forceinline__ void count_level(Shared& S, const FbgLaunch& P, int l
 }
 
 struct Thread {
-  fbg_u64* slots;       // this thread's column: tile k of slot s at slots[s * B + k * NT]
+  fbg_u64* slots;       // this thread's tiles: tile k of slot s at slots[s * B + k] (16-byte aligned pair)
   Pair acc;
   fbg_u64 coords[NTILE];   // tile coordinates: bit positions >= 6 of j
 };
 
 __device__ __forceinline__ void init_thread(Thread& T, fbg_u64* dyn_slots) {
-  T.slots = dyn_slots + threadIdx.x;
+  T.slots = dyn_slots + threadIdx.x * NTILE;
 #pragma unroll
   for (int k = 0; k < NTILE; k++) {
     T.acc.v[k] = 0;
@@ -96,8 +97,10 @@ __device__ __forceinline__ Pair fetch(const Shared& S, const Thread& T, unsigned
   // tile slots (codes below FBG_OP_SHARED) are the most frequent operands:
   // one test, and 32-bit shared-memory offsets
   if (op < FBG_OP_SHARED) {
-#pragma unroll
-    for (int k = 0; k < NTILE; k++) r.v[k] = T.slots[op * (unsigned)B + (unsigned)(k * NT)];
+    // a thread's two tiles are adjacent: one 16-byte shared-memory load
+    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(T.slots + op * (unsigned)B);
+    r.v[0] = v.x;
+    r.v[1] = v.y;
     return r;
   }
   if (op == FBG_OP_ACC) return T.acc;
@@ -145,8 +148,7 @@ __device__ __forceinline__ void exec_level(Shared& S, Thread& T, const FbgInterp
       S.svals[dst - FBG_DST_SHARED] = d.v[0];
       __syncwarp();
     } else {
-#pragma unroll
-      for (int k = 0; k < NTILE; k++) T.slots[dst * (unsigned)B + (unsigned)(k * NT)] = d.v[k];
+      *reinterpret_cast<ulonglong2*>(T.slots + dst * (unsigned)B) = make_ulonglong2(d.v[0], d.v[1]);
     }
     w = next;
   }
