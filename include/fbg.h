@@ -480,7 +480,8 @@ typedef struct {
   uint64_t count;              /* exact number of models */
   uint64_t written;            /* enumerate: models stored */
   const uint64_t *models;      /* enumerate: host array of `written` models, owned by the server */
-  double submit_s, admit_s, done_s;   /* server clock (seconds) */
+  double submit_s, admit_s, done_s;   /* server clock (seconds): entry to fbg_server_submit (before the
+                                         request's compile), admission, result ready */
 } fbg_result;
 
 fbg_status fbg_server_create(const fbg_server_options *opt, fbg_server **out);

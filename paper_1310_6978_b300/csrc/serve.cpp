@@ -625,6 +625,7 @@ fbg_status fbg_server_submit(fbg_server* s, const char* formula, int domain_k, i
                              uint64_t* request_id) {
   if (!s || !formula || !request_id || (mode != FBG_MODE_COUNT && mode != FBG_MODE_ENUMERATE))
     return set_error(FBG_EINVAL, "bad argument");
+  const double t_submit = now_s();   // a request's latency includes its compile and host build
   fbg_program* p = nullptr;
   fbg_status st = fbg_compile(formula, domain_k, &p);
   if (st != FBG_OK) return st;
@@ -651,7 +652,7 @@ fbg_status fbg_server_submit(fbg_server* s, const char* formula, int domain_k, i
   r->prog = p;
   r->mode = mode;
   r->cap = cap;
-  r->submit_s = now_s();
+  r->submit_s = t_submit;
   const bool may_jit = mode == FBG_MODE_COUNT && s->opt.jit_min_n > 0 && p->n >= s->opt.jit_min_n &&
                        p->g->root != 0 && p->g->root != 1;
   {
