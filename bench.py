@@ -588,7 +588,7 @@ def run_serving(args, torch, F, L):
     srv.close()
     # the calibration burst: all at once from the same number of clients
     # as the timed stream (submission compiles on the client's thread)
-    nclients = 16
+    nclients = 8
     calib = W.request_stream(min(800, nreq), rate_per_s=1.0, seed=55)
     srv = F.Server(jit_min_n=args.serve_jit_min_n)
 
