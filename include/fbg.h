@@ -437,9 +437,12 @@ void fbg_batch_free(fbg_batch *batch);
 
 /*
  * Serving loop: requests (formula text, domain, count or enumerate) are
- * compiled on submission, admitted while their device memory fits the budget
- * and a slot is free, and evaluated in ticks with the interpreter kernel (no
- * kernel compile on the serving path); each tick runs one launch over a
+ * compiled on submission (count requests with up to 2^20 units, model lists
+ * with up to 2^16, one letter per loop level), admitted while their device
+ * memory fits the budget and a slot is free, and evaluated in ticks with the
+ * interpreter kernel (no kernel compile on the tick loop); a request whose
+ * units are all removed at build time finishes at admission with no models;
+ * each tick runs one launch over a
  * share of the work of every admitted request (chunks of units), so requests
  * that arrive while others run join the next tick.  Partial counts stay on
  * the device across ticks.  A model list is tick work as well: its units are
