@@ -7,7 +7,7 @@
 // alternatives are compiled (NVRTC) and timed with CUDA events on the
 // caller's stream, the fastest is kept, and the program is left configured
 // with the best shape found.  Counts are timed after fbg_schedule_units, so
-// each shape is judged with its own longest-first unit order, and the
+// each shape is timed with its own longest-first unit order, and the
 // program keeps the order of the chosen shape.
 #include <cuda_runtime.h>
 

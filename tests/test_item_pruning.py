@@ -14,8 +14,9 @@ CASES = [W.posets(4), W.transitive(4), W.equivalences(4), W.triangle_free(6), W.
 
 
 @pytest.mark.parametrize("wl", CASES, ids=lambda w: f"{w.family}{w.param}")
-@pytest.mark.parametrize("shape", [{L.OPT_UNIT_BITS: 3, L.OPT_WARPS_LOG2: 1}, {L.OPT_UNIT_BITS: 5, L.OPT_WARPS_LOG2: 2}])
-def test_dead_items_have_no_models(wl, shape):
+@pytest.mark.parametrize("shape", [{L.OPT_UNIT_BITS: 3, L.OPT_WARPS_LOG2: 1}, {L.OPT_UNIT_BITS: 5, L.OPT_WARPS_LOG2: 2},
+                                   {L.OPT_UNIT_BITS: 9, L.OPT_WARPS_LOG2: 2, L.OPT_REGS_LOG2: 1}])
+def test_dead_items_have_no_models(wl, shape, par=False):
     p = F.compile(wl.text, wl.k)
     for k, v in shape.items():
         p.set_option(k, v)
@@ -35,8 +36,16 @@ def test_dead_items_have_no_models(wl, shape):
     total = 0
     for t in range(1 << (ub + wb)):
         vals = sum(((t >> b) & 1) << v for b, v in enumerate(item_vars))
-        c = th.count_cube(mask, vals)
+        c = th.count_cube_par(mask, vals) if par else th.count_cube(mask, vals)
         if t not in live:
             assert c == 0, (t, c)
         total += c
-    assert total == th.count()
+    assert total == (th.count_par(0, 1 << wl.n) if par else th.count())
+
+
+@pytest.mark.parametrize("wl", [W.cnf3(24, 5), W.posets(5), W.triangle_free(7)], ids=lambda w: f"{w.family}{w.param}")
+def test_dead_items_have_no_models_many_items(wl):
+    """The same on item spaces of 2^8 to 2^11 items, where the word-index
+    letters of a conjunct are gathered from the word number (several words,
+    per-conjunct tables)."""
+    test_dead_items_have_no_models(wl, {L.OPT_UNIT_BITS: 9, L.OPT_WARPS_LOG2: 2, L.OPT_REGS_LOG2: 1}, par=True)
