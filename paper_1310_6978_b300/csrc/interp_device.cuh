@@ -17,13 +17,6 @@
 
 namespace fbg_interp {
 
-template <int LUT>
-__device__ __forceinline__ fbg_u64 lop3_pair(fbg_u64 a, fbg_u64 b, fbg_u64 c) {
-  fbg_u32 lo = fbg_lop3<LUT>((fbg_u32)a, (fbg_u32)b, (fbg_u32)c);
-  fbg_u32 hi = fbg_lop3<LUT>((fbg_u32)(a >> 32), (fbg_u32)(b >> 32), (fbg_u32)(c >> 32));
-  return ((fbg_u64)hi << 32) | lo;
-}
-
 constexpr int B = FBG_INTERP_BLOCK;          // tiles per block (the layout's threads), slot stride
 constexpr int NT = FBG_INTERP_THREADS;       // threads per block
 constexpr int NTILE = B / NT;                // tiles per thread
@@ -35,28 +28,57 @@ struct Pair {
   fbg_u64 v[NTILE];
 };
 
-// lop3 needs its truth table as an immediate: dispatch on the (warp-uniform)
-// LUT once per instruction for both tiles
+// lop3 needs its truth table as an immediate.  The (warp-uniform) LUT byte
+// selects one of 256 code paths with one indirect branch (brx.idx over a
+// table of 256 labels, label i holding the four lop3.b32 of both tiles with
+// immediate i); a C++ switch over 256 cases is lowered to a tree of compares
+// and branches instead.  Labels are local to the asm block's braces, so
+// every inlined copy has its own.
+#define FBG_LUT_CASE(v)                                                        \
+  "L" #v ": lop3.b32 %0, %5, %9, %13, " #v ";\n\t"                           \
+  "lop3.b32 %1, %6, %10, %14, " #v ";\n\t"                                   \
+  "lop3.b32 %2, %7, %11, %15, " #v ";\n\t"                                   \
+  "lop3.b32 %3, %8, %12, %16, " #v ";\n\t"                                   \
+  "bra.uni LEND;\n"
+#define FBG_LUT_ROW(h)                                                         \
+  FBG_LUT_CASE(0x##h##0) FBG_LUT_CASE(0x##h##1) FBG_LUT_CASE(0x##h##2) FBG_LUT_CASE(0x##h##3) \
+  FBG_LUT_CASE(0x##h##4) FBG_LUT_CASE(0x##h##5) FBG_LUT_CASE(0x##h##6) FBG_LUT_CASE(0x##h##7) \
+  FBG_LUT_CASE(0x##h##8) FBG_LUT_CASE(0x##h##9) FBG_LUT_CASE(0x##h##A) FBG_LUT_CASE(0x##h##B) \
+  FBG_LUT_CASE(0x##h##C) FBG_LUT_CASE(0x##h##D) FBG_LUT_CASE(0x##h##E) FBG_LUT_CASE(0x##h##F)
+#define FBG_LUT_T(v) "L" #v
+#define FBG_LUT_TROW(h)                                                        \
+  FBG_LUT_T(0x##h##0) "," FBG_LUT_T(0x##h##1) "," FBG_LUT_T(0x##h##2) "," FBG_LUT_T(0x##h##3) "," \
+  FBG_LUT_T(0x##h##4) "," FBG_LUT_T(0x##h##5) "," FBG_LUT_T(0x##h##6) "," FBG_LUT_T(0x##h##7) "," \
+  FBG_LUT_T(0x##h##8) "," FBG_LUT_T(0x##h##9) "," FBG_LUT_T(0x##h##A) "," FBG_LUT_T(0x##h##B) "," \
+  FBG_LUT_T(0x##h##C) "," FBG_LUT_T(0x##h##D) "," FBG_LUT_T(0x##h##E) "," FBG_LUT_T(0x##h##F)
+
 __device__ __forceinline__ Pair lop3_dyn(unsigned lut, const Pair& a, const Pair& b, const Pair& c) {
+  fbg_u32 d0, d1, d2, d3;
+  asm volatile(
+      "{\n\t"
+      "LT: .branchtargets " FBG_LUT_TROW(0) "," FBG_LUT_TROW(1) "," FBG_LUT_TROW(2) "," FBG_LUT_TROW(3) ","
+      FBG_LUT_TROW(4) "," FBG_LUT_TROW(5) "," FBG_LUT_TROW(6) "," FBG_LUT_TROW(7) "," FBG_LUT_TROW(8) ","
+      FBG_LUT_TROW(9) "," FBG_LUT_TROW(A) "," FBG_LUT_TROW(B) "," FBG_LUT_TROW(C) "," FBG_LUT_TROW(D) ","
+      FBG_LUT_TROW(E) "," FBG_LUT_TROW(F) ";\n\t"
+      "brx.idx.uni %4, LT;\n"
+      FBG_LUT_ROW(0) FBG_LUT_ROW(1) FBG_LUT_ROW(2) FBG_LUT_ROW(3) FBG_LUT_ROW(4) FBG_LUT_ROW(5) FBG_LUT_ROW(6)
+      FBG_LUT_ROW(7) FBG_LUT_ROW(8) FBG_LUT_ROW(9) FBG_LUT_ROW(A) FBG_LUT_ROW(B) FBG_LUT_ROW(C) FBG_LUT_ROW(D)
+      FBG_LUT_ROW(E) FBG_LUT_ROW(F)
+      "LEND:\n\t}"
+      : "=r"(d0), "=r"(d1), "=r"(d2), "=r"(d3)
+      : "r"(lut & 0xFFu), "r"((fbg_u32)a.v[0]), "r"((fbg_u32)(a.v[0] >> 32)), "r"((fbg_u32)a.v[1]),
+        "r"((fbg_u32)(a.v[1] >> 32)), "r"((fbg_u32)b.v[0]), "r"((fbg_u32)(b.v[0] >> 32)), "r"((fbg_u32)b.v[1]),
+        "r"((fbg_u32)(b.v[1] >> 32)), "r"((fbg_u32)c.v[0]), "r"((fbg_u32)(c.v[0] >> 32)), "r"((fbg_u32)c.v[1]),
+        "r"((fbg_u32)(c.v[1] >> 32)));
   Pair d;
-  switch (lut) {
-#define FBG_C(x)                                                               \
-  case (x):                                                                    \
-    _Pragma("unroll") for (int k = 0; k < NTILE; k++) d.v[k] = lop3_pair<(x)>(a.v[k], b.v[k], c.v[k]); \
-    return d;
-#define FBG_C4(x) FBG_C(x) FBG_C((x) + 1) FBG_C((x) + 2) FBG_C((x) + 3)
-#define FBG_C16(x) FBG_C4(x) FBG_C4((x) + 4) FBG_C4((x) + 8) FBG_C4((x) + 12)
-#define FBG_C64(x) FBG_C16(x) FBG_C16((x) + 16) FBG_C16((x) + 32) FBG_C16((x) + 48)
-    FBG_C64(0) FBG_C64(64) FBG_C64(128) FBG_C64(192)
-#undef FBG_C64
-#undef FBG_C16
-#undef FBG_C4
-#undef FBG_C
-  }
-#pragma unroll
-  for (int k = 0; k < NTILE; k++) d.v[k] = 0;
+  d.v[0] = ((fbg_u64)d1 << 32) | d0;
+  d.v[1] = ((fbg_u64)d3 << 32) | d2;
   return d;
 }
+#undef FBG_LUT_TROW
+#undef FBG_LUT_T
+#undef FBG_LUT_ROW
+#undef FBG_LUT_CASE
 
 struct Shared {
   FbgInterpProg prog;
