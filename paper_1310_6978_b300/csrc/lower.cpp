@@ -313,10 +313,26 @@ std::vector<uint64_t> alive_words(const Grounded& g, const Layout& L) {
     tables[c] = std::move(t);
     tabled[c] = 1;
   }
-  std::vector<uint64_t> all(W, 0);
-  for (size_t w = 0; w < W; w++) {
-    uint64_t acc = tail;
-    for (size_t c = 0; c < progs.size() && acc; c++) {
+  // The words are visited as a binary tree over the word-index bits, top
+  // bit first: a conjunct whose lowest word-index letter is bit m is fixed
+  // on every block of 2^m consecutive words, so it is applied once per such
+  // block; a block whose AND is already zero holds no live item and is
+  // skipped whole (the level pruning of the kernels, on the host).  Conjuncts
+  // without a table are evaluated per word.
+  int nb = 0;
+  while (((size_t)1 << nb) < W) nb++;
+  std::vector<std::vector<size_t>> at_level((size_t)nb + 1);
+  for (size_t c = 0; c < progs.size(); c++) {
+    int lvl = 0;
+    if (tabled[c]) {
+      lvl = nb;
+      for (int h : tables[c].hbits) lvl = std::min(lvl, h);
+    }
+    at_level[(size_t)lvl].push_back(c);
+  }
+  auto apply = [&](int lvl, uint64_t w, uint64_t acc) {
+    for (size_t c : at_level[(size_t)lvl]) {
+      if (!acc) break;
       if (tabled[c]) {
         const Table& t = tables[c];
         uint64_t m = 0;
@@ -326,7 +342,29 @@ std::vector<uint64_t> alive_words(const Grounded& g, const Layout& L) {
         acc &= run(c, w);
       }
     }
-    all[w] = acc;
+    return acc;
+  };
+  std::vector<uint64_t> all(W, 0);
+  struct Node {
+    int lvl;        // the block holds words [w, w + 2^lvl)
+    uint64_t w;
+    uint64_t acc;   // AND of the conjuncts fixed on the block
+  };
+  std::vector<Node> stack{{nb, 0, apply(nb, 0, tail)}};
+  while (!stack.empty()) {
+    Node nd = stack.back();
+    stack.pop_back();
+    if (!nd.acc) continue;
+    if (nd.lvl == 0) {
+      all[(size_t)nd.w] = nd.acc;
+      continue;
+    }
+    const int child = nd.lvl - 1;
+    for (uint64_t half : {(uint64_t)1, (uint64_t)0}) {
+      const uint64_t w = nd.w | (half << child);
+      const uint64_t acc = apply(child, w, nd.acc);
+      if (acc) stack.push_back({child, w, acc});
+    }
   }
   return all;
 }
