@@ -566,7 +566,8 @@ def run_batched(args, torch, F, L):
 def run_serving(args, torch, F, L):
     """Poisson stream of requests (seed 5): n uniform in 16..38, a family with
     exactly n letters else 3-CNF; 90% count, 10% enumerate (cap 1e6).  The
-    rate is 0.7x the throughput of a calibration burst.  Count requests of
+    rate is 0.7x the throughput of a calibration run (4000 other requests
+    through the same clients and collector, unpaced).  Count requests of
     recurring texts with at least jit_min_n letters move to specialised
     kernels that the server compiles in the background."""
     import sys
@@ -578,90 +579,84 @@ def run_serving(args, torch, F, L):
     switch = sys.getswitchinterval()
     sys.setswitchinterval(0.0005)
     # one-time costs (module loads, the stream-ordered pool) are paid by an
-    # untimed burst of other requests; the calibration burst has texts of its
-    # own, as the stream has
+    # untimed burst of other requests; the calibration has texts of its own,
+    # as the stream has
     warm = W.request_stream(200, rate_per_s=1.0, seed=54)
     srv = F.Server(jit_min_n=args.serve_jit_min_n)
     for r in warm:
         srv.submit(r.workload.text, r.workload.k, L.MODE_ENUMERATE if r.mode == "enumerate" else L.MODE_COUNT, r.cap)
     srv.drain(600)
     srv.close()
-    # the calibration burst: all at once from the same number of clients
-    # as the timed stream (submission compiles on the client's thread)
     nclients = 8
+
+    def play(srv, reqs, paced):
+        """Submit reqs from nclients client threads (client c submits requests
+        c, c + nclients, ...; submission compiles the text on the calling
+        thread, and one thread alone could not keep up), at their arrival
+        times when paced, else as fast as they go, while this thread collects
+        the results.  Returns (per request (latency from submission, count,
+        latency from admission), per request delay past its arrival time,
+        the largest delay, wall seconds until the last result)."""
+        index = {}                           # request id -> position in reqs
+        done = [None] * len(reqs)
+        late = [0.0] * nclients              # largest delay of a submission past its arrival time
+        lag = [0.0] * len(reqs)              # each request's submission delay past its arrival time
+        start = time.perf_counter()
+
+        def producer(c):
+            for i in range(c, len(reqs), nclients):
+                r = reqs[i]
+                if paced:
+                    delay = start + r.arrival_s - time.perf_counter()
+                    if delay > 0:
+                        time.sleep(delay)
+                    else:
+                        late[c] = max(late[c], -delay)
+                    lag[i] = max(0.0, time.perf_counter() - (start + r.arrival_s))
+                rid = srv.submit(r.workload.text, r.workload.k,
+                                 L.MODE_ENUMERATE if r.mode == "enumerate" else L.MODE_COUNT, r.cap)
+                index[rid] = i
+
+        def collect():
+            # the requests finished since the last call (fbg_server_completed):
+            # read each result and release it, so that results (model lists of
+            # up to 10^6 words) do not pile up
+            got = 0
+            for rid in srv.completed():
+                while rid not in index:      # finished before the producer recorded it
+                    time.sleep(0.0005)
+                res = srv.poll(rid, models=False)
+                assert res["status"] == 0
+                done[index[rid]] = (res["done_s"] - res["submit_s"], res["count"], res["done_s"] - res["admit_s"])
+                srv.release(rid)
+                got += 1
+            return got
+
+        clients = [threading.Thread(target=producer, args=(c,)) for c in range(nclients)]
+        for th in clients:
+            th.start()
+        while any(th.is_alive() for th in clients):
+            clients[0].join(0.05)
+            collect()
+        for th in clients:
+            th.join()
+        srv.drain(max(300.0, 3 * reqs[-1].arrival_s if paced else 0.0))
+        wall = time.perf_counter() - start
+        while collect():
+            pass
+        assert all(d is not None for d in done)
+        return done, lag, max(late), wall
+
+    # the calibration: the same clients and collector with no pacing, so the
+    # throughput includes the host's compiles and the collection of results
     calib = W.request_stream(min(4000, nreq), rate_per_s=1.0, seed=55)
     srv = F.Server(jit_min_n=args.serve_jit_min_n)
-
-    def burst(c):
-        for r in calib[c::nclients]:
-            srv.submit(r.workload.text, r.workload.k, L.MODE_ENUMERATE if r.mode == "enumerate" else L.MODE_COUNT,
-                       r.cap)
-
-    t0 = time.perf_counter()
-    cal_threads = [threading.Thread(target=burst, args=(c,)) for c in range(nclients)]
-    for th in cal_threads:
-        th.start()
-    for th in cal_threads:
-        th.join()
-    srv.drain(600)
-    t_cal = time.perf_counter() - t0
+    t_cal = play(srv, calib, paced=False)[3]
     srv.close()
     rate = args.serve_rate if args.serve_rate > 0 else 0.7 * len(calib) / t_cal
     reqs = W.request_stream(nreq, rate_per_s=rate, seed=5)
     srv = F.Server(jit_min_n=args.serve_jit_min_n)
-    index = {}                           # request id -> position in the stream
-    done = [None] * len(reqs)            # (latency s, count) once collected
-    start = time.perf_counter()
-
-    # requests come from several clients (threads): submission compiles the
-    # text on the calling thread, and one thread alone could not keep up with
-    # the offered rate; client c submits requests c, c + nclients, ... at
-    # their arrival times
-    late = [0.0] * nclients              # largest delay of a submission past its arrival time
-    lag = [0.0] * len(reqs)              # each request's submission delay past its arrival time
-
-    def producer(c):
-        for i in range(c, len(reqs), nclients):
-            r = reqs[i]
-            delay = start + r.arrival_s - time.perf_counter()
-            if delay > 0:
-                time.sleep(delay)
-            else:
-                late[c] = max(late[c], -delay)
-            lag[i] = max(0.0, time.perf_counter() - (start + r.arrival_s))
-            rid = srv.submit(r.workload.text, r.workload.k,
-                             L.MODE_ENUMERATE if r.mode == "enumerate" else L.MODE_COUNT, r.cap)
-            index[rid] = i
-
-    def collect():
-        # the requests finished since the last call (fbg_server_completed):
-        # read each result and release it, so that results (model lists of up
-        # to 10^6 words) do not pile up
-        got = 0
-        for rid in srv.completed():
-            while rid not in index:      # finished before the producer recorded it
-                time.sleep(0.0005)
-            res = srv.poll(rid, models=False)
-            assert res["status"] == 0
-            done[index[rid]] = (res["done_s"] - res["submit_s"], res["count"], res["done_s"] - res["admit_s"])
-            srv.release(rid)
-            got += 1
-        return got
-
-    clients = [threading.Thread(target=producer, args=(c,)) for c in range(nclients)]
-    for th in clients:
-        th.start()
-    while any(th.is_alive() for th in clients):
-        clients[0].join(0.05)
-        collect()
-    for th in clients:
-        th.join()
-    srv.drain(max(300.0, 3 * reqs[-1].arrival_s))
-    wall = time.perf_counter() - start
-    max_lag = max(late)
-    while collect():
-        pass
-    assert all(d is not None for d in done)
+    done, lag, max_lag, wall = play(srv, reqs, paced=True)
     lat, lat_arr, lat_srv, assign, counts = [], [], [], 0, []
     for (lt, cnt, ls), r, lg in zip(done, reqs, lag):
         lat.append(lt)
