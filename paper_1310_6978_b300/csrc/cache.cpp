@@ -10,6 +10,7 @@
 #include <deque>
 #include <mutex>
 #include <unordered_map>
+#include <vector>
 
 #include "build_cache.hpp"
 #include "program.hpp"
@@ -35,13 +36,22 @@ class SharedCache {
     return it->second;
   }
   void put(const std::string& key, std::shared_ptr<const V> v) {
-    std::lock_guard<std::mutex> lk(mu_);
-    if (map_.count(key)) return;
-    map_.emplace(key, std::move(v));
-    order_.push_back(key);
-    while (order_.size() > cap_) {
-      map_.erase(order_.front());
-      order_.pop_front();
+    // entries dropped here are destroyed after the lock is released, so that
+    // freeing a large build does not hold up other threads' lookups
+    std::vector<std::shared_ptr<const V>> dropped;
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      if (map_.count(key)) return;
+      map_.emplace(key, std::move(v));
+      order_.push_back(key);
+      while (order_.size() > cap_) {
+        auto it = map_.find(order_.front());
+        if (it != map_.end()) {
+          dropped.push_back(std::move(it->second));
+          map_.erase(it);
+        }
+        order_.pop_front();
+      }
     }
   }
   void clear() {

@@ -37,6 +37,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <functional>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -57,7 +58,10 @@ double now_s() {
   return duration<double>(steady_clock::now().time_since_epoch()).count();
 }
 
-// a (text, domain) of count requests that may get a specialised kernel
+// a (text, domain) of count requests that may get a specialised kernel,
+// found by a hash of the two; the text is kept once its compile is queued,
+// and a request uses the kernel only when its own text and domain are equal
+// to it
 struct TextFamily {
   std::string text;
   int k = 1;
@@ -149,7 +153,7 @@ struct fbg_server {
   fbg_status fatal = FBG_OK;
   // recurring texts: families by text and domain, the background compile
   // thread and its queue, the side stream of the specialised launches
-  std::unordered_map<std::string, std::unique_ptr<TextFamily>> families;
+  std::unordered_map<uint64_t, std::unique_ptr<TextFamily>> families;
   std::deque<TextFamily*> jit_queue;
   std::condition_variable jit_cv;
   std::thread jit_worker;
@@ -207,7 +211,8 @@ void fbg_server::finish(Request* r, fbg_status s) {
 }
 
 fbg_status fbg_server::admit_locked(Request* r) {
-  if (r->fam && r->fam->ready && r->mode == FBG_MODE_COUNT) {
+  if (r->fam && r->fam->ready && r->mode == FBG_MODE_COUNT && r->prog->k == r->fam->k &&
+      r->prog->text == r->fam->text) {
     // the family's specialised kernel counts all of it in one launch: a slot
     // for its count, no interpreter upload
     r->jit = true;
@@ -655,26 +660,22 @@ fbg_status fbg_server_submit(fbg_server* s, const char* formula, int domain_k, i
   r->submit_s = t_submit;
   const bool may_jit = mode == FBG_MODE_COUNT && s->opt.jit_min_n > 0 && p->n >= s->opt.jit_min_n &&
                        p->g->root != 0 && p->g->root != 1;
+  const uint64_t fkey = may_jit ? std::hash<std::string>{}(p->text) ^ (0x9E3779B97F4A7C15ull * (uint64_t)(domain_k + 1))
+                                : 0;
   {
     std::lock_guard<std::mutex> lk(s->mu);
     if (may_jit) {
       // the family of this (text, domain): count its submissions, queue its
       // compile at the jit_after-th while the server keeps fewer than
       // jit_max_programs
-      std::string key(formula);
-      key += '\0';
-      key += std::to_string(domain_k);
-      auto it = s->families.find(key);
-      if (it == s->families.end()) {
-        auto fam = std::make_unique<TextFamily>();
-        fam->text = formula;
-        fam->k = domain_k;
-        it = s->families.emplace(std::move(key), std::move(fam)).first;
-      }
+      auto it = s->families.find(fkey);
+      if (it == s->families.end()) it = s->families.emplace(fkey, std::make_unique<TextFamily>()).first;
       TextFamily* fam = it->second.get();
       fam->submissions++;
       if (!fam->queued && fam->submissions >= (uint64_t)s->opt.jit_after &&
           s->jit_started < (uint64_t)s->opt.jit_max_programs) {
+        fam->text = p->text;
+        fam->k = domain_k;
         fam->queued = true;
         s->jit_started++;
         s->jit_queue.push_back(fam);
