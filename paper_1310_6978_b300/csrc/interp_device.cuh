@@ -155,10 +155,25 @@ __device__ __forceinline__ void exec_level(Shared& S, Thread& T, const FbgInterp
   for (; i < L.ins_end; i++) {
     const fbg_u64 next = i + 1 < L.ins_end ? __ldg(ins + i + 1) : 0ull;
     const unsigned lut = (unsigned)(w & 0xFF), dst = (unsigned)((w >> 8) & 0xFF);
-    const Pair a = fetch(S, T, (unsigned)((w >> 16) & 0xFFFF));
-    const Pair b = fetch(S, T, (unsigned)((w >> 32) & 0xFFFF));
-    const Pair c = fetch(S, T, (unsigned)(w >> 48));
-    const Pair d = lop3_dyn(lut, a, b, c);
+    const unsigned oa = (unsigned)((w >> 16) & 0xFFFF), ob = (unsigned)((w >> 32) & 0xFFFF), oc = (unsigned)(w >> 48);
+    Pair d;
+    if (((oa & ob & oc) & FBG_OP_VAR) && !(((oa | ob | oc) >> 6) & 0x1FFu)) {
+      // all three operands are generator words of letters at positions >= 6
+      // (no accumulator: its code has those bits set): each is all ones or
+      // all zeros on a 64-bit tile, so the LUT is read at one index per tile
+#pragma unroll
+      for (int k = 0; k < NTILE; k++) {
+        const fbg_u64 cw = T.coords[k];
+        const unsigned idx = (unsigned)((((cw >> (oa & 63u)) & 1ull) << 2) | (((cw >> (ob & 63u)) & 1ull) << 1) |
+                                        ((cw >> (oc & 63u)) & 1ull));
+        d.v[k] = ((lut >> idx) & 1u) ? ~0ull : 0ull;
+      }
+    } else {
+      const Pair a = fetch(S, T, oa);
+      const Pair b = fetch(S, T, ob);
+      const Pair c = fetch(S, T, oc);
+      d = lop3_dyn(lut, a, b, c);
+    }
     if (dst == FBG_DST_ACC) {
       T.acc = d;
     } else if (dst >= FBG_DST_SHARED) {
