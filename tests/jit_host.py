@@ -14,7 +14,6 @@ import ctypes
 import hashlib
 import os
 import subprocess
-import tempfile
 
 import numpy as np
 
@@ -106,7 +105,7 @@ def build_kernel(src: str, mode: int) -> ctypes.CDLL:
     body = (PRELUDE % HDR) + src + DRIVER.replace("fbg_jit_count(P); else fbg_jit_table(P);",
                                                    f"{kname}(P); else {kname}(P);")
     h = hashlib.sha1(body.encode()).hexdigest()[:16]
-    d = os.path.join(tempfile.gettempdir(), "fbg_jit_host")
+    d = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "_build", "jit_host")
     os.makedirs(d, exist_ok=True)
     so = os.path.join(d, f"k{h}.so")
     if not os.path.exists(so):
