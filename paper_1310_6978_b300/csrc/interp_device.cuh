@@ -1,12 +1,12 @@
-// interp_device.cuh -- device code of the bytecode interpreter, shared by the
-// nvcc-compiled kernels (interp.cu) and the NVRTC-compiled batch kernel that
-// mixes interpreted and specialised programs.  Evaluates the LUT bytecode of
-// interp_format.h on 64-bit tiles: the bitwise evaluation of Sec. 2.3 with
-// 64-bit blocks.  A block is one warp; each thread owns B / 32 tiles per
-// innermost iteration (the layout's threads lane, lane + 32, ...), so every
-// decoded instruction does the work of all of them (independent data paths
-// per instruction); values live in per-thread columns of shared memory plus an
-// accumulator register; loop levels run as an odometer; a level whose partial
+// interp_device.cuh -- device code of the bytecode interpreter (the kernels
+// of interp.cu).  Evaluates the LUT bytecode of interp_format.h on 64-bit
+// tiles: the bitwise evaluation of Sec. 2.3 with 64-bit blocks.  A block is
+// one warp; each thread owns B / 32 tiles per innermost iteration (the
+// layout's threads lane, lane + 32, ...), so every decoded instruction does
+// the work of all of them (independent data paths per instruction); values
+// live in shared memory (a thread's tiles of a slot in one 16-byte word, or
+// one word per block for values equal in every tile) plus an accumulator
+// register; loop levels run as an odometer; a level whose partial
 // conjunction is zero for the whole warp skips its inner levels.
 #pragma once
 
