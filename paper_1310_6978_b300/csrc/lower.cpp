@@ -152,19 +152,25 @@ std::vector<int> search_order(const Grounded& g, uint64_t seed) {
       if ((s >> v) & 1) occ[(size_t)v]++;
   std::vector<int> order;
   uint64_t chosen = 0;
+  std::vector<long long> done_of((size_t)n), conn_of((size_t)n);
   for (int step = 0; step < n; step++) {
+    // per candidate letter v: the conjuncts that v completes (v is their
+    // last letter not yet placed) and the letters already placed that share
+    // a conjunct with v, in one pass over the conjuncts
+    std::fill(done_of.begin(), done_of.end(), 0);
+    std::fill(conn_of.begin(), conn_of.end(), 0);
+    for (uint64_t s : conj) {
+      const uint64_t rest = s & ~chosen;
+      if (!rest) continue;
+      const long long placed = __builtin_popcountll(s & chosen);
+      if ((rest & (rest - 1)) == 0) done_of[(size_t)__builtin_ctzll(rest)]++;
+      for (uint64_t r = rest; r; r &= r - 1) conn_of[(size_t)__builtin_ctzll(r)] += placed;
+    }
     int best = -1;
     long long bk[3] = {-1, -1, -1};
     for (int v = 0; v < n; v++) {
       if ((chosen >> v) & 1) continue;
-      uint64_t with = chosen | (1ull << v);
-      long long done = 0, conn = 0;
-      for (uint64_t s : conj) {
-        if (!((s >> v) & 1)) continue;
-        if ((s & ~with) == 0) done++;
-        conn += __builtin_popcountll(s & chosen);
-      }
-      long long key[3] = {done, conn, occ[(size_t)v]};
+      long long key[3] = {done_of[(size_t)v], conn_of[(size_t)v], occ[(size_t)v]};
       const bool tie = best >= 0 && !std::lexicographical_compare(bk, bk + 3, key, key + 3) &&
                        !std::lexicographical_compare(key, key + 3, bk, bk + 3);
       if (best < 0 || std::lexicographical_compare(bk, bk + 3, key, key + 3) ||
@@ -183,9 +189,10 @@ std::vector<int> search_order(const Grounded& g, uint64_t seed) {
 // 2^(unit bits + warp bits) items: item bit b is a free generator over the
 // item index (bit t of its word vector is bit b of t, Sec. 2.2-2.3).  Each
 // kept conjunct is compiled into a short program over a small register file
-// and the programs run word by word (64 items at a time), one conjunct after
-// the other, until the word's AND is zero: nothing of the size of the item
-// vector is held but the result.
+// (or a table over its word-index letters) and applied once per block of
+// words on which it is fixed, blocks visited as a tree over the word-index
+// bits; a block whose AND is zero is skipped whole.  Nothing of the size of
+// the item vector is held but the result.
 namespace {
 struct CIns {
   uint8_t op;        // 0 const 0, 1 const 1, 2 var, 3 not, 4 and, 5 or, 6 xor, 7 copy
