@@ -490,16 +490,13 @@ fbg_status fbg_debug_batch_build(fbg_program* const* progs, int nprogs, int* spe
   if (!progs || nprogs <= 0) return set_error(FBG_EINVAL, "bad argument");
   std::string err;
   BatchPlan plan = plan_batch(progs, nprogs, &err);
+  // the compiles of fbg_batch_create, on its pool of worker threads
+  std::string lg;
+  const std::vector<bool> built = jit_check_many(plan.src, kCompileDeadlineS, &lg);
   int good = 0;
-  bool ok = true;
-  for (auto& src : plan.src) {
-    std::string lg;
-    if (jit_check(src, &lg)) good++;
-    else {
-      ok = false;
-      if (err.size() < 4096) err += lg;
-    }
-  }
+  for (bool b : built) good += b ? 1 : 0;
+  const bool ok = good == (int)built.size();
+  if (!ok && err.size() < 4096) err += lg;
   if (specialized) *specialized = good;
   if (log && loglen) {
     size_t n = std::min(loglen - 1, err.size());

@@ -319,6 +319,11 @@ std::vector<JitResult> jit_compile_many(const std::vector<std::string>& bodies, 
   return res;
 }
 
+std::vector<bool> jit_check_many(const std::vector<std::string>& bodies, double deadline_s, std::string* log) {
+  std::vector<std::string> cubins;
+  return compile_many(bodies, &cubins, deadline_s, log);
+}
+
 size_t jit_cache_size() {
   std::lock_guard<std::mutex> lk(g_mu);
   return g_cache.size();

@@ -25,5 +25,9 @@ std::vector<JitResult> jit_compile_many(const std::vector<std::string>& bodies, 
                                         double deadline_s, std::string* log);
 // Compile only (no device needed); *log receives the NVRTC/ptxas messages.
 bool jit_check(const std::string& body, std::string* log);
+// Compile only, many sources on the pool of jit_compile_many (the same
+// compiles and cache of compiled code a batch uses); per source whether it
+// compiled before deadline_s.
+std::vector<bool> jit_check_many(const std::vector<std::string>& bodies, double deadline_s, std::string* log);
 
 }  // namespace fbg
