@@ -1,6 +1,7 @@
 """Host logic of bench.py without a GPU: the clock record that rejects a
 timed run (samples inside the timed window, the median SM clock, throttle
-reasons) from synthetic nvidia-smi lines."""
+reasons) from synthetic nvidia-smi lines, and the bookkeeping of stored ncu
+figures (fingerprints of the captured sources, utilisation weights)."""
 import datetime
 import os
 import sys
@@ -79,3 +80,40 @@ def test_reference_arm_other_ranks_exit_quietly():
     out = _run_bench(["--impl", "reference", "--steps", "3", "--warmup", "3", "--ref-total-seconds", "2"],
                      {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert out == []
+
+
+def test_ncu_figures_are_reported_only_for_the_captured_sources():
+    """A stored ncu figure carries the fingerprint of the kernel sources it was
+    captured on; for any other build the bench reports null and the reason."""
+    table = {"sources_sha": "abc", "traffic_step": 7, "vector_lop3_step": 9}
+    fresh = bench.ncu_figures(table, "abc", ["traffic_step", "vector_lop3_step"])
+    assert fresh == {"traffic_step": 7, "vector_lop3_step": 9, "stale": False}
+    stale = bench.ncu_figures(table, "def", ["traffic_step"])
+    assert stale["traffic_step"] is None and stale["stale"] and "abc" in stale["reason"] and "def" in stale["reason"]
+    none = bench.ncu_figures({}, "def", ["traffic_step"])
+    assert none["traffic_step"] is None and none["reason"] == "no capture recorded"
+
+
+def test_kernel_fingerprint_follows_sources_and_shapes():
+    """The fingerprint is a function of the generated kernel sources: equal
+    for the same text and shape, different when a shape option changes."""
+    import paper_1310_6978_b300 as F
+    from paper_1310_6978_b300 import _lib as L
+    from paper_1310_6978_b300 import workloads as W
+    a = F.compile(W.TRANSITIVE6.text, W.TRANSITIVE6.k)
+    b = F.compile(W.TRANSITIVE6.text, W.TRANSITIVE6.k)
+    assert bench.kernel_fingerprint([a], 0) == bench.kernel_fingerprint([b], 0)
+    b.set_option(L.OPT_REGS_LOG2, 3)
+    assert bench.kernel_fingerprint([a], 0) != bench.kernel_fingerprint([b], 0)
+    assert bench.kernel_fingerprint([a], 0) != bench.kernel_fingerprint([a], 1)
+
+
+def test_ncu_utilisation_weights_launches_by_active_cycles():
+    per = {"issue_slots_used_pct": [40.0, 60.0, 10.0], "alu_pipe_pct": [70.0, 80.0, 30.0],
+           "sm_active_cycles": [100, 300, 0], "sm_elapsed_cycles": [200, 300, 50]}
+    u = bench.ncu_utilisation(per)
+    assert abs(u["issue_slots_used_pct_weighted"] - 55.0) < 1e-12
+    assert abs(u["alu_pipe_pct_weighted"] - 77.5) < 1e-12
+    assert u["sm_active_share"] == [0.5, 1.0, 0.0]
+    stored = bench.ncu_utilisation(bench.NCU_COUNT["per_launch"])
+    assert 0 < stored["issue_slots_used_pct_weighted"] <= 100 and 0 < stored["alu_pipe_pct_weighted"] <= 100
